@@ -1,0 +1,214 @@
+/*
+ * fgraft.h -- C ABI of the GB300 FGraft builder (libfgraft.so).
+ *
+ * The builder of "Batched Feedback and the Random-Access Wall in
+ * Search-Based Graph Construction", Section 3: a scaffold S_0 made of the
+ * union of T spatial-approximation trees (symmetrised), then B synchronous
+ * blocks (block(p) = p mod B) in which every point of the block beam-searches
+ * the frozen substrate S_b with itself as the query (width ef_h, entering at
+ * the tree roots) and the expanded vertices are occlusion-pruned (alpha) into
+ * the point's own row of at most R ids; after each block
+ *     S_{b+1} = S_b U {(p,u),(u,p) : u in A[p], p in block b}.
+ * The final graph is the harvested rows symmetrised and re-pruned, plus the
+ * tree-0 spine.  By Proposition 1 the graph is a function of
+ * (data, seed, T, R, ef_h, alpha, B) only; this library produces the same
+ * bits at every launch configuration.
+ *
+ * Conventions (all entry points):
+ *  - Every pointer is a CUDA device pointer owned by the caller unless a
+ *    comment says "host".  The library allocates device memory only inside
+ *    fgraft_build_scaffold (the index) and frees it in fgraft_index_destroy.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default
+ *    stream) and is asynchronous unless a host output is requested, in which
+ *    case the call synchronises `stream` before returning.
+ *  - Arguments are checked before anything is launched.  Errors are returned
+ *    as fgraft_status and described by fgraft_last_error(); no entry point
+ *    aborts, traps or prints.
+ *  - Distances (delta): squared L2 for FGRAFT_L2_F32 and FGRAFT_L2_U8,
+ *    1 - <x,y> for FGRAFT_ANGULAR_F32 (unit vectors; the paper L2-normalises
+ *    angular data, Section 2).  Float32 distances follow one fixed summation
+ *    order (32 virtual lanes, lane l owning elements 128k + 4l + c, fused
+ *    multiply-add per element, xor-butterfly combine), uint8 distances are
+ *    exact integers.  Every ordering is by the pair (delta, id).
+ *  - Vectors: X holds n rows of d elements (float32 or uint8) with a row
+ *    stride of ld elements; ld * element size must be a multiple of 16 and X
+ *    16-byte aligned; elements past d in a row are ignored.  uint8 needs
+ *    d <= 256 (exact float conversion of the distance); float32 d <= 1024.
+ *  - Ids are int32; n < 2^31 - 1.  Rows are padded with -1.
+ */
+#ifndef FGRAFT_H
+#define FGRAFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* fgraft_stream; /* same type as cudaStream_t */
+
+typedef enum {
+  FGRAFT_OK = 0,
+  FGRAFT_EINVAL = 1,    /* bad argument; nothing was launched */
+  FGRAFT_ENOMEM = 2,    /* a device allocation failed */
+  FGRAFT_ECUDA = 3,     /* a CUDA runtime call failed (message has the CUDA error) */
+  FGRAFT_EOVERFLOW = 4, /* an output capacity was too small, or a search outgrew its scratch */
+  FGRAFT_ETIMEOUT = 5   /* reserved: a bounded device wait gave up */
+} fgraft_status;
+
+typedef enum { FGRAFT_L2_F32 = 0, FGRAFT_ANGULAR_F32 = 1, FGRAFT_L2_U8 = 2 } fgraft_metric;
+
+/* Build parameters, named as in Section 3. */
+typedef struct {
+  int32_t T;       /* SAT trees in the scaffold, 1 <= T <= 64 and T <= n */
+  int32_t R;       /* degree bound of a harvested row, 1 <= R <= 1024 */
+  int32_t ef_h;    /* harvest beam width, 1 <= ef_h <= 128 */
+  int32_t B;       /* blocks; 0 or 1 = one frozen block (Graft) */
+  float alpha;     /* occlusion factor on the unsquared distance, >= 0 */
+  uint64_t seed;   /* keys the tree roots */
+  int32_t metric;  /* fgraft_metric */
+} fgraft_params;
+
+/* Distance-evaluation counters (Section 2: "fg counts every evaluation").
+ * Defined by the algorithm, so a correct build reports the same numbers at
+ * every launch configuration:
+ *  sat_evals          per SAT node with m points below it and k children:
+ *                     m + k(k-1)/2 + (m-k)k
+ *  harvest_evals      sum over harvested points of the size of the visited
+ *                     set of their beam (tree roots included)
+ *  prune_evals        sum over kept candidates of the alive candidates
+ *                     examined in the removal pass that follows the keep
+ *                     (no pass after the R-th keep)
+ *  final_prune_evals  sum over rows of |C(u) U spine(u)| plus the removal
+ *                     passes of the rows that are re-pruned
+ *  expansions         sum of the expanded-set sizes
+ *  ids_scanned        neighbour ids read by the harvest (measurement only;
+ *                     depends on the substrate's layout, not on the method)
+ *  reruns             harvest queries re-run on global-memory scratch because
+ *                     their visited set outgrew shared memory (measurement) */
+typedef struct {
+  uint64_t sat_evals;
+  uint64_t harvest_evals;
+  uint64_t prune_evals;
+  uint64_t final_prune_evals;
+  uint64_t expansions;
+  uint64_t ids_scanned;
+  uint64_t reruns;
+} fgraft_counters;
+
+typedef struct fgraft_index fgraft_index; /* opaque */
+
+/* Scaffold S_0 (Section 1: T spatial-approximation trees [Navarro 2002];
+ * Section 3: "the union of T SAT trees' edges, symmetrized").
+ * Root t is splitmix64(seed ^ (0x9E3779B97F4A7C15 * (t+1)) + j) mod n for
+ * the smallest j >= 0 giving a root distinct from roots 0..t-1 (keyed
+ * randomness, Proposition 1).  A SAT node a holding points P sorts P by
+ * (delta(x,a), id); x becomes a child iff delta(x,a) < delta(x,b) for every
+ * earlier child b; every other point goes to its closest child by
+ * (delta, id).
+ * X is borrowed, not copied: it must stay valid and unchanged until
+ * fgraft_index_destroy.  On success *out owns the scaffold, the row storage
+ * for the harvest and all scratch.  counters (host, optional) receives the
+ * index's cumulative counters after a stream synchronisation.  The call
+ * synchronises `stream` once per tree level. */
+fgraft_status fgraft_build_scaffold(const void* X, int64_t n, int32_t d, int64_t ld,
+                                    const fgraft_params* params, fgraft_stream stream,
+                                    fgraft_index** out, fgraft_counters* counters);
+
+/* Harvest block b (Section 3): every point p with p mod B == b (all points
+ * when B <= 1) searches S_b and writes its pruned row A[p] (at most R ids in
+ * keep order = (delta, id) order, -1 padded); then S_{b+1} is formed.
+ * Blocks must be harvested in order 0, 1, .., B-1 (EINVAL otherwise);
+ * harvesting block b again after a later block is not allowed.  Needs no
+ * host synchronisation unless counters (host, optional) is given, so the
+ * B calls can be captured in a CUDA graph. */
+fgraft_status fgraft_harvest_block(fgraft_index* ix, int32_t b, fgraft_stream stream,
+                                   fgraft_counters* counters);
+
+/* All blocks in order, then the final graph; with use_graph != 0 the block
+ * loop is captured once as a CUDA graph and replayed.  Equivalent to B calls
+ * of fgraft_harvest_block followed by fgraft_prune with no outputs. */
+fgraft_status fgraft_harvest_all(fgraft_index* ix, int32_t use_graph, fgraft_stream stream,
+                                 fgraft_counters* counters);
+
+/* Final graph (Section 3: "the harvested rows, symmetrized and re-pruned,
+ * plus the tree-0 spine").  C(u) = A[u] U {p : u in A[p]}; when |C(u)| > R
+ * the row is the occlusion prune of C(u) to R, otherwise C(u); then the
+ * tree-0 parent and children of u are added and the row is sorted by
+ * (delta(u,v), id).  The index keeps the result for fgraft_search.
+ * out_offsets (n+1 int64) and out_ids (cap int32) are optional device
+ * outputs (both NULL: keep internally only); when cap is too small the call
+ * returns EOVERFLOW and writes the size needed to *needed (host, optional).
+ * Requires every block to have been harvested. */
+fgraft_status fgraft_prune(fgraft_index* ix, fgraft_stream stream, fgraft_counters* counters,
+                           int64_t* out_offsets, int32_t* out_ids, int64_t cap, int64_t* needed);
+
+/* Stand-alone batched occlusion prune (Section 3, after FANNG and DiskANN).
+ * List i belongs to point owner[i] and holds cand_ids[cand_off[i] ..
+ * cand_off[i+1]); the owner itself and repeated ids are dropped, the rest is
+ * sorted by (delta(owner, c), id) and pruned with alpha to at most R kept
+ * ids, written to out_ids[i*R ..] (-1 padded) with the count in out_cnt[i].
+ * X as in fgraft_build_scaffold.  Lists longer than 4096 candidates return
+ * EINVAL. */
+fgraft_status fgraft_prune_lists(const void* X, int64_t n, int32_t d, int64_t ld, int32_t metric,
+                                 const int32_t* owner, const int64_t* cand_off,
+                                 const int32_t* cand_ids, int64_t nlists, float alpha, int32_t R,
+                                 int32_t* out_ids, int32_t* out_cnt, fgraft_stream stream);
+
+/* Query search (Section 2: beam search over the final graph, graded against
+ * a brute-force key).  The same beam as the harvest, width ef_s, entering at
+ * the T roots; out_ids/out_dist (nq*k) get the first k pool entries (-1 /
+ * +inf when fewer were reached); out_evals (nq, optional) the number of
+ * distance evaluations of each query.  Q: nq rows of d elements of the
+ * index's element type, stride ldq elements (16-byte rule as for X).
+ * Requires fgraft_prune to have run.  1 <= k <= ef_s <= 128. */
+fgraft_status fgraft_search(fgraft_index* ix, const void* Q, int64_t nq, int64_t ldq, int32_t k,
+                            int32_t ef_s, int32_t* out_ids, float* out_dist, uint32_t* out_evals,
+                            fgraft_stream stream);
+
+/* Dense-block ceiling (Section 4.3: the pair set fixed in advance that a
+ * blocked kernel evaluates at arithmetic rate).  block_ids holds nb blocks of
+ * bs ids (-1 = padding).  For every valid member i of a block and every other
+ * valid member j, delta(x_i, x_j) is taken, and out_ids/out_dist
+ * (nb*bs*k) receive the k smallest (delta, id) per row (-1 / +inf fill).
+ * precision 0 evaluates every pair in the canonical float32 order.
+ * Float32 metrics only; bs <= 1024, k <= 64. */
+fgraft_status fgraft_dense_block_dist(const void* X, int64_t n, int32_t d, int64_t ld,
+                                      int32_t metric, const int32_t* block_ids, int64_t nb,
+                                      int32_t bs, int32_t k, int32_t precision, int32_t* out_ids,
+                                      float* out_dist, fgraft_stream stream);
+
+/* Inspection: copies of the index's state into caller buffers (device).
+ * roots: T; parents: T*n (parent of every point in each tree, -1 at the
+ * root); s_offsets: n+1 and s_ids: scaffold size (fgraft_index_sizes);
+ * rows: n*R and counts: n (harvested rows).  Any pointer may be NULL. */
+fgraft_status fgraft_index_copy(const fgraft_index* ix, int32_t* roots, int32_t* parents,
+                                int64_t* s_offsets, int32_t* s_ids, int32_t* rows,
+                                int32_t* counts, fgraft_stream stream);
+
+/* Sizes (host outputs): n, T, R, scaffold entries, final-graph entries
+ * (0 before fgraft_prune), blocks harvested so far.  Any pointer may be
+ * NULL.  Synchronises nothing. */
+fgraft_status fgraft_index_sizes(const fgraft_index* ix, int64_t* n, int32_t* T, int32_t* R,
+                                 int64_t* scaffold_nnz, int64_t* final_nnz,
+                                 int32_t* blocks_done);
+
+/* Cumulative counters of the index (host output; synchronises `stream`). */
+fgraft_status fgraft_index_counters(fgraft_index* ix, fgraft_stream stream,
+                                    fgraft_counters* counters);
+
+/* Harvest launch configuration (measurement and tuning; results do not
+ * depend on it).  hash_log2: shared-memory visited slots per warp (2^k,
+ * 7 <= k <= 14); warps_per_cta: 1..4; 0 leaves a value unchanged. */
+fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t warps_per_cta);
+
+void fgraft_index_destroy(fgraft_index* ix);
+
+/* Message of the last non-OK status returned on this host thread. */
+const char* fgraft_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FGRAFT_H */

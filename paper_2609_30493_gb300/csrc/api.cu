@@ -1,0 +1,658 @@
+// C ABI of libfgraft: argument checks, the index object, and the host-side
+// sequencing of the kernels (SAT levels, harvest blocks with their overflow
+// re-run and reverse-list update, final graph, search, dense blocks).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fgraft.h"
+#include "beam.cuh"
+#include "internal.h"
+
+namespace fg {
+
+static thread_local std::string g_err;
+static thread_local int g_err_code = 0;
+
+void set_error(int code, const std::string& msg) {
+  g_err_code = code;
+  g_err = msg;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error(FGRAFT_ECUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
+                              cudaGetErrorString(e) + ")");
+  return FGRAFT_ECUDA;
+}
+
+bool choose_shape(int metric, int d, int* G, int* K) {
+  if (d < 1) return false;
+  if (metric == L2_U8) {
+    if (d > 256) return false;
+    const int nch = (d + 15) / 16;
+    *K = 1;
+    *G = nch <= 4 ? 4 : (nch <= 8 ? 8 : 16);
+    return true;
+  }
+  if (metric != L2_F32 && metric != ANGULAR_F32) return false;
+  if (d > 1024) return false;
+  const int nch = (d + 3) / 4;
+  if (nch <= 32) {
+    *K = 1;
+    *G = nch <= 4 ? 4 : (nch <= 8 ? 8 : (nch <= 16 ? 16 : 32));
+  } else {
+    *G = 32;
+    const int k = (nch + 31) / 32;
+    *K = k <= 2 ? 2 : (k <= 4 ? 4 : 8);
+  }
+  return true;
+}
+
+// splitmix64 (Steele, Lea and Flood, OOPSLA 2014): first output of the
+// generator started at state z.  Keys the tree roots.
+static uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+static void keyed_roots(uint64_t seed, int T, int64_t n, std::vector<int32_t>& roots) {
+  roots.resize(T);
+  for (int t = 0; t < T; ++t) {
+    const uint64_t base = seed ^ (0x9E3779B97F4A7C15ULL * (uint64_t)(t + 1));
+    for (uint64_t j = 0;; ++j) {
+      const int32_t r = (int32_t)(splitmix64(base + j) % (uint64_t)n);
+      bool dup = false;
+      for (int s = 0; s < t; ++s) dup |= roots[s] == r;
+      if (!dup) {
+        roots[t] = r;
+        break;
+      }
+    }
+  }
+}
+
+}  // namespace fg
+
+using namespace fg;
+
+#define FGS(call)                                                      \
+  do {                                                                 \
+    cudaError_t e_ = (call);                                           \
+    if (e_ != cudaSuccess) return (fgraft_status)cuda_fail(e_, #call); \
+  } while (0)
+
+enum CtrSlot {
+  C_HARVEST = 0,
+  C_EXPANSIONS = 1,
+  C_PRUNE = 2,
+  C_SCANNED = 3,
+  C_RERUNS = 4,
+  C_SAT = 5,
+  C_FINAL = 6,
+  C_SEARCH = 8,  // search-side slots 8..12 (same layout as 0..4)
+  C_COUNT = 16
+};
+
+struct fgraft_index {
+  VecLayout L;
+  fgraft_params p;
+  int32_t nb;
+  int64_t ld;
+  std::vector<int32_t> roots_h;
+  int32_t* roots = nullptr;
+  int32_t* parents = nullptr;
+  int64_t* s_off = nullptr;
+  int32_t* s_ids = nullptr;
+  int64_t s_nnz = 0;
+  int32_t* A = nullptr;
+  int32_t* cnt = nullptr;
+  int64_t* r_off = nullptr;
+  int32_t* r_ids = nullptr;
+  uint32_t* rcnt = nullptr;
+  uint32_t* rcur = nullptr;
+  int64_t* f_off = nullptr;
+  int32_t* f_ids = nullptr;
+  int64_t f_nnz = 0;
+  int64_t* scan_tmp = nullptr;
+  uint32_t* work = nullptr;  // [0] smem pass, [1] re-run pass, [2] ovf count, [3] err flag
+  int32_t* ovf_list = nullptr;
+  int64_t ovf_cap = 0;
+  char* gscratch = nullptr;
+  int64_t gscratch_per_warp = 0;
+  int32_t g_hash_log2 = 0;
+  int32_t g_ecap = 0;
+  int32_t g_warps = 0;
+  unsigned long long* ctr = nullptr;
+  int32_t blocks_done = 0;
+  int32_t hash_log2 = 12;
+  int32_t wpc = 4;
+  int32_t num_sms = 0;
+  cudaGraphExec_t graph_exec = nullptr;
+};
+
+namespace {
+
+int fail(int code, const std::string& msg) {
+  set_error(code, msg);
+  return code;
+}
+
+int check_vectors(const void* X, int64_t n, int32_t d, int64_t ld, int32_t metric,
+                  VecLayout* L) {
+  if (!X) return fail(FGRAFT_EINVAL, "X is NULL");
+  if (n < 1 || n >= 2147483647LL) return fail(FGRAFT_EINVAL, "n must be in [1, 2^31-2]");
+  int G, K;
+  if (!choose_shape(metric, d, &G, &K))
+    return fail(FGRAFT_EINVAL, "unsupported metric/d (float32: 1<=d<=1024, uint8: 1<=d<=256)");
+  const int es = metric == L2_U8 ? 1 : 4;
+  if (ld < d) return fail(FGRAFT_EINVAL, "ld < d");
+  if ((ld * es) % 16 != 0) return fail(FGRAFT_EINVAL, "row stride must be a multiple of 16 bytes");
+  if (reinterpret_cast<uintptr_t>(X) % 16 != 0)
+    return fail(FGRAFT_EINVAL, "X must be 16-byte aligned");
+  L->X = static_cast<const char*>(X);
+  L->n = n;
+  L->d = d;
+  L->ld_bytes = ld * es;
+  L->metric = metric;
+  L->nchunks = (int32_t)((d * es + 15) / 16);
+  L->G = G;
+  L->K = K;
+  return 0;
+}
+
+BeamKernelFn beam_kernel_for(int metric, int G, int K, int S) {
+  if (metric == 0) return beam_kernel_metric0(G, K, S);
+  if (metric == 1) return beam_kernel_metric1(G, K, S);
+  return beam_kernel_metric2(G, K, S);
+}
+
+int pool_slots(int ef) { return ef <= 32 ? 1 : (ef <= 64 ? 2 : 4); }
+
+int ceil_log2(int64_t v) {
+  int k = 0;
+  while ((1ll << k) < v) ++k;
+  return k;
+}
+
+// Launch the beam over `nq` work items (shared-memory pass), then the
+// overflow list on global scratch.  `a` carries everything but the scratch.
+int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStream_t s) {
+  const int S = pool_slots(a.ef);
+  BeamKernelFn kern = beam_kernel_for(ix->L.metric, ix->L.G, ix->L.K, S);
+  if (!kern) return fail(FGRAFT_EINVAL, "no beam kernel for this metric and dimension");
+  const int ecap = 1 << std::max(6, ceil_log2(2 * 32 * S));
+  const int nslots = 1 << ix->hash_log2;
+  const int wbytes = (4 * nslots + 8 * ecap + ecap / 8 + 256 + 15) / 16 * 16;
+  const int smem = wbytes * ix->wpc;
+  FG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int per_sm = 0;
+  FG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ix->wpc * 32, smem));
+  if (per_sm < 1) return fail(FGRAFT_EINVAL, "harvest launch does not fit an SM");
+  a.counters = ctr;
+  a.work = ix->work;
+  a.ovf_list = ix->ovf_list;
+  a.ovf_count = ix->work + 2;
+  a.ovf_cap = (uint32_t)ix->ovf_cap;
+  a.err_flag = ix->work + 3;
+  a.hash_log2 = ix->hash_log2;
+  a.vis_cap = (int32_t)(0.8 * nslots) - 32;
+  a.ecap = ecap;
+  a.wbytes = wbytes;
+  a.global_scratch = 0;
+  a.qlist = nullptr;
+  a.qlist_len = nullptr;
+  FG_CUDA(cudaMemsetAsync(ix->work, 0, 3 * sizeof(uint32_t), s));
+  kern<<<per_sm * ix->num_sms, ix->wpc * 32, smem, s>>>(a);
+  FG_CUDA(cudaGetLastError());
+  // re-run of the overflowed items with per-warp global scratch
+  a.global_scratch = 1;
+  a.qlist = ix->ovf_list;
+  a.qlist_len = ix->work + 2;
+  a.work = ix->work + 1;
+  a.hash_log2 = ix->g_hash_log2;
+  a.vis_cap = (int32_t)(0.8 * (1 << ix->g_hash_log2)) - 32;
+  a.ecap = ix->g_ecap;
+  a.wbytes = 256;
+  a.gscratch = ix->gscratch;
+  a.gscratch_per_warp = ix->gscratch_per_warp;
+  a.counters = ctr;
+  kern<<<ix->g_warps / 4, 128, 256 * 4, s>>>(a);
+  FG_CUDA(cudaGetLastError());
+  return 0;
+}
+
+int check_err_flag(fgraft_index* ix, cudaStream_t s) {
+  uint32_t f = 0;
+  FG_CUDA(cudaMemcpyAsync(&f, ix->work + 3, sizeof(f), cudaMemcpyDeviceToHost, s));
+  FG_CUDA(cudaStreamSynchronize(s));
+  if (f) return fail(FGRAFT_EOVERFLOW, "a search outgrew its global-memory scratch");
+  return 0;
+}
+
+int read_counters(fgraft_index* ix, cudaStream_t s, fgraft_counters* c) {
+  unsigned long long h[C_COUNT];
+  FG_CUDA(cudaMemcpyAsync(h, ix->ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
+  FG_CUDA(cudaStreamSynchronize(s));
+  c->sat_evals = h[C_SAT];
+  c->harvest_evals = h[C_HARVEST];
+  c->prune_evals = h[C_PRUNE];
+  c->final_prune_evals = h[C_FINAL];
+  c->expansions = h[C_EXPANSIONS];
+  c->ids_scanned = h[C_SCANNED];
+  c->reruns = h[C_RERUNS];
+  return check_err_flag(ix, s);
+}
+
+template <typename T>
+int dalloc(T** p, int64_t count) {
+  cudaError_t e = cudaMalloc(p, sizeof(T) * (size_t)std::max<int64_t>(count, 1));
+  if (e != cudaSuccess) {
+    set_error(FGRAFT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return FGRAFT_ENOMEM;
+  }
+  return 0;
+}
+
+void free_index(fgraft_index* ix) {
+  if (!ix) return;
+  if (ix->graph_exec) cudaGraphExecDestroy(ix->graph_exec);
+  void* ptrs[] = {ix->roots, ix->parents, ix->s_off, ix->s_ids, ix->A,   ix->cnt,
+                  ix->r_off, ix->r_ids,   ix->rcnt,  ix->rcur,  ix->f_off, ix->f_ids,
+                  ix->scan_tmp, ix->work, ix->ovf_list, ix->gscratch, ix->ctr};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete ix;
+}
+
+int harvest_block_impl(fgraft_index* ix, int32_t b, cudaStream_t s) {
+  BeamArgs a{};
+  a.X = ix->L.X;
+  a.ld_bytes = ix->L.ld_bytes;
+  a.d = ix->L.d;
+  a.nchunks = ix->L.nchunks;
+  a.n = ix->L.n;
+  a.s_off = ix->s_off;
+  a.s_ids = ix->s_ids;
+  a.A = ix->A;
+  a.cnt = ix->cnt;
+  a.R = ix->p.R;
+  a.r_off = b > 0 ? ix->r_off : nullptr;
+  a.r_ids = ix->r_ids;
+  a.B = ix->nb;
+  a.b = b;
+  a.roots = ix->roots;
+  a.T = ix->p.T;
+  a.nq = (ix->L.n - b + ix->nb - 1) / ix->nb;
+  a.q_first = b;
+  a.q_step = ix->nb;
+  a.ef = ix->p.ef_h;
+  a.mode = 0;
+  a.alpha2 = ix->p.alpha * ix->p.alpha;
+  a.A_out = ix->A;
+  a.cnt_out = ix->cnt;
+  int rc = launch_beam(ix, a, ix->ctr + C_HARVEST, s);
+  if (rc) return rc;
+  rc = reverse_rows(ix->L.n, ix->p.R, ix->nb, b, ix->A, ix->cnt, ix->rcnt, ix->rcur, ix->r_off,
+                    ix->r_ids, ix->scan_tmp, s);
+  if (rc) return rc;
+  ix->blocks_done = b + 1;
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fgraft_last_error(void) { return g_err.c_str(); }
+
+fgraft_status fgraft_build_scaffold(const void* X, int64_t n, int32_t d, int64_t ld,
+                                    const fgraft_params* params, fgraft_stream stream,
+                                    fgraft_index** out, fgraft_counters* counters) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!out) return (fgraft_status)fail(FGRAFT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!params) return (fgraft_status)fail(FGRAFT_EINVAL, "params is NULL");
+  const fgraft_params p = *params;
+  VecLayout L;
+  int rc = check_vectors(X, n, d, ld, p.metric, &L);
+  if (rc) return (fgraft_status)rc;
+  if (p.T < 1 || p.T > 64 || p.T > n) return (fgraft_status)fail(FGRAFT_EINVAL, "need 1 <= T <= min(64, n)");
+  if (p.R < 1 || p.R > 1024) return (fgraft_status)fail(FGRAFT_EINVAL, "need 1 <= R <= 1024");
+  if (p.ef_h < 1 || p.ef_h > 128) return (fgraft_status)fail(FGRAFT_EINVAL, "need 1 <= ef_h <= 128");
+  if (p.B < 0) return (fgraft_status)fail(FGRAFT_EINVAL, "need B >= 0");
+  if (!(p.alpha >= 0.0f) || !std::isfinite(p.alpha))
+    return (fgraft_status)fail(FGRAFT_EINVAL, "alpha must be finite and >= 0");
+  if (p.metric == L2_U8 && p.metric != L.metric) return (fgraft_status)fail(FGRAFT_EINVAL, "metric");
+
+  fgraft_index* ix = new fgraft_index();
+  ix->L = L;
+  ix->p = p;
+  ix->nb = p.B <= 1 ? 1 : p.B;
+  ix->ld = ld;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&ix->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t T = p.T, tot = T * n;
+  rc = 0;
+  rc = rc ? rc : dalloc(&ix->roots, T);
+  rc = rc ? rc : dalloc(&ix->parents, tot);
+  rc = rc ? rc : dalloc(&ix->s_off, n + 1);
+  rc = rc ? rc : dalloc(&ix->A, n * p.R);
+  rc = rc ? rc : dalloc(&ix->cnt, n);
+  rc = rc ? rc : dalloc(&ix->r_off, n + 1);
+  rc = rc ? rc : dalloc(&ix->r_ids, n * p.R);
+  rc = rc ? rc : dalloc(&ix->rcnt, n);
+  rc = rc ? rc : dalloc(&ix->rcur, n);
+  rc = rc ? rc : dalloc(&ix->f_off, n + 1);
+  rc = rc ? rc : dalloc(&ix->scan_tmp, scan_tmp_elems(std::max<int64_t>(tot, 2 * n)) + 1);
+  rc = rc ? rc : dalloc(&ix->work, 8);
+  ix->ovf_cap = std::max<int64_t>(n, 1 << 16);
+  rc = rc ? rc : dalloc(&ix->ovf_list, ix->ovf_cap);
+  rc = rc ? rc : dalloc(&ix->ctr, C_COUNT);
+  // re-run scratch: visited slots for any beam over n points, expanded list
+  ix->g_hash_log2 = std::min(22, std::max(12, ceil_log2((int64_t)(n / 0.8) + 64)));
+  ix->g_ecap = 1 << std::min(20, std::max(12, ceil_log2(std::min<int64_t>(n, 1 << 20))));
+  ix->g_warps = 64;
+  ix->gscratch_per_warp =
+      ((4ll << ix->g_hash_log2) + 8ll * ix->g_ecap + ix->g_ecap / 4 + 255) / 256 * 256;
+  rc = rc ? rc : dalloc(&ix->gscratch, ix->gscratch_per_warp * ix->g_warps);
+  if (rc) {
+    free_index(ix);
+    return (fgraft_status)rc;
+  }
+  keyed_roots(p.seed, p.T, n, ix->roots_h);
+#define FAILX(call)                                   \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) {                          \
+      int c_ = cuda_fail(e_, #call);                  \
+      free_index(ix);                                 \
+      return (fgraft_status)c_;                       \
+    }                                                 \
+  } while (0)
+  FAILX(cudaMemcpyAsync(ix->roots, ix->roots_h.data(), sizeof(int32_t) * T,
+                        cudaMemcpyHostToDevice, s));
+  FAILX(cudaMemsetAsync(ix->ctr, 0, sizeof(unsigned long long) * C_COUNT, s));
+  FAILX(cudaMemsetAsync(ix->work, 0, 8 * sizeof(uint32_t), s));
+  FAILX(cudaMemsetAsync(ix->cnt, 0, sizeof(int32_t) * n, s));
+  FAILX(cudaMemsetAsync(ix->A, 0xFF, sizeof(int32_t) * n * p.R, s));
+
+  // SAT forest
+  SatScratch S{};
+  rc = 0;
+  rc = rc ? rc : dalloc(&S.node_of, tot);
+  rc = rc ? rc : dalloc(&S.kcnt, tot);
+  rc = rc ? rc : dalloc(&S.kstart, tot + 1);
+  rc = rc ? rc : dalloc(&S.item_pt, tot);
+  rc = rc ? rc : dalloc(&S.kd, tot);
+  rc = rc ? rc : dalloc(&S.best, tot);
+  rc = rc ? rc : dalloc(&S.flag, tot);
+  rc = rc ? rc : dalloc(&S.seg_start, tot);
+  rc = rc ? rc : dalloc(&S.seg_len, tot);
+  rc = rc ? rc : dalloc(&S.seg_node, tot);
+  rc = rc ? rc : dalloc(&S.seg_tree, tot);
+  rc = rc ? rc : dalloc(&S.nseg, 2);
+  S.nunsettled = S.nseg + 1;
+  S.scan_tmp = ix->scan_tmp;
+  auto free_sat = [&]() {
+    void* ps[] = {S.node_of, S.kcnt, S.kstart, S.item_pt, S.kd, S.best, S.flag,
+                  S.seg_start, S.seg_len, S.seg_node, S.seg_tree, S.nseg};
+    for (void* q : ps)
+      if (q) cudaFree(q);
+  };
+  if (!rc) {
+    cudaError_t e = cudaMemsetAsync(S.kcnt, 0, sizeof(uint32_t) * tot, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemsetAsync");
+  }
+  if (!rc) rc = sat_forest(L, p.T, ix->roots, ix->parents, S, ix->ctr + C_SAT, s);
+  free_sat();
+  if (rc) {
+    free_index(ix);
+    return (fgraft_status)rc;
+  }
+  // scaffold CSR
+  uint32_t* deg = nullptr;
+  int64_t* tmp_off = nullptr;
+  int32_t* tmp_ids = nullptr;
+  rc = 0;
+  rc = rc ? rc : dalloc(&deg, n);
+  rc = rc ? rc : dalloc(&tmp_off, n + 1);
+  rc = rc ? rc : dalloc(&tmp_ids, 2 * tot);
+  if (!rc)
+    rc = scaffold_csr(n, p.T, ix->parents, ix->s_off, &ix->s_ids, &ix->s_nnz, deg, tmp_off,
+                      tmp_ids, ix->scan_tmp, s);
+  cudaStreamSynchronize(s);
+  if (deg) cudaFree(deg);
+  if (tmp_off) cudaFree(tmp_off);
+  if (tmp_ids) cudaFree(tmp_ids);
+  if (rc) {
+    free_index(ix);
+    return (fgraft_status)rc;
+  }
+  if (counters) {
+    rc = read_counters(ix, s, counters);
+    if (rc) {
+      free_index(ix);
+      return (fgraft_status)rc;
+    }
+  }
+  *out = ix;
+  return FGRAFT_OK;
+#undef FAILX
+}
+
+fgraft_status fgraft_harvest_block(fgraft_index* ix, int32_t b, fgraft_stream stream,
+                                   fgraft_counters* counters) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!ix) return (fgraft_status)fail(FGRAFT_EINVAL, "index is NULL");
+  if (b < 0 || b >= ix->nb) return (fgraft_status)fail(FGRAFT_EINVAL, "block index out of range");
+  if (b != ix->blocks_done && b != 0)
+    return (fgraft_status)fail(FGRAFT_EINVAL, "blocks must be harvested in order 0..B-1");
+  int rc = harvest_block_impl(ix, b, s);
+  if (rc) return (fgraft_status)rc;
+  if (counters) return (fgraft_status)read_counters(ix, s, counters);
+  return FGRAFT_OK;
+}
+
+fgraft_status fgraft_prune(fgraft_index* ix, fgraft_stream stream, fgraft_counters* counters,
+                           int64_t* out_offsets, int32_t* out_ids, int64_t cap, int64_t* needed) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!ix) return (fgraft_status)fail(FGRAFT_EINVAL, "index is NULL");
+  if (ix->blocks_done != ix->nb)
+    return (fgraft_status)fail(FGRAFT_EINVAL, "every block must be harvested before the final prune");
+  if ((out_offsets == nullptr) != (out_ids == nullptr))
+    return (fgraft_status)fail(FGRAFT_EINVAL, "out_offsets and out_ids go together");
+  int rc = check_err_flag(ix, s);
+  if (rc) return (fgraft_status)rc;
+  FGS(cudaMemsetAsync(ix->ctr + C_FINAL, 0, sizeof(unsigned long long), s));
+  rc = final_graph(ix->L, ix->p.R, ix->p.alpha * ix->p.alpha, ix->A, ix->cnt, ix->r_off,
+                   ix->r_ids, ix->parents, ix->f_off, &ix->f_ids, &ix->f_nnz, ix->scan_tmp,
+                   ix->ctr + C_FINAL, s);
+  if (rc) return (fgraft_status)rc;
+  if (needed) *needed = ix->f_nnz;
+  if (out_offsets) {
+    if (cap < ix->f_nnz) return (fgraft_status)fail(FGRAFT_EOVERFLOW, "out_ids capacity too small");
+    FGS(cudaMemcpyAsync(out_offsets, ix->f_off, sizeof(int64_t) * (ix->L.n + 1),
+                            cudaMemcpyDeviceToDevice, s));
+    FGS(cudaMemcpyAsync(out_ids, ix->f_ids, sizeof(int32_t) * ix->f_nnz,
+                            cudaMemcpyDeviceToDevice, s));
+  }
+  if (counters) return (fgraft_status)read_counters(ix, s, counters);
+  return FGRAFT_OK;
+}
+
+fgraft_status fgraft_harvest_all(fgraft_index* ix, int32_t use_graph, fgraft_stream stream,
+                                 fgraft_counters* counters) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!ix) return (fgraft_status)fail(FGRAFT_EINVAL, "index is NULL");
+  int rc = 0;
+  if (!use_graph) {
+    for (int b = 0; b < ix->nb && !rc; ++b) rc = harvest_block_impl(ix, b, s);
+    if (rc) return (fgraft_status)rc;
+  } else {
+    if (!ix->graph_exec) {
+      cudaStream_t cs;
+      FGS(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+      if (e == cudaSuccess) {
+        for (int b = 0; b < ix->nb && !rc; ++b) rc = harvest_block_impl(ix, b, cs);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (!rc && e2 != cudaSuccess) rc = cuda_fail(e2, "cudaStreamEndCapture");
+      } else {
+        rc = cuda_fail(e, "cudaStreamBeginCapture");
+      }
+      if (!rc) {
+        e = cudaGraphInstantiate(&ix->graph_exec, graph, 0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphInstantiate");
+      }
+      if (graph) cudaGraphDestroy(graph);
+      cudaStreamDestroy(cs);
+      if (rc) return (fgraft_status)rc;
+    }
+    FGS(cudaGraphLaunch(ix->graph_exec, s));
+    ix->blocks_done = ix->nb;
+  }
+  return fgraft_prune(ix, stream, counters, nullptr, nullptr, 0, nullptr);
+}
+
+fgraft_status fgraft_prune_lists(const void* X, int64_t n, int32_t d, int64_t ld, int32_t metric,
+                                 const int32_t* owner, const int64_t* cand_off,
+                                 const int32_t* cand_ids, int64_t nlists, float alpha, int32_t R,
+                                 int32_t* out_ids, int32_t* out_cnt, fgraft_stream stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  VecLayout L;
+  int rc = check_vectors(X, n, d, ld, metric, &L);
+  if (rc) return (fgraft_status)rc;
+  if (nlists < 0) return (fgraft_status)fail(FGRAFT_EINVAL, "nlists < 0");
+  if (nlists == 0) return FGRAFT_OK;
+  if (!owner || !cand_off || !cand_ids || !out_ids || !out_cnt)
+    return (fgraft_status)fail(FGRAFT_EINVAL, "NULL list pointer");
+  if (R < 1 || R > 1024) return (fgraft_status)fail(FGRAFT_EINVAL, "need 1 <= R <= 1024");
+  if (!(alpha >= 0.0f) || !std::isfinite(alpha))
+    return (fgraft_status)fail(FGRAFT_EINVAL, "alpha must be finite and >= 0");
+  return (fgraft_status)prune_lists(L, owner, cand_off, cand_ids, nlists, alpha * alpha, R,
+                                    out_ids, out_cnt, nullptr, s);
+}
+
+fgraft_status fgraft_search(fgraft_index* ix, const void* Q, int64_t nq, int64_t ldq, int32_t k,
+                            int32_t ef_s, int32_t* out_ids, float* out_dist, uint32_t* out_evals,
+                            fgraft_stream stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!ix) return (fgraft_status)fail(FGRAFT_EINVAL, "index is NULL");
+  if (!ix->f_ids) return (fgraft_status)fail(FGRAFT_EINVAL, "search needs fgraft_prune first");
+  if (nq < 0) return (fgraft_status)fail(FGRAFT_EINVAL, "nq < 0");
+  if (nq == 0) return FGRAFT_OK;
+  if (k < 1 || ef_s < k || ef_s > 128) return (fgraft_status)fail(FGRAFT_EINVAL, "need 1 <= k <= ef_s <= 128");
+  if (!Q || !out_ids || !out_dist) return (fgraft_status)fail(FGRAFT_EINVAL, "NULL pointer");
+  const int es = ix->L.metric == L2_U8 ? 1 : 4;
+  if (ldq < ix->L.d || (ldq * es) % 16 || reinterpret_cast<uintptr_t>(Q) % 16)
+    return (fgraft_status)fail(FGRAFT_EINVAL, "Q stride/alignment");
+  BeamArgs a{};
+  a.X = ix->L.X;
+  a.ld_bytes = ix->L.ld_bytes;
+  a.d = ix->L.d;
+  a.nchunks = ix->L.nchunks;
+  a.n = ix->L.n;
+  a.s_off = ix->f_off;
+  a.s_ids = ix->f_ids;
+  a.B = 1;
+  a.b = 0;
+  a.roots = ix->roots;
+  a.T = ix->p.T;
+  a.nq = nq;
+  a.Q = static_cast<const char*>(Q);
+  a.ldq_bytes = ldq * es;
+  a.ef = ef_s;
+  a.mode = 1;
+  a.k = k;
+  a.top_ids = out_ids;
+  a.top_d = out_dist;
+  a.q_evals = out_evals;
+  int rc = launch_beam(ix, a, ix->ctr + C_SEARCH, s);
+  return (fgraft_status)rc;
+}
+
+fgraft_status fgraft_dense_block_dist(const void* X, int64_t n, int32_t d, int64_t ld,
+                                      int32_t metric, const int32_t* block_ids, int64_t nb,
+                                      int32_t bs, int32_t k, int32_t precision, int32_t* out_ids,
+                                      float* out_dist, fgraft_stream stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  VecLayout L;
+  int rc = check_vectors(X, n, d, ld, metric, &L);
+  if (rc) return (fgraft_status)rc;
+  if (metric == L2_U8) return (fgraft_status)fail(FGRAFT_EINVAL, "dense blocks take float32 metrics");
+  if (precision != 0) return (fgraft_status)fail(FGRAFT_EINVAL, "precision must be 0 (float32)");
+  if (nb < 0 || bs < 1 || bs > 1024 || k < 1 || k > 64)
+    return (fgraft_status)fail(FGRAFT_EINVAL, "need bs in [1,1024], k in [1,64]");
+  if (nb == 0) return FGRAFT_OK;
+  if (!block_ids || !out_ids || !out_dist) return (fgraft_status)fail(FGRAFT_EINVAL, "NULL pointer");
+  return (fgraft_status)dense_block(L, block_ids, nb, bs, k, out_ids, out_dist, s);
+}
+
+fgraft_status fgraft_index_copy(const fgraft_index* ix, int32_t* roots, int32_t* parents,
+                                int64_t* s_offsets, int32_t* s_ids, int32_t* rows,
+                                int32_t* counts, fgraft_stream stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!ix) return (fgraft_status)fail(FGRAFT_EINVAL, "index is NULL");
+  const int64_t n = ix->L.n, T = ix->p.T;
+  if (roots)
+    FGS(cudaMemcpyAsync(roots, ix->roots, sizeof(int32_t) * T, cudaMemcpyDeviceToDevice, s));
+  if (parents)
+    FGS(cudaMemcpyAsync(parents, ix->parents, sizeof(int32_t) * T * n,
+                            cudaMemcpyDeviceToDevice, s));
+  if (s_offsets)
+    FGS(cudaMemcpyAsync(s_offsets, ix->s_off, sizeof(int64_t) * (n + 1),
+                            cudaMemcpyDeviceToDevice, s));
+  if (s_ids)
+    FGS(cudaMemcpyAsync(s_ids, ix->s_ids, sizeof(int32_t) * ix->s_nnz,
+                            cudaMemcpyDeviceToDevice, s));
+  if (rows)
+    FGS(cudaMemcpyAsync(rows, ix->A, sizeof(int32_t) * n * ix->p.R, cudaMemcpyDeviceToDevice,
+                            s));
+  if (counts)
+    FGS(cudaMemcpyAsync(counts, ix->cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  return FGRAFT_OK;
+}
+
+fgraft_status fgraft_index_sizes(const fgraft_index* ix, int64_t* n, int32_t* T, int32_t* R,
+                                 int64_t* scaffold_nnz, int64_t* final_nnz,
+                                 int32_t* blocks_done) {
+  if (!ix) return (fgraft_status)fail(FGRAFT_EINVAL, "index is NULL");
+  if (n) *n = ix->L.n;
+  if (T) *T = ix->p.T;
+  if (R) *R = ix->p.R;
+  if (scaffold_nnz) *scaffold_nnz = ix->s_nnz;
+  if (final_nnz) *final_nnz = ix->f_ids ? ix->f_nnz : 0;
+  if (blocks_done) *blocks_done = ix->blocks_done;
+  return FGRAFT_OK;
+}
+
+fgraft_status fgraft_index_counters(fgraft_index* ix, fgraft_stream stream,
+                                    fgraft_counters* counters) {
+  if (!ix || !counters) return (fgraft_status)fail(FGRAFT_EINVAL, "NULL argument");
+  return (fgraft_status)read_counters(ix, reinterpret_cast<cudaStream_t>(stream), counters);
+}
+
+fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t warps_per_cta) {
+  if (!ix) return (fgraft_status)fail(FGRAFT_EINVAL, "index is NULL");
+  if (hash_log2 && (hash_log2 < 7 || hash_log2 > 14))
+    return (fgraft_status)fail(FGRAFT_EINVAL, "hash_log2 must be in [7, 14]");
+  if (warps_per_cta && (warps_per_cta < 1 || warps_per_cta > 4))
+    return (fgraft_status)fail(FGRAFT_EINVAL, "warps_per_cta must be in [1, 4]");
+  if (hash_log2) ix->hash_log2 = hash_log2;
+  if (warps_per_cta) ix->wpc = warps_per_cta;
+  if (ix->graph_exec) {
+    cudaGraphExecDestroy(ix->graph_exec);
+    ix->graph_exec = nullptr;
+  }
+  return FGRAFT_OK;
+}
+
+void fgraft_index_destroy(fgraft_index* ix) { free_index(ix); }
+
+}  // extern "C"

@@ -1,0 +1,385 @@
+// Persistent warp-per-query beam search: the harvest of Section 3 (every
+// point of block b searches S_b with itself as the query and its expanded set
+// is occlusion-pruned into its own row) and the query search over the final
+// graph.
+//
+// One warp owns one query at a time (claimed with an atomic counter).  The
+// pool is the ef smallest (delta, id) keys evaluated so far, held sorted in
+// registers (entry i in slot i/32 of lane i%32, bit 0 = expanded).  Each step
+// expands the smallest unexpanded entry, streams the neighbour lists of S_b
+// 32 ids at a time through an exact shared-memory visited hash, gathers the
+// new vectors with 16-byte loads by G-lane groups, and merges the batch into
+// the pool with a bitonic network.  The pool is by definition the ef best of
+// everything evaluated, so the order in which neighbours arrive does not
+// change it.  A query whose visited set or expanded list outgrows shared
+// memory is abandoned and listed; the host runs the list again with the same
+// kernel on per-warp global scratch.
+#pragma once
+#include "common.cuh"
+
+namespace fg {
+
+struct BeamArgs {
+  // points: n rows of d elements, row stride ld_bytes, nchunks 16-byte chunks used
+  const char* X;
+  int64_t ld_bytes;
+  int32_t d;
+  int32_t nchunks;
+  int64_t n;
+  // first neighbour source: the scaffold (harvest) or the final graph (search)
+  const int64_t* s_off;
+  const int32_t* s_ids;
+  // harvest: rows of earlier blocks and their reverse lists
+  const int32_t* A;
+  const int32_t* cnt;
+  int32_t R;
+  const int64_t* r_off;
+  const int32_t* r_ids;
+  int32_t B;  // >= 1
+  int32_t b;
+  // entry points
+  const int32_t* roots;
+  int32_t T;
+  // work items w < nwork map to qidx = qlist ? qlist[w] : w; the harvest query
+  // point is p = q_first + qidx * q_step, the search query row is Q + qidx*ldq
+  const int32_t* qlist;
+  const uint32_t* qlist_len;  // device count of qlist (NULL: use nq)
+  int64_t nq;
+  int64_t q_first;
+  int64_t q_step;
+  const char* Q;
+  int64_t ldq_bytes;
+  int32_t ef;
+  int32_t mode;  // 0 = harvest + prune, 1 = search
+  float alpha2;
+  int32_t* A_out;
+  int32_t* cnt_out;
+  int32_t k;
+  int32_t* top_ids;
+  float* top_d;
+  uint32_t* q_evals;
+  // scratch
+  uint32_t* work;
+  int32_t hash_log2;
+  int32_t vis_cap;
+  int32_t ecap;  // power of two, >= 32
+  int32_t wbytes;  // shared bytes per warp
+  int32_t global_scratch;
+  char* gscratch;
+  int64_t gscratch_per_warp;
+  int32_t* ovf_list;
+  uint32_t* ovf_count;
+  uint32_t ovf_cap;  // capacity of ovf_list
+  uint32_t* err_flag;
+  unsigned long long* counters;  // evals, expansions, prune evals, ids scanned, overflows
+};
+
+template <int METRIC, int G, int K, int S>
+struct Beam {
+  static constexpr int GPW = 32 / G;
+  static constexpr int U = Unroll<G, K>::value;
+
+  // Evaluate queue[0..cnt) (cnt <= 32) against the query chunks q and merge
+  // the keys into the pool.
+  static __device__ __forceinline__ void eval_merge(const BeamArgs& a, const uint4 (&q)[K],
+                                                    const int32_t* queue, int cnt,
+                                                    uint64_t (&pool)[S], int lane) {
+    const int g = lane / G, gl = lane % G;
+    uint64_t mykey = PAD;
+    for (int base = 0; base < cnt; base += GPW * U) {
+      uint4 v[U][K];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        int idx = base + u * GPW + g;
+        if (idx < cnt) {
+          load_chunks<METRIC, G, K>(a.X + (int64_t)queue[idx] * a.ld_bytes, a.nchunks, gl, v[u]);
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < K; ++kk) v[u][kk] = make_uint4(0u, 0u, 0u, 0u);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        float dd = group_reduce<METRIC, G>(partial<METRIC, G, K>(q, v[u], a.d, gl));
+        int rel = lane - base - u * GPW;
+        float got = __shfl_sync(FULL, dd, (rel & (GPW - 1)) * G);
+        if (rel >= 0 && rel < GPW && lane < cnt) mykey = make_key(got, queue[lane]);
+      }
+    }
+    merge_into_pool<S>(pool, mykey, a.ef, lane);
+  }
+
+  static __device__ void run(const BeamArgs& a, unsigned char* smem) {
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int g = lane / G, gl = lane % G;
+    const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    unsigned char* wsm = smem + (int64_t)wib * a.wbytes;
+    const uint32_t nslots = 1u << a.hash_log2;
+    const uint32_t mask_buckets = nslots / 4 - 1;
+    uint32_t* hash;
+    uint64_t* E;
+    uint32_t* alive;
+    int32_t* queue;
+    if (a.global_scratch) {
+      char* base = a.gscratch + gwarp * a.gscratch_per_warp;
+      hash = reinterpret_cast<uint32_t*>(base);
+      E = reinterpret_cast<uint64_t*>(base + 4ll * nslots);
+      alive = reinterpret_cast<uint32_t*>(base + 4ll * nslots + 8ll * a.ecap);
+      queue = reinterpret_cast<int32_t*>(wsm);
+    } else {
+      hash = reinterpret_cast<uint32_t*>(wsm);
+      E = reinterpret_cast<uint64_t*>(wsm + 4ll * nslots);
+      alive = reinterpret_cast<uint32_t*>(wsm + 4ll * nslots + 8ll * a.ecap);
+      queue = reinterpret_cast<int32_t*>(wsm + 4ll * nslots + 8ll * a.ecap + a.ecap / 8);
+    }
+    const int64_t nwork =
+        a.qlist_len ? min((int64_t)*a.qlist_len, (int64_t)a.ovf_cap) : a.nq;
+    unsigned long long c_ev = 0, c_ex = 0, c_pe = 0, c_sc = 0, c_ovf = 0;
+
+    for (;;) {
+      uint32_t w = 0;
+      if (lane == 0) w = atomicAdd(a.work, 1u);
+      w = __shfl_sync(FULL, w, 0);
+      if ((int64_t)w >= nwork) break;
+      const int64_t qidx = a.qlist ? (int64_t)a.qlist[w] : (int64_t)w;
+      int64_t p = -1;
+      const char* qrow;
+      if (a.mode == 0) {
+        p = a.q_first + qidx * a.q_step;
+        qrow = a.X + p * a.ld_bytes;
+      } else {
+        qrow = a.Q + qidx * a.ldq_bytes;
+      }
+      uint4 q[K];
+      load_chunks<METRIC, G, K>(qrow, a.nchunks, gl, q);
+      for (uint32_t i = lane; i < nslots / 4; i += 32)
+        reinterpret_cast<uint4*>(hash)[i] = make_uint4(EMPTY, EMPTY, EMPTY, EMPTY);
+      __syncwarp();
+      uint64_t pool[S];
+#pragma unroll
+      for (int s = 0; s < S; ++s) pool[s] = PAD;
+      int qn = 0;
+      int nvis = 0, ne = 0;
+      bool ovf = false;
+      unsigned long long q_sc = 0;
+
+      // hash-insert one candidate per lane (-1 = none) and queue the new ones;
+      // full batches of 32 are evaluated and merged at once
+      auto enqueue = [&](int32_t v) {
+        bool isnew = (v >= 0) && hash_insert(hash, mask_buckets, (uint32_t)v);
+        unsigned m = __ballot_sync(FULL, isnew);
+        int pos = qn + __popc(m & ((1u << lane) - 1u));
+        if (isnew) queue[pos] = v;
+        qn += __popc(m);
+        nvis += __popc(m);
+        __syncwarp();
+        if (nvis > a.vis_cap) ovf = true;
+        if (qn >= 32) {
+          eval_merge(a, q, queue, 32, pool, lane);
+          int rest = qn - 32;
+          int32_t t = lane < rest ? queue[32 + lane] : 0;
+          __syncwarp();
+          if (lane < rest) queue[lane] = t;
+          __syncwarp();
+          qn = rest;
+        }
+      };
+      auto scan = [&](const int32_t* ids, int64_t len) {
+        for (int64_t base = 0; base < len && !ovf; base += 32) {
+          int32_t v = (base + lane < len) ? ids[base + lane] : -1;
+          enqueue(v);
+        }
+        q_sc += (unsigned long long)len;
+      };
+
+      for (int t0 = 0; t0 < a.T; t0 += 32) enqueue(t0 + lane < a.T ? a.roots[t0 + lane] : -1);
+      if (qn > 0) {
+        eval_merge(a, q, queue, qn, pool, lane);
+        qn = 0;
+        __syncwarp();
+      }
+
+      while (!ovf) {
+        int idx = -1;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          unsigned m = __ballot_sync(FULL, (pool[s] & 1ull) == 0ull);
+          if (m && idx < 0) idx = s * 32 + __ffs(m) - 1;
+        }
+        if (idx < 0) break;
+        if (ne >= a.ecap) {
+          ovf = true;
+          break;
+        }
+        uint64_t ck = 0;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          if (s == idx / 32) {
+            ck = __shfl_sync(FULL, pool[s], idx % 32);
+            if (lane == idx % 32) pool[s] |= 1ull;
+          }
+        }
+        if (lane == 0) E[ne] = ck;
+        ++ne;
+        const int32_t c = key_id(ck);
+        const int64_t s0 = a.s_off[c], s1 = a.s_off[c + 1];
+        scan(a.s_ids + s0, s1 - s0);
+        if (a.mode == 0) {
+          if (!ovf && (c % a.B) < a.b) scan(a.A + (int64_t)c * a.R, a.cnt[c]);
+          if (!ovf && a.r_off) {
+            const int64_t r0 = a.r_off[c], r1 = a.r_off[c + 1];
+            scan(a.r_ids + r0, r1 - r0);
+          }
+        }
+        if (!ovf && qn > 0) {
+          eval_merge(a, q, queue, qn, pool, lane);
+          __syncwarp();
+          qn = 0;
+        }
+      }
+      __syncwarp();
+
+      if (ovf) {
+        if (lane == 0) {
+          if (a.global_scratch) {
+            atomicOr(a.err_flag, 1u);
+          } else {
+            uint32_t pos = atomicAdd(a.ovf_count, 1u);
+            if (pos < a.ovf_cap) {
+              a.ovf_list[pos] = (int32_t)qidx;
+            } else {
+              atomicOr(a.err_flag, 1u);
+            }
+          }
+        }
+        c_ovf++;
+        continue;
+      }
+      c_ev += (unsigned long long)nvis;
+      c_ex += (unsigned long long)ne;
+      c_sc += q_sc;
+
+      if (a.mode == 1) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          int i = s * 32 + lane;
+          if (i < a.k) {
+            uint64_t kk = pool[s];
+            a.top_ids[qidx * a.k + i] = kk == PAD ? -1 : key_id(kk);
+            a.top_d[qidx * a.k + i] = kk == PAD ? __int_as_float(0x7f800000) : key_dist(kk);
+          }
+        }
+        if (lane == 0 && a.q_evals) a.q_evals[qidx] = (uint32_t)nvis;
+        continue;
+      }
+
+      // ---- occlusion prune of the expanded set (Section 3) ----
+      int NE2 = 32;
+      while (NE2 < ne) NE2 <<= 1;
+      int m = 0;
+      for (int i0 = 0; i0 < NE2; i0 += 32) {
+        int i = i0 + lane;
+        uint64_t kk = i < ne ? E[i] : PAD;
+        if (kk != PAD && key_id(kk) == (int32_t)p) kk = PAD;
+        E[i] = kk;
+        m += __popc(__ballot_sync(FULL, kk != PAD));
+      }
+      __syncwarp();
+      warp_sort_mem(E, NE2, lane);
+      const int nw = (m + 31) / 32;
+      for (int w2 = lane; w2 < nw; w2 += 32)
+        alive[w2] = (w2 * 32 + 32 <= m) ? FULL : ((1u << (m - w2 * 32)) - 1u);
+      __syncwarp();
+      int32_t* row = a.A_out + p * a.R;
+      int kept = 0, cur = -1;
+      unsigned long long q_pe = 0;
+      while (kept < a.R) {
+        int nxt = -1;
+        for (int w2 = (cur + 1) / 32; w2 < nw && nxt < 0; ++w2) {
+          uint32_t bits = alive[w2];
+          if (w2 == (cur + 1) / 32) bits &= ~((1u << ((cur + 1) % 32)) - 1u);
+          if (bits) nxt = w2 * 32 + __ffs(bits) - 1;
+        }
+        if (nxt < 0) break;
+        cur = nxt;
+        const int32_t cid = key_id(E[cur]);
+        if (lane == 0) {
+          row[kept] = cid;
+          alive[cur / 32] &= ~(1u << (cur % 32));
+        }
+        ++kept;
+        __syncwarp();
+        if (kept == a.R) break;
+        uint4 cv[K];
+        load_chunks<METRIC, G, K>(a.X + (int64_t)cid * a.ld_bytes, a.nchunks, gl, cv);
+        for (int w2 = cur / 32; w2 < nw; ++w2) {
+          uint32_t bits = alive[w2];
+          if (w2 == cur / 32) bits &= ~((2u << (cur % 32)) - 1u);
+          q_pe += (unsigned long long)__popc(bits);
+          uint32_t kill = 0;
+          while (bits) {
+            const int nb = __popc(bits);
+            uint4 v[U][K];
+            int jj[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              int r = u * GPW + g;
+              if (r < nb) {
+                jj[u] = nth_set_bit(bits, r);
+                load_chunks<METRIC, G, K>(a.X + (int64_t)key_id(E[w2 * 32 + jj[u]]) * a.ld_bytes,
+                                          a.nchunks, gl, v[u]);
+              } else {
+                jj[u] = -1;
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) v[u][kk] = make_uint4(0u, 0u, 0u, 0u);
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              float dd = group_reduce<METRIC, G>(partial<METRIC, G, K>(cv, v[u], a.d, gl));
+              if (jj[u] >= 0 && gl == 0) {
+                float dp = key_dist(E[w2 * 32 + jj[u]]);
+                if (__fmul_rn(a.alpha2, dd) <= dp) kill |= 1u << jj[u];
+              }
+            }
+            const int consumed = nb < GPW * U ? nb : GPW * U;
+            if (consumed >= nb) {
+              bits = 0;
+            } else {
+              bits &= ~((1u << nth_set_bit(bits, consumed)) - 1u);
+            }
+          }
+          kill = __reduce_or_sync(FULL, kill);
+          if (lane == 0) alive[w2] &= ~kill;
+          __syncwarp();
+        }
+      }
+      for (int r = kept + lane; r < a.R; r += 32) row[r] = -1;
+      if (lane == 0) a.cnt_out[p] = kept;
+      c_pe += q_pe;
+      __syncwarp();
+    }
+    if (lane == 0) {
+      atomicAdd(a.counters + 0, c_ev);
+      atomicAdd(a.counters + 1, c_ex);
+      atomicAdd(a.counters + 2, c_pe);
+      atomicAdd(a.counters + 3, c_sc);
+      atomicAdd(a.counters + 4, c_ovf);
+    }
+  }
+};
+
+template <int METRIC, int G, int K, int S>
+__global__ void __launch_bounds__(128) beam_kernel(const BeamArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Beam<METRIC, G, K, S>::run(a, smem);
+}
+
+// Host-side launcher table entry (defined per metric in beam_*.cu).
+using BeamKernelFn = void (*)(const BeamArgs);
+BeamKernelFn beam_kernel_metric0(int G, int K, int S);
+BeamKernelFn beam_kernel_metric1(int G, int K, int S);
+BeamKernelFn beam_kernel_metric2(int G, int K, int S);
+
+}  // namespace fg

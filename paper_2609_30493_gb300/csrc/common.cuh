@@ -1,0 +1,268 @@
+// Device helpers shared by the FGraft kernels (sm_103a).
+//
+// Canonical distance.  The paper computes Euclidean distances on float32
+// vectors, angular data being L2-normalised (Section 2).  Bit-exact results
+// need one summation order; the library fixes it as 32 virtual lanes, lane l
+// owning elements j = 128k + 4l + c (k = 0,1,..; c = 0..3) in that order with
+// acc = fma(t, t, acc), t = x_j - y_j rounded first (acc = fma(x_j, y_j, acc)
+// for the angular inner product), followed by the xor butterfly
+// +16, +8, +4, +2, +1.  A group of G lanes (G a power of two covering the
+// non-empty virtual lanes) reproduces it bit for bit, because the virtual
+// lanes it drops hold +0.0 and adding +0.0 to a non-negative-zero partial is
+// exact.  uint8 vectors use exact integer arithmetic.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fg {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr uint32_t EMPTY = 0xFFFFFFFFu;
+constexpr uint64_t PAD = ~0ull;
+
+enum Metric : int { L2_F32 = 0, ANGULAR_F32 = 1, L2_U8 = 2 };
+
+// Monotone map of a float onto uint32 (total order for finite values and inf).
+__device__ __forceinline__ uint32_t fkey(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(uint32_t k) {
+  uint32_t u = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+  return __uint_as_float(u);
+}
+// (delta, id) packed so that integer order is the (delta, id) order; bit 0 is
+// free for a flag (an entry is never compared with itself).
+__device__ __forceinline__ uint64_t make_key(float d, int32_t id) {
+  return ((uint64_t)fkey(d) << 32) | ((uint64_t)(uint32_t)id << 1);
+}
+__device__ __forceinline__ int32_t key_id(uint64_t k) { return (int32_t)((uint32_t)k >> 1); }
+__device__ __forceinline__ float key_dist(uint64_t k) { return fkey_inv((uint32_t)(k >> 32)); }
+
+__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a < b ? b : a; }
+
+// ---------------------------------------------------------------------------
+// Vector access.  A row is cut into 16-byte chunks; lane gl of a G-lane group
+// holds chunks k*G + gl, k < K.  For float32 with G < 32, K is 1, so the lane
+// holds elements 4gl..4gl+3 exactly as virtual lane gl does; for G = 32 the
+// chunk k*32 + l covers elements 128k + 4l + c.
+// ---------------------------------------------------------------------------
+template <int METRIC>
+struct ElemBytes {
+  static constexpr int value = METRIC == L2_U8 ? 1 : 4;
+};
+
+template <int METRIC, int G, int K>
+__device__ __forceinline__ void load_chunks(const char* __restrict__ row, int nchunks, int gl,
+                                            uint4 (&v)[K]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    int c = k * G + gl;
+    if (c < nchunks) {
+      v[k] = __ldg(reinterpret_cast<const uint4*>(row) + c);
+    } else {
+      v[k] = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+}
+
+// Per-lane partial of the canonical distance.  d = vector length.
+template <int METRIC, int G, int K>
+__device__ __forceinline__ float partial(const uint4 (&q)[K], const uint4 (&v)[K], int d, int gl) {
+  if constexpr (METRIC == L2_U8) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      int c = k * G + gl;
+      int nb = d - 16 * c;  // valid bytes in this chunk
+      uint32_t a[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
+      uint32_t b[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        int vb = nb - 4 * w;
+        uint32_t m = vb >= 4 ? 0xFFFFFFFFu : (vb <= 0 ? 0u : (0xFFFFFFFFu >> (8 * (4 - vb))));
+        uint32_t diff = __vabsdiffu4(a[w] & m, b[w] & m);
+        s = __dp4a(diff, diff, s);
+      }
+    }
+    return __uint_as_float(s);  // carried as raw bits; reduced as integers
+  } else {
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      int c = k * G + gl;
+      int nv = d - 4 * c;  // valid elements in this chunk
+      float x[4] = {__uint_as_float(q[k].x), __uint_as_float(q[k].y), __uint_as_float(q[k].z),
+                    __uint_as_float(q[k].w)};
+      float y[4] = {__uint_as_float(v[k].x), __uint_as_float(v[k].y), __uint_as_float(v[k].z),
+                    __uint_as_float(v[k].w)};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (nv > e) {
+          if constexpr (METRIC == ANGULAR_F32) {
+            acc = __fmaf_rn(x[e], y[e], acc);
+          } else {
+            float t = __fsub_rn(x[e], y[e]);
+            acc = __fmaf_rn(t, t, acc);
+          }
+        }
+      }
+    }
+    return acc;
+  }
+}
+
+// Combine the partials of a G-lane group; every lane of the group gets the
+// distance.
+template <int METRIC, int G>
+__device__ __forceinline__ float group_reduce(float p) {
+  if constexpr (METRIC == L2_U8) {
+    uint32_t s = __float_as_uint(p);
+#pragma unroll
+    for (int off = G / 2; off >= 1; off >>= 1) s += __shfl_xor_sync(FULL, s, off);
+    return __uint2float_rn(s);
+  } else {
+    float v = p;
+#pragma unroll
+    for (int off = G / 2; off >= 1; off >>= 1) v = __fadd_rn(v, __shfl_xor_sync(FULL, v, off));
+    if constexpr (METRIC == ANGULAR_F32) return __fsub_rn(1.0f, v);
+    return v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Warp bitonic networks on 64-bit keys.
+// ---------------------------------------------------------------------------
+// Sort one key per lane ascending across the warp.
+__device__ __forceinline__ uint64_t warp_sort32(uint64_t x, int lane) {
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      uint64_t o = __shfl_xor_sync(FULL, x, j);
+      bool up = (lane & k) == 0;
+      bool lower = (lane & j) == 0;
+      x = (lower == up) ? umin64(x, o) : umax64(x, o);
+    }
+  }
+  return x;
+}
+
+// A register list of N = 32*S keys, entry i at slot i/32 of lane i%32, that
+// is bitonic, is sorted ascending.
+template <int S>
+__device__ __forceinline__ void bitonic_merge_regs(uint64_t (&a)[S], int lane) {
+#pragma unroll
+  for (int sj = S / 2; sj >= 1; sj >>= 1) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      if ((s & sj) == 0) {
+        uint64_t x = a[s], y = a[s + sj];
+        a[s] = umin64(x, y);
+        a[s + sj] = umax64(x, y);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 16; j >= 1; j >>= 1) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      uint64_t o = __shfl_xor_sync(FULL, a[s], j);
+      a[s] = (lane & j) ? umax64(a[s], o) : umin64(a[s], o);
+    }
+  }
+}
+
+// pool := the ef smallest of pool U {cand}, pool sorted ascending in a list of
+// N = 32*S >= ef slots (entries past ef are PAD), cand one key per lane
+// (PAD = none).  Keys must be distinct.
+template <int S>
+__device__ __forceinline__ void merge_into_pool(uint64_t (&pool)[S], uint64_t cand, int ef,
+                                                int lane) {
+  uint64_t worst = PAD;
+#pragma unroll
+  for (int s = 0; s < S; ++s)
+    if (s == (ef - 1) / 32) worst = __shfl_sync(FULL, pool[s], (ef - 1) % 32);
+  if (cand >= worst) cand = PAD;
+  if (__ballot_sync(FULL, cand != PAD) == 0) return;
+  cand = warp_sort32(cand, lane);
+  uint64_t rev = __shfl_sync(FULL, cand, 31 - lane);
+  pool[S - 1] = umin64(pool[S - 1], rev);
+  bitonic_merge_regs<S>(pool, lane);
+#pragma unroll
+  for (int s = 0; s < S; ++s)
+    if (s * 32 + lane >= ef) pool[s] = PAD;
+}
+
+// Ascending bitonic sort of N keys (N a power of two) in shared or global
+// memory by one warp.
+__device__ __forceinline__ void warp_sort_mem(uint64_t* a, int N, int lane) {
+  for (int k = 2; k <= N; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < N / 2; i += 32) {
+        int lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+        int hi = lo + j;
+        bool asc = (lo & k) == 0;
+        uint64_t x = a[lo], y = a[hi];
+        if ((x > y) == asc) {
+          a[lo] = y;
+          a[hi] = x;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Exact visited set: open addressing over 4-slot buckets, linear probing by
+// bucket.  Returns true when id was absent and is now inserted.  Lanes of a
+// warp may insert concurrently (a duplicate resolves through atomicCAS).  The
+// caller keeps the load below capacity, so an empty slot is always reachable.
+__device__ __forceinline__ bool hash_insert(uint32_t* h, uint32_t mask_buckets, uint32_t id) {
+  uint32_t bkt = (id * 2654435761u) & mask_buckets;
+  for (uint32_t probe = 0; probe <= mask_buckets;) {
+    uint32_t* b = h + 4 * bkt;
+    uint4 s;
+    asm volatile("ld.volatile.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(s.x), "=r"(s.y), "=r"(s.z), "=r"(s.w)
+                 : "l"(b));
+    if (s.x == id || s.y == id || s.z == id || s.w == id) return false;
+    int j = s.x == EMPTY ? 0 : s.y == EMPTY ? 1 : s.z == EMPTY ? 2 : s.w == EMPTY ? 3 : -1;
+    if (j < 0) {
+      bkt = (bkt + 1) & mask_buckets;
+      ++probe;
+      continue;
+    }
+    uint32_t old = atomicCAS(b + j, EMPTY, id);
+    if (old == EMPTY) return true;
+    if (old == id) return false;
+    // the slot went to another id: read the same bucket again
+  }
+  return false;
+}
+
+// Position of the r-th (0-based) set bit of x; r < popc(x).
+__device__ __forceinline__ int nth_set_bit(uint32_t x, int r) {
+  int base = 0;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    int c = __popc((x >> base) & ((1u << w) - 1u));
+    if (r >= c) {
+      r -= c;
+      base += w;
+    }
+  }
+  return base;
+}
+
+// Candidates evaluated per lane group per unrolled step: enough independent
+// 16-byte loads in flight, at most 32 candidates per warp step.
+template <int G, int K>
+struct Unroll {
+  static constexpr int GPW = 32 / G;
+  static constexpr int A = (32 / GPW) < (8 / K) ? (32 / GPW) : (8 / K);
+  static constexpr int value = A < 1 ? 1 : A;
+};
+
+}  // namespace fg

@@ -1,0 +1,637 @@
+// Graph bookkeeping kernels: device-wide scan, the scaffold CSR (Section 3:
+// union of the trees' edges, symmetrised), the reverse lists that turn the
+// rows of finished blocks into S_{b+1}, the final graph (rows symmetrised,
+// re-pruned when over R, tree-0 spine added) and the stand-alone list prune.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+#include "rowops.cuh"
+
+namespace fg {
+
+// ---------------------------------------------------------------------------
+// Exclusive scan, uint32 -> int64, three passes over tiles of 2048.
+// ---------------------------------------------------------------------------
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_PER = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_PER;
+
+int64_t scan_tmp_elems(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* total) {
+  __shared__ int64_t warp_sums[SCAN_THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    int64_t y = __shfl_up_sync(FULL, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  int64_t wpre = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < SCAN_THREADS / 32; ++w) {
+    int64_t s = warp_sums[w];
+    if (w < warp) wpre += s;
+    tot += s;
+  }
+  __syncthreads();
+  *total = tot;
+  return wpre + x - v;
+}
+
+__global__ void scan_tiles_kernel(const uint32_t* in, int64_t n, int64_t* tile_sums) {
+  const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t base = tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_PER;
+    int64_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_PER; ++j)
+      if (base + j < n) s += in[base + j];
+    int64_t tot;
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) tile_sums[tile] = tot;
+  }
+}
+
+__global__ void scan_prefix_kernel(int64_t* tile_sums, int64_t ntiles) {
+  int64_t carry = 0;
+  for (int64_t base = 0; base < ntiles; base += SCAN_THREADS) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t v = i < ntiles ? tile_sums[i] : 0;
+    int64_t tot;
+    const int64_t ex = block_exclusive_scan(v, &tot);
+    if (i < ntiles) tile_sums[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) tile_sums[ntiles] = carry;
+}
+
+__global__ void scan_apply_kernel(const uint32_t* in, int64_t* out, int64_t n,
+                                  const int64_t* tile_pre) {
+  const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t base = tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_PER;
+    uint32_t v[SCAN_PER];
+    int64_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_PER; ++j) {
+      v[j] = base + j < n ? in[base + j] : 0u;
+      s += v[j];
+    }
+    int64_t tot;
+    int64_t run = tile_pre[tile] + block_exclusive_scan(s, &tot);
+#pragma unroll
+    for (int j = 0; j < SCAN_PER; ++j) {
+      if (base + j < n) out[base + j] = run;
+      run += v[j];
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = tile_pre[ntiles];
+}
+
+int scan_u32(const uint32_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStream_t s) {
+  const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 152 * 8));
+  scan_tiles_kernel<<<grid, SCAN_THREADS, 0, s>>>(in, n, tmp);
+  scan_prefix_kernel<<<1, SCAN_THREADS, 0, s>>>(tmp, ntiles);
+  scan_apply_kernel<<<grid, SCAN_THREADS, 0, s>>>(in, out, n, tmp);
+  FG_CUDA(cudaGetLastError());
+  return 0;
+}
+
+static int grid1d(int64_t tot, int threads = 256) {
+  int64_t g = (tot + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
+}
+
+// ---------------------------------------------------------------------------
+// Scaffold CSR.
+// ---------------------------------------------------------------------------
+__global__ void edge_count_kernel(int64_t n, int64_t tot, const int32_t* parents, uint32_t* deg) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = parents[i];
+    if (p >= 0) {
+      atomicAdd(&deg[i % n], 1u);
+      atomicAdd(&deg[p], 1u);
+    }
+  }
+}
+
+__global__ void edge_fill_kernel(int64_t n, int64_t tot, const int32_t* parents, uint32_t* cur,
+                                 const int64_t* off, int32_t* ids) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = parents[i];
+    if (p >= 0) {
+      const int32_t x = (int32_t)(i % n);
+      ids[off[x] + atomicSub(&cur[x], 1u) - 1u] = p;
+      ids[off[p] + atomicSub(&cur[p], 1u) - 1u] = x;
+    }
+  }
+}
+
+constexpr int ROW_WARPS = 4;
+constexpr int ROW_CAP = 1024;  // keys per warp in shared memory
+
+// Sort each row's ids ascending and drop repeats; ucnt[r] = distinct count,
+// the distinct ids at the front of the row.  Rows longer than the buffer
+// (cap) are appended to long_rows and left for the global-scratch pass.
+__global__ void __launch_bounds__(ROW_WARPS * 32)
+    sort_unique_rows_kernel(int64_t nrows, const int32_t* rowlist, const uint32_t* rowlist_len,
+                            const int64_t* off, int32_t* ids, uint32_t* ucnt, int32_t* long_rows,
+                            uint32_t* nlong, uint64_t* gbuf, int32_t gcap) {
+  __shared__ uint64_t sbuf[ROW_WARPS][ROW_CAP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t* keys = gbuf ? gbuf + ((int64_t)blockIdx.x * ROW_WARPS + warp) * gcap : sbuf[warp];
+  const int cap = gbuf ? gcap : ROW_CAP;
+  const int64_t total = rowlist_len ? (int64_t)*rowlist_len : nrows;
+  for (int64_t w = (int64_t)blockIdx.x * ROW_WARPS + warp; w < total;
+       w += (int64_t)gridDim.x * ROW_WARPS) {
+    const int64_t r = rowlist ? rowlist[w] : w;
+    const int64_t o = off[r];
+    const int len = (int)(off[r + 1] - o);
+    int N2 = 32;
+    while (N2 < len) N2 <<= 1;
+    if (N2 > cap) {
+      if (lane == 0) long_rows[atomicAdd(nlong, 1u)] = (int32_t)r;
+      continue;
+    }
+    for (int i = lane; i < len; i += 32) keys[i] = (uint64_t)(uint32_t)ids[o + i];
+    __syncwarp();
+    const int u = sort_unique(keys, len, lane);
+    for (int i = lane; i < u; i += 32) ids[o + i] = (int32_t)keys[i];
+    if (lane == 0) ucnt[r] = (uint32_t)u;
+    __syncwarp();
+  }
+}
+
+__global__ void compact_rows_kernel(int64_t n, const int64_t* src_off, const int32_t* src,
+                                    const int64_t* dst_off, int32_t* dst) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; r < n;
+       r += ((int64_t)gridDim.x * blockDim.x) / 32) {
+    const int64_t len = dst_off[r + 1] - dst_off[r];
+    for (int64_t i = lane; i < len; i += 32) dst[dst_off[r] + i] = src[src_off[r] + i];
+  }
+}
+
+__global__ void max_row_kernel(int64_t n, const int64_t* off, const int32_t* rows,
+                               const uint32_t* nrows, uint32_t* mx) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)*nrows;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = rows[i];
+    atomicMax(mx, (uint32_t)(off[r + 1] - off[r]));
+  }
+}
+
+static int pow2_at_least(int64_t v) {
+  int p = 32;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Runs the sort-unique pass, then the long rows with global scratch.
+static int sort_unique_all(int64_t n, const int64_t* off, int32_t* ids, uint32_t* ucnt,
+                           cudaStream_t s) {
+  int32_t* long_rows = nullptr;
+  uint32_t* small = nullptr;  // [0] nlong, [1] max length
+  FG_CUDA(cudaMallocAsync(&long_rows, sizeof(int32_t) * std::max<int64_t>(n, 1), s));
+  FG_CUDA(cudaMallocAsync(&small, 2 * sizeof(uint32_t), s));
+  FG_CUDA(cudaMemsetAsync(small, 0, 2 * sizeof(uint32_t), s));
+  sort_unique_rows_kernel<<<grid1d(n * 32, ROW_WARPS * 32), ROW_WARPS * 32, 0, s>>>(
+      n, nullptr, nullptr, off, ids, ucnt, long_rows, small, nullptr, 0);
+  max_row_kernel<<<64, 256, 0, s>>>(n, off, long_rows, small, small + 1);
+  FG_CUDA(cudaGetLastError());
+  uint32_t h[2];
+  FG_CUDA(cudaMemcpyAsync(h, small, sizeof(h), cudaMemcpyDeviceToHost, s));
+  FG_CUDA(cudaStreamSynchronize(s));
+  int rc = 0;
+  if (h[0] > 0) {
+    const int gcap = pow2_at_least(h[1]);
+    const int ctas = (int)std::min<uint32_t>((h[0] + ROW_WARPS - 1) / ROW_WARPS, 64);
+    uint64_t* gbuf = nullptr;
+    cudaError_t e = cudaMallocAsync(&gbuf, sizeof(uint64_t) * (int64_t)gcap * ctas * ROW_WARPS, s);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "cudaMallocAsync(long-row scratch)");
+    } else {
+      sort_unique_rows_kernel<<<ctas, ROW_WARPS * 32, 0, s>>>(n, long_rows, small, off, ids, ucnt,
+                                                             long_rows, small, gbuf, gcap);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) rc = cuda_fail(e, "sort_unique_rows_kernel(long)");
+      cudaFreeAsync(gbuf, s);
+    }
+  }
+  cudaFreeAsync(long_rows, s);
+  cudaFreeAsync(small, s);
+  return rc;
+}
+
+int scaffold_csr(int64_t n, int T, const int32_t* parents, int64_t* s_off, int32_t** s_ids,
+                 int64_t* nnz_out, uint32_t* deg, int64_t* tmp_off, int32_t* tmp_ids,
+                 int64_t* scan_tmp, cudaStream_t s) {
+  const int64_t tot = (int64_t)T * n;
+  FG_CUDA(cudaMemsetAsync(deg, 0, sizeof(uint32_t) * n, s));
+  edge_count_kernel<<<grid1d(tot), 256, 0, s>>>(n, tot, parents, deg);
+  int rc = scan_u32(deg, tmp_off, n, scan_tmp, s);
+  if (rc) return rc;
+  edge_fill_kernel<<<grid1d(tot), 256, 0, s>>>(n, tot, parents, deg, tmp_off, tmp_ids);
+  FG_CUDA(cudaGetLastError());
+  rc = sort_unique_all(n, tmp_off, tmp_ids, deg, s);
+  if (rc) return rc;
+  rc = scan_u32(deg, s_off, n, scan_tmp, s);
+  if (rc) return rc;
+  int64_t nnz = 0;
+  FG_CUDA(cudaMemcpyAsync(&nnz, s_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  FG_CUDA(cudaStreamSynchronize(s));
+  FG_CUDA(cudaMalloc(s_ids, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+  compact_rows_kernel<<<grid1d(n * 32), 256, 0, s>>>(n, tmp_off, tmp_ids, s_off, *s_ids);
+  FG_CUDA(cudaGetLastError());
+  *nnz_out = nnz;
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Reverse lists of the rows of blocks 0..b.
+// ---------------------------------------------------------------------------
+__global__ void rev_count_kernel(int64_t n, int R, int nb, int b, const int32_t* A,
+                                 const int32_t* cnt, uint32_t* rcnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * R;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = i / R;
+    const int j = (int)(i - p * R);
+    if ((int)(p % nb) <= b && j < cnt[p]) atomicAdd(&rcnt[A[i]], 1u);
+  }
+}
+
+__global__ void rev_fill_kernel(int64_t n, int R, int nb, int b, const int32_t* A,
+                                const int32_t* cnt, uint32_t* rcur, const int64_t* r_off,
+                                int32_t* r_ids) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * R;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = i / R;
+    const int j = (int)(i - p * R);
+    if ((int)(p % nb) <= b && j < cnt[p]) {
+      const int32_t u = A[i];
+      r_ids[r_off[u] + atomicAdd(&rcur[u], 1u)] = (int32_t)p;
+    }
+  }
+}
+
+int reverse_rows(int64_t n, int R, int nb, int b, const int32_t* A, const int32_t* cnt,
+                 uint32_t* rcnt, uint32_t* rcur, int64_t* r_off, int32_t* r_ids,
+                 int64_t* scan_tmp, cudaStream_t s) {
+  FG_CUDA(cudaMemsetAsync(rcnt, 0, sizeof(uint32_t) * n, s));
+  FG_CUDA(cudaMemsetAsync(rcur, 0, sizeof(uint32_t) * n, s));
+  rev_count_kernel<<<grid1d(n * R), 256, 0, s>>>(n, R, nb, b, A, cnt, rcnt);
+  int rc = scan_u32(rcnt, r_off, n, scan_tmp, s);
+  if (rc) return rc;
+  rev_fill_kernel<<<grid1d(n * R), 256, 0, s>>>(n, R, nb, b, A, cnt, rcur, r_off, r_ids);
+  FG_CUDA(cudaGetLastError());
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Final graph and list prune: one warp per row.
+// ---------------------------------------------------------------------------
+struct FinalArgs {
+  RowVec V;
+  int64_t n;
+  int32_t R;
+  float alpha2;
+  // final graph: candidate sources
+  const int32_t* A;
+  const int32_t* cnt;
+  const int64_t* r_off;
+  const int32_t* r_ids;
+  const int32_t* parent0;
+  const int64_t* c0_off;
+  const int32_t* c0_ids;
+  // list prune: candidate lists and owners
+  const int32_t* owner;
+  const int64_t* l_off;
+  const int32_t* l_ids;
+  // outputs: final rows into out_ids at out_cap_off[u] with out_cnt[u];
+  // list prune rows into out_ids[i*R] with out_cnt[i]
+  const int64_t* out_cap_off;
+  int32_t* out_ids;
+  int32_t* out_cnt;
+  // work list (NULL: all rows) and long-row spill
+  const int32_t* rowlist;
+  const uint32_t* rowlist_len;
+  int64_t nrows;
+  int32_t* long_rows;
+  uint32_t* nlong;
+  uint64_t* gbuf;
+  int32_t gcap;
+  int32_t mode;  // 0 final graph, 1 list prune
+  unsigned long long* ctr;
+};
+
+constexpr int FIN_WARPS = 4;
+constexpr int FIN_CAP = 1024;
+
+template <int METRIC, int G, int K>
+__global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalArgs a) {
+  __shared__ uint64_t sbuf[FIN_WARPS][FIN_CAP];
+  __shared__ uint32_t sbits[FIN_WARPS][2 * FIN_CAP / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gl = lane % G;
+  const int64_t gw = (int64_t)blockIdx.x * FIN_WARPS + warp;
+  uint64_t* keys;
+  uint32_t* bits;
+  int cap;
+  if (a.gbuf) {
+    keys = a.gbuf + gw * ((int64_t)a.gcap + a.gcap / 32);
+    bits = reinterpret_cast<uint32_t*>(keys + a.gcap);
+    cap = a.gcap;
+  } else {
+    keys = sbuf[warp];
+    bits = sbits[warp];
+    cap = FIN_CAP;
+  }
+  const int64_t total = a.rowlist_len ? (int64_t)*a.rowlist_len : a.nrows;
+  unsigned long long ev = 0;
+  for (int64_t w = gw; w < total; w += (int64_t)gridDim.x * FIN_WARPS) {
+    const int64_t r = a.rowlist ? a.rowlist[w] : w;
+    int32_t u;
+    const int32_t *seg0, *seg1;
+    int len0, len1;
+    int sdeg = 0;
+    if (a.mode == 0) {
+      u = (int32_t)r;
+      seg0 = a.A + (int64_t)u * a.R;
+      len0 = a.cnt[u];
+      seg1 = a.r_ids + a.r_off[u];
+      len1 = (int)(a.r_off[u + 1] - a.r_off[u]);
+      sdeg = (a.parent0[u] >= 0 ? 1 : 0) + (int)(a.c0_off[u + 1] - a.c0_off[u]);
+    } else {
+      u = a.owner[r];
+      seg0 = a.l_ids + a.l_off[r];
+      len0 = (int)(a.l_off[r + 1] - a.l_off[r]);
+      seg1 = nullptr;
+      len1 = 0;
+    }
+    const int mraw = len0 + len1;
+    const int need = max(pow2_dev(mraw), pow2_dev(min(mraw, a.R) + sdeg));
+    if (need > cap) {
+      if (lane == 0) a.long_rows[atomicAdd(a.nlong, 1u)] = (int32_t)r;
+      continue;
+    }
+    uint4 uv[K];
+    load_chunks<METRIC, G, K>(a.V.X + (int64_t)u * a.V.ld_bytes, a.V.nchunks, gl, uv);
+    eval_keys<METRIC, G, K>(a.V, uv, seg0, len0, seg1, len1, keys, 0, lane);
+    // the owner itself is not a candidate (list prune may contain it)
+    for (int i = lane; i < mraw; i += 32)
+      if (key_id(keys[i]) == u) keys[i] = PAD;
+    __syncwarp();
+    int m = sort_unique(keys, mraw, lane);
+    if (m > 0 && __shfl_sync(FULL, keys[m - 1] == PAD ? 1 : 0, 0)) --m;  // dropped owner
+    ev += (unsigned long long)m;
+    int32_t* out;
+    if (a.mode == 0) {
+      out = a.out_ids + a.out_cap_off[u];
+      // spine members not already candidates cost one evaluation each
+      const int32_t p0 = a.parent0[u];
+      const int32_t* ch = a.c0_ids + a.c0_off[u];
+      for (int j = 0; j < sdeg; ++j) {
+        const int32_t v = (p0 >= 0) ? (j == 0 ? p0 : ch[j - 1]) : ch[j];
+        if (!keys_contain(keys, m, v, lane)) ++ev;
+      }
+    } else {
+      out = a.out_ids + r * a.R;
+    }
+    int kk = m;
+    if (m > a.R || a.mode == 1) kk = prune_sorted<METRIC, G, K>(a.V, keys, m, a.alpha2, a.R, bits, &ev, lane);
+    if (a.mode == 0) {
+      const int32_t p0 = a.parent0[u];
+      const int32_t* ch = a.c0_ids + a.c0_off[u];
+      int add = 0;
+      for (int j = 0; j < sdeg; ++j) {
+        const int32_t v = (p0 >= 0) ? (j == 0 ? p0 : ch[j - 1]) : ch[j];
+        if (keys_contain(keys, kk, v, lane)) continue;
+        // evaluate delta(u, v) and append
+        eval_keys<METRIC, G, K>(a.V, uv, &v, 1, nullptr, 0, keys, kk + add, lane);
+        ++add;
+      }
+      kk = sort_unique(keys, kk + add, lane);
+      for (int i = lane; i < kk; i += 32) out[i] = key_id(keys[i]);
+      if (lane == 0) a.out_cnt[u] = kk;
+    } else {
+      for (int i = lane; i < a.R; i += 32) out[i] = i < kk ? key_id(keys[i]) : -1;
+      if (lane == 0) a.out_cnt[r] = kk;
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && ev && a.ctr) atomicAdd(a.ctr, ev);
+}
+
+using FinalKernelFn = void (*)(const FinalArgs);
+
+static FinalKernelFn final_kernel_for(int metric, int G, int K) {
+#define FX(M, GG, KK) \
+  if (metric == M && G == GG && K == KK) return final_rows_kernel<M, GG, KK>;
+#define FF(M) FX(M, 4, 1) FX(M, 8, 1) FX(M, 16, 1) FX(M, 32, 1) FX(M, 32, 2) FX(M, 32, 4) \
+  FX(M, 32, 8)
+  FF(0)
+  FF(1)
+  FX(2, 4, 1) FX(2, 8, 1) FX(2, 16, 1)
+#undef FF
+#undef FX
+  return nullptr;
+}
+
+__global__ void child_count_kernel(int64_t n, const int32_t* parent0, uint32_t* c) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (parent0[i] >= 0) atomicAdd(&c[parent0[i]], 1u);
+}
+__global__ void child_fill_kernel(int64_t n, const int32_t* parent0, uint32_t* cur,
+                                  const int64_t* off, int32_t* ids) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = parent0[i];
+    if (p >= 0) ids[off[p] + atomicAdd(&cur[p], 1u)] = (int32_t)i;
+  }
+}
+__global__ void final_cap_kernel(int64_t n, int R, const int32_t* parent0, const int64_t* c0_off,
+                                 uint32_t* cap) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    cap[i] = (uint32_t)(R + (parent0[i] >= 0 ? 1 : 0) + (c0_off[i + 1] - c0_off[i]));
+}
+__global__ void max_final_need_kernel(int64_t n, const int32_t* rows, const uint32_t* nrows,
+                                      int mode, int R, const int32_t* cnt, const int64_t* r_off,
+                                      const int32_t* parent0, const int64_t* c0_off,
+                                      const int64_t* l_off, uint32_t* mx) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)*nrows;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = rows[i];
+    int64_t mraw, sdeg = 0;
+    if (mode == 0) {
+      mraw = cnt[r] + (r_off[r + 1] - r_off[r]);
+      sdeg = (parent0[r] >= 0 ? 1 : 0) + (c0_off[r + 1] - c0_off[r]);
+    } else {
+      mraw = l_off[r + 1] - l_off[r];
+    }
+    int64_t need = max(mraw, min(mraw, (int64_t)R) + sdeg);
+    atomicMax(mx, (uint32_t)need);
+  }
+}
+
+static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, cudaStream_t s) {
+  FinalKernelFn kern = final_kernel_for(L.metric, L.G, L.K);
+  if (!kern) {
+    set_error(1, "no row kernel for this metric and dimension");
+    return 1;
+  }
+  int32_t* long_rows = nullptr;
+  uint32_t* small = nullptr;
+  FG_CUDA(cudaMallocAsync(&long_rows, sizeof(int32_t) * std::max<int64_t>(nrows, 1), s));
+  FG_CUDA(cudaMallocAsync(&small, 2 * sizeof(uint32_t), s));
+  FG_CUDA(cudaMemsetAsync(small, 0, 2 * sizeof(uint32_t), s));
+  a.rowlist = nullptr;
+  a.rowlist_len = nullptr;
+  a.nrows = nrows;
+  a.long_rows = long_rows;
+  a.nlong = small;
+  a.gbuf = nullptr;
+  a.gcap = 0;
+  kern<<<grid1d(nrows * 32, FIN_WARPS * 32), FIN_WARPS * 32, 0, s>>>(a);
+  max_final_need_kernel<<<64, 256, 0, s>>>(nrows, long_rows, small, a.mode, a.R, a.cnt, a.r_off,
+                                           a.parent0, a.c0_off, a.l_off, small + 1);
+  FG_CUDA(cudaGetLastError());
+  uint32_t h[2];
+  FG_CUDA(cudaMemcpyAsync(h, small, sizeof(h), cudaMemcpyDeviceToHost, s));
+  FG_CUDA(cudaStreamSynchronize(s));
+  int rc = 0;
+  if (h[0] > 0) {
+    const int gcap = pow2_at_least(h[1]);
+    const int ctas = (int)std::min<uint32_t>((h[0] + FIN_WARPS - 1) / FIN_WARPS, 64);
+    uint64_t* gbuf = nullptr;
+    cudaError_t e = cudaMallocAsync(
+        &gbuf, sizeof(uint64_t) * ((int64_t)gcap + gcap / 32) * ctas * FIN_WARPS, s);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "cudaMallocAsync(long-row scratch)");
+    } else {
+      a.rowlist = long_rows;
+      a.rowlist_len = small;
+      a.gbuf = gbuf;
+      a.gcap = gcap;
+      kern<<<ctas, FIN_WARPS * 32, 0, s>>>(a);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) rc = cuda_fail(e, "final_rows_kernel(long)");
+      cudaFreeAsync(gbuf, s);
+    }
+  }
+  cudaFreeAsync(long_rows, s);
+  cudaFreeAsync(small, s);
+  return rc;
+}
+
+int final_graph(const VecLayout& L, int R, float alpha2, const int32_t* A, const int32_t* cnt,
+                const int64_t* r_off, const int32_t* r_ids, const int32_t* parent0,
+                int64_t* f_off, int32_t** f_ids, int64_t* f_nnz, int64_t* scan_tmp,
+                unsigned long long* ctr, cudaStream_t s) {
+  const int64_t n = L.n;
+  uint32_t *c0cnt = nullptr, *capc = nullptr;
+  int64_t *c0_off = nullptr, *cap_off = nullptr;
+  int32_t *c0_ids = nullptr, *tmp_ids = nullptr, *rowcnt = nullptr;
+  int rc = 0;
+  auto cleanup = [&]() {
+    cudaFreeAsync(c0cnt, s);
+    cudaFreeAsync(capc, s);
+    cudaFreeAsync(c0_off, s);
+    cudaFreeAsync(cap_off, s);
+    cudaFreeAsync(c0_ids, s);
+    cudaFreeAsync(tmp_ids, s);
+    cudaFreeAsync(rowcnt, s);
+  };
+#define FG_TRY(call)                                \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) {                        \
+      rc = cuda_fail(e_, #call);                    \
+      cleanup();                                    \
+      return rc;                                    \
+    }                                               \
+  } while (0)
+  FG_TRY(cudaMallocAsync(&c0cnt, sizeof(uint32_t) * n, s));
+  FG_TRY(cudaMallocAsync(&capc, sizeof(uint32_t) * n, s));
+  FG_TRY(cudaMallocAsync(&c0_off, sizeof(int64_t) * (n + 1), s));
+  FG_TRY(cudaMallocAsync(&cap_off, sizeof(int64_t) * (n + 1), s));
+  FG_TRY(cudaMallocAsync(&c0_ids, sizeof(int32_t) * std::max<int64_t>(n, 1), s));
+  FG_TRY(cudaMallocAsync(&rowcnt, sizeof(int32_t) * n, s));
+  FG_TRY(cudaMemsetAsync(c0cnt, 0, sizeof(uint32_t) * n, s));
+  child_count_kernel<<<grid1d(n), 256, 0, s>>>(n, parent0, c0cnt);
+  rc = scan_u32(c0cnt, c0_off, n, scan_tmp, s);
+  if (rc) return cleanup(), rc;
+  FG_TRY(cudaMemsetAsync(c0cnt, 0, sizeof(uint32_t) * n, s));
+  child_fill_kernel<<<grid1d(n), 256, 0, s>>>(n, parent0, c0cnt, c0_off, c0_ids);
+  final_cap_kernel<<<grid1d(n), 256, 0, s>>>(n, R, parent0, c0_off, capc);
+  rc = scan_u32(capc, cap_off, n, scan_tmp, s);
+  if (rc) return cleanup(), rc;
+  int64_t capn = 0;
+  FG_TRY(cudaMemcpyAsync(&capn, cap_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  FG_TRY(cudaStreamSynchronize(s));
+  FG_TRY(cudaMallocAsync(&tmp_ids, sizeof(int32_t) * std::max<int64_t>(capn, 1), s));
+  FinalArgs a{};
+  a.V = RowVec{L.X, L.ld_bytes, L.d, L.nchunks};
+  a.n = n;
+  a.R = R;
+  a.alpha2 = alpha2;
+  a.A = A;
+  a.cnt = cnt;
+  a.r_off = r_off;
+  a.r_ids = r_ids;
+  a.parent0 = parent0;
+  a.c0_off = c0_off;
+  a.c0_ids = c0_ids;
+  a.out_cap_off = cap_off;
+  a.out_ids = tmp_ids;
+  a.out_cnt = rowcnt;
+  a.mode = 0;
+  a.ctr = ctr;
+  rc = run_final_rows(a, L, n, s);
+  if (rc) return cleanup(), rc;
+  // final CSR
+  rc = scan_u32(reinterpret_cast<const uint32_t*>(rowcnt), f_off, n, scan_tmp, s);
+  if (rc) return cleanup(), rc;
+  int64_t nnz = 0;
+  FG_TRY(cudaMemcpyAsync(&nnz, f_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  FG_TRY(cudaStreamSynchronize(s));
+  if (*f_ids) {
+    cudaFree(*f_ids);
+    *f_ids = nullptr;
+  }
+  FG_TRY(cudaMalloc(f_ids, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+  compact_rows_kernel<<<grid1d(n * 32), 256, 0, s>>>(n, cap_off, tmp_ids, f_off, *f_ids);
+  FG_TRY(cudaGetLastError());
+  *f_nnz = nnz;
+  cleanup();
+  return 0;
+#undef FG_TRY
+}
+
+int prune_lists(const VecLayout& L, const int32_t* owner, const int64_t* l_off,
+                const int32_t* l_ids, int64_t nlists, float alpha2, int R, int32_t* out_ids,
+                int32_t* out_cnt, unsigned long long* ctr, cudaStream_t s) {
+  FinalArgs a{};
+  a.V = RowVec{L.X, L.ld_bytes, L.d, L.nchunks};
+  a.n = L.n;
+  a.R = R;
+  a.alpha2 = alpha2;
+  a.owner = owner;
+  a.l_off = l_off;
+  a.l_ids = l_ids;
+  a.out_ids = out_ids;
+  a.out_cnt = out_cnt;
+  a.mode = 1;
+  a.ctr = ctr;
+  return run_final_rows(a, L, nlists, s);
+}
+
+}  // namespace fg

@@ -1,0 +1,92 @@
+// Host-side declarations shared by the translation units of libfgraft.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+namespace fg {
+
+// Status plumbing: the C ABI maps these to fgraft_status.
+struct Err {
+  int code;  // fgraft_status value
+  std::string msg;
+};
+
+void set_error(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define FG_CUDA(call)                              \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+// Vector layout of a point set for the kernels.
+struct VecLayout {
+  const char* X;
+  int64_t n;
+  int32_t d;
+  int64_t ld_bytes;
+  int32_t metric;
+  int32_t nchunks;  // 16-byte chunks covering d elements
+  int32_t G, K;     // lanes per vector and chunks per lane
+};
+
+// Picks the lane-group shape for a metric and dimension; false if unsupported.
+bool choose_shape(int metric, int d, int* G, int* K);
+
+// Exclusive scan of n uint32 counts into n+1 int64 offsets (out[n] = total).
+// tmp must hold scan_tmp_elems(n) int64.
+int64_t scan_tmp_elems(int64_t n);
+int scan_u32(const uint32_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStream_t s);
+
+// SAT forest: parents [T*n] (-1 at each root), sat work counter added to ctr.
+struct SatScratch {
+  int32_t* node_of;     // T*n
+  uint32_t* kcnt;       // T*n (zero on entry and exit)
+  int64_t* kstart;      // T*n + 1
+  int32_t* item_pt;     // T*n
+  float* kd;            // T*n
+  uint64_t* best;       // T*n
+  uint8_t* flag;        // T*n
+  int64_t* seg_start;   // T*n
+  int32_t* seg_len;     // T*n
+  int32_t* seg_node;    // T*n
+  int32_t* seg_tree;    // T*n
+  uint32_t* nseg;       // 1
+  uint32_t* nunsettled; // 1
+  int64_t* scan_tmp;
+};
+int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* parents,
+               SatScratch& S, unsigned long long* ctr_sat, cudaStream_t s);
+
+// Scaffold CSR from the parents of T trees (rows sorted by id, no repeats).
+// tmp_off: n+1, tmp_ids: 2*T*n, ucnt: n, deg: n.  On return *nnz_out holds
+// the size and s_ids (allocated here with cudaMalloc) the ids.
+int scaffold_csr(int64_t n, int T, const int32_t* parents, int64_t* s_off, int32_t** s_ids,
+                 int64_t* nnz_out, uint32_t* deg, int64_t* tmp_off, int32_t* tmp_ids,
+                 int64_t* scan_tmp, cudaStream_t s);
+
+// Reverse lists of the rows of blocks 0..b: r_off (n+1), r_ids (<= n*R).
+int reverse_rows(int64_t n, int R, int nb, int b, const int32_t* A, const int32_t* cnt,
+                 uint32_t* rcnt, uint32_t* rcur, int64_t* r_off, int32_t* r_ids,
+                 int64_t* scan_tmp, cudaStream_t s);
+
+// Final graph (rows of all blocks symmetrised, re-pruned when over R, tree-0
+// spine added, sorted).  f_ids is (re)allocated here.
+int final_graph(const VecLayout& L, int R, float alpha2, const int32_t* A, const int32_t* cnt,
+                const int64_t* r_off, const int32_t* r_ids, const int32_t* parent0,
+                int64_t* f_off, int32_t** f_ids, int64_t* f_nnz, int64_t* scan_tmp,
+                unsigned long long* ctr, cudaStream_t s);
+
+// Batched occlusion prune of explicit candidate lists.
+int prune_lists(const VecLayout& L, const int32_t* owner, const int64_t* l_off,
+                const int32_t* l_ids, int64_t nlists, float alpha2, int R, int32_t* out_ids,
+                int32_t* out_cnt, unsigned long long* ctr, cudaStream_t s);
+
+// Dense-block top-k (canonical float32 distances of every pair of a block).
+int dense_block(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs, int k,
+                int32_t* out_ids, float* out_dist, cudaStream_t s);
+
+}  // namespace fg

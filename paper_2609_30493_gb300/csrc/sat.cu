@@ -1,0 +1,309 @@
+// Spatial-approximation forest on the GPU (the scaffold of Section 1 and
+// Section 3, after Navarro 2002), built level by level for all T trees at
+// once.
+//
+// A node a holding the point set P picks its children by the sorted greedy
+// scan: in (delta(x,a), id) order, x joins iff delta(x,a) < delta(x,b) for
+// every child b already chosen.  Here the scan is run without a sort, as a
+// sequence of minimum selections: the next child is the smallest key among
+// the points no child has rejected yet (every smaller key is a child or
+// rejected, so this is exactly the point the scan would accept next), and the
+// new child then rejects every remaining point y with
+// delta(y,b) <= delta(y,a).  The same pass keeps, for every point, its
+// closest child by (delta, id), which is the assignment of the non-children.
+// One CTA owns one node; the points of all nodes of a level are grouped by a
+// counting sort keyed on (tree, node).
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace fg {
+
+struct SatSegArgs {
+  const char* X;
+  int64_t ld_bytes;
+  int32_t d;
+  int32_t nchunks;
+  int64_t n;
+  const int32_t* item_pt;
+  const int64_t* seg_start;
+  const int32_t* seg_len;
+  const int32_t* seg_node;
+  const int32_t* seg_tree;
+  float* kd;
+  uint64_t* best;
+  uint8_t* flag;  // 0 candidate, 1 rejected, 2 child
+  int32_t* node_of;
+  int32_t* parent;
+  unsigned long long* ctr;
+};
+
+template <int NW>
+__device__ __forceinline__ void block_argmin(uint64_t& key, int& idx, uint64_t (*rk)[NW],
+                                             int (*ri)[NW], int parity) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    uint64_t ok = __shfl_xor_sync(FULL, key, off);
+    int oi = __shfl_xor_sync(FULL, idx, off);
+    if (ok < key) {
+      key = ok;
+      idx = oi;
+    }
+  }
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    rk[parity][warp] = key;
+    ri[parity][warp] = idx;
+  }
+  __syncthreads();
+  key = PAD;
+  idx = -1;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    uint64_t kk = rk[parity][w];
+    if (kk < key) {
+      key = kk;
+      idx = ri[parity][w];
+    }
+  }
+}
+
+template <int METRIC, int G, int K, int NW>
+__global__ void __launch_bounds__(NW * 32) sat_segment_kernel(const SatSegArgs a) {
+  constexpr int GPW = 32 / G;
+  constexpr int U = Unroll<G, K>::value;
+  constexpr int STEP = GPW * U;
+  __shared__ uint64_t rk[2][NW];
+  __shared__ int ri[2][NW];
+  const int s = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane / G, gl = lane % G;
+  const int64_t start = a.seg_start[s];
+  const int m = a.seg_len[s];
+  const int32_t anode = a.seg_node[s];
+  const int64_t tbase = (int64_t)a.seg_tree[s] * a.n;
+
+  uint4 cv[K];
+  load_chunks<METRIC, G, K>(a.X + (int64_t)anode * a.ld_bytes, a.nchunks, gl, cv);
+  uint64_t bk = PAD;
+  int bi = -1;
+  for (int base = warp * STEP; base < m; base += NW * STEP) {
+    uint4 v[U][K];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int idx = base + u * GPW + g;
+      if (idx < m) {
+        load_chunks<METRIC, G, K>(a.X + (int64_t)a.item_pt[start + idx] * a.ld_bytes, a.nchunks,
+                                  gl, v[u]);
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) v[u][kk] = make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      float dd = group_reduce<METRIC, G>(partial<METRIC, G, K>(cv, v[u], a.d, gl));
+      int idx = base + u * GPW + g;
+      if (idx < m && gl == 0) {
+        a.kd[start + idx] = dd;
+        a.best[start + idx] = PAD;
+        a.flag[start + idx] = 0;
+        uint64_t key = make_key(dd, a.item_pt[start + idx]);
+        if (key < bk) {
+          bk = key;
+          bi = idx;
+        }
+      }
+    }
+  }
+  int parity = 0;
+  block_argmin<NW>(bk, bi, rk, ri, parity);
+  long long k = 0;
+  while (bk != PAD) {
+    const int32_t bpt = key_id(bk);
+    if (threadIdx.x == 0) {
+      a.flag[start + bi] = 2;
+      a.parent[tbase + bpt] = anode;
+    }
+    ++k;
+    load_chunks<METRIC, G, K>(a.X + (int64_t)bpt * a.ld_bytes, a.nchunks, gl, cv);
+    __syncthreads();
+    bk = PAD;
+    bi = -1;
+    for (int base = warp * STEP; base < m; base += NW * STEP) {
+      uint4 v[U][K];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        int idx = base + u * GPW + g;
+        if (idx < m) {
+          load_chunks<METRIC, G, K>(a.X + (int64_t)a.item_pt[start + idx] * a.ld_bytes,
+                                    a.nchunks, gl, v[u]);
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < K; ++kk) v[u][kk] = make_uint4(0u, 0u, 0u, 0u);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        float dd = group_reduce<METRIC, G>(partial<METRIC, G, K>(cv, v[u], a.d, gl));
+        int idx = base + u * GPW + g;
+        if (idx < m && gl == 0) {
+          const int64_t it = start + idx;
+          const uint8_t f = a.flag[it];
+          if (f != 2) {
+            uint64_t ck = make_key(dd, bpt);
+            if (ck < a.best[it]) a.best[it] = ck;
+            if (f == 0) {
+              const float kdv = a.kd[it];
+              if (dd <= kdv) {
+                a.flag[it] = 1;
+              } else {
+                uint64_t key = make_key(kdv, a.item_pt[it]);
+                if (key < bk) {
+                  bk = key;
+                  bi = idx;
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+    parity ^= 1;
+    block_argmin<NW>(bk, bi, rk, ri, parity);
+  }
+  for (int i = threadIdx.x; i < m; i += NW * 32) {
+    const int64_t it = start + i;
+    const int32_t pt = a.item_pt[it];
+    a.node_of[tbase + pt] = a.flag[it] == 2 ? -1 : key_id(a.best[it]);
+  }
+  if (threadIdx.x == 0) {
+    const long long mm = m;
+    atomicAdd(a.ctr, (unsigned long long)(mm + k * (k - 1) / 2 + (mm - k) * k));
+  }
+}
+
+using SatKernelFn = void (*)(const SatSegArgs);
+constexpr int SAT_NW = 8;
+
+static SatKernelFn sat_kernel_for(int metric, int G, int K) {
+#define SATX(M, GG, KK) \
+  if (metric == M && G == GG && K == KK) return sat_segment_kernel<M, GG, KK, SAT_NW>;
+#define SATF(M) SATX(M, 4, 1) SATX(M, 8, 1) SATX(M, 16, 1) SATX(M, 32, 1) SATX(M, 32, 2) \
+  SATX(M, 32, 4) SATX(M, 32, 8)
+  SATF(0)
+  SATF(1)
+  SATX(2, 4, 1) SATX(2, 8, 1) SATX(2, 16, 1)
+#undef SATF
+#undef SATX
+  return nullptr;
+}
+
+__global__ void sat_init_kernel(int64_t n, int T, const int32_t* roots, int32_t* node_of,
+                                int32_t* parent) {
+  const int64_t tot = (int64_t)T * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(i / n);
+    const int32_t x = (int32_t)(i - (int64_t)t * n);
+    node_of[i] = (x == roots[t]) ? -1 : roots[t];
+    parent[i] = -1;
+  }
+}
+
+__global__ void sat_count_kernel(int64_t n, int64_t tot, const int32_t* node_of, uint32_t* kcnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = node_of[i];
+    if (a >= 0) {
+      const int64_t t = i / n;
+      atomicAdd(&kcnt[t * n + a], 1u);
+    }
+  }
+}
+
+__global__ void sat_segments_kernel(int64_t n, int64_t tot, const uint32_t* kcnt,
+                                    const int64_t* kstart, int64_t* seg_start, int32_t* seg_len,
+                                    int32_t* seg_node, int32_t* seg_tree, uint32_t* nseg) {
+  for (int64_t key = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; key < tot;
+       key += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = kcnt[key];
+    if (c) {
+      const uint32_t s = atomicAdd(nseg, 1u);
+      seg_start[s] = kstart[key];
+      seg_len[s] = (int32_t)c;
+      seg_node[s] = (int32_t)(key % n);
+      seg_tree[s] = (int32_t)(key / n);
+    }
+  }
+}
+
+__global__ void sat_scatter_kernel(int64_t n, int64_t tot, const int32_t* node_of,
+                                   uint32_t* kcnt, const int64_t* kstart, int32_t* item_pt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = node_of[i];
+    if (a >= 0) {
+      const int64_t t = i / n;
+      const int64_t key = t * n + a;
+      const uint32_t r = atomicSub(&kcnt[key], 1u) - 1u;
+      item_pt[kstart[key] + r] = (int32_t)(i - t * n);
+    }
+  }
+}
+
+static int grid_for(int64_t tot) {
+  int64_t g = (tot + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
+}
+
+int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* parents,
+               SatScratch& S, unsigned long long* ctr_sat, cudaStream_t s) {
+  SatKernelFn kern = sat_kernel_for(L.metric, L.G, L.K);
+  if (!kern) {
+    set_error(1, "no SAT kernel for this metric and dimension");
+    return 1;
+  }
+  const int64_t n = L.n, tot = (int64_t)T * n;
+  sat_init_kernel<<<grid_for(tot), 256, 0, s>>>(n, T, roots_d, S.node_of, parents);
+  FG_CUDA(cudaGetLastError());
+  SatSegArgs a;
+  a.X = L.X;
+  a.ld_bytes = L.ld_bytes;
+  a.d = L.d;
+  a.nchunks = L.nchunks;
+  a.n = n;
+  a.item_pt = S.item_pt;
+  a.seg_start = S.seg_start;
+  a.seg_len = S.seg_len;
+  a.seg_node = S.seg_node;
+  a.seg_tree = S.seg_tree;
+  a.kd = S.kd;
+  a.best = S.best;
+  a.flag = S.flag;
+  a.node_of = S.node_of;
+  a.parent = parents;
+  a.ctr = ctr_sat;
+  for (int64_t level = 0; level <= n; ++level) {
+    FG_CUDA(cudaMemsetAsync(S.nseg, 0, sizeof(uint32_t), s));
+    sat_count_kernel<<<grid_for(tot), 256, 0, s>>>(n, tot, S.node_of, S.kcnt);
+    int rc = scan_u32(S.kcnt, S.kstart, tot, S.scan_tmp, s);
+    if (rc) return rc;
+    sat_segments_kernel<<<grid_for(tot), 256, 0, s>>>(n, tot, S.kcnt, S.kstart, S.seg_start,
+                                                      S.seg_len, S.seg_node, S.seg_tree, S.nseg);
+    sat_scatter_kernel<<<grid_for(tot), 256, 0, s>>>(n, tot, S.node_of, S.kcnt, S.kstart,
+                                                     S.item_pt);
+    FG_CUDA(cudaGetLastError());
+    uint32_t nseg = 0;
+    FG_CUDA(cudaMemcpyAsync(&nseg, S.nseg, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    FG_CUDA(cudaStreamSynchronize(s));
+    if (nseg == 0) return 0;
+    kern<<<nseg, SAT_NW * 32, 0, s>>>(a);
+    FG_CUDA(cudaGetLastError());
+  }
+  set_error(1, "SAT construction did not terminate");
+  return 1;
+}
+
+}  // namespace fg

@@ -1,0 +1,182 @@
+"""Parity of the CUDA library (through its C ABI) with the CPU oracle.
+
+Integer and index results (tree parents, scaffold, harvested rows, final
+graph, search ids, dense-block ids) must match bit for bit, float distances
+must match bit for bit too (both sides use the same fixed float32 order),
+and the algorithmic counters must be equal.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2609_30493_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_30493_gb300 import build, fgraft
+    build.build()
+    fgraft.load()
+    return fgraft
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _np(t):
+    return t.cpu().numpy()
+
+
+def _build_both(fg, ps, T, R, ef, B, alpha=1.2, seed=0, use_graph=False, hash_log2=0):
+    X = _dev(ps.X)
+    p = fg.Params(T=T, R=R, ef_h=ef, B=B, alpha=alpha, seed=seed, metric=ps.metric)
+    ix, c0 = fg.fgraft_build_scaffold(X, ps.d, p, counters=True)
+    if hash_log2:
+        fg.fgraft_index_tune(ix, hash_log2=hash_log2)
+    ctr = fg.fgraft_harvest_all(ix, use_graph=use_graph, counters=True)
+    off, ids = fg.fgraft_prune(ix)
+    st = fg.fgraft_index_copy(ix)
+    D = oracle.Data(ps.X, ps.d, ps.metric)
+    ref = oracle.build_graph(D, T, R, ef, B, alpha, seed)
+    return ix, ctr, st, (off, ids), D, ref
+
+
+def _compare(ctr, st, fin, ref, check_final=True):
+    assert np.array_equal(_np(st["roots"]), ref["roots"])
+    assert np.array_equal(_np(st["parents"]), ref["parents"])
+    assert np.array_equal(_np(st["s_off"]), ref["s_off"])
+    assert np.array_equal(_np(st["s_ids"]), ref["s_ids"])
+    cnt = _np(st["counts"])
+    rows = _np(st["rows"])
+    bad = np.flatnonzero((cnt != ref["cnt"]) | (rows != ref["A"]).any(1))
+    assert bad.size == 0, f"{bad.size} rows differ, first {bad[:5]}"
+    rc = ref["counters"]
+    for k in ("sat_evals", "harvest_evals", "prune_evals", "expansions"):
+        assert ctr[k] == rc[k], (k, ctr[k], rc[k])
+    if check_final:
+        off, ids = fin
+        assert np.array_equal(_np(off), ref["f_off"])
+        assert np.array_equal(_np(ids), ref["f_ids"])
+        assert ctr["final_prune_evals"] == rc["final_prune_evals"]
+
+
+@pytest.mark.parametrize("B", [1, 4])
+def test_tiny_gauss_parity(fg, B):
+    ps = synth.gaussian_mixture(2000, 16, 8, seed=0)
+    ix, ctr, st, fin, D, ref = _build_both(fg, ps, T=4, R=16, ef=32, B=B)
+    _compare(ctr, st, fin, ref)
+    Q = synth.queries(ps, 200, 1)
+    for ef_s in (10, 32, 64):
+        gi, gd, ge = fg.fgraft_search(ix, _dev(Q), 10, ef_s)
+        oi, od, oe = oracle.search(D, ref["f_off"], ref["f_ids"], ref["roots"], Q, 10, ef_s)
+        assert np.array_equal(_np(gi), oi)
+        assert np.array_equal(_np(gd), od)
+        assert np.array_equal(_np(ge).astype(np.uint32), oe)
+
+
+def test_graph_capture_same_graph(fg):
+    ps = synth.gaussian_mixture(2000, 16, 8, seed=0)
+    ix, ctr, st, fin, D, ref = _build_both(fg, ps, T=4, R=16, ef=32, B=4, use_graph=True)
+    _compare(ctr, st, fin, ref)
+
+
+@pytest.mark.parametrize("case", [
+    dict(kind="vmf", n=3000, d=100, k=16, T=8, R=32, ef=64, B=8),
+    dict(kind="gauss", n=1500, d=960, k=8, T=4, R=16, ef=32, B=2),
+    dict(kind="u8", n=2500, d=128, k=8, T=8, R=32, ef=64, B=8),
+    dict(kind="gauss", n=1200, d=3, k=4, T=3, R=8, ef=16, B=3),
+    dict(kind="gauss", n=1300, d=129, k=4, T=4, R=12, ef=40, B=2),
+    dict(kind="vmf", n=1700, d=300, k=8, T=5, R=24, ef=100, B=5),
+    dict(kind="u8", n=900, d=20, k=4, T=2, R=10, ef=20, B=3),
+])
+def test_shapes_parity(fg, case):
+    if case["kind"] == "vmf":
+        ps = synth.vmf_like(case["n"], case["d"], case["k"], seed=3)
+    elif case["kind"] == "u8":
+        ps = synth.uint8_mixture(case["n"], case["d"], case["k"], seed=3)
+    else:
+        ps = synth.gaussian_mixture(case["n"], case["d"], case["k"], seed=3)
+    ix, ctr, st, fin, D, ref = _build_both(fg, ps, case["T"], case["R"], case["ef"], case["B"])
+    _compare(ctr, st, fin, ref)
+
+
+def test_overflow_rerun_is_exact(fg):
+    # a 128-slot visited set overflows for most queries; the global-memory
+    # re-run must give the same graph and counters
+    ps = synth.gaussian_mixture(2000, 16, 8, seed=0)
+    ix, ctr, st, fin, D, ref = _build_both(fg, ps, T=4, R=16, ef=32, B=4, hash_log2=7)
+    assert ctr["reruns"] > 0
+    _compare(ctr, st, fin, ref)
+
+
+def test_edge_cases(fg):
+    # few points, duplicates (ties everywhere), R = 1, ef = 1, T = n
+    rng = np.random.default_rng(0)
+    base = rng.integers(0, 3, size=(40, 4)).astype(np.float32)
+    X = np.concatenate([base, base[:20], base[:5]])
+    ps = synth.PointSet(X, 4, 0, np.zeros(len(X), np.int32), np.zeros((1, 4)),
+                        dict(kind="gauss", sigma=1.0))
+    for T, R, ef, B in [(3, 1, 1, 2), (4, 8, 16, 3), (2, 4, 128, 1)]:
+        ix, ctr, st, fin, D, ref = _build_both(fg, ps, T, R, ef, B)
+        _compare(ctr, st, fin, ref)
+    tiny = synth.gaussian_mixture(5, 8, 1, seed=1)
+    ix, ctr, st, fin, D, ref = _build_both(fg, tiny, T=5, R=3, ef=4, B=2)
+    _compare(ctr, st, fin, ref)
+
+
+def test_prune_lists_parity(fg):
+    ps = synth.vmf_like(3000, 100, 8, seed=4)
+    D = oracle.Data(ps.X, 100, 1)
+    rng = np.random.default_rng(2)
+    nl, R = 300, 16
+    owners = rng.integers(0, 3000, size=nl).astype(np.int32)
+    lens = rng.integers(0, 200, size=nl)
+    lens[:3] = [0, 1, 1500]
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    cand = rng.integers(0, 3000, size=int(off[-1])).astype(np.int32)
+    cand[off[5]] = owners[5]  # the owner itself appears in a list
+    out, cnt = fg.fgraft_prune_lists(_dev(ps.X), 100, 1, _dev(owners), _dev(off), _dev(cand),
+                                     1.2, R)
+    out, cnt = _np(out), _np(cnt)
+    for i in range(nl):
+        kept, _ = oracle.prune_list(D, int(owners[i]), cand[off[i]:off[i + 1]], 1.2, R)
+        assert cnt[i] == len(kept)
+        assert out[i, :cnt[i]].tolist() == kept.tolist()
+        assert (out[i, cnt[i]:] == -1).all()
+
+
+@pytest.mark.parametrize("metric,d,k", [(1, 100, 32), (0, 960, 64), (0, 16, 10)])
+def test_dense_block_parity(fg, metric, d, k):
+    ps = synth.vmf_like(4000, d, 4, seed=5) if metric == 1 else \
+        synth.gaussian_mixture(4000, d, 4, seed=5)
+    blocks = synth.intra_cluster_blocks(ps.labels, 3, 1000, seed=1)
+    blocks[2, -7:] = -1
+    gi, gd = fg.fgraft_dense_block_dist(_dev(ps.X), d, metric, _dev(blocks), k)
+    D = oracle.Data(ps.X, d, metric)
+    oi, od, _ = oracle.dense_block(D, blocks, k)
+    assert np.array_equal(_np(gi), oi)
+    assert np.array_equal(_np(gd), od)
+
+
+def test_api_rejects_bad_arguments(fg):
+    ps = synth.gaussian_mixture(100, 16, 2, seed=0)
+    X = _dev(ps.X)
+    with pytest.raises(fg.FgraftError, match="EINVAL"):
+        fg.fgraft_build_scaffold(X, 16, fg.Params(T=0, R=8, ef_h=8, B=1, alpha=1.2))
+    with pytest.raises(fg.FgraftError, match="EINVAL"):
+        fg.fgraft_build_scaffold(X, 16, fg.Params(T=2, R=8, ef_h=200, B=1, alpha=1.2))
+    with pytest.raises(fg.FgraftError, match="EINVAL"):
+        fg.fgraft_build_scaffold(X, 17, fg.Params(T=2, R=8, ef_h=8, B=1, alpha=-1.0))
+    ix = fg.fgraft_build_scaffold(X, 16, fg.Params(T=2, R=8, ef_h=8, B=3, alpha=1.2))
+    with pytest.raises(fg.FgraftError, match="EINVAL"):
+        fg.fgraft_harvest_block(ix, 2)  # out of order
+    with pytest.raises(fg.FgraftError, match="EINVAL"):
+        fg.fgraft_prune(ix)  # blocks missing
+    with pytest.raises(fg.FgraftError, match="EINVAL"):
+        fg.fgraft_search(ix, X[:4], 10, 16)  # no final graph yet
