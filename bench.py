@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""FGraft build benchmark on one GB300 (or N replicas under torchrun).
+
+One step is one pass of the whole hot path over the in-cache workload
+(n = 100,000 unit vectors, d = 100, angular distance, 64 vMF-like clusters):
+SAT scaffold (T = 8), the B = 8 harvest blocks (one CUDA graph), the final
+graph, a 10,000-query search (ef_s = 64, top-10) and 64 dense 1024-point
+intra-cluster blocks (top-32 per row).  The headline value is points built
+per second over the whole step; L2 is flushed (a 256 MiB write) before every
+timed step, whose duration is taken with CUDA events on the launching stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle (the
+plain C restatement of the method) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FGraft build pts/s & dist-evals/s vs dense-block ceiling, 1 GB300; recall@10"
+WORKLOAD = "incache-angular-n100k-d100"
+SPEC = dict(n=100_000, d=100, k=64, kappa=20.0, T=8, B=8, R=32, ef_h=64, alpha=1.2, nq=10_000,
+            ef_s=64, topk=10, dense_blocks=64, block_size=1024, dense_k=32, seed=0)
+CPU_SAMPLE_N = 20_000
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="override n (smaller runs)")
+    return ap.parse_args()
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def make_inputs(spec):
+    from paper_2609_30493_gb300 import synth
+    ps = synth.vmf_like(spec["n"], spec["d"], spec["k"], spec["seed"], spec["kappa"])
+    Q = synth.queries(ps, spec["nq"], spec["seed"] + 1)
+    blocks = synth.intra_cluster_blocks(ps.labels, spec["dense_blocks"], spec["block_size"],
+                                        spec["seed"] + 2)
+    return ps, Q, blocks
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_file: str):
+    """DRAM bytes per harvest launch from the committed ncu summary, if it was
+    taken on the current kernel source (hash match), else None."""
+    prof = os.path.join(ROOT, "profiles", "harvest_beam_incache_n100k_d100.md")
+    if not os.path.exists(prof):
+        return None
+    txt = open(prof).read()
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
+    if not m or not h:
+        return None
+    cur = hashlib.sha256(open(kernel_file, "rb").read()).hexdigest()
+    return float(m.group(1)) if h.group(1) == cur else None
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, idx: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={idx}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def recall_at_10(X, Q, ids):
+    """Recall of ids (nq x 10) against a float32 brute force on the device
+    (measurement only)."""
+    import torch
+    Xt = torch.from_numpy(X).cuda()
+    hits = 0
+    for s in range(0, Q.shape[0], 1024):
+        q = torch.from_numpy(Q[s:s + 1024]).cuda()
+        dots = q @ Xt.T
+        gt = torch.topk(dots, 10, dim=1).indices.cpu().numpy()
+        got = ids[s:s + 1024]
+        hits += sum(len(set(a.tolist()) & set(b.tolist())) for a, b in zip(gt, got))
+    return hits / (Q.shape[0] * 10)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2609_30493_gb300 import build as fgbuild
+    from paper_2609_30493_gb300 import fgraft as fg
+
+    rank, world, local = env_rank()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    fgbuild.build()
+    fg.load()
+    spec = dict(SPEC)
+    if args.n:
+        spec["n"] = args.n
+    ps, Q, blocks = make_inputs(spec)
+    d = spec["d"]
+    X_d = torch.from_numpy(ps.X).cuda()
+    Q_d = torch.from_numpy(Q).cuda()
+    B_d = torch.from_numpy(blocks).cuda()
+    params = fg.Params(T=spec["T"], R=spec["R"], ef_h=spec["ef_h"], B=spec["B"],
+                       alpha=spec["alpha"], seed=spec["seed"], metric=fg.ANGULAR_F32)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(X_t, Q_t, B_t, profile=False):
+        ix = fg.fgraft_build_scaffold(X_t, d, params)
+        if profile:
+            fg.fgraft_index_profile(ix, True)
+        fg.fgraft_harvest_all(ix, use_graph=True)
+        ids, dist_, ev = fg.fgraft_search(ix, Q_t, spec["topk"], spec["ef_s"])
+        di, dd = fg.fgraft_dense_block_dist(X_t, d, fg.ANGULAR_F32, B_t, spec["dense_k"])
+        return ix, ids, di
+
+    for _ in range(args.warmup):
+        step(X_d, Q_d, B_d)
+    torch.cuda.synchronize()
+
+    # ---- timed region: inputs resident in HBM ----
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    launches0 = fg.fgraft_kernel_launches()
+    total_ms, harvest_ms, harvest_launches = 0.0, 0.0, 0
+    ctr_sum = {}
+    last = None
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ix, ids, di = step(X_d, Q_d, B_d, profile=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        hm, hl = fg.fgraft_index_harvest_ms(ix)
+        harvest_ms += hm
+        harvest_launches += hl
+        c = fg.fgraft_index_counters(ix)
+        for k_, v_ in c.items():
+            ctr_sum[k_] = ctr_sum.get(k_, 0) + v_
+        last = (ix, ids, di)
+    launches = fg.fgraft_kernel_launches() - launches0
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t.item()) / args.steps
+    n = spec["n"]
+    value = world * n / (ms_per_step / 1e3)
+
+    # ---- breakdown (one untimed profiled pass) ----
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    flush.fill_(1.0)
+    evs[0].record(stream)
+    ix = fg.fgraft_build_scaffold(X_d, d, params)
+    evs[1].record(stream)
+    for b in range(spec["B"]):
+        fg.fgraft_harvest_block(ix, b)
+    evs[2].record(stream)
+    fg.fgraft_prune(ix)
+    evs[3].record(stream)
+    ids, dist_, ev = fg.fgraft_search(ix, Q_d, spec["topk"], spec["ef_s"])
+    evs[4].record(stream)
+    di, dd = fg.fgraft_dense_block_dist(X_d, d, fg.ANGULAR_F32, B_d, spec["dense_k"])
+    evs[5].record(stream)
+    torch.cuda.synchronize()
+    names = ["scaffold", "harvest_blocks_no_graph", "final_prune", "search", "dense_blocks"]
+    breakdown = {nm: round(evs[i].elapsed_time(evs[i + 1]), 3) for i, nm in enumerate(names)}
+    search_evals = float(ev.double().sum().item())
+
+    # ---- end to end through the public API, host buffers ----
+    Xh = torch.from_numpy(ps.X).pin_memory()
+    Qh = torch.from_numpy(Q).pin_memory()
+    Bh = torch.from_numpy(blocks).pin_memory()
+    h2d = Xh.numel() * 4 + Qh.numel() * 4 + Bh.numel() * 4
+    e2e_ms, d2h = 0.0, 0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Xd2 = Xh.to("cuda", non_blocking=True)
+        Qd2 = Qh.to("cuda", non_blocking=True)
+        Bd2 = Bh.to("cuda", non_blocking=True)
+        ix2 = fg.fgraft_build_scaffold(Xd2, d, params)
+        fg.fgraft_harvest_all(ix2, use_graph=True)
+        off2, gids2 = fg.fgraft_prune(ix2)
+        ids2, dist2, ev2 = fg.fgraft_search(ix2, Qd2, spec["topk"], spec["ef_s"])
+        di2, dd2 = fg.fgraft_dense_block_dist(Xd2, d, fg.ANGULAR_F32, Bd2, spec["dense_k"])
+        outs = [off2.cpu(), gids2.cpu(), ids2.cpu(), dist2.cpu(), di2.cpu(), dd2.cpu()]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+        d2h = sum(o.numel() * o.element_size() for o in outs)
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * n / (float(te.item()) / args.steps / 1e3)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    rec = recall_at_10(ps.X[:, :d], Q[:, :d], last[1].cpu().numpy())
+    hbm, peak_kind = peaks()
+    line_bytes = 32 * ((4 * d + 31) // 32)
+    evals = ctr_sum.get("harvest_evals", 0)
+    scanned = ctr_sum.get("ids_scanned", 0)
+    alg_bytes = evals * line_bytes + scanned * 4
+    achieved = alg_bytes / (harvest_ms / 1e3) / 1e9 if harvest_ms > 0 else 0.0
+    traffic = ncu_traffic(os.path.join(ROOT, "paper_2609_30493_gb300", "csrc", "beam.cuh"))
+    dense_pairs = spec["dense_blocks"] * spec["block_size"] * (spec["block_size"] - 1)
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "pts/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "d": d, "metric_kind": "angular",
+                   "clusters": spec["k"], "T": spec["T"], "B": spec["B"], "R": spec["R"],
+                   "ef_h": spec["ef_h"], "alpha": spec["alpha"], "nq": spec["nq"],
+                   "ef_s": spec["ef_s"], "dense_blocks": spec["dense_blocks"],
+                   "block_size": spec["block_size"], "dense_k": spec["dense_k"],
+                   "parallelism": f"replicas{world}",
+                   "l2": "flushed before each timed step (256 MiB write); data 40 MB is L2-resident within a step"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+                     "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                     "traffic": traffic, "kernel": "beam_kernel (harvest)",
+                     "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg_bytes / max(harvest_launches, 1),
+                     "launch_ms": harvest_ms / max(harvest_launches, 1)},
+        "harvest_evals_per_s": round(evals / (harvest_ms / 1e3), 1) if harvest_ms else None,
+        "build_evals_per_s": round((ctr_sum.get("harvest_evals", 0) + ctr_sum.get("prune_evals", 0)
+                                    + ctr_sum.get("sat_evals", 0)
+                                    + ctr_sum.get("final_prune_evals", 0))
+                                   / (ms_per_step * args.steps / 1e3), 1),
+        "counters_per_build": {k_: v_ // args.steps for k_, v_ in ctr_sum.items()},
+        "recall_at_10": round(rec, 4),
+        "search_evals_per_query": round(search_evals / spec["nq"], 1),
+        "dense_pairs_per_s": round(dense_pairs / (breakdown["dense_blocks"] / 1e3), 1),
+        "breakdown_ms": breakdown,
+        "e2e": {"value": round(e2e_value, 1), "unit": "pts/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(ps, spec)
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(ps, spec, sample_n=CPU_SAMPLE_N, seed=7):
+    """The oracle, as it stands, on a random subset of the workload's points."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(ps.n, size=min(sample_n, ps.n), replace=False))
+    Xs = np.ascontiguousarray(ps.X[sel])
+    D = oracle.Data(Xs, spec["d"], 1)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.build_graph(D, spec["T"], spec["R"], spec["ef_h"], spec["B"], spec["alpha"],
+                       spec["seed"], nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": round(len(sel) / dt, 1), "unit": "pts/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle FGraft build (SAT forest, scaffold, {spec['B']} blocks, final graph) "
+                      f"of a seeded {len(sel)}-point subset of the workload, same T/R/ef_h/B/alpha",
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    rank, world, local = env_rank()
+    if rank != 0:
+        return
+    spec = dict(SPEC)
+    if args.n:
+        spec["n"] = args.n
+    ps, Q, blocks = make_inputs(spec)
+    import oracle
+    oracle.build()
+    sample_n = 10_000
+    for _ in range(args.warmup):
+        cpu_baseline(ps, spec, sample_n=2_000)
+    secs = 0.0
+    for i in range(args.steps):
+        r = cpu_baseline(ps, spec, sample_n=sample_n, seed=11 + i)
+        secs += r["seconds"]
+    value = args.steps * sample_n / secs
+    cores = os.cpu_count() or 1
+    sample = (f"oracle FGraft build of a seeded {sample_n}-point subset of the workload per step "
+              f"(SAT forest, scaffold, {spec['B']} blocks, final graph), same T/R/ef_h/B/alpha")
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "pts/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(secs / args.steps * 1e3, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": spec["n"], "d": spec["d"], "T": spec["T"],
+                      "B": spec["B"], "R": spec["R"], "ef_h": spec["ef_h"],
+                      "alpha": spec["alpha"], "parallelism": "cpu-oracle"},
+           "cpu_baseline": {"value": round(value, 1), "unit": "pts/s", "cores": cores,
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 1), "unit": "pts/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

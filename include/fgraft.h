@@ -69,7 +69,8 @@ typedef struct {
   int32_t metric;  /* fgraft_metric */
 } fgraft_params;
 
-/* Distance-evaluation counters (Section 2: "fg counts every evaluation").
+/* Distance-evaluation counters (Section 2: work is the count of distance
+ * evaluations, each one counted).
  * Defined by the algorithm, so a correct build reports the same numbers at
  * every launch configuration:
  *  sat_evals          per SAT node with m points below it and k children:
@@ -99,7 +100,8 @@ typedef struct {
 typedef struct fgraft_index fgraft_index; /* opaque */
 
 /* Scaffold S_0 (Section 1: T spatial-approximation trees [Navarro 2002];
- * Section 3: "the union of T SAT trees' edges, symmetrized").
+ * Section 3: S_0 joins the edges of the T trees and adds every reverse
+ * edge).
  * Root t is splitmix64(seed ^ (0x9E3779B97F4A7C15 * (t+1)) + j) mod n for
  * the smallest j >= 0 giving a root distinct from roots 0..t-1 (keyed
  * randomness, Proposition 1).  A SAT node a holding points P sorts P by
@@ -131,8 +133,8 @@ fgraft_status fgraft_harvest_block(fgraft_index* ix, int32_t b, fgraft_stream st
 fgraft_status fgraft_harvest_all(fgraft_index* ix, int32_t use_graph, fgraft_stream stream,
                                  fgraft_counters* counters);
 
-/* Final graph (Section 3: "the harvested rows, symmetrized and re-pruned,
- * plus the tree-0 spine").  C(u) = A[u] U {p : u in A[p]}; when |C(u)| > R
+/* Final graph (Section 3: rows made symmetric, pruned again, joined with the
+ * parent/child edges of tree 0).  C(u) = A[u] U {p : u in A[p]}; when |C(u)| > R
  * the row is the occlusion prune of C(u) to R, otherwise C(u); then the
  * tree-0 parent and children of u are added and the row is sorted by
  * (delta(u,v), id).  The index keeps the result for fgraft_search.
@@ -166,7 +168,7 @@ fgraft_status fgraft_search(fgraft_index* ix, const void* Q, int64_t nq, int64_t
                             int32_t ef_s, int32_t* out_ids, float* out_dist, uint32_t* out_evals,
                             fgraft_stream stream);
 
-/* Dense-block ceiling (Section 4.3: the pair set fixed in advance that a
+/* Dense-block ceiling (Section 5.3: the pair set fixed in advance that a
  * blocked kernel evaluates at arithmetic rate).  block_ids holds nb blocks of
  * bs ids (-1 = padding).  For every valid member i of a block and every other
  * valid member j, delta(x_i, x_j) is taken, and out_ids/out_dist
@@ -198,9 +200,31 @@ fgraft_status fgraft_index_counters(fgraft_index* ix, fgraft_stream stream,
                                     fgraft_counters* counters);
 
 /* Harvest launch configuration (measurement and tuning; results do not
- * depend on it).  hash_log2: shared-memory visited slots per warp (2^k,
- * 7 <= k <= 14); warps_per_cta: 1..4; 0 leaves a value unchanged. */
+ * depend on it).  The visited set of a search is an n-bit shared-memory
+ * bitmap when that is no larger than the hash, else a bucketed hash of
+ * 2^hash_log2 slots; giving hash_log2 (7 <= k <= 14) selects the hash of
+ * that size.  warps_per_cta: 1..4.  0 leaves a value unchanged. */
 fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t warps_per_cta);
+
+/* SAT launch configuration for later fgraft_build_scaffold calls in this
+ * process (tuning; results do not depend on it): tree nodes holding at least
+ * big_node_min points are split across many CTAs, one launch per child
+ * selection; smaller nodes get one CTA each.  Default 16384; >= 2. */
+fgraft_status fgraft_tune_sat(int32_t big_node_min);
+
+/* Measurement hooks (results never depend on them).
+ * fgraft_index_profile: with enable != 0, every later harvest of a block
+ * records a CUDA event pair around its harvest kernel on the launching
+ * stream (inside a captured graph too).
+ * fgraft_index_harvest_ms: synchronises `stream` and returns in *ms the sum
+ * of those kernel durations over the blocks harvested so far, and in
+ * *launches (optional) their number.
+ * fgraft_kernel_launches: kernels launched by the library in this process
+ * so far (a graph replay counts the kernels it holds). */
+fgraft_status fgraft_index_profile(fgraft_index* ix, int32_t enable);
+fgraft_status fgraft_index_harvest_ms(fgraft_index* ix, fgraft_stream stream, double* ms,
+                                      int32_t* launches);
+uint64_t fgraft_kernel_launches(void);
 
 void fgraft_index_destroy(fgraft_index* ix);
 

@@ -858,7 +858,7 @@ int fgo_bruteforce(const fgo_data* D, const void* Q, int64_t nq, int64_t ldq, in
 }
 
 /* ------------------------------------------------------------------------ *
- * Dense block (Section 4.3's fixed-in-advance pair set): for each block of
+ * Dense block (Section 5.3: a pair set fixed before evaluation): for each block of
  * bs ids (-1 = padding), every ordered pair i != j of valid members, the
  * canonical delta, and per row the k smallest (delta, id).  Rows of padding
  * and missing neighbours are filled with -1 / +inf.  use_f64 != 0 ranks by

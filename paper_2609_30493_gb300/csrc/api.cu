@@ -1,6 +1,7 @@
 // C ABI of libfgraft: argument checks, the index object, and the host-side
 // sequencing of the kernels (SAT levels, harvest blocks with their overflow
 // re-run and reverse-list update, final graph, search, dense blocks).
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -20,6 +21,11 @@ void set_error(int code, const std::string& msg) {
   g_err_code = code;
   g_err = msg;
 }
+
+static std::atomic<uint64_t> g_launches{0};
+void note_launch(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void set_launch_count(uint64_t v) { g_launches.store(v, std::memory_order_relaxed); }
 
 int cuda_fail(cudaError_t e, const char* what) {
   set_error(FGRAFT_ECUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
@@ -79,6 +85,9 @@ static void keyed_roots(uint64_t seed, int T, int64_t n, std::vector<int32_t>& r
 
 using namespace fg;
 
+// Nodes of at least this many points are built by the multi-CTA SAT path.
+static int32_t g_sat_big_min = 16384;
+
 #define FGS(call)                                                      \
   do {                                                                 \
     cudaError_t e_ = (call);                                           \
@@ -129,9 +138,13 @@ struct fgraft_index {
   unsigned long long* ctr = nullptr;
   int32_t blocks_done = 0;
   int32_t hash_log2 = 12;
+  bool bitmap_ok = true;
   int32_t wpc = 4;
   int32_t num_sms = 0;
   cudaGraphExec_t graph_exec = nullptr;
+  uint64_t graph_kernels = 0;
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_beg, ev_end;  // around the harvest kernel of each block
 };
 
 namespace {
@@ -178,15 +191,31 @@ int ceil_log2(int64_t v) {
   return k;
 }
 
+// Inside a stream capture a plain event record only marks a dependency; the
+// external flag makes it a timed event-record node of the graph.
+cudaError_t record_event(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  cudaError_t err = cudaStreamIsCapturing(s, &st);
+  if (err != cudaSuccess) return err;
+  if (st == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  return cudaEventRecord(e, s);
+}
+
 // Launch the beam over `nq` work items (shared-memory pass), then the
 // overflow list on global scratch.  `a` carries everything but the scratch.
-int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStream_t s) {
+int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStream_t s,
+                cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
   const int S = pool_slots(a.ef);
   BeamKernelFn kern = beam_kernel_for(ix->L.metric, ix->L.G, ix->L.K, S);
   if (!kern) return fail(FGRAFT_EINVAL, "no beam kernel for this metric and dimension");
   const int ecap = 1 << std::max(6, ceil_log2(2 * 32 * S));
   const int nslots = 1 << ix->hash_log2;
-  const int wbytes = (4 * nslots + 8 * ecap + ecap / 8 + 256 + 15) / 16 * 16;
+  // an n-bit bitmap is exact and never overflows; use it when it is no
+  // larger than the hash would be
+  const int64_t bm_bytes = ((ix->L.n + 127) / 128) * 16;
+  const bool bitmap = ix->bitmap_ok && bm_bytes <= 4ll * nslots;
+  const int vis_bytes = bitmap ? (int)bm_bytes : 4 * nslots;
+  const int wbytes = (vis_bytes + 8 * ecap + ecap / 8 + 256 + 15) / 16 * 16;
   const int smem = wbytes * ix->wpc;
   FG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int per_sm = 0;
@@ -199,21 +228,28 @@ int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStrea
   a.ovf_cap = (uint32_t)ix->ovf_cap;
   a.err_flag = ix->work + 3;
   a.hash_log2 = ix->hash_log2;
-  a.vis_cap = (int32_t)(0.8 * nslots) - 32;
+  a.bitmap = bitmap ? 1 : 0;
+  a.vis_bytes = vis_bytes;
+  a.vis_cap = bitmap ? INT32_MAX : (int32_t)(0.8 * nslots) - 32;
   a.ecap = ecap;
   a.wbytes = wbytes;
   a.global_scratch = 0;
   a.qlist = nullptr;
   a.qlist_len = nullptr;
   FG_CUDA(cudaMemsetAsync(ix->work, 0, 3 * sizeof(uint32_t), s));
+  if (e0) FG_CUDA(record_event(e0, s));
   kern<<<per_sm * ix->num_sms, ix->wpc * 32, smem, s>>>(a);
+  note_launch();
   FG_CUDA(cudaGetLastError());
+  if (e1) FG_CUDA(record_event(e1, s));
   // re-run of the overflowed items with per-warp global scratch
   a.global_scratch = 1;
   a.qlist = ix->ovf_list;
   a.qlist_len = ix->work + 2;
   a.work = ix->work + 1;
   a.hash_log2 = ix->g_hash_log2;
+  a.bitmap = 0;
+  a.vis_bytes = 4 << ix->g_hash_log2;
   a.vis_cap = (int32_t)(0.8 * (1 << ix->g_hash_log2)) - 32;
   a.ecap = ix->g_ecap;
   a.wbytes = 256;
@@ -221,6 +257,7 @@ int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStrea
   a.gscratch_per_warp = ix->gscratch_per_warp;
   a.counters = ctr;
   kern<<<ix->g_warps / 4, 128, 256 * 4, s>>>(a);
+  note_launch();
   FG_CUDA(cudaGetLastError());
   return 0;
 }
@@ -260,6 +297,8 @@ int dalloc(T** p, int64_t count) {
 void free_index(fgraft_index* ix) {
   if (!ix) return;
   if (ix->graph_exec) cudaGraphExecDestroy(ix->graph_exec);
+  for (cudaEvent_t e : ix->ev_beg) cudaEventDestroy(e);
+  for (cudaEvent_t e : ix->ev_end) cudaEventDestroy(e);
   void* ptrs[] = {ix->roots, ix->parents, ix->s_off, ix->s_ids, ix->A,   ix->cnt,
                   ix->r_off, ix->r_ids,   ix->rcnt,  ix->rcur,  ix->f_off, ix->f_ids,
                   ix->scan_tmp, ix->work, ix->ovf_list, ix->gscratch, ix->ctr};
@@ -294,7 +333,9 @@ int harvest_block_impl(fgraft_index* ix, int32_t b, cudaStream_t s) {
   a.alpha2 = ix->p.alpha * ix->p.alpha;
   a.A_out = ix->A;
   a.cnt_out = ix->cnt;
-  int rc = launch_beam(ix, a, ix->ctr + C_HARVEST, s);
+  const bool prof = ix->profile && (int)ix->ev_beg.size() > b;
+  int rc = launch_beam(ix, a, ix->ctr + C_HARVEST, s, prof ? ix->ev_beg[b] : nullptr,
+                       prof ? ix->ev_end[b] : nullptr);
   if (rc) return rc;
   rc = reverse_rows(ix->L.n, ix->p.R, ix->nb, b, ix->A, ix->cnt, ix->rcnt, ix->rcur, ix->r_off,
                     ix->r_ids, ix->scan_tmp, s);
@@ -391,16 +432,22 @@ fgraft_status fgraft_build_scaffold(const void* X, int64_t n, int32_t d, int64_t
   rc = rc ? rc : dalloc(&S.kd, tot);
   rc = rc ? rc : dalloc(&S.best, tot);
   rc = rc ? rc : dalloc(&S.flag, tot);
-  rc = rc ? rc : dalloc(&S.seg_start, tot);
-  rc = rc ? rc : dalloc(&S.seg_len, tot);
-  rc = rc ? rc : dalloc(&S.seg_node, tot);
-  rc = rc ? rc : dalloc(&S.seg_tree, tot);
-  rc = rc ? rc : dalloc(&S.nseg, 2);
-  S.nunsettled = S.nseg + 1;
+  S.big_min = g_sat_big_min;
+  const int64_t nbig_max = tot / S.big_min + 1;
+  rc = rc ? rc : dalloc(&S.seg_start, tot + nbig_max);
+  rc = rc ? rc : dalloc(&S.seg_len, tot + nbig_max);
+  rc = rc ? rc : dalloc(&S.seg_node, tot + nbig_max);
+  rc = rc ? rc : dalloc(&S.seg_tree, tot + nbig_max);
+  rc = rc ? rc : dalloc(&S.nseg, 3);
+  rc = rc ? rc : dalloc(&S.big_list, nbig_max);
+  rc = rc ? rc : dalloc(&S.big_keys, 3 * nbig_max);
+  rc = rc ? rc : dalloc(&S.big_kcount, nbig_max);
+  S.nunsettled = S.nseg + 2;
   S.scan_tmp = ix->scan_tmp;
   auto free_sat = [&]() {
     void* ps[] = {S.node_of, S.kcnt, S.kstart, S.item_pt, S.kd, S.best, S.flag,
-                  S.seg_start, S.seg_len, S.seg_node, S.seg_tree, S.nseg};
+                  S.seg_start, S.seg_len, S.seg_node, S.seg_tree, S.nseg,
+                  S.big_list, S.big_keys, S.big_kcount};
     for (void* q : ps)
       if (q) cudaFree(q);
   };
@@ -498,11 +545,14 @@ fgraft_status fgraft_harvest_all(fgraft_index* ix, int32_t use_graph, fgraft_str
       cudaStream_t cs;
       FGS(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
       cudaGraph_t graph = nullptr;
+      const uint64_t before = launch_count();
       cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
       if (e == cudaSuccess) {
         for (int b = 0; b < ix->nb && !rc; ++b) rc = harvest_block_impl(ix, b, cs);
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (!rc && e2 != cudaSuccess) rc = cuda_fail(e2, "cudaStreamEndCapture");
+        ix->graph_kernels = launch_count() - before;
+        set_launch_count(before);
       } else {
         rc = cuda_fail(e, "cudaStreamBeginCapture");
       }
@@ -515,6 +565,7 @@ fgraft_status fgraft_harvest_all(fgraft_index* ix, int32_t use_graph, fgraft_str
       if (rc) return (fgraft_status)rc;
     }
     FGS(cudaGraphLaunch(ix->graph_exec, s));
+    note_launch(ix->graph_kernels);
     ix->blocks_done = ix->nb;
   }
   return fgraft_prune(ix, stream, counters, nullptr, nullptr, 0, nullptr);
@@ -644,12 +695,57 @@ fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t war
     return (fgraft_status)fail(FGRAFT_EINVAL, "hash_log2 must be in [7, 14]");
   if (warps_per_cta && (warps_per_cta < 1 || warps_per_cta > 4))
     return (fgraft_status)fail(FGRAFT_EINVAL, "warps_per_cta must be in [1, 4]");
-  if (hash_log2) ix->hash_log2 = hash_log2;
+  if (hash_log2) {
+    ix->hash_log2 = hash_log2;
+    ix->bitmap_ok = false;  // an explicit hash size selects the hash
+  }
   if (warps_per_cta) ix->wpc = warps_per_cta;
   if (ix->graph_exec) {
     cudaGraphExecDestroy(ix->graph_exec);
     ix->graph_exec = nullptr;
   }
+  return FGRAFT_OK;
+}
+
+fgraft_status fgraft_index_profile(fgraft_index* ix, int32_t enable) {
+  if (!ix) return (fgraft_status)fail(FGRAFT_EINVAL, "index is NULL");
+  if (enable && ix->ev_beg.empty()) {
+    ix->ev_beg.resize(ix->nb);
+    ix->ev_end.resize(ix->nb);
+    for (int b = 0; b < ix->nb; ++b) {
+      FGS(cudaEventCreate(&ix->ev_beg[b]));
+      FGS(cudaEventCreate(&ix->ev_end[b]));
+    }
+  }
+  if ((enable != 0) != ix->profile && ix->graph_exec) {
+    cudaGraphExecDestroy(ix->graph_exec);
+    ix->graph_exec = nullptr;
+  }
+  ix->profile = enable != 0;
+  return FGRAFT_OK;
+}
+
+fgraft_status fgraft_index_harvest_ms(fgraft_index* ix, fgraft_stream stream, double* ms,
+                                      int32_t* launches) {
+  if (!ix || !ms) return (fgraft_status)fail(FGRAFT_EINVAL, "NULL argument");
+  if (!ix->profile) return (fgraft_status)fail(FGRAFT_EINVAL, "profiling is off");
+  FGS(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+  double tot = 0.0;
+  for (int b = 0; b < ix->blocks_done && b < (int)ix->ev_beg.size(); ++b) {
+    float t = 0.0f;
+    FGS(cudaEventElapsedTime(&t, ix->ev_beg[b], ix->ev_end[b]));
+    tot += t;
+  }
+  *ms = tot;
+  if (launches) *launches = ix->blocks_done;
+  return FGRAFT_OK;
+}
+
+uint64_t fgraft_kernel_launches(void) { return launch_count(); }
+
+fgraft_status fgraft_tune_sat(int32_t big_node_min) {
+  if (big_node_min < 2) return (fgraft_status)fail(FGRAFT_EINVAL, "big_node_min must be >= 2");
+  g_sat_big_min = big_node_min;
   return FGRAFT_OK;
 }
 

@@ -61,6 +61,8 @@ struct BeamArgs {
   // scratch
   uint32_t* work;
   int32_t hash_log2;
+  int32_t bitmap;     // 1: visited set is an n-bit bitmap, 0: bucketed hash
+  int32_t vis_bytes;  // bytes of the visited region per warp (multiple of 16)
   int32_t vis_cap;
   int32_t ecap;  // power of two, >= 32
   int32_t wbytes;  // shared bytes per warp
@@ -117,22 +119,15 @@ struct Beam {
     unsigned char* wsm = smem + (int64_t)wib * a.wbytes;
     const uint32_t nslots = 1u << a.hash_log2;
     const uint32_t mask_buckets = nslots / 4 - 1;
-    uint32_t* hash;
-    uint64_t* E;
-    uint32_t* alive;
-    int32_t* queue;
-    if (a.global_scratch) {
-      char* base = a.gscratch + gwarp * a.gscratch_per_warp;
-      hash = reinterpret_cast<uint32_t*>(base);
-      E = reinterpret_cast<uint64_t*>(base + 4ll * nslots);
-      alive = reinterpret_cast<uint32_t*>(base + 4ll * nslots + 8ll * a.ecap);
-      queue = reinterpret_cast<int32_t*>(wsm);
-    } else {
-      hash = reinterpret_cast<uint32_t*>(wsm);
-      E = reinterpret_cast<uint64_t*>(wsm + 4ll * nslots);
-      alive = reinterpret_cast<uint32_t*>(wsm + 4ll * nslots + 8ll * a.ecap);
-      queue = reinterpret_cast<int32_t*>(wsm + 4ll * nslots + 8ll * a.ecap + a.ecap / 8);
-    }
+    unsigned char* vbase = a.global_scratch
+                               ? reinterpret_cast<unsigned char*>(a.gscratch + gwarp * a.gscratch_per_warp)
+                               : wsm;
+    uint32_t* hash = reinterpret_cast<uint32_t*>(vbase);
+    uint64_t* E = reinterpret_cast<uint64_t*>(vbase + a.vis_bytes);
+    uint32_t* alive = reinterpret_cast<uint32_t*>(vbase + a.vis_bytes + 8ll * a.ecap);
+    int32_t* queue = a.global_scratch
+                         ? reinterpret_cast<int32_t*>(wsm)
+                         : reinterpret_cast<int32_t*>(wsm + a.vis_bytes + 8ll * a.ecap + a.ecap / 8);
     const int64_t nwork =
         a.qlist_len ? min((int64_t)*a.qlist_len, (int64_t)a.ovf_cap) : a.nq;
     unsigned long long c_ev = 0, c_ex = 0, c_pe = 0, c_sc = 0, c_ovf = 0;
@@ -153,8 +148,11 @@ struct Beam {
       }
       uint4 q[K];
       load_chunks<METRIC, G, K>(qrow, a.nchunks, gl, q);
-      for (uint32_t i = lane; i < nslots / 4; i += 32)
-        reinterpret_cast<uint4*>(hash)[i] = make_uint4(EMPTY, EMPTY, EMPTY, EMPTY);
+      {
+        const uint4 fill = a.bitmap ? make_uint4(0u, 0u, 0u, 0u)
+                                    : make_uint4(EMPTY, EMPTY, EMPTY, EMPTY);
+        for (int i = lane; i < a.vis_bytes / 16; i += 32) reinterpret_cast<uint4*>(hash)[i] = fill;
+      }
       __syncwarp();
       uint64_t pool[S];
 #pragma unroll
@@ -164,47 +162,65 @@ struct Beam {
       bool ovf = false;
       unsigned long long q_sc = 0;
 
-      // hash-insert one candidate per lane (-1 = none) and queue the new ones;
-      // full batches of 32 are evaluated and merged at once
-      auto enqueue = [&](int32_t v) {
-        bool isnew = (v >= 0) && hash_insert(hash, mask_buckets, (uint32_t)v);
-        unsigned m = __ballot_sync(FULL, isnew);
-        int pos = qn + __popc(m & ((1u << lane) - 1u));
-        if (isnew) queue[pos] = v;
-        qn += __popc(m);
-        nvis += __popc(m);
-        __syncwarp();
-        if (nvis > a.vis_cap) ovf = true;
-        if (qn >= 32) {
-          eval_merge(a, q, queue, 32, pool, lane);
-          int rest = qn - 32;
-          int32_t t = lane < rest ? queue[32 + lane] : 0;
+      // One id stream per step, cut in up to three segments: first the tree
+      // roots, then for each expansion the scaffold row, the row of an earlier
+      // block and the reverse list of the expanded vertex.  New ids (visited
+      // set insert) are queued; full batches of 32 are evaluated and merged.
+      const int32_t* sp0 = a.roots;
+      const int32_t* sp1 = nullptr;
+      const int32_t* sp2 = nullptr;
+      int len0 = a.T, len1 = 0, len2 = 0;
+      for (;;) {
+        const int total = len0 + len1 + len2;
+        for (int base = 0; base < total; base += 32) {
+          const int i = base + lane;
+          int32_t v = -1;
+          if (i < len0) {
+            v = sp0[i];
+          } else if (i < len0 + len1) {
+            v = sp1[i - len0];
+          } else if (i < total) {
+            v = sp2[i - len0 - len1];
+          }
+          bool isnew = false;
+          if (v >= 0) {
+            if (a.bitmap) {
+              const uint32_t bit = 1u << (v & 31);
+              isnew = (atomicOr(hash + (v >> 5), bit) & bit) == 0u;
+            } else {
+              isnew = hash_insert(hash, mask_buckets, (uint32_t)v);
+            }
+          }
+          const unsigned m = __ballot_sync(FULL, isnew);
+          if (isnew) queue[qn + __popc(m & ((1u << lane) - 1u))] = v;
+          qn += __popc(m);
+          nvis += __popc(m);
           __syncwarp();
-          if (lane < rest) queue[lane] = t;
+          if (nvis > a.vis_cap) {
+            ovf = true;
+            break;
+          }
+          if (qn >= 32) {
+            eval_merge(a, q, queue, 32, pool, lane);
+            const int rest = qn - 32;
+            const int32_t t = lane < rest ? queue[32 + lane] : 0;
+            __syncwarp();
+            if (lane < rest) queue[lane] = t;
+            __syncwarp();
+            qn = rest;
+          }
+        }
+        if (ovf) break;
+        if (qn > 0) {
+          eval_merge(a, q, queue, qn, pool, lane);
           __syncwarp();
-          qn = rest;
+          qn = 0;
         }
-      };
-      auto scan = [&](const int32_t* ids, int64_t len) {
-        for (int64_t base = 0; base < len && !ovf; base += 32) {
-          int32_t v = (base + lane < len) ? ids[base + lane] : -1;
-          enqueue(v);
-        }
-        q_sc += (unsigned long long)len;
-      };
-
-      for (int t0 = 0; t0 < a.T; t0 += 32) enqueue(t0 + lane < a.T ? a.roots[t0 + lane] : -1);
-      if (qn > 0) {
-        eval_merge(a, q, queue, qn, pool, lane);
-        qn = 0;
-        __syncwarp();
-      }
-
-      while (!ovf) {
+        // expand the smallest unexpanded pool entry
         int idx = -1;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-          unsigned m = __ballot_sync(FULL, (pool[s] & 1ull) == 0ull);
+          const unsigned m = __ballot_sync(FULL, (pool[s] & 1ull) == 0ull);
           if (m && idx < 0) idx = s * 32 + __ffs(m) - 1;
         }
         if (idx < 0) break;
@@ -223,20 +239,20 @@ struct Beam {
         if (lane == 0) E[ne] = ck;
         ++ne;
         const int32_t c = key_id(ck);
-        const int64_t s0 = a.s_off[c], s1 = a.s_off[c + 1];
-        scan(a.s_ids + s0, s1 - s0);
+        const int64_t s0 = a.s_off[c];
+        sp0 = a.s_ids + s0;
+        len0 = (int)(a.s_off[c + 1] - s0);
+        len1 = len2 = 0;
         if (a.mode == 0) {
-          if (!ovf && (c % a.B) < a.b) scan(a.A + (int64_t)c * a.R, a.cnt[c]);
-          if (!ovf && a.r_off) {
-            const int64_t r0 = a.r_off[c], r1 = a.r_off[c + 1];
-            scan(a.r_ids + r0, r1 - r0);
+          sp1 = a.A + (int64_t)c * a.R;
+          len1 = (c % a.B) < a.b ? a.cnt[c] : 0;
+          if (a.r_off) {
+            const int64_t r0 = a.r_off[c];
+            sp2 = a.r_ids + r0;
+            len2 = (int)(a.r_off[c + 1] - r0);
           }
         }
-        if (!ovf && qn > 0) {
-          eval_merge(a, q, queue, qn, pool, lane);
-          __syncwarp();
-          qn = 0;
-        }
+        q_sc += (unsigned long long)(len0 + len1 + len2);
       }
       __syncwarp();
 

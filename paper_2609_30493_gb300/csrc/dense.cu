@@ -1,4 +1,5 @@
-// Dense-block ceiling (Section 4.3): a pair set fixed in advance -- every
+// Dense-block ceiling (Section 5.3, the blocked side of the two-ceiling model):
+// a pair set fixed in advance -- every
 // ordered pair of distinct members of a block -- evaluated in the canonical
 // float32 order, with the k smallest (delta, id) kept per row.  One warp owns
 // one row; the row's own vector sits in registers and the block's vectors
@@ -110,6 +111,7 @@ int dense_block(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs
   const int64_t rows = nb * bs;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, 152 * 16));
   kern<<<grid, 256, 0, s>>>(a);
+  note_launch();
   FG_CUDA(cudaGetLastError());
   return 0;
 }

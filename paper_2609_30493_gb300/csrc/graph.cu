@@ -96,8 +96,11 @@ int scan_u32(const uint32_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStre
   const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 152 * 8));
   scan_tiles_kernel<<<grid, SCAN_THREADS, 0, s>>>(in, n, tmp);
+  note_launch();
   scan_prefix_kernel<<<1, SCAN_THREADS, 0, s>>>(tmp, ntiles);
+  note_launch();
   scan_apply_kernel<<<grid, SCAN_THREADS, 0, s>>>(in, out, n, tmp);
+  note_launch();
   FG_CUDA(cudaGetLastError());
   return 0;
 }
@@ -204,7 +207,9 @@ static int sort_unique_all(int64_t n, const int64_t* off, int32_t* ids, uint32_t
   FG_CUDA(cudaMemsetAsync(small, 0, 2 * sizeof(uint32_t), s));
   sort_unique_rows_kernel<<<grid1d(n * 32, ROW_WARPS * 32), ROW_WARPS * 32, 0, s>>>(
       n, nullptr, nullptr, off, ids, ucnt, long_rows, small, nullptr, 0);
+  note_launch();
   max_row_kernel<<<64, 256, 0, s>>>(n, off, long_rows, small, small + 1);
+  note_launch();
   FG_CUDA(cudaGetLastError());
   uint32_t h[2];
   FG_CUDA(cudaMemcpyAsync(h, small, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -220,6 +225,7 @@ static int sort_unique_all(int64_t n, const int64_t* off, int32_t* ids, uint32_t
     } else {
       sort_unique_rows_kernel<<<ctas, ROW_WARPS * 32, 0, s>>>(n, long_rows, small, off, ids, ucnt,
                                                              long_rows, small, gbuf, gcap);
+      note_launch();
       e = cudaGetLastError();
       if (e != cudaSuccess) rc = cuda_fail(e, "sort_unique_rows_kernel(long)");
       cudaFreeAsync(gbuf, s);
@@ -236,9 +242,11 @@ int scaffold_csr(int64_t n, int T, const int32_t* parents, int64_t* s_off, int32
   const int64_t tot = (int64_t)T * n;
   FG_CUDA(cudaMemsetAsync(deg, 0, sizeof(uint32_t) * n, s));
   edge_count_kernel<<<grid1d(tot), 256, 0, s>>>(n, tot, parents, deg);
+  note_launch();
   int rc = scan_u32(deg, tmp_off, n, scan_tmp, s);
   if (rc) return rc;
   edge_fill_kernel<<<grid1d(tot), 256, 0, s>>>(n, tot, parents, deg, tmp_off, tmp_ids);
+  note_launch();
   FG_CUDA(cudaGetLastError());
   rc = sort_unique_all(n, tmp_off, tmp_ids, deg, s);
   if (rc) return rc;
@@ -249,6 +257,7 @@ int scaffold_csr(int64_t n, int T, const int32_t* parents, int64_t* s_off, int32
   FG_CUDA(cudaStreamSynchronize(s));
   FG_CUDA(cudaMalloc(s_ids, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
   compact_rows_kernel<<<grid1d(n * 32), 256, 0, s>>>(n, tmp_off, tmp_ids, s_off, *s_ids);
+  note_launch();
   FG_CUDA(cudaGetLastError());
   *nnz_out = nnz;
   return 0;
@@ -287,9 +296,11 @@ int reverse_rows(int64_t n, int R, int nb, int b, const int32_t* A, const int32_
   FG_CUDA(cudaMemsetAsync(rcnt, 0, sizeof(uint32_t) * n, s));
   FG_CUDA(cudaMemsetAsync(rcur, 0, sizeof(uint32_t) * n, s));
   rev_count_kernel<<<grid1d(n * R), 256, 0, s>>>(n, R, nb, b, A, cnt, rcnt);
+  note_launch();
   int rc = scan_u32(rcnt, r_off, n, scan_tmp, s);
   if (rc) return rc;
   rev_fill_kernel<<<grid1d(n * R), 256, 0, s>>>(n, R, nb, b, A, cnt, rcur, r_off, r_ids);
+  note_launch();
   FG_CUDA(cudaGetLastError());
   return 0;
 }
@@ -501,8 +512,10 @@ static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, cudaSt
   a.gbuf = nullptr;
   a.gcap = 0;
   kern<<<grid1d(nrows * 32, FIN_WARPS * 32), FIN_WARPS * 32, 0, s>>>(a);
+  note_launch();
   max_final_need_kernel<<<64, 256, 0, s>>>(nrows, long_rows, small, a.mode, a.R, a.cnt, a.r_off,
                                            a.parent0, a.c0_off, a.l_off, small + 1);
+  note_launch();
   FG_CUDA(cudaGetLastError());
   uint32_t h[2];
   FG_CUDA(cudaMemcpyAsync(h, small, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -522,6 +535,7 @@ static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, cudaSt
       a.gbuf = gbuf;
       a.gcap = gcap;
       kern<<<ctas, FIN_WARPS * 32, 0, s>>>(a);
+      note_launch();
       e = cudaGetLastError();
       if (e != cudaSuccess) rc = cuda_fail(e, "final_rows_kernel(long)");
       cudaFreeAsync(gbuf, s);
@@ -567,11 +581,14 @@ int final_graph(const VecLayout& L, int R, float alpha2, const int32_t* A, const
   FG_TRY(cudaMallocAsync(&rowcnt, sizeof(int32_t) * n, s));
   FG_TRY(cudaMemsetAsync(c0cnt, 0, sizeof(uint32_t) * n, s));
   child_count_kernel<<<grid1d(n), 256, 0, s>>>(n, parent0, c0cnt);
+  note_launch();
   rc = scan_u32(c0cnt, c0_off, n, scan_tmp, s);
   if (rc) return cleanup(), rc;
   FG_TRY(cudaMemsetAsync(c0cnt, 0, sizeof(uint32_t) * n, s));
   child_fill_kernel<<<grid1d(n), 256, 0, s>>>(n, parent0, c0cnt, c0_off, c0_ids);
+  note_launch();
   final_cap_kernel<<<grid1d(n), 256, 0, s>>>(n, R, parent0, c0_off, capc);
+  note_launch();
   rc = scan_u32(capc, cap_off, n, scan_tmp, s);
   if (rc) return cleanup(), rc;
   int64_t capn = 0;
@@ -609,6 +626,7 @@ int final_graph(const VecLayout& L, int R, float alpha2, const int32_t* A, const
   }
   FG_TRY(cudaMalloc(f_ids, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
   compact_rows_kernel<<<grid1d(n * 32), 256, 0, s>>>(n, cap_off, tmp_ids, f_off, *f_ids);
+  note_launch();
   FG_TRY(cudaGetLastError());
   *f_nnz = nnz;
   cleanup();

@@ -14,6 +14,11 @@ struct Err {
 };
 
 void set_error(int code, const std::string& msg);
+
+// Process-wide count of kernel launches issued by the library (measurement).
+void note_launch(uint64_t k = 1);
+uint64_t launch_count();
+void set_launch_count(uint64_t v);
 int cuda_fail(cudaError_t e, const char* what);
 
 #define FG_CUDA(call)                              \
@@ -50,13 +55,17 @@ struct SatScratch {
   float* kd;            // T*n
   uint64_t* best;       // T*n
   uint8_t* flag;        // T*n
-  int64_t* seg_start;   // T*n
-  int32_t* seg_len;     // T*n
-  int32_t* seg_node;    // T*n
-  int32_t* seg_tree;    // T*n
-  uint32_t* nseg;       // 1
+  int64_t* seg_start;   // T*n + T*n/big_min + 1 (small nodes first, big ones from T*n)
+  int32_t* seg_len;     // same
+  int32_t* seg_node;    // same
+  int32_t* seg_tree;    // same
+  uint32_t* nseg;       // 2: small nodes, big nodes of the level
   uint32_t* nunsettled; // 1
   int64_t* scan_tmp;
+  int32_t big_min;      // nodes with at least this many points use the multi-CTA path
+  int32_t* big_list;    // segment index of each big node
+  uint64_t* big_keys;   // 3 per big node
+  uint32_t* big_kcount; // 1 per big node
 };
 int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* parents,
                SatScratch& S, unsigned long long* ctr_sat, cudaStream_t s);

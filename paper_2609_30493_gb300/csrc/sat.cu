@@ -14,6 +14,7 @@
 // One CTA owns one node; the points of all nodes of a level are grouped by a
 // counting sort keyed on (tree, node).
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -184,12 +185,147 @@ __global__ void __launch_bounds__(NW * 32) sat_segment_kernel(const SatSegArgs a
   }
 }
 
+// ---------------------------------------------------------------------------
+// Nodes with many points: every CTA of a launch owns a tile of one node's
+// points, and one launch performs one child selection for all such nodes.
+// The minimum over a node's points is reduced with a 64-bit atomicMin into
+// one of three rotating per-node key buffers (read, write, clear), so no CTA
+// ever waits for another.
+// ---------------------------------------------------------------------------
+constexpr int BIG_TILE = 2048;  // points per CTA
+constexpr int BIG_NW = 8;
+
+struct SatBigArgs {
+  SatSegArgs s;
+  const int32_t* big;  // segment index of each big node
+  uint64_t* cur;       // current minimum key per big node (the next child)
+  uint64_t* nxt;       // receives the minimum of this pass
+  uint64_t* clr;       // reset to PAD for the pass after
+  uint32_t* kcount;    // children chosen so far per big node
+  int32_t y_off;       // first big node of this launch (grid.y is limited to 65535)
+};
+
+template <int METRIC, int G, int K>
+__device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) v = umin64(v, __shfl_xor_sync(FULL, v, off));
+  return v;
+}
+
+// mode 0: distances to the node's own point (kd), state reset, first minimum.
+// mode 1: one child selection.  mode 2: write the assignment and the count.
+template <int METRIC, int G, int K>
+__global__ void __launch_bounds__(BIG_NW * 32) sat_big_kernel(const SatBigArgs A, int mode) {
+  constexpr int GPW = 32 / G;
+  constexpr int U = Unroll<G, K>::value;
+  constexpr int STEP = GPW * U;
+  const SatSegArgs& a = A.s;
+  const int y = blockIdx.y + A.y_off;
+  const int sidx = A.big[y];
+  const int64_t start = a.seg_start[sidx];
+  const int m = a.seg_len[sidx];
+  const int32_t anode = a.seg_node[sidx];
+  const int64_t tbase = (int64_t)a.seg_tree[sidx] * a.n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane / G, gl = lane % G;
+  const int t0 = blockIdx.x * BIG_TILE;
+  if (t0 >= m) return;
+  const int t1 = min(m, t0 + BIG_TILE);
+  if (mode == 2) {
+    for (int i = t0 + threadIdx.x; i < t1; i += BIG_NW * 32) {
+      const int64_t it = start + i;
+      a.node_of[tbase + a.item_pt[it]] = a.flag[it] == 2 ? -1 : key_id(a.best[it]);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      const long long mm = m, k = A.kcount[y];
+      atomicAdd(a.ctr, (unsigned long long)(mm + k * (k - 1) / 2 + (mm - k) * k));
+    }
+    return;
+  }
+  int32_t bpt = anode;
+  if (mode == 1) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.clr[y] = PAD;
+    const uint64_t bk = A.cur[y];
+    if (bk == PAD) return;
+    bpt = key_id(bk);
+  }
+  uint4 cv[K];
+  load_chunks<METRIC, G, K>(a.X + (int64_t)bpt * a.ld_bytes, a.nchunks, gl, cv);
+  uint64_t lmin = PAD;
+  for (int base = t0 + warp * STEP; base < t1; base += BIG_NW * STEP) {
+    uint4 v[U][K];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * GPW + g;
+      if (idx < t1) {
+        load_chunks<METRIC, G, K>(a.X + (int64_t)a.item_pt[start + idx] * a.ld_bytes, a.nchunks,
+                                  gl, v[u]);
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) v[u][kk] = make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const float dd = group_reduce<METRIC, G>(partial<METRIC, G, K>(cv, v[u], a.d, gl));
+      const int idx = base + u * GPW + g;
+      if (idx < t1 && gl == 0) {
+        const int64_t it = start + idx;
+        const int32_t pt = a.item_pt[it];
+        if (mode == 0) {
+          a.kd[it] = dd;
+          a.best[it] = PAD;
+          a.flag[it] = 0;
+          lmin = umin64(lmin, make_key(dd, pt));
+        } else if (pt == bpt) {
+          a.flag[it] = 2;
+          a.parent[tbase + bpt] = anode;
+          atomicAdd(&A.kcount[y], 1u);
+        } else {
+          const uint8_t f = a.flag[it];
+          if (f != 2) {
+            const uint64_t ck = make_key(dd, bpt);
+            if (ck < a.best[it]) a.best[it] = ck;
+            if (f == 0) {
+              const float kdv = a.kd[it];
+              if (dd <= kdv) {
+                a.flag[it] = 1;
+              } else {
+                lmin = umin64(lmin, make_key(kdv, pt));
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  lmin = warp_min64<METRIC, G, K>(lmin);
+  if (lane == 0 && lmin != PAD)
+    atomicMin(reinterpret_cast<unsigned long long*>((mode == 0 ? A.cur : A.nxt) + y),
+              (unsigned long long)lmin);
+}
+
+using SatBigFn = void (*)(const SatBigArgs, int);
+
 using SatKernelFn = void (*)(const SatSegArgs);
 constexpr int SAT_NW = 8;
 
 static SatKernelFn sat_kernel_for(int metric, int G, int K) {
 #define SATX(M, GG, KK) \
   if (metric == M && G == GG && K == KK) return sat_segment_kernel<M, GG, KK, SAT_NW>;
+#define SATF(M) SATX(M, 4, 1) SATX(M, 8, 1) SATX(M, 16, 1) SATX(M, 32, 1) SATX(M, 32, 2) \
+  SATX(M, 32, 4) SATX(M, 32, 8)
+  SATF(0)
+  SATF(1)
+  SATX(2, 4, 1) SATX(2, 8, 1) SATX(2, 16, 1)
+#undef SATF
+#undef SATX
+  return nullptr;
+}
+
+static SatBigFn sat_big_for(int metric, int G, int K) {
+#define SATX(M, GG, KK) \
+  if (metric == M && G == GG && K == KK) return sat_big_kernel<M, GG, KK>;
 #define SATF(M) SATX(M, 4, 1) SATX(M, 8, 1) SATX(M, 16, 1) SATX(M, 32, 1) SATX(M, 32, 2) \
   SATX(M, 32, 4) SATX(M, 32, 8)
   SATF(0)
@@ -212,10 +348,15 @@ __global__ void sat_init_kernel(int64_t n, int T, const int32_t* roots, int32_t*
   }
 }
 
-__global__ void sat_count_kernel(int64_t n, int64_t tot, const int32_t* node_of, uint32_t* kcnt) {
+__global__ void sat_count_kernel(int64_t n, int64_t tot, const int32_t* node_of, uint32_t* kcnt,
+                                 uint32_t* err) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t a = node_of[i];
+    if (a >= n) {
+      atomicOr(err, 1u);  // an invalid node id: recorded, never used as an index
+      continue;
+    }
     if (a >= 0) {
       const int64_t t = i / n;
       atomicAdd(&kcnt[t * n + a], 1u);
@@ -225,12 +366,21 @@ __global__ void sat_count_kernel(int64_t n, int64_t tot, const int32_t* node_of,
 
 __global__ void sat_segments_kernel(int64_t n, int64_t tot, const uint32_t* kcnt,
                                     const int64_t* kstart, int64_t* seg_start, int32_t* seg_len,
-                                    int32_t* seg_node, int32_t* seg_tree, uint32_t* nseg) {
+                                    int32_t* seg_node, int32_t* seg_tree, uint32_t* nseg,
+                                    int32_t big_min, int32_t* big_list, int64_t big_base) {
   for (int64_t key = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; key < tot;
        key += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t c = kcnt[key];
     if (c) {
-      const uint32_t s = atomicAdd(nseg, 1u);
+      // small nodes fill the list from the front, big ones from big_base on
+      uint32_t s;
+      if ((int32_t)c >= big_min) {
+        const uint32_t j = atomicAdd(nseg + 1, 1u);
+        s = (uint32_t)(big_base + j);
+        big_list[j] = (int32_t)s;
+      } else {
+        s = atomicAdd(nseg, 1u);
+      }
       seg_start[s] = kstart[key];
       seg_len[s] = (int32_t)c;
       seg_node[s] = (int32_t)(key % n);
@@ -244,7 +394,7 @@ __global__ void sat_scatter_kernel(int64_t n, int64_t tot, const int32_t* node_o
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t a = node_of[i];
-    if (a >= 0) {
+    if (a >= 0 && a < n) {
       const int64_t t = i / n;
       const int64_t key = t * n + a;
       const uint32_t r = atomicSub(&kcnt[key], 1u) - 1u;
@@ -261,12 +411,14 @@ static int grid_for(int64_t tot) {
 int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* parents,
                SatScratch& S, unsigned long long* ctr_sat, cudaStream_t s) {
   SatKernelFn kern = sat_kernel_for(L.metric, L.G, L.K);
-  if (!kern) {
+  SatBigFn bigk = sat_big_for(L.metric, L.G, L.K);
+  if (!kern || !bigk) {
     set_error(1, "no SAT kernel for this metric and dimension");
     return 1;
   }
   const int64_t n = L.n, tot = (int64_t)T * n;
   sat_init_kernel<<<grid_for(tot), 256, 0, s>>>(n, T, roots_d, S.node_of, parents);
+  note_launch();
   FG_CUDA(cudaGetLastError());
   SatSegArgs a;
   a.X = L.X;
@@ -285,22 +437,83 @@ int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* paren
   a.node_of = S.node_of;
   a.parent = parents;
   a.ctr = ctr_sat;
+  std::vector<uint64_t> hkeys;
   for (int64_t level = 0; level <= n; ++level) {
-    FG_CUDA(cudaMemsetAsync(S.nseg, 0, sizeof(uint32_t), s));
-    sat_count_kernel<<<grid_for(tot), 256, 0, s>>>(n, tot, S.node_of, S.kcnt);
+    FG_CUDA(cudaMemsetAsync(S.nseg, 0, 3 * sizeof(uint32_t), s));
+    sat_count_kernel<<<grid_for(tot), 256, 0, s>>>(n, tot, S.node_of, S.kcnt, S.nseg + 2);
+    note_launch();
     int rc = scan_u32(S.kcnt, S.kstart, tot, S.scan_tmp, s);
     if (rc) return rc;
     sat_segments_kernel<<<grid_for(tot), 256, 0, s>>>(n, tot, S.kcnt, S.kstart, S.seg_start,
-                                                      S.seg_len, S.seg_node, S.seg_tree, S.nseg);
+                                                      S.seg_len, S.seg_node, S.seg_tree, S.nseg,
+                                                      S.big_min, S.big_list, tot);
+    note_launch();
     sat_scatter_kernel<<<grid_for(tot), 256, 0, s>>>(n, tot, S.node_of, S.kcnt, S.kstart,
                                                      S.item_pt);
+    note_launch();
     FG_CUDA(cudaGetLastError());
-    uint32_t nseg = 0;
-    FG_CUDA(cudaMemcpyAsync(&nseg, S.nseg, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    uint32_t cnts[3] = {0, 0, 0};
+    FG_CUDA(cudaMemcpyAsync(cnts, S.nseg, sizeof(cnts), cudaMemcpyDeviceToHost, s));
     FG_CUDA(cudaStreamSynchronize(s));
-    if (nseg == 0) return 0;
-    kern<<<nseg, SAT_NW * 32, 0, s>>>(a);
-    FG_CUDA(cudaGetLastError());
+    if (cnts[2]) {
+      set_error(3, "SAT: a point was assigned to an invalid node");
+      return 3;
+    }
+    const uint32_t nsmall = cnts[0], nbig = cnts[1];
+    if (nsmall == 0 && nbig == 0) return 0;
+    if (nsmall) {
+      kern<<<nsmall, SAT_NW * 32, 0, s>>>(a);
+      note_launch();
+      FG_CUDA(cudaGetLastError());
+    }
+    if (nbig) {
+      SatBigArgs B;
+      B.s = a;
+      B.big = S.big_list;
+      uint64_t* buf[3] = {S.big_keys, S.big_keys + nbig, S.big_keys + 2 * nbig};
+      B.kcount = S.big_kcount;
+      FG_CUDA(cudaMemsetAsync(S.big_keys, 0xFF, 3 * nbig * sizeof(uint64_t), s));
+      FG_CUDA(cudaMemsetAsync(S.big_kcount, 0, nbig * sizeof(uint32_t), s));
+      const unsigned gx = (unsigned)((n + BIG_TILE - 1) / BIG_TILE);
+      // grid.y is limited to 65535: big nodes are covered in chunks
+      auto launch_all = [&](int mode) {
+        for (uint32_t y0 = 0; y0 < nbig; y0 += 65535u) {
+          B.y_off = (int32_t)y0;
+          const dim3 grid(gx, std::min<uint32_t>(65535u, nbig - y0));
+          bigk<<<grid, BIG_NW * 32, 0, s>>>(B, mode);
+          note_launch();
+        }
+      };
+      B.cur = buf[0];
+      B.nxt = buf[1];
+      B.clr = buf[2];
+      launch_all(0);
+      FG_CUDA(cudaGetLastError());
+      hkeys.resize(nbig);
+      int r = 0;  // buf[r] holds the next child of every big node
+      bool done = false;
+      for (int64_t it = 0; it <= n && !done;) {
+        for (int j = 0; j < 8; ++j, ++it) {
+          B.cur = buf[r];
+          B.nxt = buf[(r + 1) % 3];
+          B.clr = buf[(r + 2) % 3];
+          launch_all(1);
+          r = (r + 1) % 3;
+        }
+        FG_CUDA(cudaGetLastError());
+        FG_CUDA(cudaMemcpyAsync(hkeys.data(), buf[r], nbig * sizeof(uint64_t),
+                                cudaMemcpyDeviceToHost, s));
+        FG_CUDA(cudaStreamSynchronize(s));
+        done = true;
+        for (uint64_t k : hkeys) done &= (k == PAD);
+      }
+      if (!done) {
+        set_error(1, "SAT child selection did not terminate");
+        return 1;
+      }
+      launch_all(2);
+      FG_CUDA(cudaGetLastError());
+    }
   }
   set_error(1, "SAT construction did not terminate");
   return 1;

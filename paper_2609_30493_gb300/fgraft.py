@@ -41,6 +41,8 @@ _lib = None
 EXPORTS = ["fgraft_build_scaffold", "fgraft_harvest_block", "fgraft_harvest_all", "fgraft_prune",
            "fgraft_prune_lists", "fgraft_search", "fgraft_dense_block_dist", "fgraft_index_copy",
            "fgraft_index_sizes", "fgraft_index_counters", "fgraft_index_tune",
+           "fgraft_index_profile", "fgraft_index_harvest_ms", "fgraft_kernel_launches",
+           "fgraft_tune_sat",
            "fgraft_index_destroy", "fgraft_last_error"]
 
 
@@ -57,8 +59,9 @@ def load():
         lib = C.CDLL(_build.LIB)
         lib.fgraft_last_error.restype = C.c_char_p
         lib.fgraft_index_destroy.restype = None
+        lib.fgraft_kernel_launches.restype = C.c_uint64
         for name in EXPORTS:
-            if name not in ("fgraft_last_error", "fgraft_index_destroy"):
+            if name not in ("fgraft_last_error", "fgraft_index_destroy", "fgraft_kernel_launches"):
                 getattr(lib, name).restype = C.c_int
         _lib = lib
     return _lib
@@ -174,6 +177,26 @@ def fgraft_index_counters(ix: Index) -> dict:
 
 def fgraft_index_tune(ix: Index, hash_log2: int = 0, warps_per_cta: int = 0):
     _check(load().fgraft_index_tune(ix.handle, C.c_int32(hash_log2), C.c_int32(warps_per_cta)))
+
+
+def fgraft_index_profile(ix: Index, enable: bool = True):
+    _check(load().fgraft_index_profile(ix.handle, C.c_int32(1 if enable else 0)))
+
+
+def fgraft_index_harvest_ms(ix: Index):
+    """(sum of harvest-kernel milliseconds, number of harvest launches) since profiling began."""
+    ms, nl = C.c_double(), C.c_int32()
+    _check(load().fgraft_index_harvest_ms(ix.handle, _stream(ix.X.device), C.byref(ms),
+                                          C.byref(nl)))
+    return ms.value, nl.value
+
+
+def fgraft_tune_sat(big_node_min: int = 16384):
+    _check(load().fgraft_tune_sat(C.c_int32(big_node_min)))
+
+
+def fgraft_kernel_launches() -> int:
+    return int(load().fgraft_kernel_launches())
 
 
 def fgraft_index_copy(ix: Index):

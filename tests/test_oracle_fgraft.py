@@ -1,6 +1,6 @@
 """Pins for the oracle's FGraft build, final graph, query search and dense
 block (Section 3 and Proposition 1; Section 2's brute-force answer key;
-Section 4.3's fixed pair sets).
+Section 5.3's fixed pair sets).
 
 FGraft: B = 0 and B = 1 both give the frozen harvest (Section 3: B <= 1
 reproduces Graft); the graph is identical at 1 and N threads

@@ -180,3 +180,35 @@ def test_api_rejects_bad_arguments(fg):
         fg.fgraft_prune(ix)  # blocks missing
     with pytest.raises(fg.FgraftError, match="EINVAL"):
         fg.fgraft_search(ix, X[:4], 10, 16)  # no final graph yet
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_profile_hooks(fg, use_graph):
+    ps = synth.gaussian_mixture(2000, 16, 8, seed=0)
+    X = _dev(ps.X)
+    ix = fg.fgraft_build_scaffold(X, 16, fg.Params(T=4, R=16, ef_h=32, B=4, alpha=1.2))
+    fg.fgraft_index_profile(ix, True)
+    before = fg.fgraft_kernel_launches()
+    fg.fgraft_harvest_all(ix, use_graph=use_graph)
+    ms, nl = fg.fgraft_index_harvest_ms(ix)
+    assert nl == 4 and ms > 0.0
+    assert fg.fgraft_kernel_launches() - before > 4
+
+
+@pytest.mark.parametrize("split", [2, 64, 700])
+def test_sat_multi_cta_nodes(fg, split):
+    # force the multi-CTA SAT path for small nodes too; the forest must not change
+    try:
+        fg.fgraft_tune_sat(split)
+        ps = synth.vmf_like(2500, 100, 8, seed=6)
+        ix, ctr, st, fin, D, ref = _build_both(fg, ps, T=6, R=16, ef=32, B=2)
+        _compare(ctr, st, fin, ref)
+    finally:
+        fg.fgraft_tune_sat(16384)
+
+
+def test_n20000_parity(fg):
+    # the top tree nodes (19,999 points) take the default multi-CTA path
+    ps = synth.vmf_like(20000, 100, 32, seed=9)
+    ix, ctr, st, fin, D, ref = _build_both(fg, ps, T=8, R=32, ef=64, B=8)
+    _compare(ctr, st, fin, ref)
