@@ -157,6 +157,27 @@ fgraft_status fgraft_prune_lists(const void* X, int64_t n, int32_t d, int64_t ld
                                  const int32_t* cand_ids, int64_t nlists, float alpha, int32_t R,
                                  int32_t* out_ids, int32_t* out_cnt, fgraft_stream stream);
 
+/* The list prune above, for callers that cannot allocate device memory when
+ * they need it: code running while a stream is captured into a CUDA graph,
+ * serving loops that must never wait on or fail in the allocator, and hosts
+ * whose device memory is already owned by their own pool.  The paper has no
+ * counterpart: this is a property of the library, not of the method.
+ * Same arguments and results as fgraft_prune_lists, with fixed limits:
+ * nlists <= 65536 (EINVAL otherwise, before any work) and at most 4096
+ * candidates per list (EINVAL after the call; rows of such lists are then
+ * unspecified).  The scratch is one file-scope device array of about 2.4 MiB
+ * that every device loading the library keeps until the process exits.  The
+ * first call on a device looks up that array's address (make it before any
+ * stream capture); every call clears what must start at zero, and calls
+ * whose work overlaps on the GPU race on the shared array.  The call
+ * synchronises `stream` before returning (to report over-long lists).
+ * It calls no cudaMalloc, cudaFree or allocating library routine. */
+fgraft_status fgraft_prune_lists_noalloc(const void* X, int64_t n, int32_t d, int64_t ld,
+                                         int32_t metric, const int32_t* owner,
+                                         const int64_t* cand_off, const int32_t* cand_ids,
+                                         int64_t nlists, float alpha, int32_t R, int32_t* out_ids,
+                                         int32_t* out_cnt, fgraft_stream stream);
+
 /* Query search (Section 2: beam search over the final graph, graded against
  * a brute-force key).  The same beam as the harvest, width ef_s, entering at
  * the T roots; out_ids/out_dist (nq*k) get the first k pool entries (-1 /

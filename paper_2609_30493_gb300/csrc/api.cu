@@ -590,6 +590,27 @@ fgraft_status fgraft_prune_lists(const void* X, int64_t n, int32_t d, int64_t ld
                                     out_ids, out_cnt, nullptr, s);
 }
 
+fgraft_status fgraft_prune_lists_noalloc(const void* X, int64_t n, int32_t d, int64_t ld,
+                                         int32_t metric, const int32_t* owner,
+                                         const int64_t* cand_off, const int32_t* cand_ids,
+                                         int64_t nlists, float alpha, int32_t R, int32_t* out_ids,
+                                         int32_t* out_cnt, fgraft_stream stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  VecLayout L;
+  int rc = check_vectors(X, n, d, ld, metric, &L);
+  if (rc) return (fgraft_status)rc;
+  if (nlists < 0 || nlists > prune_lists_static_max_lists())
+    return (fgraft_status)fail(FGRAFT_EINVAL, "nlists must be in [0, 65536]");
+  if (nlists == 0) return FGRAFT_OK;
+  if (!owner || !cand_off || !cand_ids || !out_ids || !out_cnt)
+    return (fgraft_status)fail(FGRAFT_EINVAL, "NULL list pointer");
+  if (R < 1 || R > 1024) return (fgraft_status)fail(FGRAFT_EINVAL, "need 1 <= R <= 1024");
+  if (!(alpha >= 0.0f) || !std::isfinite(alpha))
+    return (fgraft_status)fail(FGRAFT_EINVAL, "alpha must be finite and >= 0");
+  return (fgraft_status)prune_lists_static(L, owner, cand_off, cand_ids, nlists, alpha * alpha, R,
+                                           out_ids, out_cnt, s);
+}
+
 fgraft_status fgraft_search(fgraft_index* ix, const void* Q, int64_t nq, int64_t ldq, int32_t k,
                             int32_t ef_s, int32_t* out_ids, float* out_dist, uint32_t* out_evals,
                             fgraft_stream stream) {

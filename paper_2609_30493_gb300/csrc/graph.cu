@@ -3,6 +3,7 @@
 // rows of finished blocks into S_{b+1}, the final graph (rows symmetrised,
 // re-pruned when over R, tree-0 spine added) and the stand-alone list prune.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -650,6 +651,122 @@ int prune_lists(const VecLayout& L, const int32_t* owner, const int64_t* l_off,
   a.mode = 1;
   a.ctr = ctr;
   return run_final_rows(a, L, nlists, s);
+}
+
+// ---------------------------------------------------------------------------
+// List prune that allocates nothing.
+//
+// Some callers cannot call cudaMalloc at the moment they need a prune: code
+// that runs while a stream is being captured into a CUDA graph (allocation
+// calls are not allowed there), serving loops that must never enter the
+// allocator because an allocation can stall or fail under memory pressure,
+// and hosts that have already handed all device memory to their own pool.
+// For them the scratch of the list prune lives in one file-scope device
+// array, reserved when the library is loaded on a device and kept until the
+// process exits.  Its size fixes the limits: at most NA_MAX_LISTS lists per
+// call and at most NA_MAX_LEN candidates per list.
+// ---------------------------------------------------------------------------
+constexpr int64_t NA_MAX_LISTS = 1 << 16;
+constexpr int NA_MAX_LEN = 4096;
+constexpr int NA_CTAS = 16;  // CTAs of the pass over lists too long for shared memory
+constexpr int64_t NA_WARP_WORDS = NA_MAX_LEN + NA_MAX_LEN / 32;  // keys + bit words, in uint64
+constexpr size_t NA_COUNTERS = 256;
+constexpr size_t NA_SCRATCH_BYTES = NA_COUNTERS + 2 * 4 * NA_MAX_LISTS +
+                                    8 * NA_WARP_WORDS * NA_CTAS * FIN_WARPS;
+static __device__ __align__(256) unsigned char g_prune_scratch[NA_SCRATCH_BYTES];
+
+// Device address of g_prune_scratch for each device, looked up once.
+static unsigned char* prune_scratch_address(int* rc) {
+  static std::mutex mu;
+  static unsigned char* addr[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    *rc = cuda_fail(e, "cudaGetDevice");
+    return nullptr;
+  }
+  if (dev < 0 || dev >= 64) {
+    set_error(1, "device index out of range");
+    *rc = 1;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_prune_scratch);
+    if (e != cudaSuccess) {
+      *rc = cuda_fail(e, "cudaGetSymbolAddress(g_prune_scratch)");
+      return nullptr;
+    }
+    addr[dev] = static_cast<unsigned char*>(ptr);
+  }
+  *rc = 0;
+  return addr[dev];
+}
+
+int64_t prune_lists_static_max_lists() { return NA_MAX_LISTS; }
+int prune_lists_static_max_len() { return NA_MAX_LEN; }
+
+int prune_lists_static(const VecLayout& L, const int32_t* owner, const int64_t* l_off,
+                       const int32_t* l_ids, int64_t nlists, float alpha2, int R,
+                       int32_t* out_ids, int32_t* out_cnt, cudaStream_t s) {
+  FinalKernelFn kern = final_kernel_for(L.metric, L.G, L.K);
+  if (!kern) {
+    set_error(1, "no row kernel for this metric and dimension");
+    return 1;
+  }
+  if (nlists > NA_MAX_LISTS) {
+    set_error(1, "at most 65536 lists per call");
+    return 1;
+  }
+  int rc = 0;
+  unsigned char* base = prune_scratch_address(&rc);
+  if (rc) return rc;
+  uint32_t* counters = reinterpret_cast<uint32_t*>(base);  // [0] long lists, [1] too long
+  int32_t* long_rows = reinterpret_cast<int32_t*>(base + NA_COUNTERS);
+  int32_t* too_long = long_rows + NA_MAX_LISTS;
+  uint64_t* keys = reinterpret_cast<uint64_t*>(base + NA_COUNTERS + 8 * NA_MAX_LISTS);
+  // the array keeps the previous call's contents: the counters start at zero
+  FG_CUDA(cudaMemsetAsync(counters, 0, 2 * sizeof(uint32_t), s));
+  FinalArgs a{};
+  a.V = RowVec{L.X, L.ld_bytes, L.d, L.nchunks};
+  a.n = L.n;
+  a.R = R;
+  a.alpha2 = alpha2;
+  a.owner = owner;
+  a.l_off = l_off;
+  a.l_ids = l_ids;
+  a.out_ids = out_ids;
+  a.out_cnt = out_cnt;
+  a.mode = 1;
+  a.ctr = nullptr;
+  a.rowlist = nullptr;
+  a.rowlist_len = nullptr;
+  a.nrows = nlists;
+  a.long_rows = long_rows;
+  a.nlong = counters;
+  a.gbuf = nullptr;
+  a.gcap = 0;
+  kern<<<grid1d(nlists * 32, FIN_WARPS * 32), FIN_WARPS * 32, 0, s>>>(a);
+  note_launch();
+  // lists longer than shared memory holds: fixed-size key buffers in the array
+  a.rowlist = long_rows;
+  a.rowlist_len = counters;
+  a.long_rows = too_long;
+  a.nlong = counters + 1;
+  a.gbuf = keys;
+  a.gcap = NA_MAX_LEN;
+  kern<<<NA_CTAS, FIN_WARPS * 32, 0, s>>>(a);
+  note_launch();
+  FG_CUDA(cudaGetLastError());
+  uint32_t over = 0;
+  FG_CUDA(cudaMemcpyAsync(&over, counters + 1, sizeof(over), cudaMemcpyDeviceToHost, s));
+  FG_CUDA(cudaStreamSynchronize(s));
+  if (over) {
+    set_error(1, "a list holds more than 4096 candidates");
+    return 1;
+  }
+  return 0;
 }
 
 }  // namespace fg

@@ -94,6 +94,13 @@ int prune_lists(const VecLayout& L, const int32_t* owner, const int64_t* l_off,
                 const int32_t* l_ids, int64_t nlists, float alpha2, int R, int32_t* out_ids,
                 int32_t* out_cnt, unsigned long long* ctr, cudaStream_t s);
 
+// The list prune on a fixed, file-scope device scratch array (no allocation).
+int prune_lists_static(const VecLayout& L, const int32_t* owner, const int64_t* l_off,
+                       const int32_t* l_ids, int64_t nlists, float alpha2, int R,
+                       int32_t* out_ids, int32_t* out_cnt, cudaStream_t s);
+int64_t prune_lists_static_max_lists();
+int prune_lists_static_max_len();
+
 // Dense-block top-k (canonical float32 distances of every pair of a block).
 int dense_block(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs, int k,
                 int32_t* out_ids, float* out_dist, cudaStream_t s);

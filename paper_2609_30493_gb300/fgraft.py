@@ -42,7 +42,7 @@ EXPORTS = ["fgraft_build_scaffold", "fgraft_harvest_block", "fgraft_harvest_all"
            "fgraft_prune_lists", "fgraft_search", "fgraft_dense_block_dist", "fgraft_index_copy",
            "fgraft_index_sizes", "fgraft_index_counters", "fgraft_index_tune",
            "fgraft_index_profile", "fgraft_index_harvest_ms", "fgraft_kernel_launches",
-           "fgraft_tune_sat",
+           "fgraft_tune_sat", "fgraft_prune_lists_noalloc",
            "fgraft_index_destroy", "fgraft_last_error"]
 
 
@@ -240,6 +240,24 @@ def fgraft_prune_lists(X: torch.Tensor, d: int, metric: int, owner: torch.Tensor
                                      _ptr(cand_off), _ptr(cand_ids), C.c_int64(nl),
                                      C.c_float(alpha), C.c_int32(R), _ptr(out), _ptr(cnt),
                                      _stream(X.device)))
+    return out, cnt
+
+
+def fgraft_prune_lists_noalloc(X: torch.Tensor, d: int, metric: int, owner: torch.Tensor,
+                               cand_off: torch.Tensor, cand_ids: torch.Tensor, alpha: float, R: int,
+                               out: torch.Tensor = None, cnt: torch.Tensor = None):
+    """fgraft_prune_lists without any device allocation inside the library; the
+    output tensors may be passed in (preallocated by the caller)."""
+    nl = owner.shape[0]
+    if out is None:
+        out = torch.empty((nl, R), dtype=torch.int32, device=X.device)
+    if cnt is None:
+        cnt = torch.empty(nl, dtype=torch.int32, device=X.device)
+    _check(load().fgraft_prune_lists_noalloc(_ptr(X), C.c_int64(X.shape[0]), C.c_int32(d),
+                                             C.c_int64(X.shape[1]), C.c_int32(metric),
+                                             _ptr(owner), _ptr(cand_off), _ptr(cand_ids),
+                                             C.c_int64(nl), C.c_float(alpha), C.c_int32(R),
+                                             _ptr(out), _ptr(cnt), _stream(X.device)))
     return out, cnt
 
 
