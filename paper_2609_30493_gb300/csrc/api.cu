@@ -91,7 +91,8 @@ static int32_t g_sat_big_min = 16384;
 #define FGS(call)                                                      \
   do {                                                                 \
     cudaError_t e_ = (call);                                           \
-    if (e_ != cudaSuccess) return (fgraft_status)cuda_fail(e_, #call); \
+    if (e_ != cudaSuccess) \
+      return (fgraft_status)cuda_fail(e_, #call " at " __FILE__ ":" FG_STR(__LINE__)); \
   } while (0)
 
 enum CtrSlot {
@@ -215,7 +216,9 @@ int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStrea
   const int64_t bm_bytes = ((ix->L.n + 127) / 128) * 16;
   const bool bitmap = ix->bitmap_ok && bm_bytes <= 4ll * nslots;
   const int vis_bytes = bitmap ? (int)bm_bytes : 4 * nslots;
-  const int wbytes = (vis_bytes + 8 * ecap + ecap / 8 + 256 + 15) / 16 * 16;
+  const int qbytes = 16 * ix->L.nchunks;  // staged query (then c* in the prune)
+  const int alive_bytes = (ecap / 8 + 15) / 16 * 16;  // kept a multiple of 16 (see beam.cuh)
+  const int wbytes = vis_bytes + 8 * ecap + alive_bytes + 256 + qbytes;
   const int smem = wbytes * ix->wpc;
   FG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int per_sm = 0;
@@ -233,6 +236,7 @@ int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStrea
   a.vis_cap = bitmap ? INT32_MAX : (int32_t)(0.8 * nslots) - 32;
   a.ecap = ecap;
   a.wbytes = wbytes;
+  a.qbytes = qbytes;
   a.global_scratch = 0;
   a.qlist = nullptr;
   a.qlist_len = nullptr;
@@ -252,11 +256,11 @@ int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStrea
   a.vis_bytes = 4 << ix->g_hash_log2;
   a.vis_cap = (int32_t)(0.8 * (1 << ix->g_hash_log2)) - 32;
   a.ecap = ix->g_ecap;
-  a.wbytes = 256;
+  a.wbytes = 256 + qbytes;
   a.gscratch = ix->gscratch;
   a.gscratch_per_warp = ix->gscratch_per_warp;
   a.counters = ctr;
-  kern<<<ix->g_warps / 4, 128, 256 * 4, s>>>(a);
+  kern<<<ix->g_warps / 4, 128, a.wbytes * 4, s>>>(a);
   note_launch();
   FG_CUDA(cudaGetLastError());
   return 0;

@@ -66,6 +66,7 @@ struct BeamArgs {
   int32_t vis_cap;
   int32_t ecap;  // power of two, >= 32
   int32_t wbytes;  // shared bytes per warp
+  int32_t qbytes;  // staging bytes per warp for one vector (16 * nchunks, rounded)
   int32_t global_scratch;
   char* gscratch;
   int64_t gscratch_per_warp;
@@ -78,43 +79,39 @@ struct BeamArgs {
 
 template <int METRIC, int G, int K, int S>
 struct Beam {
-  static constexpr int GPW = 32 / G;
-  static constexpr int U = Unroll<G, K>::value;
 
-  // Evaluate queue[0..cnt) (cnt <= 32) against the query chunks q and merge
-  // the keys into the pool.
-  static __device__ __forceinline__ void eval_merge(const BeamArgs& a, const uint4 (&q)[K],
+  // Evaluate queue[0..cnt) (cnt <= 32) against the staged query qs and merge
+  // the keys into the pool.  Lane groups of P lanes take one candidate each.
+  static __device__ __forceinline__ void eval_merge(const BeamArgs& a, const uint4* qs,
                                                     const int32_t* queue, int cnt,
                                                     uint64_t (&pool)[S], int lane) {
-    const int g = lane / G, gl = lane % G;
+    using L = Lanes<G, K>;
+    const int g = lane / L::P, j = lane % L::P;
     uint64_t mykey = PAD;
-    for (int base = 0; base < cnt; base += GPW * U) {
-      uint4 v[U][K];
+    for (int base = 0; base < cnt; base += L::CPW * L::UW) {
+      uint4 y[L::UW][L::VL][K];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        int idx = base + u * GPW + g;
-        if (idx < cnt) {
-          load_chunks<METRIC, G, K>(a.X + (int64_t)queue[idx] * a.ld_bytes, a.nchunks, gl, v[u]);
-        } else {
-#pragma unroll
-          for (int kk = 0; kk < K; ++kk) v[u][kk] = make_uint4(0u, 0u, 0u, 0u);
-        }
+      for (int u = 0; u < L::UW; ++u) {
+        const int idx = base + u * L::CPW + g;
+        const int32_t id = idx < cnt ? queue[idx] : queue[0];
+        load_slots<G, K>(a.X + (int64_t)id * a.ld_bytes, a.nchunks, j, y[u]);
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        float dd = group_reduce<METRIC, G>(partial<METRIC, G, K>(q, v[u], a.d, gl));
-        int rel = lane - base - u * GPW;
-        float got = __shfl_sync(FULL, dd, (rel & (GPW - 1)) * G);
-        if (rel >= 0 && rel < GPW && lane < cnt) mykey = make_key(got, queue[lane]);
+      for (int u = 0; u < L::UW; ++u) {
+        const float dd = slots_dist<METRIC, G, K>(qs, y[u], a.nchunks, a.d, j);
+        const int rel = lane - base - u * L::CPW;
+        const float got = __shfl_sync(FULL, dd, (rel & (L::CPW - 1)) * L::P);
+        if (rel >= 0 && rel < L::CPW && lane < cnt) mykey = make_key(got, queue[lane]);
       }
     }
     merge_into_pool<S>(pool, mykey, a.ef, lane);
   }
 
   static __device__ void run(const BeamArgs& a, unsigned char* smem) {
+    using L = Lanes<G, K>;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int g = lane / G, gl = lane % G;
+    const int g = lane / L::P, j = lane % L::P;
     const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     unsigned char* wsm = smem + (int64_t)wib * a.wbytes;
     const uint32_t nslots = 1u << a.hash_log2;
@@ -125,9 +122,12 @@ struct Beam {
     uint32_t* hash = reinterpret_cast<uint32_t*>(vbase);
     uint64_t* E = reinterpret_cast<uint64_t*>(vbase + a.vis_bytes);
     uint32_t* alive = reinterpret_cast<uint32_t*>(vbase + a.vis_bytes + 8ll * a.ecap);
-    int32_t* queue = a.global_scratch
-                         ? reinterpret_cast<int32_t*>(wsm)
-                         : reinterpret_cast<int32_t*>(wsm + a.vis_bytes + 8ll * a.ecap + a.ecap / 8);
+    // the alive bits take ecap/8 bytes, rounded up so that the staged vector
+    // after the queue keeps its 16-byte alignment
+    unsigned char* tail =
+        a.global_scratch ? wsm : wsm + a.vis_bytes + 8ll * a.ecap + ((a.ecap / 8 + 15) & ~15);
+    int32_t* queue = reinterpret_cast<int32_t*>(tail);
+    uint4* qs = reinterpret_cast<uint4*>(tail + 256);
     const int64_t nwork =
         a.qlist_len ? min((int64_t)*a.qlist_len, (int64_t)a.ovf_cap) : a.nq;
     unsigned long long c_ev = 0, c_ex = 0, c_pe = 0, c_sc = 0, c_ovf = 0;
@@ -146,8 +146,7 @@ struct Beam {
       } else {
         qrow = a.Q + qidx * a.ldq_bytes;
       }
-      uint4 q[K];
-      load_chunks<METRIC, G, K>(qrow, a.nchunks, gl, q);
+      stage_row(qs, qrow, a.nchunks, lane);
       {
         const uint4 fill = a.bitmap ? make_uint4(0u, 0u, 0u, 0u)
                                     : make_uint4(EMPTY, EMPTY, EMPTY, EMPTY);
@@ -201,7 +200,7 @@ struct Beam {
             break;
           }
           if (qn >= 32) {
-            eval_merge(a, q, queue, 32, pool, lane);
+            eval_merge(a, qs, queue, 32, pool, lane);
             const int rest = qn - 32;
             const int32_t t = lane < rest ? queue[32 + lane] : 0;
             __syncwarp();
@@ -212,7 +211,7 @@ struct Beam {
         }
         if (ovf) break;
         if (qn > 0) {
-          eval_merge(a, q, queue, qn, pool, lane);
+          eval_merge(a, qs, queue, qn, pool, lane);
           __syncwarp();
           qn = 0;
         }
@@ -327,8 +326,9 @@ struct Beam {
         ++kept;
         __syncwarp();
         if (kept == a.R) break;
-        uint4 cv[K];
-        load_chunks<METRIC, G, K>(a.X + (int64_t)cid * a.ld_bytes, a.nchunks, gl, cv);
+        // the query is no longer needed: stage c* in its place
+        __syncwarp();
+        stage_row(qs, a.X + (int64_t)cid * a.ld_bytes, a.nchunks, lane);
         for (int w2 = cur / 32; w2 < nw; ++w2) {
           uint32_t bits = alive[w2];
           if (w2 == cur / 32) bits &= ~((2u << (cur % 32)) - 1u);
@@ -336,30 +336,24 @@ struct Beam {
           uint32_t kill = 0;
           while (bits) {
             const int nb = __popc(bits);
-            uint4 v[U][K];
-            int jj[U];
+            uint4 y[L::UW][L::VL][K];
+            int jj[L::UW];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-              int r = u * GPW + g;
-              if (r < nb) {
-                jj[u] = nth_set_bit(bits, r);
-                load_chunks<METRIC, G, K>(a.X + (int64_t)key_id(E[w2 * 32 + jj[u]]) * a.ld_bytes,
-                                          a.nchunks, gl, v[u]);
-              } else {
-                jj[u] = -1;
-#pragma unroll
-                for (int kk = 0; kk < K; ++kk) v[u][kk] = make_uint4(0u, 0u, 0u, 0u);
-              }
+            for (int u = 0; u < L::UW; ++u) {
+              const int r = u * L::CPW + g;
+              jj[u] = r < nb ? nth_set_bit(bits, r) : -1;
+              const int e = w2 * 32 + (jj[u] >= 0 ? jj[u] : 0);
+              load_slots<G, K>(a.X + (int64_t)key_id(E[e]) * a.ld_bytes, a.nchunks, j, y[u]);
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-              float dd = group_reduce<METRIC, G>(partial<METRIC, G, K>(cv, v[u], a.d, gl));
-              if (jj[u] >= 0 && gl == 0) {
-                float dp = key_dist(E[w2 * 32 + jj[u]]);
+            for (int u = 0; u < L::UW; ++u) {
+              const float dd = slots_dist<METRIC, G, K>(qs, y[u], a.nchunks, a.d, j);
+              if (jj[u] >= 0 && j == 0) {
+                const float dp = key_dist(E[w2 * 32 + jj[u]]);
                 if (__fmul_rn(a.alpha2, dd) <= dp) kill |= 1u << jj[u];
               }
             }
-            const int consumed = nb < GPW * U ? nb : GPW * U;
+            const int consumed = nb < L::CPW * L::UW ? nb : L::CPW * L::UW;
             if (consumed >= nb) {
               bits = 0;
             } else {

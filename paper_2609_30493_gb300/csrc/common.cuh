@@ -132,6 +132,131 @@ __device__ __forceinline__ float group_reduce(float p) {
 }
 
 // ---------------------------------------------------------------------------
+// Lane-group distance.  A vector is evaluated by P physical lanes; lane j of
+// the group holds the virtual lanes l = j, j+P, j+2P, .. (V/P of them, V = G
+// the virtual lanes in use) and, of each, the chunks 32k + l, k < K.  The
+// per-virtual-lane sums are exactly the canonical ones; the butterfly levels
+// s >= P combine virtual lanes held by the same physical lane (in registers,
+// v[i] + v[i + s/P], the operand order of the canonical tree) and the levels
+// s < P use shuffles inside the group.  Result: bit-identical to the
+// canonical order at a fraction of the shuffles.
+// ---------------------------------------------------------------------------
+template <int G, int K>
+struct Lanes {
+  static constexpr int P = G <= 8 ? 1 : (G == 16 ? 2 : 4 * K);  // lanes per vector
+  static constexpr int VL = G / P;                               // virtual lanes per lane
+  static constexpr int CPW = 32 / P;                             // vectors per warp step
+  static constexpr int SLOTS = VL * K;                           // 16-byte chunks per lane
+  static constexpr int U = SLOTS >= 8 ? 1 : 8 / SLOTS;           // vectors in flight per group
+  static constexpr int UW = CPW * U > 32 ? 32 / CPW : U;          // same, for at most 32 vectors
+};
+
+// Copy a row's chunks into shared memory (whole warp), then sync the warp.
+__device__ __forceinline__ void stage_row(uint4* dst, const char* __restrict__ row, int nchunks,
+                                          int lane) {
+  for (int c = lane; c < nchunks; c += 32) dst[c] = __ldg(reinterpret_cast<const uint4*>(row) + c);
+  __syncwarp();
+}
+
+// The chunks lane j of a group needs from row; indices past the row are
+// clamped to its last chunk (the values are masked out later), so every load
+// is issued without a branch.
+template <int G, int K>
+__device__ __forceinline__ void load_slots(const char* __restrict__ row, int nchunks, int j,
+                                           uint4 (&y)[Lanes<G, K>::VL][K]) {
+  using L = Lanes<G, K>;
+#pragma unroll
+  for (int i = 0; i < L::VL; ++i) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int c = min(32 * k + j + L::P * i, nchunks - 1);
+      y[i][k] = __ldg(reinterpret_cast<const uint4*>(row) + c);
+    }
+  }
+}
+
+// Canonical distance between the staged vector qs (shared memory) and the
+// chunks y of one group member; every lane of the group returns it.
+template <int METRIC, int G, int K>
+__device__ __forceinline__ float slots_dist(const uint4* qs, const uint4 (&y)[Lanes<G, K>::VL][K],
+                                            int nchunks, int d, int j) {
+  using L = Lanes<G, K>;
+  if constexpr (METRIC == L2_U8) {
+    uint32_t v[L::VL];
+#pragma unroll
+    for (int i = 0; i < L::VL; ++i) {
+      uint32_t acc = 0;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int c = 32 * k + j + L::P * i;
+        if (c < nchunks) {
+          const uint4 x = qs[c];
+          const int nb = d - 16 * c;
+          const uint32_t a[4] = {x.x, x.y, x.z, x.w};
+          const uint32_t b[4] = {y[i][k].x, y[i][k].y, y[i][k].z, y[i][k].w};
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const int vb = nb - 4 * w;
+            const uint32_t m =
+                vb >= 4 ? 0xFFFFFFFFu : (vb <= 0 ? 0u : (0xFFFFFFFFu >> (8 * (4 - vb))));
+            const uint32_t df = __vabsdiffu4(a[w] & m, b[w] & m);
+            acc = __dp4a(df, df, acc);
+          }
+        }
+      }
+      v[i] = acc;
+    }
+    uint32_t t = 0;
+#pragma unroll
+    for (int i = 0; i < L::VL; ++i) t += v[i];
+#pragma unroll
+    for (int off = L::P / 2; off >= 1; off >>= 1) t += __shfl_xor_sync(FULL, t, off);
+    return __uint2float_rn(t);
+  } else {
+    float v[L::VL];
+#pragma unroll
+    for (int i = 0; i < L::VL; ++i) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int c = 32 * k + j + L::P * i;
+        if (c < nchunks) {
+          const uint4 xq = qs[c];
+          const int nv = d - 4 * c;
+          const float x[4] = {__uint_as_float(xq.x), __uint_as_float(xq.y),
+                              __uint_as_float(xq.z), __uint_as_float(xq.w)};
+          const float yy[4] = {__uint_as_float(y[i][k].x), __uint_as_float(y[i][k].y),
+                               __uint_as_float(y[i][k].z), __uint_as_float(y[i][k].w)};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (nv > e) {
+              if constexpr (METRIC == ANGULAR_F32) {
+                acc = __fmaf_rn(x[e], yy[e], acc);
+              } else {
+                const float t = __fsub_rn(x[e], yy[e]);
+                acc = __fmaf_rn(t, t, acc);
+              }
+            }
+          }
+        }
+      }
+      v[i] = acc;
+    }
+    // butterfly levels inside the lane: virtual lanes j + P*i and j + P*i + s
+#pragma unroll
+    for (int s = G / 2; s >= L::P; s >>= 1) {
+#pragma unroll
+      for (int i = 0; i < s / L::P; ++i) v[i] = __fadd_rn(v[i], v[i + s / L::P]);
+    }
+    float r = v[0];
+#pragma unroll
+    for (int off = L::P / 2; off >= 1; off >>= 1) r = __fadd_rn(r, __shfl_xor_sync(FULL, r, off));
+    if constexpr (METRIC == ANGULAR_F32) return __fsub_rn(1.0f, r);
+    return r;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Warp bitonic networks on 64-bit keys.
 // ---------------------------------------------------------------------------
 // Sort one key per lane ascending across the warp.

@@ -26,10 +26,11 @@ struct DenseArgs {
 
 template <int METRIC, int G, int K, int S>
 __global__ void __launch_bounds__(256) dense_rows_kernel(const DenseArgs a) {
-  constexpr int GPW = 32 / G;
-  constexpr int U = Unroll<G, K>::value;
-  const int lane = threadIdx.x & 31;
-  const int g = lane / G, gl = lane % G;
+  using L = Lanes<G, K>;
+  __shared__ __align__(16) uint4 srow[8][256];  // the row's vector, per warp
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane / L::P, j = lane % L::P;
+  uint4* qs = srow[warp];
   const int64_t rows = a.nb * a.bs;
   for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; r < rows;
        r += ((int64_t)gridDim.x * blockDim.x) / 32) {
@@ -41,31 +42,27 @@ __global__ void __launch_bounds__(256) dense_rows_kernel(const DenseArgs a) {
 #pragma unroll
     for (int s = 0; s < S; ++s) pool[s] = PAD;
     if (xi >= 0) {
-      uint4 q[K];
-      load_chunks<METRIC, G, K>(a.X + (int64_t)xi * a.ld_bytes, a.nchunks, gl, q);
+      __syncwarp();
+      stage_row(qs, a.X + (int64_t)xi * a.ld_bytes, a.nchunks, lane);
       for (int base = 0; base < a.bs; base += 32) {
         uint64_t mykey = PAD;
-        for (int sub = 0; sub < 32 && base + sub < a.bs; sub += GPW * U) {
-          uint4 v[U][K];
-          int32_t jd[U];
+        for (int sub = 0; sub < 32 && base + sub < a.bs; sub += L::CPW * L::UW) {
+          uint4 y[L::UW][L::VL][K];
+          int32_t jd[L::UW];
 #pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int j = base + sub + u * GPW + g;
-            jd[u] = (j < a.bs && j != i) ? ids[j] : -1;
-            if (jd[u] >= 0) {
-              load_chunks<METRIC, G, K>(a.X + (int64_t)jd[u] * a.ld_bytes, a.nchunks, gl, v[u]);
-            } else {
-#pragma unroll
-              for (int kk = 0; kk < K; ++kk) v[u][kk] = make_uint4(0u, 0u, 0u, 0u);
-            }
+          for (int u = 0; u < L::UW; ++u) {
+            const int jj = base + sub + u * L::CPW + g;
+            jd[u] = (jj < a.bs && jj != i) ? ids[jj] : -1;
+            load_slots<G, K>(a.X + (int64_t)(jd[u] >= 0 ? jd[u] : xi) * a.ld_bytes, a.nchunks, j,
+                             y[u]);
           }
 #pragma unroll
-          for (int u = 0; u < U; ++u) {
-            float dd = group_reduce<METRIC, G>(partial<METRIC, G, K>(q, v[u], a.d, gl));
-            const int rel = lane - sub - u * GPW;
-            float got = __shfl_sync(FULL, dd, (rel & (GPW - 1)) * G);
-            const int32_t jid = __shfl_sync(FULL, jd[u], (rel & (GPW - 1)) * G);
-            if (rel >= 0 && rel < GPW && jid >= 0) mykey = make_key(got, jid);
+          for (int u = 0; u < L::UW; ++u) {
+            const float dd = slots_dist<METRIC, G, K>(qs, y[u], a.nchunks, a.d, j);
+            const int rel = lane - sub - u * L::CPW;
+            const float got = __shfl_sync(FULL, dd, (rel & (L::CPW - 1)) * L::P);
+            const int32_t jid = __shfl_sync(FULL, jd[u], (rel & (L::CPW - 1)) * L::P);
+            if (rel >= 0 && rel < L::CPW && jid >= 0) mykey = make_key(got, jid);
           }
         }
         merge_into_pool<S>(pool, mykey, a.k, lane);

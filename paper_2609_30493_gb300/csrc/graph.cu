@@ -340,19 +340,25 @@ struct FinalArgs {
   uint64_t* gbuf;
   int32_t gcap;
   int32_t mode;  // 0 final graph, 1 list prune
+  int32_t qbytes;  // bytes of one staged vector (16 * nchunks)
   unsigned long long* ctr;
 };
 
 constexpr int FIN_WARPS = 4;
 constexpr int FIN_CAP = 1024;
 
+// Shared memory per warp: key buffer and bit words (unless the row works in
+// global scratch), then two staged vectors (the row's owner, the kept c*).
+__host__ __device__ inline int fin_warp_bytes(bool global_keys, int qbytes) {
+  return (global_keys ? 0 : 8 * FIN_CAP + FIN_CAP / 4) + 2 * qbytes;
+}
+
 template <int METRIC, int G, int K>
 __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalArgs a) {
-  __shared__ uint64_t sbuf[FIN_WARPS][FIN_CAP];
-  __shared__ uint32_t sbits[FIN_WARPS][2 * FIN_CAP / 32];
+  extern __shared__ __align__(16) unsigned char fsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gl = lane % G;
   const int64_t gw = (int64_t)blockIdx.x * FIN_WARPS + warp;
+  unsigned char* wsm = fsm + (int64_t)warp * fin_warp_bytes(a.gbuf != nullptr, a.qbytes);
   uint64_t* keys;
   uint32_t* bits;
   int cap;
@@ -361,10 +367,13 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
     bits = reinterpret_cast<uint32_t*>(keys + a.gcap);
     cap = a.gcap;
   } else {
-    keys = sbuf[warp];
-    bits = sbits[warp];
+    keys = reinterpret_cast<uint64_t*>(wsm);
+    bits = reinterpret_cast<uint32_t*>(wsm + 8 * FIN_CAP);
+    wsm += 8 * FIN_CAP + FIN_CAP / 4;
     cap = FIN_CAP;
   }
+  uint4* us = reinterpret_cast<uint4*>(wsm);
+  uint4* cs = reinterpret_cast<uint4*>(wsm + a.qbytes);
   const int64_t total = a.rowlist_len ? (int64_t)*a.rowlist_len : a.nrows;
   unsigned long long ev = 0;
   for (int64_t w = gw; w < total; w += (int64_t)gridDim.x * FIN_WARPS) {
@@ -393,9 +402,8 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
       if (lane == 0) a.long_rows[atomicAdd(a.nlong, 1u)] = (int32_t)r;
       continue;
     }
-    uint4 uv[K];
-    load_chunks<METRIC, G, K>(a.V.X + (int64_t)u * a.V.ld_bytes, a.V.nchunks, gl, uv);
-    eval_keys<METRIC, G, K>(a.V, uv, seg0, len0, seg1, len1, keys, 0, lane);
+    stage_row(us, a.V.X + (int64_t)u * a.V.ld_bytes, a.V.nchunks, lane);
+    eval_keys<METRIC, G, K>(a.V, us, seg0, len0, seg1, len1, keys, 0, lane);
     // the owner itself is not a candidate (list prune may contain it)
     for (int i = lane; i < mraw; i += 32)
       if (key_id(keys[i]) == u) keys[i] = PAD;
@@ -417,7 +425,8 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
       out = a.out_ids + r * a.R;
     }
     int kk = m;
-    if (m > a.R || a.mode == 1) kk = prune_sorted<METRIC, G, K>(a.V, keys, m, a.alpha2, a.R, bits, &ev, lane);
+    if (m > a.R || a.mode == 1)
+      kk = prune_sorted<METRIC, G, K>(a.V, keys, m, a.alpha2, a.R, bits, cs, &ev, lane);
     if (a.mode == 0) {
       const int32_t p0 = a.parent0[u];
       const int32_t* ch = a.c0_ids + a.c0_off[u];
@@ -426,7 +435,7 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
         const int32_t v = (p0 >= 0) ? (j == 0 ? p0 : ch[j - 1]) : ch[j];
         if (keys_contain(keys, kk, v, lane)) continue;
         // evaluate delta(u, v) and append
-        eval_keys<METRIC, G, K>(a.V, uv, &v, 1, nullptr, 0, keys, kk + add, lane);
+        eval_keys<METRIC, G, K>(a.V, us, &v, 1, nullptr, 0, keys, kk + add, lane);
         ++add;
       }
       kk = sort_unique(keys, kk + add, lane);
@@ -494,12 +503,26 @@ __global__ void max_final_need_kernel(int64_t n, const int32_t* rows, const uint
   }
 }
 
+// Dynamic shared memory of the two final_rows_kernel launches (shared-memory
+// keys, global-scratch keys); the function's maximum is set to the larger.
+static int fin_smem(FinalKernelFn kern, int qbytes, int* sm_shared, int* sm_global) {
+  *sm_shared = FIN_WARPS * fin_warp_bytes(false, qbytes);
+  *sm_global = FIN_WARPS * fin_warp_bytes(true, qbytes);
+  FG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               std::max(*sm_shared, *sm_global)));
+  return 0;
+}
+
 static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, cudaStream_t s) {
   FinalKernelFn kern = final_kernel_for(L.metric, L.G, L.K);
   if (!kern) {
     set_error(1, "no row kernel for this metric and dimension");
     return 1;
   }
+  a.qbytes = 16 * L.nchunks;
+  int sm0 = 0, sm1 = 0;
+  const int rc0 = fin_smem(kern, a.qbytes, &sm0, &sm1);
+  if (rc0) return rc0;
   int32_t* long_rows = nullptr;
   uint32_t* small = nullptr;
   FG_CUDA(cudaMallocAsync(&long_rows, sizeof(int32_t) * std::max<int64_t>(nrows, 1), s));
@@ -512,7 +535,7 @@ static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, cudaSt
   a.nlong = small;
   a.gbuf = nullptr;
   a.gcap = 0;
-  kern<<<grid1d(nrows * 32, FIN_WARPS * 32), FIN_WARPS * 32, 0, s>>>(a);
+  kern<<<grid1d(nrows * 32, FIN_WARPS * 32), FIN_WARPS * 32, sm0, s>>>(a);
   note_launch();
   max_final_need_kernel<<<64, 256, 0, s>>>(nrows, long_rows, small, a.mode, a.R, a.cnt, a.r_off,
                                            a.parent0, a.c0_off, a.l_off, small + 1);
@@ -535,7 +558,7 @@ static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, cudaSt
       a.rowlist_len = small;
       a.gbuf = gbuf;
       a.gcap = gcap;
-      kern<<<ctas, FIN_WARPS * 32, 0, s>>>(a);
+      kern<<<ctas, FIN_WARPS * 32, sm1, s>>>(a);
       note_launch();
       e = cudaGetLastError();
       if (e != cudaSuccess) rc = cuda_fail(e, "final_rows_kernel(long)");
@@ -722,6 +745,10 @@ int prune_lists_static(const VecLayout& L, const int32_t* owner, const int64_t* 
   int rc = 0;
   unsigned char* base = prune_scratch_address(&rc);
   if (rc) return rc;
+  const int qbytes = 16 * L.nchunks;
+  int sm0 = 0, sm1 = 0;
+  rc = fin_smem(kern, qbytes, &sm0, &sm1);
+  if (rc) return rc;
   uint32_t* counters = reinterpret_cast<uint32_t*>(base);  // [0] long lists, [1] too long
   int32_t* long_rows = reinterpret_cast<int32_t*>(base + NA_COUNTERS);
   int32_t* too_long = long_rows + NA_MAX_LISTS;
@@ -739,6 +766,7 @@ int prune_lists_static(const VecLayout& L, const int32_t* owner, const int64_t* 
   a.out_ids = out_ids;
   a.out_cnt = out_cnt;
   a.mode = 1;
+  a.qbytes = qbytes;
   a.ctr = nullptr;
   a.rowlist = nullptr;
   a.rowlist_len = nullptr;
@@ -747,7 +775,7 @@ int prune_lists_static(const VecLayout& L, const int32_t* owner, const int64_t* 
   a.nlong = counters;
   a.gbuf = nullptr;
   a.gcap = 0;
-  kern<<<grid1d(nlists * 32, FIN_WARPS * 32), FIN_WARPS * 32, 0, s>>>(a);
+  kern<<<grid1d(nlists * 32, FIN_WARPS * 32), FIN_WARPS * 32, sm0, s>>>(a);
   note_launch();
   // lists longer than shared memory holds: fixed-size key buffers in the array
   a.rowlist = long_rows;
@@ -756,7 +784,7 @@ int prune_lists_static(const VecLayout& L, const int32_t* owner, const int64_t* 
   a.nlong = counters + 1;
   a.gbuf = keys;
   a.gcap = NA_MAX_LEN;
-  kern<<<NA_CTAS, FIN_WARPS * 32, 0, s>>>(a);
+  kern<<<NA_CTAS, FIN_WARPS * 32, sm1, s>>>(a);
   note_launch();
   FG_CUDA(cudaGetLastError());
   uint32_t over = 0;

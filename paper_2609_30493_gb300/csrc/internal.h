@@ -21,10 +21,12 @@ uint64_t launch_count();
 void set_launch_count(uint64_t v);
 int cuda_fail(cudaError_t e, const char* what);
 
-#define FG_CUDA(call)                              \
-  do {                                             \
-    cudaError_t e_ = (call);                       \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+#define FG_STR2(x) #x
+#define FG_STR(x) FG_STR2(x)
+#define FG_CUDA(call)                                                                 \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call " at " __FILE__ ":" FG_STR(__LINE__)); \
   } while (0)
 
 // Vector layout of a point set for the kernels.

@@ -21,34 +21,30 @@ struct RowVec {
   int32_t nchunks;
 };
 
-// keys[i] = key(delta(u, c_i), c_i) for the candidates c_0.. of two id
-// segments (seg0[0..len0) then seg1[0..len1)), written at keys[at + i].
+// keys[at + i] = key(delta(u, c_i), c_i) for the candidates c_0.. of two id
+// segments (seg0[0..len0) then seg1[0..len1)); us = u's vector staged in
+// shared memory.
 template <int METRIC, int G, int K>
-__device__ void eval_keys(const RowVec& V, const uint4 (&uv)[K], const int32_t* seg0, int len0,
+__device__ void eval_keys(const RowVec& V, const uint4* us, const int32_t* seg0, int len0,
                           const int32_t* seg1, int len1, uint64_t* keys, int at, int lane) {
-  constexpr int GPW = 32 / G;
-  constexpr int U = Unroll<G, K>::value;
-  const int g = lane / G, gl = lane % G;
+  using L = Lanes<G, K>;
+  const int g = lane / L::P, j = lane % L::P;
   const int len = len0 + len1;
-  for (int base = 0; base < len; base += GPW * U) {
-    uint4 v[U][K];
-    int32_t id[U];
+  for (int base = 0; base < len; base += L::CPW * L::U) {
+    uint4 y[L::U][L::VL][K];
+    int32_t id[L::U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      int i = base + u * GPW + g;
+    for (int u = 0; u < L::U; ++u) {
+      const int i = base + u * L::CPW + g;
       id[u] = i < len0 ? seg0[i] : (i < len ? seg1[i - len0] : -1);
-      if (id[u] >= 0) {
-        load_chunks<METRIC, G, K>(V.X + (int64_t)id[u] * V.ld_bytes, V.nchunks, gl, v[u]);
-      } else {
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) v[u][kk] = make_uint4(0u, 0u, 0u, 0u);
-      }
+      const int32_t ld_id = id[u] >= 0 ? id[u] : (len0 > 0 ? seg0[0] : seg1[0]);
+      load_slots<G, K>(V.X + (int64_t)ld_id * V.ld_bytes, V.nchunks, j, y[u]);
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      float dd = group_reduce<METRIC, G>(partial<METRIC, G, K>(uv, v[u], V.d, gl));
-      int i = base + u * GPW + g;
-      if (i < len && gl == 0) keys[at + i] = make_key(dd, id[u]);
+    for (int u = 0; u < L::U; ++u) {
+      const float dd = slots_dist<METRIC, G, K>(us, y[u], V.nchunks, V.d, j);
+      const int i = base + u * L::CPW + g;
+      if (i < len && j == 0) keys[at + i] = make_key(dd, id[u]);
     }
   }
   __syncwarp();
@@ -84,10 +80,9 @@ __device__ inline int sort_unique(uint64_t* keys, int len, int lane) {
 // scratch.  *evals accumulates the alive candidates examined.
 template <int METRIC, int G, int K>
 __device__ int prune_sorted(const RowVec& V, uint64_t* keys, int m, float alpha2, int R,
-                            uint32_t* alive, unsigned long long* evals, int lane) {
-  constexpr int GPW = 32 / G;
-  constexpr int U = Unroll<G, K>::value;
-  const int g = lane / G, gl = lane % G;
+                            uint32_t* alive, uint4* cs, unsigned long long* evals, int lane) {
+  using L = Lanes<G, K>;
+  const int g = lane / L::P, j = lane % L::P;
   const int nw = (m + 31) / 32;
   for (int w = lane; w < nw; w += 32) alive[w] = (w * 32 + 32 <= m) ? FULL : ((1u << (m - w * 32)) - 1u);
   __syncwarp();
@@ -114,8 +109,7 @@ __device__ int prune_sorted(const RowVec& V, uint64_t* keys, int m, float alpha2
     ++kept;
     __syncwarp();
     if (kept == R) break;
-    uint4 cv[K];
-    load_chunks<METRIC, G, K>(V.X + (int64_t)key_id(keys[cur]) * V.ld_bytes, V.nchunks, gl, cv);
+    stage_row(cs, V.X + (int64_t)key_id(keys[cur]) * V.ld_bytes, V.nchunks, lane);
     for (int w = cur / 32; w < nw; ++w) {
       uint32_t bits = alive[w];
       if (w == cur / 32) bits &= ~((2u << (cur % 32)) - 1u);
@@ -123,30 +117,24 @@ __device__ int prune_sorted(const RowVec& V, uint64_t* keys, int m, float alpha2
       uint32_t kill = 0;
       while (bits) {
         const int nb = __popc(bits);
-        uint4 v[U][K];
-        int jj[U];
+        uint4 y[L::UW][L::VL][K];
+        int jj[L::UW];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          int r = u * GPW + g;
-          if (r < nb) {
-            jj[u] = nth_set_bit(bits, r);
-            load_chunks<METRIC, G, K>(V.X + (int64_t)key_id(keys[w * 32 + jj[u]]) * V.ld_bytes,
-                                      V.nchunks, gl, v[u]);
-          } else {
-            jj[u] = -1;
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) v[u][kk] = make_uint4(0u, 0u, 0u, 0u);
-          }
+        for (int u = 0; u < L::UW; ++u) {
+          const int r = u * L::CPW + g;
+          jj[u] = r < nb ? nth_set_bit(bits, r) : -1;
+          const int e = w * 32 + (jj[u] >= 0 ? jj[u] : 0);
+          load_slots<G, K>(V.X + (int64_t)key_id(keys[e]) * V.ld_bytes, V.nchunks, j, y[u]);
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          float dd = group_reduce<METRIC, G>(partial<METRIC, G, K>(cv, v[u], V.d, gl));
-          if (jj[u] >= 0 && gl == 0) {
-            float dp = key_dist(keys[w * 32 + jj[u]]);
+        for (int u = 0; u < L::UW; ++u) {
+          const float dd = slots_dist<METRIC, G, K>(cs, y[u], V.nchunks, V.d, j);
+          if (jj[u] >= 0 && j == 0) {
+            const float dp = key_dist(keys[w * 32 + jj[u]]);
             if (__fmul_rn(alpha2, dd) <= dp) kill |= 1u << jj[u];
           }
         }
-        const int consumed = nb < GPW * U ? nb : GPW * U;
+        const int consumed = nb < L::CPW * L::UW ? nb : L::CPW * L::UW;
         if (consumed >= nb) {
           bits = 0;
         } else {

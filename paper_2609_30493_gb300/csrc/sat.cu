@@ -70,47 +70,48 @@ __device__ __forceinline__ void block_argmin(uint64_t& key, int& idx, uint64_t (
   }
 }
 
+// Stage a row in shared memory with the whole CTA.
+__device__ __forceinline__ void stage_row_cta(uint4* dst, const char* __restrict__ row,
+                                              int nchunks) {
+  for (int c = threadIdx.x; c < nchunks; c += blockDim.x)
+    dst[c] = __ldg(reinterpret_cast<const uint4*>(row) + c);
+}
+
 template <int METRIC, int G, int K, int NW>
 __global__ void __launch_bounds__(NW * 32) sat_segment_kernel(const SatSegArgs a) {
-  constexpr int GPW = 32 / G;
-  constexpr int U = Unroll<G, K>::value;
-  constexpr int STEP = GPW * U;
+  using L = Lanes<G, K>;
+  constexpr int STEP = L::CPW * L::U;
   __shared__ uint64_t rk[2][NW];
   __shared__ int ri[2][NW];
+  __shared__ __align__(16) uint4 cvec[256];  // the node's point, then each new child
   const int s = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane / G, gl = lane % G;
+  const int g = lane / L::P, j = lane % L::P;
   const int64_t start = a.seg_start[s];
   const int m = a.seg_len[s];
   const int32_t anode = a.seg_node[s];
   const int64_t tbase = (int64_t)a.seg_tree[s] * a.n;
 
-  uint4 cv[K];
-  load_chunks<METRIC, G, K>(a.X + (int64_t)anode * a.ld_bytes, a.nchunks, gl, cv);
+  stage_row_cta(cvec, a.X + (int64_t)anode * a.ld_bytes, a.nchunks);
+  __syncthreads();
   uint64_t bk = PAD;
   int bi = -1;
   for (int base = warp * STEP; base < m; base += NW * STEP) {
-    uint4 v[U][K];
+    uint4 y[L::U][L::VL][K];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      int idx = base + u * GPW + g;
-      if (idx < m) {
-        load_chunks<METRIC, G, K>(a.X + (int64_t)a.item_pt[start + idx] * a.ld_bytes, a.nchunks,
-                                  gl, v[u]);
-      } else {
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) v[u][kk] = make_uint4(0u, 0u, 0u, 0u);
-      }
+    for (int u = 0; u < L::U; ++u) {
+      const int idx = min(base + u * L::CPW + g, m - 1);
+      load_slots<G, K>(a.X + (int64_t)a.item_pt[start + idx] * a.ld_bytes, a.nchunks, j, y[u]);
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      float dd = group_reduce<METRIC, G>(partial<METRIC, G, K>(cv, v[u], a.d, gl));
-      int idx = base + u * GPW + g;
-      if (idx < m && gl == 0) {
+    for (int u = 0; u < L::U; ++u) {
+      const float dd = slots_dist<METRIC, G, K>(cvec, y[u], a.nchunks, a.d, j);
+      const int idx = base + u * L::CPW + g;
+      if (idx < m && j == 0) {
         a.kd[start + idx] = dd;
         a.best[start + idx] = PAD;
         a.flag[start + idx] = 0;
-        uint64_t key = make_key(dd, a.item_pt[start + idx]);
+        const uint64_t key = make_key(dd, a.item_pt[start + idx]);
         if (key < bk) {
           bk = key;
           bi = idx;
@@ -128,39 +129,33 @@ __global__ void __launch_bounds__(NW * 32) sat_segment_kernel(const SatSegArgs a
       a.parent[tbase + bpt] = anode;
     }
     ++k;
-    load_chunks<METRIC, G, K>(a.X + (int64_t)bpt * a.ld_bytes, a.nchunks, gl, cv);
+    stage_row_cta(cvec, a.X + (int64_t)bpt * a.ld_bytes, a.nchunks);
     __syncthreads();
     bk = PAD;
     bi = -1;
     for (int base = warp * STEP; base < m; base += NW * STEP) {
-      uint4 v[U][K];
+      uint4 y[L::U][L::VL][K];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        int idx = base + u * GPW + g;
-        if (idx < m) {
-          load_chunks<METRIC, G, K>(a.X + (int64_t)a.item_pt[start + idx] * a.ld_bytes,
-                                    a.nchunks, gl, v[u]);
-        } else {
-#pragma unroll
-          for (int kk = 0; kk < K; ++kk) v[u][kk] = make_uint4(0u, 0u, 0u, 0u);
-        }
+      for (int u = 0; u < L::U; ++u) {
+        const int idx = min(base + u * L::CPW + g, m - 1);
+        load_slots<G, K>(a.X + (int64_t)a.item_pt[start + idx] * a.ld_bytes, a.nchunks, j, y[u]);
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        float dd = group_reduce<METRIC, G>(partial<METRIC, G, K>(cv, v[u], a.d, gl));
-        int idx = base + u * GPW + g;
-        if (idx < m && gl == 0) {
+      for (int u = 0; u < L::U; ++u) {
+        const float dd = slots_dist<METRIC, G, K>(cvec, y[u], a.nchunks, a.d, j);
+        const int idx = base + u * L::CPW + g;
+        if (idx < m && j == 0) {
           const int64_t it = start + idx;
           const uint8_t f = a.flag[it];
           if (f != 2) {
-            uint64_t ck = make_key(dd, bpt);
+            const uint64_t ck = make_key(dd, bpt);
             if (ck < a.best[it]) a.best[it] = ck;
             if (f == 0) {
               const float kdv = a.kd[it];
               if (dd <= kdv) {
                 a.flag[it] = 1;
               } else {
-                uint64_t key = make_key(kdv, a.item_pt[it]);
+                const uint64_t key = make_key(kdv, a.item_pt[it]);
                 if (key < bk) {
                   bk = key;
                   bi = idx;
@@ -216,9 +211,9 @@ __device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
 // mode 1: one child selection.  mode 2: write the assignment and the count.
 template <int METRIC, int G, int K>
 __global__ void __launch_bounds__(BIG_NW * 32) sat_big_kernel(const SatBigArgs A, int mode) {
-  constexpr int GPW = 32 / G;
-  constexpr int U = Unroll<G, K>::value;
-  constexpr int STEP = GPW * U;
+  using L = Lanes<G, K>;
+  constexpr int STEP = L::CPW * L::U;
+  __shared__ __align__(16) uint4 cvec[256];
   const SatSegArgs& a = A.s;
   const int y = blockIdx.y + A.y_off;
   const int sidx = A.big[y];
@@ -227,7 +222,7 @@ __global__ void __launch_bounds__(BIG_NW * 32) sat_big_kernel(const SatBigArgs A
   const int32_t anode = a.seg_node[sidx];
   const int64_t tbase = (int64_t)a.seg_tree[sidx] * a.n;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane / G, gl = lane % G;
+  const int g = lane / L::P, j = lane % L::P;
   const int t0 = blockIdx.x * BIG_TILE;
   if (t0 >= m) return;
   const int t1 = min(m, t0 + BIG_TILE);
@@ -249,27 +244,21 @@ __global__ void __launch_bounds__(BIG_NW * 32) sat_big_kernel(const SatBigArgs A
     if (bk == PAD) return;
     bpt = key_id(bk);
   }
-  uint4 cv[K];
-  load_chunks<METRIC, G, K>(a.X + (int64_t)bpt * a.ld_bytes, a.nchunks, gl, cv);
+  stage_row_cta(cvec, a.X + (int64_t)bpt * a.ld_bytes, a.nchunks);
+  __syncthreads();
   uint64_t lmin = PAD;
   for (int base = t0 + warp * STEP; base < t1; base += BIG_NW * STEP) {
-    uint4 v[U][K];
+    uint4 yv[L::U][L::VL][K];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int idx = base + u * GPW + g;
-      if (idx < t1) {
-        load_chunks<METRIC, G, K>(a.X + (int64_t)a.item_pt[start + idx] * a.ld_bytes, a.nchunks,
-                                  gl, v[u]);
-      } else {
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) v[u][kk] = make_uint4(0u, 0u, 0u, 0u);
-      }
+    for (int u = 0; u < L::U; ++u) {
+      const int idx = min(base + u * L::CPW + g, t1 - 1);
+      load_slots<G, K>(a.X + (int64_t)a.item_pt[start + idx] * a.ld_bytes, a.nchunks, j, yv[u]);
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const float dd = group_reduce<METRIC, G>(partial<METRIC, G, K>(cv, v[u], a.d, gl));
-      const int idx = base + u * GPW + g;
-      if (idx < t1 && gl == 0) {
+    for (int u = 0; u < L::U; ++u) {
+      const float dd = slots_dist<METRIC, G, K>(cvec, yv[u], a.nchunks, a.d, j);
+      const int idx = base + u * L::CPW + g;
+      if (idx < t1 && j == 0) {
         const int64_t it = start + idx;
         const int32_t pt = a.item_pt[it];
         if (mode == 0) {
