@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="override n (smaller runs)")
+    ap.add_argument("--mode", default="step", choices=["step", "dims", "paper"],
+                    help="step: the benchmark line; dims: adaptive vs dense cost per evaluation "
+                         "across d; paper: the paper-scale angular arms")
     return ap.parse_args()
 
 
@@ -237,6 +240,19 @@ def run_ours(args):
     names = ["scaffold", "harvest_blocks_no_graph", "final_prune", "search", "dense_blocks"]
     breakdown = {nm: round(evs[i].elapsed_time(evs[i + 1]), 3) for i, nm in enumerate(names)}
     search_evals = float(ev.double().sum().item())
+    # the same blocks replayed as one CUDA graph (with the final graph), against
+    # one launch sequence per block (with the final graph)
+    ixg = fg.fgraft_build_scaffold(X_d, d, params)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(1.0)
+    g0.record(stream)
+    fg.fgraft_harvest_all(ixg, use_graph=True)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    breakdown["harvest_graph_plus_final"] = round(g0.elapsed_time(g1), 3)
+    breakdown["harvest_plain_plus_final"] = round(breakdown["harvest_blocks_no_graph"]
+                                                  + breakdown["final_prune"], 3)
+    del ixg
 
     # ---- end to end through the public API, host buffers ----
     Xh = torch.from_numpy(ps.X).pin_memory()
@@ -374,10 +390,157 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def _sm_clock_mhz():
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=10).stdout.split()
+        return float(out[0])
+    except Exception:
+        return None
+
+
+def run_dims(args):
+    """Cost per distance evaluation of the adaptive harvest and of the dense block,
+    across d (Section 5.4, Table 5): Gaussian mixture, 128 clusters, L2, T = 8, B = 8,
+    R = 32, ef_h = 64, plus byte vectors at d = 128."""
+    import torch
+    from paper_2609_30493_gb300 import build as fgbuild
+    from paper_2609_30493_gb300 import fgraft as fg
+    from paper_2609_30493_gb300 import synth
+    fgbuild.build()
+    fg.load()
+    n = args.n or 1_000_000
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    rows = []
+    for d, kind in [(32, "f32"), (64, "f32"), (128, "f32"), (256, "f32"), (512, "f32"),
+                    (960, "f32"), (128, "u8")]:
+        ps = synth.uint8_mixture(n, d, 128, 0) if kind == "u8" else synth.gaussian_mixture(n, d, 128, 0)
+        X = torch.from_numpy(ps.X).cuda()
+        p = fg.Params(T=8, R=32, ef_h=64, B=8, alpha=1.2, seed=0, metric=ps.metric)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ix = fg.fgraft_build_scaffold(X, d, p)
+        torch.cuda.synchronize()
+        t_sc = time.perf_counter() - t0
+        fg.fgraft_index_profile(ix, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for b in range(8):
+            fg.fgraft_harvest_block(ix, b)
+        e1.record()
+        torch.cuda.synchronize()
+        hms, hl = fg.fgraft_index_harvest_ms(ix)
+        c = fg.fgraft_index_counters(ix)
+        clk = _sm_clock_mhz() or 2070.0
+        evals = c["harvest_evals"]
+        rate = evals / (hms / 1e3)
+        dense = None
+        if kind == "f32":
+            blocks = synth.intra_cluster_blocks(ps.labels, 64, 1024, 2)
+            Bd = torch.from_numpy(blocks).cuda()
+            fg.fgraft_dense_block_dist(X, d, 0, Bd, 32)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record()
+            for _ in range(3):
+                fg.fgraft_dense_block_dist(X, d, 0, Bd, 32)
+            f1.record()
+            torch.cuda.synchronize()
+            dms = f0.elapsed_time(f1) / 3
+            dense = 64 * 1024 * 1023 / (dms / 1e3)
+        row = {"mode": "dims", "d": d, "kind": kind, "n": n, "scaffold_s": round(t_sc, 3),
+               "harvest_ms": round(hms, 2), "harvest_evals": evals,
+               "harvest_evals_per_s": round(rate, 1),
+               "sm_cycles_per_eval": round(hms / 1e3 * clk * 1e6 * nsm / evals, 1),
+               "harvest_bytes_per_eval": 32 * ((ps.X.itemsize * d + 31) // 32),
+               "harvest_GBps": round(rate * 32 * ((ps.X.itemsize * d + 31) // 32) / 1e9, 1),
+               "dense_pairs_per_s": round(dense, 1) if dense else None,
+               "gap_W": round(dense / rate, 2) if dense else None,
+               "reruns": c["reruns"]}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+        del ix, X
+        torch.cuda.empty_cache()
+    f = [r for r in rows if r["kind"] == "f32"]
+    ld = np.log([r["d"] for r in f])
+    ka = np.polyfit(ld, np.log([1.0 / r["harvest_evals_per_s"] for r in f]), 1)[0]
+    kd = np.polyfit(ld, np.log([1.0 / r["dense_pairs_per_s"] for r in f]), 1)[0]
+    print(json.dumps({"mode": "dims-fit", "adaptive_cost_exponent": round(float(ka), 3),
+                      "dense_cost_exponent": round(float(kd), 3),
+                      "gap_exponent": round(float(ka - kd), 3)}), flush=True)
+
+
+def run_paper(args):
+    """Paper-scale angular arms (Section 4, Table 1 shape): n = 1,183,514, d = 100,
+    256 clusters with Zipf(1.1) sizes; frozen T = 32 and FGraft T = 8 at
+    B = 1, 2, 4, 8, 16; R = 64, ef_h = 100; recall@10 and evaluations per query
+    over a beam-width ladder, d@0.95 interpolated (Section 2)."""
+    import torch
+    from paper_2609_30493_gb300 import build as fgbuild
+    from paper_2609_30493_gb300 import fgraft as fg
+    from paper_2609_30493_gb300 import synth
+    fgbuild.build()
+    fg.load()
+    n = args.n or 1_183_514
+    ps = synth.vmf_like(n, 100, 256, 0, 20.0, sizes="zipf")
+    Q = synth.queries(ps, 10_000, 1)
+    X = torch.from_numpy(ps.X).cuda()
+    Qd = torch.from_numpy(Q).cuda()
+    Xt = X[:, :100]
+    gts = []
+    for s0 in range(0, len(Q), 1024):
+        gts.append(torch.topk(Qd[s0:s0 + 1024, :100] @ Xt.T, 10, dim=1).indices.cpu().numpy())
+    gt = np.concatenate(gts)
+    for T, B in [(32, 1), (8, 1), (8, 2), (8, 4), (8, 8), (8, 16)]:
+        p = fg.Params(T=T, R=64, ef_h=100, B=B, alpha=1.2, seed=0, metric=fg.ANGULAR_F32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ix = fg.fgraft_build_scaffold(X, 100, p)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        fg.fgraft_index_profile(ix, True)
+        fg.fgraft_harvest_all(ix, use_graph=True)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        hms, hl = fg.fgraft_index_harvest_ms(ix)
+        c = fg.fgraft_index_counters(ix)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        fg.fgraft_prune(ix)  # the final graph again, timed alone
+        f1.record()
+        torch.cuda.synchronize()
+        final_s = f0.elapsed_time(f1) / 1e3
+        ladder = []
+        for ef in [10, 16, 24, 32, 48, 64, 96, 128]:
+            ids, dist, ev = fg.fgraft_search(ix, Qd, 10, ef)
+            ids = ids.cpu().numpy()
+            rec = float(np.mean([len(set(a.tolist()) & set(b.tolist())) / 10 for a, b in zip(ids, gt)]))
+            ladder.append((ef, rec, float(ev.double().mean().item())))
+        d95 = None
+        for (e0, r0, v0), (e1_, r1, v1) in zip(ladder, ladder[1:]):
+            if r0 < 0.95 <= r1:
+                d95 = v0 + (0.95 - r0) * (v1 - v0) / (r1 - r0)
+        row = {"mode": "paper", "n": n, "T": T, "B": B, "R": 64, "ef_h": 100,
+               "scaffold_s": round(t1 - t0, 3), "harvest_and_final_s": round(t2 - t1, 3),
+               "final_s": round(final_s, 3),
+               "build_s": round(t2 - t0, 3), "pts_per_s": round(n / (t2 - t0), 1),
+               "harvest_kernel_ms": round(hms, 1),
+               "harvest_evals_per_s": round(c["harvest_evals"] / (hms / 1e3), 1),
+               "counters": c, "recall_ladder": ladder,
+               "dist_per_query_at_0.95": round(d95, 1) if d95 else None}
+        print(json.dumps(row), flush=True)
+        del ix
+        torch.cuda.empty_cache()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "dims":
+        run_dims(args)
+    elif args.mode == "paper":
+        run_paper(args)
     else:
         run_ours(args)
 

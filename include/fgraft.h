@@ -224,8 +224,13 @@ fgraft_status fgraft_index_counters(fgraft_index* ix, fgraft_stream stream,
  * depend on it).  The visited set of a search is an n-bit shared-memory
  * bitmap when that is no larger than the hash, else a bucketed hash of
  * 2^hash_log2 slots; giving hash_log2 (7 <= k <= 14) selects the hash of
- * that size.  warps_per_cta: 1..4.  0 leaves a value unchanged. */
-fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t warps_per_cta);
+ * that size.  warps_per_cta: 1..4.  overflow_mode: what a search does when
+ * its visited set outgrows the hash: 1 moves it to a per-warp n-bit bitmap
+ * in global memory and continues (default), 2 abandons the query and runs it
+ * again on global-memory scratch after the launch.  0 leaves a value
+ * unchanged. */
+fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t warps_per_cta,
+                                int32_t overflow_mode);
 
 /* SAT launch configuration for later fgraft_build_scaffold calls in this
  * process (tuning; results do not depend on it): tree nodes holding at least

@@ -133,13 +133,16 @@ struct fgraft_index {
   int64_t ovf_cap = 0;
   char* gscratch = nullptr;
   int64_t gscratch_per_warp = 0;
-  int32_t g_hash_log2 = 0;
   int32_t g_ecap = 0;
   int32_t g_warps = 0;
   unsigned long long* ctr = nullptr;
   int32_t blocks_done = 0;
   int32_t hash_log2 = 12;
   bool bitmap_ok = true;
+  int32_t overflow_mode = 1;   // 1: continue in a global bitmap, 2: abandon and re-run
+  uint32_t* gvbits = nullptr;  // per-warp global bitmaps for visited sets that outgrow the hash
+  int64_t gvbits_words = 0;
+  int64_t gvbits_warps = 0;
   int32_t wpc = 4;
   int32_t num_sms = 0;
   cudaGraphExec_t graph_exec = nullptr;
@@ -235,11 +238,20 @@ int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStrea
   a.vis_bytes = vis_bytes;
   a.vis_cap = bitmap ? INT32_MAX : (int32_t)(0.8 * nslots) - 32;
   a.ecap = ecap;
+  // visited sets that outgrow the hash continue in per-warp global bitmaps
+  // (sized for the largest harvest grid when the index is built or tuned)
+  const int64_t grid_warps = (int64_t)per_sm * ix->num_sms * ix->wpc;
+  const bool migrate = !bitmap && ix->overflow_mode == 1 && grid_warps <= ix->gvbits_warps;
+  a.gvbits = migrate ? ix->gvbits : nullptr;
+  a.gvbits_words = ix->gvbits_words;
   a.wbytes = wbytes;
   a.qbytes = qbytes;
   a.global_scratch = 0;
   a.qlist = nullptr;
   a.qlist_len = nullptr;
+  // the per-warp layout must be complete before any launch
+  if (a.wbytes < a.vis_bytes + 8 * a.ecap + 256 + a.qbytes || a.qbytes < 16 * ix->L.nchunks)
+    return fail(FGRAFT_EINVAL, "internal: harvest shared-memory layout incomplete");
   FG_CUDA(cudaMemsetAsync(ix->work, 0, 3 * sizeof(uint32_t), s));
   if (e0) FG_CUDA(record_event(e0, s));
   kern<<<per_sm * ix->num_sms, ix->wpc * 32, smem, s>>>(a);
@@ -251,18 +263,58 @@ int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStrea
   a.qlist = ix->ovf_list;
   a.qlist_len = ix->work + 2;
   a.work = ix->work + 1;
-  a.hash_log2 = ix->g_hash_log2;
-  a.bitmap = 0;
-  a.vis_bytes = 4 << ix->g_hash_log2;
-  a.vis_cap = (int32_t)(0.8 * (1 << ix->g_hash_log2)) - 32;
+  a.hash_log2 = 7;
+  a.bitmap = 1;  // this warp's n-bit bitmap in gvbits: exact, never full
+  a.vis_bytes = (int32_t)(4 * ix->gvbits_words);
+  a.vis_cap = INT32_MAX;
+  a.gvbits = ix->gvbits;
+  a.gvbits_words = ix->gvbits_words;
   a.ecap = ix->g_ecap;
   a.wbytes = 256 + qbytes;
+  if (ix->gvbits_warps < ix->g_warps || !ix->gvbits)
+    return fail(FGRAFT_EINVAL, "internal: re-run bitmaps missing");
   a.gscratch = ix->gscratch;
   a.gscratch_per_warp = ix->gscratch_per_warp;
   a.counters = ctr;
   kern<<<ix->g_warps / 4, 128, a.wbytes * 4, s>>>(a);
   note_launch();
   FG_CUDA(cudaGetLastError());
+  return 0;
+}
+
+// Per-warp n-bit bitmaps for visited sets that outgrow the shared-memory
+// hash: enough warps for the largest harvest or search grid at the current
+// tuning (and for the re-run pass).  Not called during stream capture.
+int size_visited_bitmaps(fgraft_index* ix) {
+  int64_t need = ix->g_warps;
+  const int nslots = 1 << ix->hash_log2;
+  const int64_t bm_bytes = ((ix->L.n + 127) / 128) * 16;
+  for (int S = 1; S <= 4; S *= 2) {
+    BeamKernelFn kern = beam_kernel_for(ix->L.metric, ix->L.G, ix->L.K, S);
+    if (!kern) continue;
+    const int ecap = 1 << std::max(6, ceil_log2(2 * 32 * S));
+    const bool bitmap = ix->bitmap_ok && bm_bytes <= 4ll * nslots;
+    const int vis_bytes = bitmap ? (int)bm_bytes : 4 * nslots;
+    const int wbytes =
+        vis_bytes + 8 * ecap + (ecap / 8 + 15) / 16 * 16 + 256 + 16 * ix->L.nchunks;
+    FG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 wbytes * ix->wpc));
+    int per_sm = 0;
+    FG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ix->wpc * 32,
+                                                          wbytes * ix->wpc));
+    need = std::max<int64_t>(need, (int64_t)per_sm * ix->num_sms * ix->wpc);
+  }
+  if (need <= ix->gvbits_warps) return 0;
+  if (ix->gvbits) cudaFree(ix->gvbits);
+  ix->gvbits = nullptr;
+  ix->gvbits_warps = 0;
+  ix->gvbits_words = (ix->L.n + 127) / 128 * 4;
+  cudaError_t e = cudaMalloc(&ix->gvbits, sizeof(uint32_t) * ix->gvbits_words * need);
+  if (e != cudaSuccess) {
+    set_error(FGRAFT_ENOMEM, std::string("cudaMalloc(visited bitmaps): ") + cudaGetErrorString(e));
+    return FGRAFT_ENOMEM;
+  }
+  ix->gvbits_warps = need;
   return 0;
 }
 
@@ -305,7 +357,7 @@ void free_index(fgraft_index* ix) {
   for (cudaEvent_t e : ix->ev_end) cudaEventDestroy(e);
   void* ptrs[] = {ix->roots, ix->parents, ix->s_off, ix->s_ids, ix->A,   ix->cnt,
                   ix->r_off, ix->r_ids,   ix->rcnt,  ix->rcur,  ix->f_off, ix->f_ids,
-                  ix->scan_tmp, ix->work, ix->ovf_list, ix->gscratch, ix->ctr};
+                  ix->scan_tmp, ix->work, ix->ovf_list, ix->gscratch, ix->ctr, ix->gvbits};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete ix;
@@ -398,13 +450,13 @@ fgraft_status fgraft_build_scaffold(const void* X, int64_t n, int32_t d, int64_t
   ix->ovf_cap = std::max<int64_t>(n, 1 << 16);
   rc = rc ? rc : dalloc(&ix->ovf_list, ix->ovf_cap);
   rc = rc ? rc : dalloc(&ix->ctr, C_COUNT);
-  // re-run scratch: visited slots for any beam over n points, expanded list
-  ix->g_hash_log2 = std::min(22, std::max(12, ceil_log2((int64_t)(n / 0.8) + 64)));
+  // re-run scratch: expanded list (up to 2^20 entries) and alive bits per warp;
+  // the re-run's visited sets are the first g_warps bitmaps of gvbits
   ix->g_ecap = 1 << std::min(20, std::max(12, ceil_log2(std::min<int64_t>(n, 1 << 20))));
   ix->g_warps = 64;
-  ix->gscratch_per_warp =
-      ((4ll << ix->g_hash_log2) + 8ll * ix->g_ecap + ix->g_ecap / 4 + 255) / 256 * 256;
+  ix->gscratch_per_warp = (8ll * ix->g_ecap + ix->g_ecap / 8 + 255) / 256 * 256;
   rc = rc ? rc : dalloc(&ix->gscratch, ix->gscratch_per_warp * ix->g_warps);
+  if (!rc) rc = size_visited_bitmaps(ix);
   if (rc) {
     free_index(ix);
     return (fgraft_status)rc;
@@ -714,8 +766,12 @@ fgraft_status fgraft_index_counters(fgraft_index* ix, fgraft_stream stream,
   return (fgraft_status)read_counters(ix, reinterpret_cast<cudaStream_t>(stream), counters);
 }
 
-fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t warps_per_cta) {
+fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t warps_per_cta,
+                                int32_t overflow_mode) {
   if (!ix) return (fgraft_status)fail(FGRAFT_EINVAL, "index is NULL");
+  if (overflow_mode < 0 || overflow_mode > 2)
+    return (fgraft_status)fail(FGRAFT_EINVAL, "overflow_mode must be 0, 1 or 2");
+  if (overflow_mode) ix->overflow_mode = overflow_mode;
   if (hash_log2 && (hash_log2 < 7 || hash_log2 > 14))
     return (fgraft_status)fail(FGRAFT_EINVAL, "hash_log2 must be in [7, 14]");
   if (warps_per_cta && (warps_per_cta < 1 || warps_per_cta > 4))
@@ -725,6 +781,8 @@ fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t war
     ix->bitmap_ok = false;  // an explicit hash size selects the hash
   }
   if (warps_per_cta) ix->wpc = warps_per_cta;
+  const int rc = size_visited_bitmaps(ix);
+  if (rc) return (fgraft_status)rc;
   if (ix->graph_exec) {
     cudaGraphExecDestroy(ix->graph_exec);
     ix->graph_exec = nullptr;

@@ -64,6 +64,10 @@ struct BeamArgs {
   int32_t bitmap;     // 1: visited set is an n-bit bitmap, 0: bucketed hash
   int32_t vis_bytes;  // bytes of the visited region per warp (multiple of 16)
   int32_t vis_cap;
+  // per-warp n-bit bitmaps in global memory: a query whose hash fills up moves
+  // its visited ids there and continues (NULL: abandon and re-run instead)
+  uint32_t* gvbits;
+  int64_t gvbits_words;  // per warp, a multiple of 4
   int32_t ecap;  // power of two, >= 32
   int32_t wbytes;  // shared bytes per warp
   int32_t qbytes;  // staging bytes per warp for one vector (16 * nchunks, rounded)
@@ -116,16 +120,27 @@ struct Beam {
     unsigned char* wsm = smem + (int64_t)wib * a.wbytes;
     const uint32_t nslots = 1u << a.hash_log2;
     const uint32_t mask_buckets = nslots / 4 - 1;
-    unsigned char* vbase = a.global_scratch
-                               ? reinterpret_cast<unsigned char*>(a.gscratch + gwarp * a.gscratch_per_warp)
-                               : wsm;
-    uint32_t* hash = reinterpret_cast<uint32_t*>(vbase);
-    uint64_t* E = reinterpret_cast<uint64_t*>(vbase + a.vis_bytes);
-    uint32_t* alive = reinterpret_cast<uint32_t*>(vbase + a.vis_bytes + 8ll * a.ecap);
-    // the alive bits take ecap/8 bytes, rounded up so that the staged vector
-    // after the queue keeps its 16-byte alignment
-    unsigned char* tail =
-        a.global_scratch ? wsm : wsm + a.vis_bytes + 8ll * a.ecap + ((a.ecap / 8 + 15) & ~15);
+    // Shared-memory pass: [visited | expanded list | alive bits | queue | staged vector]
+    // per warp.  Re-run pass (global_scratch): the visited set is this warp's
+    // n-bit bitmap in gvbits, the expanded list and alive bits live in gscratch,
+    // and shared memory holds only the queue and the staged vector.
+    uint32_t* vis0;
+    uint64_t* E;
+    uint32_t* alive;
+    unsigned char* tail;
+    if (a.global_scratch) {
+      vis0 = a.gvbits + gwarp * a.gvbits_words;
+      E = reinterpret_cast<uint64_t*>(a.gscratch + gwarp * a.gscratch_per_warp);
+      alive = reinterpret_cast<uint32_t*>(E + a.ecap);
+      tail = wsm;
+    } else {
+      vis0 = reinterpret_cast<uint32_t*>(wsm);
+      E = reinterpret_cast<uint64_t*>(wsm + a.vis_bytes);
+      alive = reinterpret_cast<uint32_t*>(wsm + a.vis_bytes + 8ll * a.ecap);
+      // the alive bits take ecap/8 bytes, rounded up so that the staged vector
+      // after the queue keeps its 16-byte alignment
+      tail = wsm + a.vis_bytes + 8ll * a.ecap + ((a.ecap / 8 + 15) & ~15);
+    }
     int32_t* queue = reinterpret_cast<int32_t*>(tail);
     uint4* qs = reinterpret_cast<uint4*>(tail + 256);
     const int64_t nwork =
@@ -147,9 +162,11 @@ struct Beam {
         qrow = a.Q + qidx * a.ldq_bytes;
       }
       stage_row(qs, qrow, a.nchunks, lane);
+      uint32_t* hash = vis0;
+      bool bm = a.bitmap != 0;
+      int vis_cap = a.vis_cap;
       {
-        const uint4 fill = a.bitmap ? make_uint4(0u, 0u, 0u, 0u)
-                                    : make_uint4(EMPTY, EMPTY, EMPTY, EMPTY);
+        const uint4 fill = bm ? make_uint4(0u, 0u, 0u, 0u) : make_uint4(EMPTY, EMPTY, EMPTY, EMPTY);
         for (int i = lane; i < a.vis_bytes / 16; i += 32) reinterpret_cast<uint4*>(hash)[i] = fill;
       }
       __syncwarp();
@@ -183,7 +200,7 @@ struct Beam {
           }
           bool isnew = false;
           if (v >= 0) {
-            if (a.bitmap) {
+            if (bm) {
               const uint32_t bit = 1u << (v & 31);
               isnew = (atomicOr(hash + (v >> 5), bit) & bit) == 0u;
             } else {
@@ -195,9 +212,24 @@ struct Beam {
           qn += __popc(m);
           nvis += __popc(m);
           __syncwarp();
-          if (nvis > a.vis_cap) {
-            ovf = true;
-            break;
+          if (nvis > vis_cap) {
+            if (a.gvbits == nullptr) {
+              ovf = true;
+              break;
+            }
+            // move the hash's ids into this warp's global bitmap and go on
+            uint32_t* gb = a.gvbits + gwarp * a.gvbits_words;
+            for (int64_t w = lane; w < a.gvbits_words / 4; w += 32)
+              reinterpret_cast<uint4*>(gb)[w] = make_uint4(0u, 0u, 0u, 0u);
+            __syncwarp();
+            for (uint32_t slot = lane; slot < nslots; slot += 32) {
+              const uint32_t id = hash[slot];
+              if (id != EMPTY) atomicOr(gb + (id >> 5), 1u << (id & 31));
+            }
+            __syncwarp();
+            hash = gb;
+            bm = true;
+            vis_cap = INT_MAX;
           }
           if (qn >= 32) {
             eval_merge(a, qs, queue, 32, pool, lane);

@@ -175,8 +175,10 @@ def fgraft_index_counters(ix: Index) -> dict:
     return _counters_dict(ctr)
 
 
-def fgraft_index_tune(ix: Index, hash_log2: int = 0, warps_per_cta: int = 0):
-    _check(load().fgraft_index_tune(ix.handle, C.c_int32(hash_log2), C.c_int32(warps_per_cta)))
+def fgraft_index_tune(ix: Index, hash_log2: int = 0, warps_per_cta: int = 0,
+                      overflow_mode: int = 0):
+    _check(load().fgraft_index_tune(ix.handle, C.c_int32(hash_log2), C.c_int32(warps_per_cta),
+                                    C.c_int32(overflow_mode)))
 
 
 def fgraft_index_profile(ix: Index, enable: bool = True):

@@ -33,12 +33,13 @@ def _np(t):
     return t.cpu().numpy()
 
 
-def _build_both(fg, ps, T, R, ef, B, alpha=1.2, seed=0, use_graph=False, hash_log2=0):
+def _build_both(fg, ps, T, R, ef, B, alpha=1.2, seed=0, use_graph=False, hash_log2=0,
+                overflow_mode=0):
     X = _dev(ps.X)
     p = fg.Params(T=T, R=R, ef_h=ef, B=B, alpha=alpha, seed=seed, metric=ps.metric)
     ix, c0 = fg.fgraft_build_scaffold(X, ps.d, p, counters=True)
-    if hash_log2:
-        fg.fgraft_index_tune(ix, hash_log2=hash_log2)
+    if hash_log2 or overflow_mode:
+        fg.fgraft_index_tune(ix, hash_log2=hash_log2, overflow_mode=overflow_mode)
     ctr = fg.fgraft_harvest_all(ix, use_graph=use_graph, counters=True)
     off, ids = fg.fgraft_prune(ix)
     st = fg.fgraft_index_copy(ix)
@@ -106,13 +107,23 @@ def test_shapes_parity(fg, case):
     _compare(ctr, st, fin, ref)
 
 
-def test_overflow_rerun_is_exact(fg):
-    # a 128-slot visited set overflows for most queries; the global-memory
-    # re-run must give the same graph and counters
+@pytest.mark.parametrize("mode", [1, 2])
+def test_overflow_is_exact(fg, mode):
+    # a 128-slot visited set overflows for most queries; moving to the global
+    # bitmap (mode 1) or re-running on global scratch (mode 2) must give the
+    # same graph and counters
     ps = synth.gaussian_mixture(2000, 16, 8, seed=0)
-    ix, ctr, st, fin, D, ref = _build_both(fg, ps, T=4, R=16, ef=32, B=4, hash_log2=7)
-    assert ctr["reruns"] > 0
+    ix, ctr, st, fin, D, ref = _build_both(fg, ps, T=4, R=16, ef=32, B=4, hash_log2=7,
+                                           overflow_mode=mode)
+    if mode == 2:
+        assert ctr["reruns"] > 0
+    else:
+        assert ctr["reruns"] == 0
     _compare(ctr, st, fin, ref)
+    Q = synth.queries(ps, 100, 1)
+    gi, gd, ge = fg.fgraft_search(ix, _dev(Q), 10, 32)
+    oi, od, oe = oracle.search(D, ref["f_off"], ref["f_ids"], ref["roots"], Q, 10, 32)
+    assert np.array_equal(_np(gi), oi) and np.array_equal(_np(gd), od)
 
 
 def test_edge_cases(fg):
