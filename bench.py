@@ -177,7 +177,8 @@ def run_ours(args):
             fg.fgraft_index_profile(ix, True)
         fg.fgraft_harvest_all(ix, use_graph=True)
         ids, dist_, ev = fg.fgraft_search(ix, Q_t, spec["topk"], spec["ef_s"])
-        di, dd = fg.fgraft_dense_block_dist(X_t, d, fg.ANGULAR_F32, B_t, spec["dense_k"])
+        di, dd = fg.fgraft_dense_block_dist(X_t, d, fg.ANGULAR_F32, B_t, spec["dense_k"],
+                                            precision=1)
         return ix, ids, di
 
     for _ in range(args.warmup):
@@ -234,7 +235,8 @@ def run_ours(args):
     evs[3].record(stream)
     ids, dist_, ev = fg.fgraft_search(ix, Q_d, spec["topk"], spec["ef_s"])
     evs[4].record(stream)
-    di, dd = fg.fgraft_dense_block_dist(X_d, d, fg.ANGULAR_F32, B_d, spec["dense_k"])
+    di, dd, dst = fg.fgraft_dense_block_dist(X_d, d, fg.ANGULAR_F32, B_d, spec["dense_k"],
+                                             precision=1, stats=True)
     evs[5].record(stream)
     torch.cuda.synchronize()
     names = ["scaffold", "harvest_blocks_no_graph", "final_prune", "search", "dense_blocks"]
@@ -273,7 +275,8 @@ def run_ours(args):
         fg.fgraft_harvest_all(ix2, use_graph=True)
         off2, gids2 = fg.fgraft_prune(ix2)
         ids2, dist2, ev2 = fg.fgraft_search(ix2, Qd2, spec["topk"], spec["ef_s"])
-        di2, dd2 = fg.fgraft_dense_block_dist(Xd2, d, fg.ANGULAR_F32, Bd2, spec["dense_k"])
+        di2, dd2 = fg.fgraft_dense_block_dist(Xd2, d, fg.ANGULAR_F32, Bd2, spec["dense_k"],
+                                              precision=1)
         outs = [off2.cpu(), gids2.cpu(), ids2.cpu(), dist2.cpu(), di2.cpu(), dd2.cpu()]
         e1.record(stream)
         torch.cuda.synchronize()
@@ -324,6 +327,9 @@ def run_ours(args):
         "recall_at_10": round(rec, 4),
         "search_evals_per_query": round(search_evals / spec["nq"], 1),
         "dense_pairs_per_s": round(dense_pairs / (breakdown["dense_blocks"] / 1e3), 1),
+        "dense_gram_pairs_per_s": round(dense_pairs / (dst[1] / 1e3), 1) if dst[1] else None,
+        "dense_gram_tflops": round(2 * d * dense_pairs / (dst[1] / 1e3) / 1e12, 2) if dst[1] else None,
+        "dense_rerank_fraction": round(dst[0], 5),
         "breakdown_ms": breakdown,
         "e2e": {"value": round(e2e_value, 1), "unit": "pts/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -434,20 +440,27 @@ def run_dims(args):
         clk = _sm_clock_mhz() or 2070.0
         evals = c["harvest_evals"]
         rate = evals / (hms / 1e3)
-        dense = None
+        dense = dense_simt = gram = rerank = None
         if kind == "f32":
             blocks = synth.intra_cluster_blocks(ps.labels, 64, 1024, 2)
             Bd = torch.from_numpy(blocks).cuda()
-            fg.fgraft_dense_block_dist(X, d, 0, Bd, 32)
-            torch.cuda.synchronize()
-            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            f0.record()
-            for _ in range(3):
-                fg.fgraft_dense_block_dist(X, d, 0, Bd, 32)
-            f1.record()
-            torch.cuda.synchronize()
-            dms = f0.elapsed_time(f1) / 3
-            dense = 64 * 1024 * 1023 / (dms / 1e3)
+            pairs = 64 * 1024 * 1023
+            for prec in (0, 1):
+                fg.fgraft_dense_block_dist(X, d, 0, Bd, 32, precision=prec)
+                torch.cuda.synchronize()
+                f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                f0.record()
+                for _ in range(3):
+                    _, _, st = fg.fgraft_dense_block_dist(X, d, 0, Bd, 32, precision=prec,
+                                                          stats=True)
+                f1.record()
+                torch.cuda.synchronize()
+                rate = pairs / (f0.elapsed_time(f1) / 3 / 1e3)
+                if prec == 0:
+                    dense_simt = rate
+                else:
+                    dense, gram, rerank = rate, pairs / (st[1] / 1e3), st[0]
+            rate = evals / (hms / 1e3)
         row = {"mode": "dims", "d": d, "kind": kind, "n": n, "scaffold_s": round(t_sc, 3),
                "harvest_ms": round(hms, 2), "harvest_evals": evals,
                "harvest_evals_per_s": round(rate, 1),
@@ -455,7 +468,11 @@ def run_dims(args):
                "harvest_bytes_per_eval": 32 * ((ps.X.itemsize * d + 31) // 32),
                "harvest_GBps": round(rate * 32 * ((ps.X.itemsize * d + 31) // 32) / 1e9, 1),
                "dense_pairs_per_s": round(dense, 1) if dense else None,
+               "dense_gram_pairs_per_s": round(gram, 1) if gram else None,
+               "dense_rerank_fraction": round(rerank, 5) if rerank is not None else None,
+               "dense_simt_pairs_per_s": round(dense_simt, 1) if dense_simt else None,
                "gap_W": round(dense / rate, 2) if dense else None,
+               "gap_W_gram": round(gram / rate, 2) if gram else None,
                "reruns": c["reruns"]}
         rows.append(row)
         print(json.dumps(row), flush=True)
@@ -465,9 +482,12 @@ def run_dims(args):
     ld = np.log([r["d"] for r in f])
     ka = np.polyfit(ld, np.log([1.0 / r["harvest_evals_per_s"] for r in f]), 1)[0]
     kd = np.polyfit(ld, np.log([1.0 / r["dense_pairs_per_s"] for r in f]), 1)[0]
+    kg = np.polyfit(ld, np.log([1.0 / r["dense_gram_pairs_per_s"] for r in f]), 1)[0]
     print(json.dumps({"mode": "dims-fit", "adaptive_cost_exponent": round(float(ka), 3),
                       "dense_cost_exponent": round(float(kd), 3),
-                      "gap_exponent": round(float(ka - kd), 3)}), flush=True)
+                      "gap_exponent": round(float(ka - kd), 3),
+                      "gram_cost_exponent": round(float(kg), 3),
+                      "gram_gap_exponent": round(float(ka - kg), 3)}), flush=True)
 
 
 def run_paper(args):

@@ -191,15 +191,25 @@ fgraft_status fgraft_search(fgraft_index* ix, const void* Q, int64_t nq, int64_t
 
 /* Dense-block ceiling (Section 5.3: the pair set fixed in advance that a
  * blocked kernel evaluates at arithmetic rate).  block_ids holds nb blocks of
- * bs ids (-1 = padding).  For every valid member i of a block and every other
- * valid member j, delta(x_i, x_j) is taken, and out_ids/out_dist
- * (nb*bs*k) receive the k smallest (delta, id) per row (-1 / +inf fill).
- * precision 0 evaluates every pair in the canonical float32 order.
- * Float32 metrics only; bs <= 1024, k <= 64. */
+ * bs ids (-1 = padding; ids of a block distinct).  For every valid member i
+ * of a block and every other valid member j, delta(x_i, x_j) is taken, and
+ * out_ids/out_dist (nb*bs*k) receive the k smallest (delta, id) per row
+ * (-1 / +inf fill).  The result is the canonical float32 top-k whatever the
+ * precision:
+ *   precision 0  every pair in the canonical float32 order (CUDA cores);
+ *   precision 1  BF16 tensor-core filter (tcgen05, FP32 accumulation) on the
+ *                block centred on its mean, then every pair within twice a
+ *                rounding-error bound of the k-th approximate distance is
+ *                recomputed in the canonical order.
+ * stats (host, optional, 4 doubles; the call then synchronises `stream`):
+ * fraction of pairs recomputed, Gram-kernel ms, select ms, prep ms
+ * (precision 1; zeros for precision 0).  Float32 metrics only; bs <= 1024,
+ * k <= 64, nb <= 65535.  Precision 1 allocates its scratch stream-ordered and
+ * synchronises `stream` to check its bounded waits (FGRAFT_ETIMEOUT). */
 fgraft_status fgraft_dense_block_dist(const void* X, int64_t n, int32_t d, int64_t ld,
                                       int32_t metric, const int32_t* block_ids, int64_t nb,
                                       int32_t bs, int32_t k, int32_t precision, int32_t* out_ids,
-                                      float* out_dist, fgraft_stream stream);
+                                      float* out_dist, double* stats, fgraft_stream stream);
 
 /* Inspection: copies of the index's state into caller buffers (device).
  * roots: T; parents: T*n (parent of every point in each tree, -1 at the

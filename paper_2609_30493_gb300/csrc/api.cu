@@ -708,18 +708,25 @@ fgraft_status fgraft_search(fgraft_index* ix, const void* Q, int64_t nq, int64_t
 fgraft_status fgraft_dense_block_dist(const void* X, int64_t n, int32_t d, int64_t ld,
                                       int32_t metric, const int32_t* block_ids, int64_t nb,
                                       int32_t bs, int32_t k, int32_t precision, int32_t* out_ids,
-                                      float* out_dist, fgraft_stream stream) {
+                                      float* out_dist, double* stats, fgraft_stream stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   VecLayout L;
   int rc = check_vectors(X, n, d, ld, metric, &L);
   if (rc) return (fgraft_status)rc;
   if (metric == L2_U8) return (fgraft_status)fail(FGRAFT_EINVAL, "dense blocks take float32 metrics");
-  if (precision != 0) return (fgraft_status)fail(FGRAFT_EINVAL, "precision must be 0 (float32)");
-  if (nb < 0 || bs < 1 || bs > 1024 || k < 1 || k > 64)
-    return (fgraft_status)fail(FGRAFT_EINVAL, "need bs in [1,1024], k in [1,64]");
+  if (precision != 0 && precision != 1)
+    return (fgraft_status)fail(FGRAFT_EINVAL, "precision must be 0 (float32) or 1 (BF16 filter)");
+  if (nb < 0 || nb > 65535 || bs < 1 || bs > 1024 || k < 1 || k > 64)
+    return (fgraft_status)fail(FGRAFT_EINVAL, "need nb <= 65535, bs in [1,1024], k in [1,64]");
+  if (stats)
+    for (int i = 0; i < 4; ++i) stats[i] = 0.0;
   if (nb == 0) return FGRAFT_OK;
   if (!block_ids || !out_ids || !out_dist) return (fgraft_status)fail(FGRAFT_EINVAL, "NULL pointer");
-  return (fgraft_status)dense_block(L, block_ids, nb, bs, k, out_ids, out_dist, s);
+  if (precision == 1)
+    return (fgraft_status)dense_block_tc(L, block_ids, nb, bs, k, out_ids, out_dist, stats, s);
+  rc = dense_block(L, block_ids, nb, bs, k, out_ids, out_dist, s);
+  if (!rc && stats) FGS(cudaStreamSynchronize(s));
+  return (fgraft_status)rc;
 }
 
 fgraft_status fgraft_index_copy(const fgraft_index* ix, int32_t* roots, int32_t* parents,

@@ -1,0 +1,506 @@
+// Dense-block ceiling on the 5th-generation tensor cores (Section 5.3: a pair
+// set fixed before evaluation is a dense product and runs at arithmetic rate).
+//
+// Each block of up to 1024 points is centred on its float32 mean and rounded
+// to BF16; its Gram matrix is computed by tcgen05.mma (kind::f16, BF16 in,
+// FP32 accumulated in tensor memory), one 128 x 256 tile per CTA, and turned
+// into approximate distances.  They are only a filter: per row, every pair
+// whose approximate distance is within 2*eps of the k-th smallest is
+// recomputed in the canonical float32 order and the k smallest (delta, id) are
+// selected from those, where eps bounds |approximate - canonical| for the row
+// (BF16 input rounding, FP32 accumulation in any order, the canonical sum's
+// own rounding; times 2).  For every pair of the exact top-k,
+// approx <= canonical + eps <= k-th canonical + eps <= k-th approx + 2 eps, so
+// the result equals the canonical float32 top-k.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+#include "rowops.cuh"
+
+namespace fg {
+
+constexpr int TC_ROWS = 1024;  // rows of a block after padding
+constexpr int TC_M = 128;      // rows per CTA (one per TMEM lane)
+constexpr int TC_N = 256;      // columns per CTA (TMEM columns)
+constexpr int TC_K = 64;       // K elements per staged slice (8 core matrices)
+constexpr int TC_THREADS = 128;
+constexpr uint32_t TC_TMEM_COLS = 256;
+
+// --------------------------------------------------------------------------
+// PTX wrappers (tcgen05, mbarrier, proxy fences)
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulator
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+      "[%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor, no swizzle, K-major: core matrices of
+// 8 rows x 16 bytes, `lbo` bytes apart along K, `sbo` bytes apart along M/N.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of this architecture
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = FP32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (row r, k) of a staged K-slice: core matrix
+// (r/8, k/8) at (r/8)*1024 + (k/8)*128, row r%8 at +16*(r%8).
+__host__ __device__ constexpr uint32_t tile_off(int r, int k) {
+  return (uint32_t)((r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// --------------------------------------------------------------------------
+// 1. Centre, round to BF16, norms
+// --------------------------------------------------------------------------
+struct TcArgs {
+  const char* X;
+  int64_t ld_bytes;
+  int32_t d;
+  int32_t dpad;  // d rounded up to TC_K
+  int32_t metric;
+  const int32_t* block_ids;
+  int64_t nb;
+  int32_t bs;
+  __nv_bfloat16* Xb;  // [nb][1024][dpad]
+  float* nrm;         // [nb][1024] squared norm of the centred float32 row
+  float* cc;          // [nb][1024] angular: (1 - |x|^2) / 2
+  float* Mx;          // [nb] largest centred norm
+  float* LP;          // [nb][1024][1024] approximate distances
+  uint32_t* err;
+  unsigned long long* pairs;  // valid ordered pairs over all blocks
+};
+
+__global__ void __launch_bounds__(256) dense_prep_kernel(const TcArgs a) {
+  __shared__ float mu[1024];
+  __shared__ int nvalid;
+  const int64_t blk = blockIdx.x;
+  const int32_t* ids = a.block_ids + blk * a.bs;
+  if (threadIdx.x == 0) nvalid = 0;
+  __syncthreads();
+  int cnt = 0;
+  for (int r = threadIdx.x; r < a.bs; r += blockDim.x) cnt += ids[r] >= 0;
+  atomicAdd(&nvalid, cnt);
+  __syncthreads();
+  const float inv = nvalid > 0 ? 1.0f / (float)nvalid : 0.0f;
+  if (threadIdx.x == 0 && nvalid > 1)
+    atomicAdd(a.pairs, (unsigned long long)nvalid * (unsigned long long)(nvalid - 1));
+  for (int j = threadIdx.x; j < a.d; j += blockDim.x) {
+    float s = 0.0f;
+    for (int r = 0; r < a.bs; ++r) {
+      const int32_t id = ids[r];
+      if (id >= 0) s += reinterpret_cast<const float*>(a.X + (int64_t)id * a.ld_bytes)[j];
+    }
+    mu[j] = s * inv;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = warp; r < TC_ROWS; r += 8) {
+    const int32_t id = r < a.bs ? ids[r] : -1;
+    __nv_bfloat16* dst = a.Xb + (blk * TC_ROWS + r) * (int64_t)a.dpad;
+    float s2 = 0.0f, x2 = 0.0f;
+    const float* xr = id >= 0 ? reinterpret_cast<const float*>(a.X + (int64_t)id * a.ld_bytes)
+                              : nullptr;
+    for (int j = lane; j < a.dpad; j += 32) {
+      float v = 0.0f;
+      if (id >= 0 && j < a.d) {
+        const float x = xr[j];
+        v = x - mu[j];
+        x2 = __fmaf_rn(x, x, x2);
+      }
+      s2 = __fmaf_rn(v, v, s2);
+      dst[j] = __float2bfloat16_rn(v);
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      s2 += __shfl_xor_sync(FULL, s2, off);
+      x2 += __shfl_xor_sync(FULL, x2, off);
+    }
+    if (lane == 0) {
+      a.nrm[blk * TC_ROWS + r] = s2;
+      a.cc[blk * TC_ROWS + r] = id >= 0 ? 0.5f * (1.0f - x2) : 0.0f;
+      if (id >= 0) atomicMax(reinterpret_cast<unsigned int*>(a.Mx + blk), __float_as_uint(sqrtf(s2)));
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// 2. Gram tile on the tensor cores and approximate distances
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(TC_THREADS) dense_gram_kernel(const TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  unsigned char* As = tsm;                      // 128 x 64 BF16 = 16 KB
+  unsigned char* Bs = tsm + TC_M * TC_K * 2;    // 256 x 64 BF16 = 32 KB
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + TC_N * TC_K * 2);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int rt = blockIdx.x, ct = blockIdx.y;
+  const int64_t blk = blockIdx.z;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, TC_TMEM_COLS);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const __nv_bfloat16* Ag = a.Xb + (blk * TC_ROWS + rt * TC_M) * (int64_t)a.dpad;
+  const __nv_bfloat16* Bg = a.Xb + (blk * TC_ROWS + ct * TC_N) * (int64_t)a.dpad;
+  constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
+  bool ok = true;
+  const int nslices = a.dpad / TC_K;
+  for (int sl = 0; sl < nslices; ++sl) {
+    const int k0 = sl * TC_K;
+    // stage the slices: 16-byte units (row, 8 K elements), 8 per row
+    for (int u = tid; u < TC_M * 8; u += TC_THREADS) {
+      const int r = u >> 3, kc = u & 7;
+      *reinterpret_cast<uint4*>(As + tile_off(r, kc * 8)) =
+          *reinterpret_cast<const uint4*>(Ag + (int64_t)r * a.dpad + k0 + kc * 8);
+    }
+    for (int u = tid; u < TC_N * 8; u += TC_THREADS) {
+      const int r = u >> 3, kc = u & 7;
+      *reinterpret_cast<uint4*>(Bs + tile_off(r, kc * 8)) =
+          *reinterpret_cast<const uint4*>(Bg + (int64_t)r * a.dpad + k0 + kc * 8);
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+#pragma unroll
+      for (int kk = 0; kk < TC_K / 16; ++kk) {
+        // a K=16 step spans two core matrices along K (2 x 128 bytes)
+        mma_bf16(tmem, smem_desc(a0 + kk * 256, 128, 1024), smem_desc(b0 + kk * 256, 128, 1024),
+                 idesc, (sl > 0 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(bar);
+    }
+    // wait (bounded) for the slice's products before its buffers are reused;
+    // every thread takes the same decision
+    bool done = false;
+    for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(bar, sl & 1);
+    done = __syncthreads_and(done);
+    if (!done) {
+      ok = false;
+      if (tid == 0) atomicOr(a.err, 1u);
+      break;
+    }
+    tc_fence_after();
+  }
+
+  if (ok) {
+    // epilogue: warp w reads TMEM lanes 32w..32w+31 (rows), 32 columns at a time
+    const int i = rt * TC_M + warp * 32 + lane;
+    const int64_t rowbase = blk * TC_ROWS;
+    const float ni = a.nrm[rowbase + i];
+    const float ci = a.cc[rowbase + i];
+    float* out = a.LP + (rowbase + i) * (int64_t)TC_ROWS + ct * TC_N;
+    for (int c0 = 0; c0 < TC_N; c0 += 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+      for (int t = 0; t < 32; ++t) {
+        const int j = ct * TC_N + c0 + t;
+        const float g = __uint_as_float(v[t]);
+        const float s = a.nrm[rowbase + j] + ni - 2.0f * g;
+        out[c0 + t] = a.metric == ANGULAR_F32 ? 0.5f * s + ci + a.cc[rowbase + j] : s;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, TC_TMEM_COLS);
+}
+
+// --------------------------------------------------------------------------
+// 3. Per row: filter threshold, canonical rerank of the candidates, top-k
+// --------------------------------------------------------------------------
+constexpr int SEL_WARPS = 4;
+
+template <int METRIC, int G, int K>
+__global__ void __launch_bounds__(SEL_WARPS * 32)
+    dense_select_kernel(const TcArgs a, int k, int32_t* out_ids, float* out_dist,
+                        unsigned long long* reranked) {
+  using L = Lanes<G, K>;
+  extern __shared__ __align__(16) unsigned char ssm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane / L::P, j = lane % L::P;
+  const int nch = (a.d * 4 + 15) / 16;
+  const int wbytes = 8 * TC_ROWS + 16 * nch;
+  uint64_t* keys = reinterpret_cast<uint64_t*>(ssm + warp * wbytes);
+  uint4* qs = reinterpret_cast<uint4*>(ssm + warp * wbytes + 8 * TC_ROWS);
+  const int64_t rows = a.nb * a.bs;
+  const float u_b = 1.0f / 256.0f, gam = 1.0f / 16777216.0f;
+  const float dk = (float)(a.d + 8);
+  unsigned long long nre = 0;
+  for (int64_t r = (int64_t)blockIdx.x * SEL_WARPS + warp; r < rows;
+       r += (int64_t)gridDim.x * SEL_WARPS) {
+    const int64_t blk = r / a.bs;
+    const int i = (int)(r - blk * a.bs);
+    const int32_t* ids = a.block_ids + blk * a.bs;
+    const int32_t xi = ids[i];
+    int kk = 0;
+    if (xi >= 0) {
+      const float* lp = a.LP + (blk * TC_ROWS + i) * (int64_t)TC_ROWS;
+      for (int c = lane; c < TC_ROWS; c += 32) {
+        const bool valid = c < a.bs && c != i && ids[c] >= 0;
+        keys[c] = valid ? (((uint64_t)fkey(lp[c]) << 32) | (uint32_t)c) : PAD;
+      }
+      __syncwarp();
+      warp_sort_mem(keys, TC_ROWS, lane);
+      int nv = 0;
+      for (int base = 0; base < TC_ROWS; base += 32)
+        nv += __popc(__ballot_sync(FULL, keys[base + lane] != PAD));
+      // eps for this row (see the file header)
+      const float Ai = sqrtf(a.nrm[blk * TC_ROWS + i]), M = a.Mx[blk];
+      float eps = 2.0f * ((4.0f * u_b + 6.0f * dk * gam) * Ai * M +
+                          6.0f * dk * gam * (Ai * Ai + M * M));
+      if (a.metric == ANGULAR_F32) eps = 0.5f * eps + 2.0f * (3.0f * dk * gam + 2.0f * gam);
+      int cand = nv;
+      if (nv > k) {
+        const float tau = fkey_inv((uint32_t)(keys[k - 1] >> 32));
+        const float theta = tau + 2.0f * eps;
+        cand = 0;
+        for (int base = 0; base < nv; base += 32) {
+          const int c = base + lane;
+          const bool in = c < nv && fkey_inv((uint32_t)(keys[c] >> 32)) <= theta;
+          cand += __popc(__ballot_sync(FULL, in));
+        }
+      }
+      nre += (unsigned long long)cand;
+      // canonical distances of the candidates, in place
+      stage_row(qs, a.X + (int64_t)xi * a.ld_bytes, nch, lane);
+      for (int base = 0; base < cand; base += L::CPW) {
+        const int c = base + g;
+        // groups past the candidates load the row's own vector (keys[0..base)
+        // already hold (distance, id) keys, not column indices)
+        const int32_t cid = c < cand ? ids[(int)(uint32_t)keys[c]] : xi;
+        uint4 y[L::VL][K];
+        load_slots<G, K>(a.X + (int64_t)cid * a.ld_bytes, nch, j, y);
+        const float dd = slots_dist<METRIC, G, K>(qs, y, nch, a.d, j);
+        __syncwarp();
+        if (c < cand && j == 0) keys[c] = make_key(dd, cid);
+        __syncwarp();
+      }
+      kk = sort_unique(keys, cand, lane);
+      kk = kk < k ? kk : k;
+    }
+    for (int t = lane; t < k; t += 32) {
+      out_ids[r * k + t] = t < kk ? key_id(keys[t]) : -1;
+      out_dist[r * k + t] = t < kk ? key_dist(keys[t]) : __int_as_float(0x7f800000);
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && nre) atomicAdd(reranked, nre);
+}
+
+using SelectFn = void (*)(const TcArgs, int, int32_t*, float*, unsigned long long*);
+
+static SelectFn select_kernel_for(int metric, int G, int K) {
+#define SX(M, GG, KK) \
+  if (metric == M && G == GG && K == KK) return dense_select_kernel<M, GG, KK>;
+#define SF(M) SX(M, 4, 1) SX(M, 8, 1) SX(M, 16, 1) SX(M, 32, 1) SX(M, 32, 2) SX(M, 32, 4) \
+  SX(M, 32, 8)
+  SF(0)
+  SF(1)
+#undef SF
+#undef SX
+  return nullptr;
+}
+
+int dense_block_tc(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs, int k,
+                   int32_t* out_ids, float* out_dist, double* stats, cudaStream_t s) {
+  SelectFn sel = select_kernel_for(L.metric, L.G, L.K);
+  if (!sel || L.metric == L2_U8) {
+    set_error(1, "tensor-core dense blocks take float32 metrics");
+    return 1;
+  }
+  if (bs > TC_ROWS || nb > 65535) {
+    set_error(1, "tensor-core dense blocks: bs <= 1024 and nb <= 65535");
+    return 1;
+  }
+  TcArgs a{};
+  a.X = L.X;
+  a.ld_bytes = L.ld_bytes;
+  a.d = L.d;
+  a.dpad = (L.d + TC_K - 1) / TC_K * TC_K;
+  a.metric = L.metric;
+  a.block_ids = block_ids;
+  a.nb = nb;
+  a.bs = bs;
+  char* scratch = nullptr;
+  const size_t xb = sizeof(__nv_bfloat16) * nb * TC_ROWS * (size_t)a.dpad;
+  const size_t vec = sizeof(float) * nb * TC_ROWS;
+  const size_t lp = sizeof(float) * nb * (size_t)TC_ROWS * TC_ROWS;
+  const size_t total = xb + 2 * vec + 256 * ((nb * 4 + 255) / 256 + 1) + lp + 256;
+  FG_CUDA(cudaMallocAsync(&scratch, total, s));
+  size_t off = 0;
+  a.Xb = reinterpret_cast<__nv_bfloat16*>(scratch + off);
+  off += (xb + 255) / 256 * 256;
+  a.nrm = reinterpret_cast<float*>(scratch + off);
+  off += (vec + 255) / 256 * 256;
+  a.cc = reinterpret_cast<float*>(scratch + off);
+  off += (vec + 255) / 256 * 256;
+  a.Mx = reinterpret_cast<float*>(scratch + off);
+  off += (nb * 4 + 255) / 256 * 256;
+  a.err = reinterpret_cast<uint32_t*>(scratch + off);
+  a.pairs = reinterpret_cast<unsigned long long*>(scratch + off + 8);
+  unsigned long long* reranked = reinterpret_cast<unsigned long long*>(scratch + off + 16);
+  off += 256;
+  a.LP = reinterpret_cast<float*>(scratch + off);
+  int rc = 0;
+  cudaEvent_t ev[4] = {};
+  for (int i = 0; i < 4 && stats; ++i) cudaEventCreate(&ev[i]);
+  do {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(a.Mx, 0, nb * sizeof(float), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(a.err, 0, 256, s)) != cudaSuccess) {
+      rc = cuda_fail(e, "cudaMemsetAsync(dense scratch)");
+      break;
+    }
+    if (stats) cudaEventRecord(ev[0], s);
+    dense_prep_kernel<<<(unsigned)nb, 256, 0, s>>>(a);
+    note_launch();
+    if (stats) cudaEventRecord(ev[1], s);
+    const int gsm = 100 * 1024;  // 48 KB used; asking for more keeps 2 CTAs (512 TMEM columns) per SM
+    if ((e = cudaFuncSetAttribute(dense_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  gsm)) != cudaSuccess) {
+      rc = cuda_fail(e, "cudaFuncSetAttribute(dense_gram_kernel)");
+      break;
+    }
+    dense_gram_kernel<<<dim3(TC_ROWS / TC_M, TC_ROWS / TC_N, (unsigned)nb), TC_THREADS, gsm, s>>>(a);
+    note_launch();
+    if (stats) cudaEventRecord(ev[2], s);
+    const int nch = (L.d * 4 + 15) / 16;
+    const int ssm = SEL_WARPS * (8 * TC_ROWS + 16 * nch);
+    if ((e = cudaFuncSetAttribute(sel, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm)) !=
+        cudaSuccess) {
+      rc = cuda_fail(e, "cudaFuncSetAttribute(dense_select_kernel)");
+      break;
+    }
+    const int64_t rows = nb * bs;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((rows + SEL_WARPS - 1) / SEL_WARPS,
+                                                                 152 * 16));
+    sel<<<grid, SEL_WARPS * 32, ssm, s>>>(a, k, out_ids, out_dist, reranked);
+    note_launch();
+    if (stats) cudaEventRecord(ev[3], s);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+      rc = cuda_fail(e, "dense tensor-core kernels");
+      break;
+    }
+    uint32_t h[6] = {};
+    if ((e = cudaMemcpyAsync(h, a.err, 24, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+      rc = cuda_fail(e, "dense tensor-core status");
+      break;
+    }
+    if (h[0]) {
+      set_error(5, "tensor-core dense block: a bounded wait for the MMA gave up");
+      rc = 5;
+      break;
+    }
+    if (stats) {
+      const unsigned long long pairs = (unsigned long long)h[2] | ((unsigned long long)h[3] << 32);
+      const unsigned long long rr = (unsigned long long)h[4] | ((unsigned long long)h[5] << 32);
+      float t1 = 0, t2 = 0, t3 = 0;
+      cudaEventElapsedTime(&t1, ev[0], ev[1]);
+      cudaEventElapsedTime(&t2, ev[1], ev[2]);
+      cudaEventElapsedTime(&t3, ev[2], ev[3]);
+      stats[0] = pairs ? (double)rr / (double)pairs : 0.0;
+      stats[1] = t2;
+      stats[2] = t3;
+      stats[3] = t1;
+    }
+  } while (0);
+  for (int i = 0; i < 4 && stats; ++i) cudaEventDestroy(ev[i]);
+  cudaFreeAsync(scratch, s);
+  return rc;
+}
+
+}  // namespace fg

@@ -103,6 +103,11 @@ int prune_lists_static(const VecLayout& L, const int32_t* owner, const int64_t* 
 int64_t prune_lists_static_max_lists();
 int prune_lists_static_max_len();
 
+// Dense-block top-k with the BF16 tensor-core filter and canonical rerank;
+// stats (host, optional): rerank fraction, Gram ms, select ms, prep ms.
+int dense_block_tc(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs, int k,
+                   int32_t* out_ids, float* out_dist, double* stats, cudaStream_t s);
+
 // Dense-block top-k (canonical float32 distances of every pair of a block).
 int dense_block(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs, int k,
                 int32_t* out_ids, float* out_dist, cudaStream_t s);

@@ -162,17 +162,21 @@ def test_prune_lists_parity(fg):
         assert (out[i, cnt[i]:] == -1).all()
 
 
-@pytest.mark.parametrize("metric,d,k", [(1, 100, 32), (0, 960, 64), (0, 16, 10)])
-def test_dense_block_parity(fg, metric, d, k):
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("metric,d,k", [(1, 100, 32), (0, 960, 64), (0, 16, 10), (1, 300, 20)])
+def test_dense_block_parity(fg, metric, d, k, precision):
     ps = synth.vmf_like(4000, d, 4, seed=5) if metric == 1 else \
         synth.gaussian_mixture(4000, d, 4, seed=5)
     blocks = synth.intra_cluster_blocks(ps.labels, 3, 1000, seed=1)
     blocks[2, -7:] = -1
-    gi, gd = fg.fgraft_dense_block_dist(_dev(ps.X), d, metric, _dev(blocks), k)
+    gi, gd, st = fg.fgraft_dense_block_dist(_dev(ps.X), d, metric, _dev(blocks), k,
+                                            precision=precision, stats=True)
     D = oracle.Data(ps.X, d, metric)
     oi, od, _ = oracle.dense_block(D, blocks, k)
     assert np.array_equal(_np(gi), oi)
     assert np.array_equal(_np(gd), od)
+    if precision == 1:
+        assert 0.0 < st[0] <= 1.0 and st[1] > 0.0
 
 
 def test_api_rejects_bad_arguments(fg):
