@@ -191,7 +191,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = Clocks(local)
     launches0 = fg.fgraft_kernel_launches()
-    total_ms, harvest_ms, harvest_launches = 0.0, 0.0, 0
+    total_ms, harvest_ms, harvest_launches, prune_ms = 0.0, 0.0, 0, 0.0
     ctr_sum = {}
     last = None
     for _ in range(args.steps):
@@ -203,9 +203,10 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         total_ms += e0.elapsed_time(e1)
-        hm, hl = fg.fgraft_index_harvest_ms(ix)
+        hm, hl, pm = fg.fgraft_index_harvest_ms(ix, with_prune=True)
         harvest_ms += hm
         harvest_launches += hl
+        prune_ms += pm
         c = fg.fgraft_index_counters(ix)
         for k_, v_ in c.items():
             ctr_sum[k_] = ctr_sum.get(k_, 0) + v_
@@ -319,6 +320,9 @@ def run_ours(args):
                      "alg_bytes_per_launch": alg_bytes / max(harvest_launches, 1),
                      "launch_ms": harvest_ms / max(harvest_launches, 1)},
         "harvest_evals_per_s": round(evals / (harvest_ms / 1e3), 1) if harvest_ms else None,
+        "harvest_prune_ms_per_block": round(prune_ms / max(harvest_launches, 1), 4),
+        "prune_evals_per_s": round(ctr_sum.get("prune_evals", 0) / (prune_ms / 1e3), 1)
+        if prune_ms else None,
         "build_evals_per_s": round((ctr_sum.get("harvest_evals", 0) + ctr_sum.get("prune_evals", 0)
                                     + ctr_sum.get("sat_evals", 0)
                                     + ctr_sum.get("final_prune_evals", 0))

@@ -253,13 +253,15 @@ fgraft_status fgraft_tune_sat(int32_t big_node_min);
  * records a CUDA event pair around its harvest kernel on the launching
  * stream (inside a captured graph too).
  * fgraft_index_harvest_ms: synchronises `stream` and returns in *ms the sum
- * of those kernel durations over the blocks harvested so far, and in
- * *launches (optional) their number.
+ * of those kernel durations over the blocks harvested so far, in *launches
+ * (optional) their number, and in *prune_ms (optional) the summed time from
+ * the end of each harvest kernel to the end of its block's prune kernel (the
+ * re-run pass and the occlusion prune).
  * fgraft_kernel_launches: kernels launched by the library in this process
  * so far (a graph replay counts the kernels it holds). */
 fgraft_status fgraft_index_profile(fgraft_index* ix, int32_t enable);
 fgraft_status fgraft_index_harvest_ms(fgraft_index* ix, fgraft_stream stream, double* ms,
-                                      int32_t* launches);
+                                      int32_t* launches, double* prune_ms);
 uint64_t fgraft_kernel_launches(void);
 
 void fgraft_index_destroy(fgraft_index* ix);

@@ -140,6 +140,10 @@ struct fgraft_index {
   int32_t hash_log2 = 12;
   bool bitmap_ok = true;
   int32_t overflow_mode = 1;   // 1: continue in a global bitmap, 2: abandon and re-run
+  uint64_t* Eg = nullptr;      // expanded lists handed from the search to the prune kernel
+  int32_t* Eg_cnt = nullptr;
+  int32_t eg_ecap = 0;
+  int32_t prune_ns = 0;        // candidates staged per warp by the prune kernel (0: prune in place)
   uint32_t* gvbits = nullptr;  // per-warp global bitmaps for visited sets that outgrow the hash
   int64_t gvbits_words = 0;
   int64_t gvbits_warps = 0;
@@ -149,6 +153,7 @@ struct fgraft_index {
   uint64_t graph_kernels = 0;
   bool profile = false;
   std::vector<cudaEvent_t> ev_beg, ev_end;  // around the harvest kernel of each block
+  std::vector<cudaEvent_t> ev_pend;         // after the prune kernel of each block
 };
 
 namespace {
@@ -258,8 +263,10 @@ int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStrea
   note_launch();
   FG_CUDA(cudaGetLastError());
   if (e1) FG_CUDA(record_event(e1, s));
-  // re-run of the overflowed items with per-warp global scratch
+  // re-run of the overflowed items with per-warp global scratch (pruned in place)
   a.global_scratch = 1;
+  a.Eg = nullptr;
+  a.Eg_cnt = nullptr;
   a.qlist = ix->ovf_list;
   a.qlist_len = ix->work + 2;
   a.work = ix->work + 1;
@@ -355,9 +362,11 @@ void free_index(fgraft_index* ix) {
   if (ix->graph_exec) cudaGraphExecDestroy(ix->graph_exec);
   for (cudaEvent_t e : ix->ev_beg) cudaEventDestroy(e);
   for (cudaEvent_t e : ix->ev_end) cudaEventDestroy(e);
+  for (cudaEvent_t e : ix->ev_pend) cudaEventDestroy(e);
   void* ptrs[] = {ix->roots, ix->parents, ix->s_off, ix->s_ids, ix->A,   ix->cnt,
                   ix->r_off, ix->r_ids,   ix->rcnt,  ix->rcur,  ix->f_off, ix->f_ids,
-                  ix->scan_tmp, ix->work, ix->ovf_list, ix->gscratch, ix->ctr, ix->gvbits};
+                  ix->scan_tmp, ix->work, ix->ovf_list, ix->gscratch, ix->ctr, ix->gvbits,
+                  ix->Eg, ix->Eg_cnt};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete ix;
@@ -389,10 +398,20 @@ int harvest_block_impl(fgraft_index* ix, int32_t b, cudaStream_t s) {
   a.alpha2 = ix->p.alpha * ix->p.alpha;
   a.A_out = ix->A;
   a.cnt_out = ix->cnt;
+  const bool sep = ix->prune_ns > 0;
+  a.Eg = sep ? ix->Eg : nullptr;
+  a.Eg_cnt = sep ? ix->Eg_cnt : nullptr;
   const bool prof = ix->profile && (int)ix->ev_beg.size() > b;
   int rc = launch_beam(ix, a, ix->ctr + C_HARVEST, s, prof ? ix->ev_beg[b] : nullptr,
                        prof ? ix->ev_end[b] : nullptr);
   if (rc) return rc;
+  if (sep) {
+    rc = harvest_prune(ix->L, ix->Eg, ix->Eg_cnt, ix->eg_ecap, a.nq, a.q_first,
+                       a.q_step, ix->p.R, a.alpha2, ix->A, ix->cnt, ix->ctr + C_PRUNE,
+                       ix->num_sms, s);
+    if (rc) return rc;
+  }
+  if (prof) FG_CUDA(record_event(ix->ev_pend[b], s));
   rc = reverse_rows(ix->L.n, ix->p.R, ix->nb, b, ix->A, ix->cnt, ix->rcnt, ix->rcur, ix->r_off,
                     ix->r_ids, ix->scan_tmp, s);
   if (rc) return rc;
@@ -457,6 +476,18 @@ fgraft_status fgraft_build_scaffold(const void* X, int64_t n, int32_t d, int64_t
   ix->gscratch_per_warp = (8ll * ix->g_ecap + ix->g_ecap / 8 + 255) / 256 * 256;
   rc = rc ? rc : dalloc(&ix->gscratch, ix->gscratch_per_warp * ix->g_warps);
   if (!rc) rc = size_visited_bitmaps(ix);
+  // the prune kernel stages a point's whole candidate list in shared memory;
+  // when that does not fit (large d or ef) the search prunes in place instead
+  {
+    const int S = pool_slots(p.ef_h);
+    ix->eg_ecap = 1 << std::max(6, ceil_log2(2 * 32 * S));
+    ix->prune_ns = harvest_prune_smem(ix->eg_ecap, L.nchunks) <= 112 * 1024 ? ix->eg_ecap : 0;
+    if (ix->prune_ns) {
+      const int64_t nq_max = (n + ix->nb - 1) / ix->nb;
+      rc = rc ? rc : dalloc(&ix->Eg, nq_max * ix->eg_ecap);
+      rc = rc ? rc : dalloc(&ix->Eg_cnt, nq_max);
+    }
+  }
   if (rc) {
     free_index(ix);
     return (fgraft_status)rc;
@@ -802,9 +833,11 @@ fgraft_status fgraft_index_profile(fgraft_index* ix, int32_t enable) {
   if (enable && ix->ev_beg.empty()) {
     ix->ev_beg.resize(ix->nb);
     ix->ev_end.resize(ix->nb);
+    ix->ev_pend.resize(ix->nb);
     for (int b = 0; b < ix->nb; ++b) {
       FGS(cudaEventCreate(&ix->ev_beg[b]));
       FGS(cudaEventCreate(&ix->ev_end[b]));
+      FGS(cudaEventCreate(&ix->ev_pend[b]));
     }
   }
   if ((enable != 0) != ix->profile && ix->graph_exec) {
@@ -816,18 +849,21 @@ fgraft_status fgraft_index_profile(fgraft_index* ix, int32_t enable) {
 }
 
 fgraft_status fgraft_index_harvest_ms(fgraft_index* ix, fgraft_stream stream, double* ms,
-                                      int32_t* launches) {
+                                      int32_t* launches, double* prune_ms) {
   if (!ix || !ms) return (fgraft_status)fail(FGRAFT_EINVAL, "NULL argument");
   if (!ix->profile) return (fgraft_status)fail(FGRAFT_EINVAL, "profiling is off");
   FGS(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
-  double tot = 0.0;
+  double tot = 0.0, ptot = 0.0;
   for (int b = 0; b < ix->blocks_done && b < (int)ix->ev_beg.size(); ++b) {
-    float t = 0.0f;
+    float t = 0.0f, t2 = 0.0f;
     FGS(cudaEventElapsedTime(&t, ix->ev_beg[b], ix->ev_end[b]));
+    FGS(cudaEventElapsedTime(&t2, ix->ev_end[b], ix->ev_pend[b]));
     tot += t;
+    ptot += t2;
   }
   *ms = tot;
   if (launches) *launches = ix->blocks_done;
+  if (prune_ms) *prune_ms = ptot;
   return FGRAFT_OK;
 }
 

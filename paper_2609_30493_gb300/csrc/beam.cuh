@@ -77,6 +77,11 @@ struct BeamArgs {
   int32_t* ovf_list;
   uint32_t* ovf_count;
   uint32_t ovf_cap;  // capacity of ovf_list
+  // harvest with a separate prune kernel: the expanded list of query qidx is
+  // written to Eg[qidx * ecap ..] with its length in Eg_cnt[qidx] (-1 when the
+  // query was handed to the re-run pass, which prunes in place)
+  uint64_t* Eg;
+  int32_t* Eg_cnt;
   uint32_t* err_flag;
   unsigned long long* counters;  // evals, expansions, prune evals, ids scanned, overflows
 };
@@ -289,6 +294,7 @@ struct Beam {
 
       if (ovf) {
         if (lane == 0) {
+          if (a.Eg) a.Eg_cnt[qidx] = -1;
           if (a.global_scratch) {
             atomicOr(a.err_flag, 1u);
           } else {
@@ -318,6 +324,15 @@ struct Beam {
           }
         }
         if (lane == 0 && a.q_evals) a.q_evals[qidx] = (uint32_t)nvis;
+        continue;
+      }
+
+      if (a.Eg) {
+        // the prune runs in its own kernel with the candidates staged on chip
+        uint64_t* dst = a.Eg + qidx * (int64_t)a.ecap;
+        for (int i = lane; i < ne; i += 32) dst[i] = E[i];
+        if (lane == 0) a.Eg_cnt[qidx] = ne;
+        __syncwarp();
         continue;
       }
 

@@ -175,11 +175,99 @@ __device__ __forceinline__ void load_slots(const char* __restrict__ row, int nch
   }
 }
 
+// The same chunks from a row staged in shared memory.
+template <int G, int K>
+__device__ __forceinline__ void load_slots_smem(const uint4* row, int nchunks, int j,
+                                                uint4 (&y)[Lanes<G, K>::VL][K]) {
+  using L = Lanes<G, K>;
+#pragma unroll
+  for (int i = 0; i < L::VL; ++i) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) y[i][k] = row[min(32 * k + j + L::P * i, nchunks - 1)];
+  }
+}
+
 // Canonical distance between the staged vector qs (shared memory) and the
 // chunks y of one group member; every lane of the group returns it.
+// The same distance with the first vector's chunks in registers too (loaded
+// by load_slots / load_slots_smem with the same lane mapping).
+template <int METRIC, int G, int K>
+__device__ __forceinline__ float regs_dist(const uint4 (&xq)[Lanes<G, K>::VL][K],
+                                           const uint4 (&y)[Lanes<G, K>::VL][K], int nchunks,
+                                           int d, int j, unsigned mask) {
+  using L = Lanes<G, K>;
+  if constexpr (METRIC == L2_U8) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int i = 0; i < L::VL; ++i) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int c = 32 * k + j + L::P * i;
+        if (c < nchunks) {
+          const int nb = d - 16 * c;
+          const uint32_t a[4] = {xq[i][k].x, xq[i][k].y, xq[i][k].z, xq[i][k].w};
+          const uint32_t b[4] = {y[i][k].x, y[i][k].y, y[i][k].z, y[i][k].w};
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const int vb = nb - 4 * w;
+            const uint32_t m =
+                vb >= 4 ? 0xFFFFFFFFu : (vb <= 0 ? 0u : (0xFFFFFFFFu >> (8 * (4 - vb))));
+            const uint32_t df = __vabsdiffu4(a[w] & m, b[w] & m);
+            t = __dp4a(df, df, t);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int off = L::P / 2; off >= 1; off >>= 1) t += __shfl_xor_sync(mask, t, off);
+    return __uint2float_rn(t);
+  } else {
+    float v[L::VL];
+#pragma unroll
+    for (int i = 0; i < L::VL; ++i) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int c = 32 * k + j + L::P * i;
+        if (c < nchunks) {
+          const int nv = d - 4 * c;
+          const float x[4] = {__uint_as_float(xq[i][k].x), __uint_as_float(xq[i][k].y),
+                              __uint_as_float(xq[i][k].z), __uint_as_float(xq[i][k].w)};
+          const float yy[4] = {__uint_as_float(y[i][k].x), __uint_as_float(y[i][k].y),
+                               __uint_as_float(y[i][k].z), __uint_as_float(y[i][k].w)};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (nv > e) {
+              if constexpr (METRIC == ANGULAR_F32) {
+                acc = __fmaf_rn(x[e], yy[e], acc);
+              } else {
+                const float t = __fsub_rn(x[e], yy[e]);
+                acc = __fmaf_rn(t, t, acc);
+              }
+            }
+          }
+        }
+      }
+      v[i] = acc;
+    }
+#pragma unroll
+    for (int s = G / 2; s >= L::P; s >>= 1) {
+#pragma unroll
+      for (int i = 0; i < s / L::P; ++i) v[i] = __fadd_rn(v[i], v[i + s / L::P]);
+    }
+    float r = v[0];
+#pragma unroll
+    for (int off = L::P / 2; off >= 1; off >>= 1) r = __fadd_rn(r, __shfl_xor_sync(mask, r, off));
+    if constexpr (METRIC == ANGULAR_F32) return __fsub_rn(1.0f, r);
+    return r;
+  }
+}
+
+// `mask` names the lanes that execute the call together: the whole warp, or
+// only the calling P-lane group when groups run different trip counts.
 template <int METRIC, int G, int K>
 __device__ __forceinline__ float slots_dist(const uint4* qs, const uint4 (&y)[Lanes<G, K>::VL][K],
-                                            int nchunks, int d, int j) {
+                                            int nchunks, int d, int j, unsigned mask = FULL) {
   using L = Lanes<G, K>;
   if constexpr (METRIC == L2_U8) {
     uint32_t v[L::VL];
@@ -210,7 +298,7 @@ __device__ __forceinline__ float slots_dist(const uint4* qs, const uint4 (&y)[La
 #pragma unroll
     for (int i = 0; i < L::VL; ++i) t += v[i];
 #pragma unroll
-    for (int off = L::P / 2; off >= 1; off >>= 1) t += __shfl_xor_sync(FULL, t, off);
+    for (int off = L::P / 2; off >= 1; off >>= 1) t += __shfl_xor_sync(mask, t, off);
     return __uint2float_rn(t);
   } else {
     float v[L::VL];
@@ -250,7 +338,7 @@ __device__ __forceinline__ float slots_dist(const uint4* qs, const uint4 (&y)[La
     }
     float r = v[0];
 #pragma unroll
-    for (int off = L::P / 2; off >= 1; off >>= 1) r = __fadd_rn(r, __shfl_xor_sync(FULL, r, off));
+    for (int off = L::P / 2; off >= 1; off >>= 1) r = __fadd_rn(r, __shfl_xor_sync(mask, r, off));
     if constexpr (METRIC == ANGULAR_F32) return __fsub_rn(1.0f, r);
     return r;
   }

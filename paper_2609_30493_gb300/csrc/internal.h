@@ -103,6 +103,13 @@ int prune_lists_static(const VecLayout& L, const int32_t* owner, const int64_t* 
 int64_t prune_lists_static_max_lists();
 int prune_lists_static_max_len();
 
+// Harvest prune as its own kernel over the expanded lists the search wrote.
+int harvest_prune_smem(int ecap, int nchunks);
+int harvest_prune(const VecLayout& L, const uint64_t* Eg, const int32_t* Eg_cnt, int ecap,
+                  int64_t nq, int64_t q_first, int64_t q_step, int R, float alpha2,
+                  int32_t* A_out, int32_t* cnt_out, unsigned long long* prune_ctr, int num_sms,
+                  cudaStream_t s);
+
 // Dense-block top-k with the BF16 tensor-core filter and canonical rerank;
 // stats (host, optional): rerank fraction, Gram ms, select ms, prep ms.
 int dense_block_tc(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs, int k,

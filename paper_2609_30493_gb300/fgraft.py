@@ -185,12 +185,13 @@ def fgraft_index_profile(ix: Index, enable: bool = True):
     _check(load().fgraft_index_profile(ix.handle, C.c_int32(1 if enable else 0)))
 
 
-def fgraft_index_harvest_ms(ix: Index):
-    """(sum of harvest-kernel milliseconds, number of harvest launches) since profiling began."""
-    ms, nl = C.c_double(), C.c_int32()
+def fgraft_index_harvest_ms(ix: Index, with_prune: bool = False):
+    """(sum of harvest-kernel milliseconds, number of harvest launches) since profiling
+    began; with_prune adds the summed milliseconds of the re-run and prune kernels."""
+    ms, nl, pm = C.c_double(), C.c_int32(), C.c_double()
     _check(load().fgraft_index_harvest_ms(ix.handle, _stream(ix.X.device), C.byref(ms),
-                                          C.byref(nl)))
-    return ms.value, nl.value
+                                          C.byref(nl), C.byref(pm)))
+    return (ms.value, nl.value, pm.value) if with_prune else (ms.value, nl.value)
 
 
 def fgraft_tune_sat(big_node_min: int = 16384):
