@@ -245,8 +245,12 @@ fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t war
 /* SAT launch configuration for later fgraft_build_scaffold calls in this
  * process (tuning; results do not depend on it): tree nodes holding at least
  * big_node_min points are split across many CTAs, one launch per child
- * selection; smaller nodes get one CTA each.  Default 16384; >= 2. */
-fgraft_status fgraft_tune_sat(int32_t big_node_min);
+ * selection, until the list of points no child has rejected yet is at most
+ * finish_len long for every such node; then one CTA per node finishes the
+ * selection.  Smaller nodes get one CTA each from the start.
+ * Defaults 16384 and 2048; big_node_min >= 2, finish_len >= 1; 0 leaves a
+ * value unchanged. */
+fgraft_status fgraft_tune_sat(int32_t big_node_min, int32_t finish_len);
 
 /* Measurement hooks (results never depend on them).
  * fgraft_index_profile: with enable != 0, every later harvest of a block

@@ -87,6 +87,7 @@ using namespace fg;
 
 // Nodes of at least this many points are built by the multi-CTA SAT path.
 static int32_t g_sat_big_min = 16384;
+static int32_t g_sat_finish_len = 2048;
 
 #define FGS(call)                                                      \
   do {                                                                 \
@@ -516,9 +517,9 @@ fgraft_status fgraft_build_scaffold(const void* X, int64_t n, int32_t d, int64_t
   rc = rc ? rc : dalloc(&S.kcnt, tot);
   rc = rc ? rc : dalloc(&S.kstart, tot + 1);
   rc = rc ? rc : dalloc(&S.item_pt, tot);
-  rc = rc ? rc : dalloc(&S.kd, tot);
+  rc = rc ? rc : dalloc(&S.lst, 2 * tot);
   rc = rc ? rc : dalloc(&S.best, tot);
-  rc = rc ? rc : dalloc(&S.flag, tot);
+  rc = rc ? rc : dalloc(&S.kid, tot);
   S.big_min = g_sat_big_min;
   const int64_t nbig_max = tot / S.big_min + 1;
   rc = rc ? rc : dalloc(&S.seg_start, tot + nbig_max);
@@ -529,12 +530,14 @@ fgraft_status fgraft_build_scaffold(const void* X, int64_t n, int32_t d, int64_t
   rc = rc ? rc : dalloc(&S.big_list, nbig_max);
   rc = rc ? rc : dalloc(&S.big_keys, 3 * nbig_max);
   rc = rc ? rc : dalloc(&S.big_kcount, nbig_max);
+  rc = rc ? rc : dalloc(&S.big_lens, 3 * nbig_max);
+  S.finish_len = g_sat_finish_len;
   S.nunsettled = S.nseg + 2;
   S.scan_tmp = ix->scan_tmp;
   auto free_sat = [&]() {
-    void* ps[] = {S.node_of, S.kcnt, S.kstart, S.item_pt, S.kd, S.best, S.flag,
+    void* ps[] = {S.node_of, S.kcnt, S.kstart, S.item_pt, S.lst, S.best, S.kid,
                   S.seg_start, S.seg_len, S.seg_node, S.seg_tree, S.nseg,
-                  S.big_list, S.big_keys, S.big_kcount};
+                  S.big_list, S.big_keys, S.big_kcount, S.big_lens};
     for (void* q : ps)
       if (q) cudaFree(q);
   };
@@ -869,9 +872,12 @@ fgraft_status fgraft_index_harvest_ms(fgraft_index* ix, fgraft_stream stream, do
 
 uint64_t fgraft_kernel_launches(void) { return launch_count(); }
 
-fgraft_status fgraft_tune_sat(int32_t big_node_min) {
-  if (big_node_min < 2) return (fgraft_status)fail(FGRAFT_EINVAL, "big_node_min must be >= 2");
-  g_sat_big_min = big_node_min;
+fgraft_status fgraft_tune_sat(int32_t big_node_min, int32_t finish_len) {
+  if (big_node_min == 1 || big_node_min < 0)
+    return (fgraft_status)fail(FGRAFT_EINVAL, "big_node_min must be >= 2");
+  if (finish_len < 0) return (fgraft_status)fail(FGRAFT_EINVAL, "finish_len must be >= 1");
+  if (big_node_min) g_sat_big_min = big_node_min;
+  if (finish_len) g_sat_finish_len = finish_len;
   return FGRAFT_OK;
 }
 

@@ -54,9 +54,9 @@ struct SatScratch {
   uint32_t* kcnt;       // T*n (zero on entry and exit)
   int64_t* kstart;      // T*n + 1
   int32_t* item_pt;     // T*n
-  float* kd;            // T*n
+  uint64_t* lst;        // 2*T*n (open lists)
   uint64_t* best;       // T*n
-  uint8_t* flag;        // T*n
+  int32_t* kid;         // T*n (children of a node at the start of its item range)
   int64_t* seg_start;   // T*n + T*n/big_min + 1 (small nodes first, big ones from T*n)
   int32_t* seg_len;     // same
   int32_t* seg_node;    // same
@@ -68,6 +68,8 @@ struct SatScratch {
   int32_t* big_list;    // segment index of each big node
   uint64_t* big_keys;   // 3 per big node
   uint32_t* big_kcount; // 1 per big node
+  uint32_t* big_lens;   // 3 per big node
+  int32_t finish_len;   // open lists this short finish in one CTA per node
 };
 int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* parents,
                SatScratch& S, unsigned long long* ctr_sat, cudaStream_t s);

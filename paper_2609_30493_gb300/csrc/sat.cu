@@ -8,11 +8,14 @@
 // sequence of minimum selections: the next child is the smallest key among
 // the points no child has rejected yet (every smaller key is a child or
 // rejected, so this is exactly the point the scan would accept next), and the
-// new child then rejects every remaining point y with
-// delta(y,b) <= delta(y,a).  The same pass keeps, for every point, its
-// closest child by (delta, id), which is the assignment of the non-children.
-// One CTA owns one node; the points of all nodes of a level are grouped by a
-// counting sort keyed on (tree, node).
+// new child then rejects every remaining point y with delta(y,b) <= delta(y,a).
+// Only the points not yet rejected are evaluated in this phase, a few percent
+// of |P| x children on clustered data.  A second, coherent phase then gives
+// every other point its closest child by (delta, id): the children are staged
+// in shared memory and each point is read once per chunk of children.
+// Small nodes get one CTA; nodes of many points are split across CTAs, one
+// launch per child selection.  The points of all nodes of a level are grouped
+// by a counting sort keyed on (tree, node).
 #include <algorithm>
 #include <vector>
 
@@ -32,42 +35,48 @@ struct SatSegArgs {
   const int32_t* seg_len;
   const int32_t* seg_node;
   const int32_t* seg_tree;
-  float* kd;
-  uint64_t* best;
-  uint8_t* flag;  // 0 candidate, 1 rejected, 2 child
+  uint64_t* lst0;  // open lists: keys (delta to the node's point, id) of the points
+  uint64_t* lst1;  // no child has rejected yet, two buffers over each item range
+  uint64_t* best;  // closest child by (delta, id); bit 0 marks a child itself
+  int32_t* kid;    // kid[start + t] = t-th child of the node of that item range
+  int32_t kc;      // children staged per chunk in the assignment phase
   int32_t* node_of;
   int32_t* parent;
   unsigned long long* ctr;
 };
 
+// Minimum of one key per thread over the CTA; rk[parity] is the scratch, and
+// consecutive calls alternate the parity so no second barrier is needed.
 template <int NW>
-__device__ __forceinline__ void block_argmin(uint64_t& key, int& idx, uint64_t (*rk)[NW],
-                                             int (*ri)[NW], int parity) {
+__device__ __forceinline__ uint64_t block_min64(uint64_t key, uint64_t (*rk)[NW], int parity) {
 #pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) {
-    uint64_t ok = __shfl_xor_sync(FULL, key, off);
-    int oi = __shfl_xor_sync(FULL, idx, off);
-    if (ok < key) {
-      key = ok;
-      idx = oi;
-    }
-  }
+  for (int off = 16; off >= 1; off >>= 1) key = umin64(key, __shfl_xor_sync(FULL, key, off));
   const int warp = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    rk[parity][warp] = key;
-    ri[parity][warp] = idx;
-  }
+  if ((threadIdx.x & 31) == 0) rk[parity][warp] = key;
   __syncthreads();
   key = PAD;
-  idx = -1;
 #pragma unroll
-  for (int w = 0; w < NW; ++w) {
-    uint64_t kk = rk[parity][w];
-    if (kk < key) {
-      key = kk;
-      idx = ri[parity][w];
-    }
-  }
+  for (int w = 0; w < NW; ++w) key = umin64(key, rk[parity][w]);
+  return key;
+}
+
+__device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) v = umin64(v, __shfl_xor_sync(FULL, v, off));
+  return v;
+}
+
+// Slot in an append-only list for every lane with keep set (one atomic per
+// warp).  All 32 lanes must call it.
+__device__ __forceinline__ uint32_t warp_append(bool keep, uint32_t* counter) {
+  const unsigned bal = __ballot_sync(FULL, keep);
+  if (bal == 0) return 0;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(bal) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(counter, (uint32_t)__popc(bal));
+  base = __shfl_sync(FULL, base, leader);
+  return base + (uint32_t)__popc(bal & ((1u << lane) - 1u));
 }
 
 // Stage a row in shared memory with the whole CTA.
@@ -77,115 +86,196 @@ __device__ __forceinline__ void stage_row_cta(uint4* dst, const char* __restrict
     dst[c] = __ldg(reinterpret_cast<const uint4*>(row) + c);
 }
 
+// Distances from the node's point (staged in cvec) to the items [t0, t1) of
+// the node: their keys go to lst[t0 .. t1); returns this thread's minimum.
 template <int METRIC, int G, int K, int NW>
-__global__ void __launch_bounds__(NW * 32) sat_segment_kernel(const SatSegArgs a) {
+__device__ uint64_t sat_first(const SatSegArgs& a, int64_t start, int t0, int t1,
+                              const uint4* cvec, uint64_t* lst) {
   using L = Lanes<G, K>;
   constexpr int STEP = L::CPW * L::U;
-  __shared__ uint64_t rk[2][NW];
-  __shared__ int ri[2][NW];
-  __shared__ __align__(16) uint4 cvec[256];  // the node's point, then each new child
-  const int s = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane / L::P, j = lane % L::P;
-  const int64_t start = a.seg_start[s];
-  const int m = a.seg_len[s];
-  const int32_t anode = a.seg_node[s];
-  const int64_t tbase = (int64_t)a.seg_tree[s] * a.n;
-
-  stage_row_cta(cvec, a.X + (int64_t)anode * a.ld_bytes, a.nchunks);
-  __syncthreads();
-  uint64_t bk = PAD;
-  int bi = -1;
-  for (int base = warp * STEP; base < m; base += NW * STEP) {
+  uint64_t lmin = PAD;
+  for (int base = t0 + warp * STEP; base < t1; base += NW * STEP) {
     uint4 y[L::U][L::VL][K];
+    int32_t pt[L::U];
 #pragma unroll
     for (int u = 0; u < L::U; ++u) {
-      const int idx = min(base + u * L::CPW + g, m - 1);
-      load_slots<G, K>(a.X + (int64_t)a.item_pt[start + idx] * a.ld_bytes, a.nchunks, j, y[u]);
+      pt[u] = a.item_pt[start + min(base + u * L::CPW + g, t1 - 1)];
+      load_slots<G, K>(a.X + (int64_t)pt[u] * a.ld_bytes, a.nchunks, j, y[u]);
     }
 #pragma unroll
     for (int u = 0; u < L::U; ++u) {
       const float dd = slots_dist<METRIC, G, K>(cvec, y[u], a.nchunks, a.d, j);
       const int idx = base + u * L::CPW + g;
-      if (idx < m && j == 0) {
-        a.kd[start + idx] = dd;
-        a.best[start + idx] = PAD;
-        a.flag[start + idx] = 0;
-        const uint64_t key = make_key(dd, a.item_pt[start + idx]);
-        if (key < bk) {
-          bk = key;
-          bi = idx;
-        }
+      if (idx < t1 && j == 0) {
+        const uint64_t key = make_key(dd, pt[u]);
+        lst[idx] = key;
+        lmin = umin64(lmin, key);
       }
     }
   }
-  int parity = 0;
-  block_argmin<NW>(bk, bi, rk, ri, parity);
-  long long k = 0;
+  return lmin;
+}
+
+// One child selection step over the open entries lin[e0, e1): the child b
+// (key bk, staged in cvec) leaves the list, every entry y with
+// delta(y, b) <= delta(y, a) is rejected, the rest are appended to lout
+// through *cnt.  Returns this thread's minimum surviving key.
+template <int METRIC, int G, int K, int NW>
+__device__ uint64_t sat_step(const SatSegArgs& a, const uint64_t* lin, uint64_t* lout, int e0,
+                             int e1, uint64_t bk, const uint4* cvec, uint32_t* cnt) {
+  using L = Lanes<G, K>;
+  constexpr int STEP = L::CPW * L::U;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane / L::P, j = lane % L::P;
+  uint64_t lmin = PAD;
+  for (int base = e0 + warp * STEP; base < e1; base += NW * STEP) {  // warp-uniform
+    uint4 y[L::U][L::VL][K];
+    uint64_t e[L::U];
+#pragma unroll
+    for (int u = 0; u < L::U; ++u) {
+      e[u] = lin[min(base + u * L::CPW + g, e1 - 1)];
+      load_slots<G, K>(a.X + (int64_t)key_id(e[u]) * a.ld_bytes, a.nchunks, j, y[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < L::U; ++u) {
+      const float dd = slots_dist<METRIC, G, K>(cvec, y[u], a.nchunks, a.d, j);
+      const bool keep =
+          j == 0 && base + u * L::CPW + g < e1 && e[u] != bk && dd > key_dist(e[u]);
+      const uint32_t pos = warp_append(keep, cnt);
+      if (keep) {
+        lout[pos] = e[u];
+        lmin = umin64(lmin, e[u]);
+      }
+    }
+  }
+  return lmin;
+}
+
+// The rest of a node's selection inside one CTA: starting from the open list
+// lin (L entries, smallest key bk) and k children chosen so far, select until
+// the list is empty.  scnt[0..1] must be zero and visible before the call.
+// Returns the number of children.
+template <int METRIC, int G, int K, int NW>
+__device__ int sat_select(const SatSegArgs& a, int64_t start, int32_t anode, int64_t tbase,
+                          uint64_t* lin, uint64_t* lout, int L, uint64_t bk, int k, uint4* cvec,
+                          uint64_t (*rk)[NW], uint32_t* scnt) {
+  int parity = 1;
   while (bk != PAD) {
-    const int32_t bpt = key_id(bk);
+    const int32_t b = key_id(bk);
     if (threadIdx.x == 0) {
-      a.flag[start + bi] = 2;
-      a.parent[tbase + bpt] = anode;
+      a.kid[start + k] = b;
+      a.parent[tbase + b] = anode;
     }
     ++k;
-    stage_row_cta(cvec, a.X + (int64_t)bpt * a.ld_bytes, a.nchunks);
+    const int c = k & 1;
+    stage_row_cta(cvec, a.X + (int64_t)b * a.ld_bytes, a.nchunks);
     __syncthreads();
-    bk = PAD;
-    bi = -1;
-    for (int base = warp * STEP; base < m; base += NW * STEP) {
-      uint4 y[L::U][L::VL][K];
-#pragma unroll
-      for (int u = 0; u < L::U; ++u) {
-        const int idx = min(base + u * L::CPW + g, m - 1);
-        load_slots<G, K>(a.X + (int64_t)a.item_pt[start + idx] * a.ld_bytes, a.nchunks, j, y[u]);
+    const uint64_t lmin = sat_step<METRIC, G, K, NW>(a, lin, lout, 0, L, bk, cvec, scnt + c);
+    bk = block_min64<NW>(lmin, rk, parity);
+    parity ^= 1;
+    L = (int)scnt[c];
+    uint64_t* t = lin;
+    lin = lout;
+    lout = t;
+    // every thread read scnt[c ^ 1] before the barrier of this step
+    if (threadIdx.x == 0) scnt[c ^ 1] = 0;
+  }
+  return k;
+}
+
+// Assignment phase shared by both kernels: every item of [t0, t1) of the
+// node gets its closest child by (delta, id) among the k children
+// kid[start .. start+k), children staged kc at a time in kvec; children
+// themselves get -1.  Called by all threads of the CTA.
+template <int METRIC, int G, int K, int NW>
+__device__ void sat_assign(const SatSegArgs& a, int64_t start, int t0, int t1, int k,
+                           int64_t tbase, uint4* kvec, int32_t* kids) {
+  using L = Lanes<G, K>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane / L::P, j = lane % L::P;
+  const int NG = NW * L::CPW;
+  const int gid = warp * L::CPW + g;
+  const int nch = a.nchunks;
+  for (int c0 = 0; c0 < k; c0 += a.kc) {
+    const int kn = min(a.kc, k - c0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kn * nch; idx += NW * 32) {
+      const int t = idx / nch, ch = idx - t * nch;
+      kvec[idx] = __ldg(reinterpret_cast<const uint4*>(
+                            a.X + (int64_t)a.kid[start + c0 + t] * a.ld_bytes) + ch);
+    }
+    for (int t = threadIdx.x; t < kn; t += NW * 32) kids[t] = a.kid[start + c0 + t];
+    __syncthreads();
+    for (int base = t0; base < t1; base += NG) {
+      const int64_t it = start + min(base + gid, t1 - 1);
+      const int32_t pt = a.item_pt[it];
+      uint4 xq[L::VL][K];
+      load_slots<G, K>(a.X + (int64_t)pt * a.ld_bytes, nch, j, xq);
+      uint64_t bk = PAD & ~1ull;
+      bool self = false;
+      for (int t = 0; t < kn; ++t) {
+        uint4 y[L::VL][K];
+        load_slots_smem<G, K>(kvec + (int64_t)t * nch, nch, j, y);
+        const float dd = regs_dist<METRIC, G, K>(xq, y, nch, a.d, j, FULL);
+        bk = umin64(bk, make_key(dd, kids[t]));
+        self |= kids[t] == pt;
       }
-#pragma unroll
-      for (int u = 0; u < L::U; ++u) {
-        const float dd = slots_dist<METRIC, G, K>(cvec, y[u], a.nchunks, a.d, j);
-        const int idx = base + u * L::CPW + g;
-        if (idx < m && j == 0) {
-          const int64_t it = start + idx;
-          const uint8_t f = a.flag[it];
-          if (f != 2) {
-            const uint64_t ck = make_key(dd, bpt);
-            if (ck < a.best[it]) a.best[it] = ck;
-            if (f == 0) {
-              const float kdv = a.kd[it];
-              if (dd <= kdv) {
-                a.flag[it] = 1;
-              } else {
-                const uint64_t key = make_key(kdv, a.item_pt[it]);
-                if (key < bk) {
-                  bk = key;
-                  bi = idx;
-                }
-              }
-            }
-          }
-        }
+      if (base + gid < t1 && j == 0) {
+        const uint64_t prev = c0 == 0 ? (PAD & ~1ull) : a.best[it];
+        a.best[it] = umin64(prev & ~1ull, bk) | (prev & 1ull) | (self ? 1ull : 0ull);
       }
     }
-    parity ^= 1;
-    block_argmin<NW>(bk, bi, rk, ri, parity);
   }
-  for (int i = threadIdx.x; i < m; i += NW * 32) {
+  __syncthreads();
+  for (int i = t0 + threadIdx.x; i < t1; i += NW * 32) {
     const int64_t it = start + i;
-    const int32_t pt = a.item_pt[it];
-    a.node_of[tbase + pt] = a.flag[it] == 2 ? -1 : key_id(a.best[it]);
-  }
-  if (threadIdx.x == 0) {
-    const long long mm = m;
-    atomicAdd(a.ctr, (unsigned long long)(mm + k * (k - 1) / 2 + (mm - k) * k));
+    const uint64_t bk = a.best[it];
+    a.node_of[tbase + a.item_pt[it]] = (bk & 1ull) ? -1 : key_id(bk);
   }
 }
 
+__device__ __forceinline__ void sat_count(const SatSegArgs& a, int m, int k) {
+  const long long mm = m, kk = k;
+  atomicAdd(a.ctr, (unsigned long long)(mm + kk * (kk - 1) / 2 + (mm - kk) * kk));
+}
+
+// A node with fewer points: one CTA runs the whole construction of its
+// children.
+template <int METRIC, int G, int K, int NW>
+__global__ void __launch_bounds__(NW * 32) sat_segment_kernel(const SatSegArgs a) {
+  __shared__ uint64_t rk[2][NW];
+  __shared__ uint32_t scnt[2];
+  extern __shared__ __align__(16) unsigned char ssat[];
+  uint4* cvec = reinterpret_cast<uint4*>(ssat);  // the node's point, then each new child
+  uint4* kvec = cvec + a.nchunks;               // children staged for the assignment
+  int32_t* kids = reinterpret_cast<int32_t*>(kvec + (int64_t)a.kc * a.nchunks);
+  const int s = blockIdx.x;
+  const int64_t start = a.seg_start[s];
+  const int m = a.seg_len[s];
+  const int32_t anode = a.seg_node[s];
+  const int64_t tbase = (int64_t)a.seg_tree[s] * a.n;
+  if (threadIdx.x == 0) scnt[0] = scnt[1] = 0;
+  stage_row_cta(cvec, a.X + (int64_t)anode * a.ld_bytes, a.nchunks);
+  __syncthreads();
+  uint64_t* l0 = a.lst0 + start;
+  const uint64_t lmin = sat_first<METRIC, G, K, NW>(a, start, 0, m, cvec, l0);
+  const uint64_t bk = block_min64<NW>(lmin, rk, 0);
+  const int k = sat_select<METRIC, G, K, NW>(a, start, anode, tbase, l0, a.lst1 + start, m, bk,
+                                             0, cvec, rk, scnt);
+  sat_assign<METRIC, G, K, NW>(a, start, 0, m, k, tbase, kvec, kids);
+  if (threadIdx.x == 0) sat_count(a, m, k);
+}
+
 // ---------------------------------------------------------------------------
-// Nodes with many points: every CTA of a launch owns a tile of one node's
-// points, and one launch performs one child selection for all such nodes.
-// The minimum over a node's points is reduced with a 64-bit atomicMin into
-// one of three rotating per-node key buffers (read, write, clear), so no CTA
-// ever waits for another.
+// Nodes with many points.  While a node's open list is long, every CTA of a
+// launch owns a tile of it and one launch performs one child selection for
+// all such nodes: survivors are appended to the other list through a global
+// counter, and the minimum is reduced with a 64-bit atomicMin, both into one
+// of three rotating per-node buffers (read, write, clear), so no CTA ever
+// waits for another.  Once the lists are short, one CTA per node finishes
+// the selection, and the assignment is again split into tiles.
 // ---------------------------------------------------------------------------
 constexpr int BIG_TILE = 2048;  // points per CTA
 constexpr int BIG_NW = 8;
@@ -196,108 +286,97 @@ struct SatBigArgs {
   uint64_t* cur;       // current minimum key per big node (the next child)
   uint64_t* nxt;       // receives the minimum of this pass
   uint64_t* clr;       // reset to PAD for the pass after
+  uint32_t* curlen;    // open list length per big node, same rotation
+  uint32_t* nxtlen;
+  uint32_t* clrlen;
+  uint64_t* lin;       // open lists read by this pass (offset by the item range)
+  uint64_t* lout;      // and written
   uint32_t* kcount;    // children chosen so far per big node
   int32_t y_off;       // first big node of this launch (grid.y is limited to 65535)
 };
 
-template <int METRIC, int G, int K>
-__device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) v = umin64(v, __shfl_xor_sync(FULL, v, off));
-  return v;
-}
-
-// mode 0: distances to the node's own point (kd), state reset, first minimum.
-// mode 1: one child selection.  mode 2: write the assignment and the count.
+// mode 0: keys of every point to the node's point, first minimum.
+// mode 1: one child selection, tiles of the open list across CTAs.
+// mode 3: the remaining selections, one CTA per node.
+// mode 2: closest child of every point, the assignment and the count.
 template <int METRIC, int G, int K>
 __global__ void __launch_bounds__(BIG_NW * 32) sat_big_kernel(const SatBigArgs A, int mode) {
-  using L = Lanes<G, K>;
-  constexpr int STEP = L::CPW * L::U;
-  __shared__ __align__(16) uint4 cvec[256];
+  __shared__ uint64_t rk[2][BIG_NW];
+  __shared__ uint32_t scnt[2];
+  extern __shared__ __align__(16) unsigned char sbig[];
   const SatSegArgs& a = A.s;
+  uint4* cvec = reinterpret_cast<uint4*>(sbig);
+  uint4* kvec = cvec + a.nchunks;
+  int32_t* kids = reinterpret_cast<int32_t*>(kvec + (int64_t)a.kc * a.nchunks);
   const int y = blockIdx.y + A.y_off;
   const int sidx = A.big[y];
   const int64_t start = a.seg_start[sidx];
   const int m = a.seg_len[sidx];
   const int32_t anode = a.seg_node[sidx];
   const int64_t tbase = (int64_t)a.seg_tree[sidx] * a.n;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane / L::P, j = lane % L::P;
-  const int t0 = blockIdx.x * BIG_TILE;
-  if (t0 >= m) return;
-  const int t1 = min(m, t0 + BIG_TILE);
-  if (mode == 2) {
-    for (int i = t0 + threadIdx.x; i < t1; i += BIG_NW * 32) {
-      const int64_t it = start + i;
-      a.node_of[tbase + a.item_pt[it]] = a.flag[it] == 2 ? -1 : key_id(a.best[it]);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      const long long mm = m, k = A.kcount[y];
-      atomicAdd(a.ctr, (unsigned long long)(mm + k * (k - 1) / 2 + (mm - k) * k));
-    }
+  if (mode == 3) {
+    if (threadIdx.x == 0) scnt[0] = scnt[1] = 0;
+    const uint64_t bk = A.cur[y];
+    int k = (int)A.kcount[y];
+    if (bk != PAD)
+      k = sat_select<METRIC, G, K, BIG_NW>(a, start, anode, tbase, A.lin + start,
+                                           A.lout + start, (int)A.curlen[y], bk, k, cvec, rk,
+                                           scnt);
+    if (threadIdx.x == 0) A.kcount[y] = (uint32_t)k;
     return;
   }
-  int32_t bpt = anode;
-  if (mode == 1) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) A.clr[y] = PAD;
-    const uint64_t bk = A.cur[y];
-    if (bk == PAD) return;
-    bpt = key_id(bk);
+  if (mode == 2) {
+    const int t0 = blockIdx.x * BIG_TILE;
+    if (t0 >= m) return;
+    const int k = (int)A.kcount[y];
+    sat_assign<METRIC, G, K, BIG_NW>(a, start, t0, min(m, t0 + BIG_TILE), k, tbase, kvec, kids);
+    if (blockIdx.x == 0 && threadIdx.x == 0) sat_count(a, m, k);
+    return;
   }
-  stage_row_cta(cvec, a.X + (int64_t)bpt * a.ld_bytes, a.nchunks);
+  if (mode == 0) {
+    const int t0 = blockIdx.x * BIG_TILE;
+    if (t0 >= m) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.curlen[y] = (uint32_t)m;
+    stage_row_cta(cvec, a.X + (int64_t)anode * a.ld_bytes, a.nchunks);
+    __syncthreads();
+    uint64_t lmin = sat_first<METRIC, G, K, BIG_NW>(a, start, t0, min(m, t0 + BIG_TILE), cvec,
+                                                    A.lin + start);
+    lmin = warp_min64(lmin);
+    if ((threadIdx.x & 31) == 0 && lmin != PAD)
+      atomicMin(reinterpret_cast<unsigned long long*>(A.cur + y), (unsigned long long)lmin);
+    return;
+  }
+  // mode 1
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    A.clr[y] = PAD;
+    A.clrlen[y] = 0;
+  }
+  const uint64_t bk = A.cur[y];
+  if (bk == PAD) return;
+  const int32_t b = key_id(bk);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const uint32_t k = A.kcount[y];
+    a.kid[start + k] = b;
+    a.parent[tbase + b] = anode;
+    A.kcount[y] = k + 1;
+  }
+  const int L = (int)A.curlen[y];
+  const int e0 = blockIdx.x * BIG_TILE;
+  if (e0 >= L) return;
+  stage_row_cta(cvec, a.X + (int64_t)b * a.ld_bytes, a.nchunks);
   __syncthreads();
-  uint64_t lmin = PAD;
-  for (int base = t0 + warp * STEP; base < t1; base += BIG_NW * STEP) {
-    uint4 yv[L::U][L::VL][K];
-#pragma unroll
-    for (int u = 0; u < L::U; ++u) {
-      const int idx = min(base + u * L::CPW + g, t1 - 1);
-      load_slots<G, K>(a.X + (int64_t)a.item_pt[start + idx] * a.ld_bytes, a.nchunks, j, yv[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < L::U; ++u) {
-      const float dd = slots_dist<METRIC, G, K>(cvec, yv[u], a.nchunks, a.d, j);
-      const int idx = base + u * L::CPW + g;
-      if (idx < t1 && j == 0) {
-        const int64_t it = start + idx;
-        const int32_t pt = a.item_pt[it];
-        if (mode == 0) {
-          a.kd[it] = dd;
-          a.best[it] = PAD;
-          a.flag[it] = 0;
-          lmin = umin64(lmin, make_key(dd, pt));
-        } else if (pt == bpt) {
-          a.flag[it] = 2;
-          a.parent[tbase + bpt] = anode;
-          atomicAdd(&A.kcount[y], 1u);
-        } else {
-          const uint8_t f = a.flag[it];
-          if (f != 2) {
-            const uint64_t ck = make_key(dd, bpt);
-            if (ck < a.best[it]) a.best[it] = ck;
-            if (f == 0) {
-              const float kdv = a.kd[it];
-              if (dd <= kdv) {
-                a.flag[it] = 1;
-              } else {
-                lmin = umin64(lmin, make_key(kdv, pt));
-              }
-            }
-          }
-        }
-      }
-    }
-  }
-  lmin = warp_min64<METRIC, G, K>(lmin);
-  if (lane == 0 && lmin != PAD)
-    atomicMin(reinterpret_cast<unsigned long long*>((mode == 0 ? A.cur : A.nxt) + y),
-              (unsigned long long)lmin);
+  uint64_t lmin = sat_step<METRIC, G, K, BIG_NW>(a, A.lin + start, A.lout + start, e0,
+                                                 min(L, e0 + BIG_TILE), bk, cvec, A.nxtlen + y);
+  lmin = warp_min64(lmin);
+  if ((threadIdx.x & 31) == 0 && lmin != PAD)
+    atomicMin(reinterpret_cast<unsigned long long*>(A.nxt + y), (unsigned long long)lmin);
 }
 
 using SatBigFn = void (*)(const SatBigArgs, int);
 
 using SatKernelFn = void (*)(const SatSegArgs);
 constexpr int SAT_NW = 8;
+constexpr int SAT_SMEM = 32768;
 
 static SatKernelFn sat_kernel_for(int metric, int G, int K) {
 #define SATX(M, GG, KK) \
@@ -420,13 +499,19 @@ int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* paren
   a.seg_len = S.seg_len;
   a.seg_node = S.seg_node;
   a.seg_tree = S.seg_tree;
-  a.kd = S.kd;
+  a.lst0 = S.lst;
+  a.lst1 = S.lst + tot;
   a.best = S.best;
-  a.flag = S.flag;
+  a.kid = S.kid;
+  // children staged per assignment chunk: about 32 KB of shared memory per CTA
+  const int row16 = L.nchunks * 16;
+  a.kc = std::max(1, std::min(256, (SAT_SMEM - row16) / (row16 + 4)));
+  const size_t smem = (size_t)row16 * (1 + a.kc) + sizeof(int32_t) * a.kc;
   a.node_of = S.node_of;
   a.parent = parents;
   a.ctr = ctr_sat;
   std::vector<uint64_t> hkeys;
+  std::vector<uint32_t> hlens;
   for (int64_t level = 0; level <= n; ++level) {
     FG_CUDA(cudaMemsetAsync(S.nseg, 0, 3 * sizeof(uint32_t), s));
     sat_count_kernel<<<grid_for(tot), 256, 0, s>>>(n, tot, S.node_of, S.kcnt, S.nseg + 2);
@@ -451,7 +536,7 @@ int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* paren
     const uint32_t nsmall = cnts[0], nbig = cnts[1];
     if (nsmall == 0 && nbig == 0) return 0;
     if (nsmall) {
-      kern<<<nsmall, SAT_NW * 32, 0, s>>>(a);
+      kern<<<nsmall, SAT_NW * 32, smem, s>>>(a);
       note_launch();
       FG_CUDA(cudaGetLastError());
     }
@@ -459,48 +544,60 @@ int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* paren
       SatBigArgs B;
       B.s = a;
       B.big = S.big_list;
-      uint64_t* buf[3] = {S.big_keys, S.big_keys + nbig, S.big_keys + 2 * nbig};
       B.kcount = S.big_kcount;
+      uint64_t* kb[3] = {S.big_keys, S.big_keys + nbig, S.big_keys + 2 * nbig};
+      uint32_t* lb[3] = {S.big_lens, S.big_lens + nbig, S.big_lens + 2 * nbig};
+      uint64_t* lists[2] = {a.lst0, a.lst1};
       FG_CUDA(cudaMemsetAsync(S.big_keys, 0xFF, 3 * nbig * sizeof(uint64_t), s));
+      FG_CUDA(cudaMemsetAsync(S.big_lens, 0, 3 * nbig * sizeof(uint32_t), s));
       FG_CUDA(cudaMemsetAsync(S.big_kcount, 0, nbig * sizeof(uint32_t), s));
       const unsigned gx = (unsigned)((n + BIG_TILE - 1) / BIG_TILE);
+      int r = 0, par = 0;  // kb[r], lb[r], lists[par]: the current step's state
       // grid.y is limited to 65535: big nodes are covered in chunks
-      auto launch_all = [&](int mode) {
+      auto launch_all = [&](int mode, unsigned gxm) {
+        B.cur = kb[r];
+        B.nxt = kb[(r + 1) % 3];
+        B.clr = kb[(r + 2) % 3];
+        B.curlen = lb[r];
+        B.nxtlen = lb[(r + 1) % 3];
+        B.clrlen = lb[(r + 2) % 3];
+        B.lin = lists[par];
+        B.lout = lists[par ^ 1];
         for (uint32_t y0 = 0; y0 < nbig; y0 += 65535u) {
           B.y_off = (int32_t)y0;
-          const dim3 grid(gx, std::min<uint32_t>(65535u, nbig - y0));
-          bigk<<<grid, BIG_NW * 32, 0, s>>>(B, mode);
+          const dim3 grid(gxm, std::min<uint32_t>(65535u, nbig - y0));
+          bigk<<<grid, BIG_NW * 32, smem, s>>>(B, mode);
           note_launch();
         }
       };
-      B.cur = buf[0];
-      B.nxt = buf[1];
-      B.clr = buf[2];
-      launch_all(0);
+      launch_all(0, gx);
       FG_CUDA(cudaGetLastError());
       hkeys.resize(nbig);
-      int r = 0;  // buf[r] holds the next child of every big node
-      bool done = false;
-      for (int64_t it = 0; it <= n && !done;) {
-        for (int j = 0; j < 8; ++j, ++it) {
-          B.cur = buf[r];
-          B.nxt = buf[(r + 1) % 3];
-          B.clr = buf[(r + 2) % 3];
-          launch_all(1);
+      hlens.resize(nbig);
+      // tiled selection steps while some open list is long
+      bool short_lists = false;
+      for (int64_t it = 0; it <= n && !short_lists;) {
+        for (int j = 0; j < 4; ++j, ++it) {
+          launch_all(1, gx);
           r = (r + 1) % 3;
+          par ^= 1;
         }
         FG_CUDA(cudaGetLastError());
-        FG_CUDA(cudaMemcpyAsync(hkeys.data(), buf[r], nbig * sizeof(uint64_t),
+        FG_CUDA(cudaMemcpyAsync(hkeys.data(), kb[r], nbig * sizeof(uint64_t),
+                                cudaMemcpyDeviceToHost, s));
+        FG_CUDA(cudaMemcpyAsync(hlens.data(), lb[r], nbig * sizeof(uint32_t),
                                 cudaMemcpyDeviceToHost, s));
         FG_CUDA(cudaStreamSynchronize(s));
-        done = true;
-        for (uint64_t k : hkeys) done &= (k == PAD);
+        short_lists = true;
+        for (uint32_t i = 0; i < nbig; ++i)
+          short_lists &= (hkeys[i] == PAD || hlens[i] <= (uint32_t)S.finish_len);
       }
-      if (!done) {
+      if (!short_lists) {
         set_error(1, "SAT child selection did not terminate");
         return 1;
       }
-      launch_all(2);
+      launch_all(3, 1);
+      launch_all(2, gx);
       FG_CUDA(cudaGetLastError());
     }
   }

@@ -194,8 +194,8 @@ def fgraft_index_harvest_ms(ix: Index, with_prune: bool = False):
     return (ms.value, nl.value, pm.value) if with_prune else (ms.value, nl.value)
 
 
-def fgraft_tune_sat(big_node_min: int = 16384):
-    _check(load().fgraft_tune_sat(C.c_int32(big_node_min)))
+def fgraft_tune_sat(big_node_min: int = 0, finish_len: int = 0):
+    _check(load().fgraft_tune_sat(C.c_int32(big_node_min), C.c_int32(finish_len)))
 
 
 def fgraft_kernel_launches() -> int:

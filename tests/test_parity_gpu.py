@@ -210,16 +210,17 @@ def test_profile_hooks(fg, use_graph):
     assert fg.fgraft_kernel_launches() - before > 4
 
 
-@pytest.mark.parametrize("split", [2, 64, 700])
-def test_sat_multi_cta_nodes(fg, split):
-    # force the multi-CTA SAT path for small nodes too; the forest must not change
+@pytest.mark.parametrize("split,finish", [(2, 1), (64, 16), (700, 2048), (300, 100)])
+def test_sat_multi_cta_nodes(fg, split, finish):
+    # force the multi-CTA SAT path for small nodes too, with tiled selection
+    # steps down to lists of `finish` points; the forest must not change
     try:
-        fg.fgraft_tune_sat(split)
+        fg.fgraft_tune_sat(split, finish)
         ps = synth.vmf_like(2500, 100, 8, seed=6)
         ix, ctr, st, fin, D, ref = _build_both(fg, ps, T=6, R=16, ef=32, B=2)
         _compare(ctr, st, fin, ref)
     finally:
-        fg.fgraft_tune_sat(16384)
+        fg.fgraft_tune_sat(16384, 2048)
 
 
 def test_n20000_parity(fg):
