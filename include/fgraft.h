@@ -248,7 +248,7 @@ fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t war
  * selection, until the list of points no child has rejected yet is at most
  * finish_len long for every such node; then one CTA per node finishes the
  * selection.  Smaller nodes get one CTA each from the start.
- * Defaults 16384 and 2048; big_node_min >= 2, finish_len >= 1; 0 leaves a
+ * Defaults 16384 and 512; big_node_min >= 2, finish_len >= 1; 0 leaves a
  * value unchanged. */
 fgraft_status fgraft_tune_sat(int32_t big_node_min, int32_t finish_len);
 

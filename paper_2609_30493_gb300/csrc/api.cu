@@ -87,7 +87,7 @@ using namespace fg;
 
 // Nodes of at least this many points are built by the multi-CTA SAT path.
 static int32_t g_sat_big_min = 16384;
-static int32_t g_sat_finish_len = 2048;
+static int32_t g_sat_finish_len = 512;
 
 #define FGS(call)                                                      \
   do {                                                                 \
@@ -526,17 +526,17 @@ fgraft_status fgraft_build_scaffold(const void* X, int64_t n, int32_t d, int64_t
   rc = rc ? rc : dalloc(&S.seg_len, tot + nbig_max);
   rc = rc ? rc : dalloc(&S.seg_node, tot + nbig_max);
   rc = rc ? rc : dalloc(&S.seg_tree, tot + nbig_max);
-  rc = rc ? rc : dalloc(&S.nseg, 3);
+  rc = rc ? rc : dalloc(&S.seg_k, tot + nbig_max);
+  rc = rc ? rc : dalloc(&S.nseg, 4);
   rc = rc ? rc : dalloc(&S.big_list, nbig_max);
   rc = rc ? rc : dalloc(&S.big_keys, 3 * nbig_max);
   rc = rc ? rc : dalloc(&S.big_kcount, nbig_max);
   rc = rc ? rc : dalloc(&S.big_lens, 3 * nbig_max);
   S.finish_len = g_sat_finish_len;
-  S.nunsettled = S.nseg + 2;
   S.scan_tmp = ix->scan_tmp;
   auto free_sat = [&]() {
     void* ps[] = {S.node_of, S.kcnt, S.kstart, S.item_pt, S.lst, S.best, S.kid,
-                  S.seg_start, S.seg_len, S.seg_node, S.seg_tree, S.nseg,
+                  S.seg_start, S.seg_len, S.seg_node, S.seg_tree, S.seg_k, S.nseg,
                   S.big_list, S.big_keys, S.big_kcount, S.big_lens};
     for (void* q : ps)
       if (q) cudaFree(q);

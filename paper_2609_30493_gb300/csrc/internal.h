@@ -57,12 +57,12 @@ struct SatScratch {
   uint64_t* lst;        // 2*T*n (open lists)
   uint64_t* best;       // T*n
   int32_t* kid;         // T*n (children of a node at the start of its item range)
+  int32_t* seg_k;       // like seg_start (children per node)
   int64_t* seg_start;   // T*n + T*n/big_min + 1 (small nodes first, big ones from T*n)
   int32_t* seg_len;     // same
   int32_t* seg_node;    // same
   int32_t* seg_tree;    // same
-  uint32_t* nseg;       // 2: small nodes, big nodes of the level
-  uint32_t* nunsettled; // 1
+  uint32_t* nseg;       // 4: tiny, big nodes of the level, error flag, other nodes
   int64_t* scan_tmp;
   int32_t big_min;      // nodes with at least this many points use the multi-CTA path
   int32_t* big_list;    // segment index of each big node

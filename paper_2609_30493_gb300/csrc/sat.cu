@@ -40,6 +40,10 @@ struct SatSegArgs {
   uint64_t* best;  // closest child by (delta, id); bit 0 marks a child itself
   int32_t* kid;    // kid[start + t] = t-th child of the node of that item range
   int32_t kc;      // children staged per chunk in the assignment phase
+  int32_t ls;      // open points the selection can stage in shared memory
+  int64_t seg_off; // first segment of a launch of the one-CTA-per-node kernel
+  int32_t* seg_k;  // children per segment when the assignment runs as its own launch,
+                   // else null (the node's CTA assigns its points itself)
   int32_t* node_of;
   int32_t* parent;
   unsigned long long* ctr;
@@ -57,6 +61,37 @@ __device__ __forceinline__ uint64_t block_min64(uint64_t key, uint64_t (*rk)[NW]
   key = PAD;
 #pragma unroll
   for (int w = 0; w < NW; ++w) key = umin64(key, rk[parity][w]);
+  return key;
+}
+
+// The same with the index of the minimum carried along (keys are unique).
+template <int NW>
+__device__ __forceinline__ uint64_t block_argmin64(uint64_t key, int& idx, uint64_t (*rk)[NW],
+                                                   int (*ri)[NW], int parity) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const uint64_t ok = __shfl_xor_sync(FULL, key, off);
+    const int oi = __shfl_xor_sync(FULL, idx, off);
+    if (ok < key) {
+      key = ok;
+      idx = oi;
+    }
+  }
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    rk[parity][warp] = key;
+    ri[parity][warp] = idx;
+  }
+  __syncthreads();
+  key = PAD;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const uint64_t kk = rk[parity][w];
+    if (kk < key) {
+      key = kk;
+      idx = ri[parity][w];
+    }
+  }
   return key;
 }
 
@@ -153,24 +188,41 @@ __device__ uint64_t sat_step(const SatSegArgs& a, const uint64_t* lin, uint64_t*
   return lmin;
 }
 
+// Shared-memory state of a CTA's selection once the open list is short: the
+// rows of the open points, their keys and two index lists over them.
+struct SelSmem {
+  uint4* rows;     // ls rows of nchunks chunks
+  uint64_t* skey;  // ls keys
+  int32_t* sl0;    // ls indices
+  int32_t* sl1;    // ls indices
+  int32_t ls;      // capacity
+};
+
 // The rest of a node's selection inside one CTA: starting from the open list
 // lin (L entries, smallest key bk) and k children chosen so far, select until
-// the list is empty.  scnt[0..1] must be zero and visible before the call.
-// Returns the number of children.
+// the list is empty.  Steps read the open points from global memory while
+// the list is longer than sm.ls; then the open points are staged once in
+// shared memory and the remaining steps touch no global memory.
+// Step k appends through scnt[k % 3] and clears scnt[(k + 2) % 3] after its
+// barrier (that counter was last read in step k - 1 and is next appended to
+// in step k + 2, after another barrier), so all three must be zero and
+// visible before the call.  Returns the number of children.
 template <int METRIC, int G, int K, int NW>
 __device__ int sat_select(const SatSegArgs& a, int64_t start, int32_t anode, int64_t tbase,
                           uint64_t* lin, uint64_t* lout, int L, uint64_t bk, int k, uint4* cvec,
-                          uint64_t (*rk)[NW], uint32_t* scnt) {
+                          const SelSmem& sm, uint64_t (*rk)[NW], int (*ri)[NW], uint32_t* scnt) {
+  using Ln = Lanes<G, K>;
+  const int nch = a.nchunks;
   int parity = 1;
-  while (bk != PAD) {
+  while (bk != PAD && L > sm.ls) {
     const int32_t b = key_id(bk);
     if (threadIdx.x == 0) {
       a.kid[start + k] = b;
       a.parent[tbase + b] = anode;
     }
     ++k;
-    const int c = k & 1;
-    stage_row_cta(cvec, a.X + (int64_t)b * a.ld_bytes, a.nchunks);
+    const int c = k % 3;
+    stage_row_cta(cvec, a.X + (int64_t)b * a.ld_bytes, nch);
     __syncthreads();
     const uint64_t lmin = sat_step<METRIC, G, K, NW>(a, lin, lout, 0, L, bk, cvec, scnt + c);
     bk = block_min64<NW>(lmin, rk, parity);
@@ -179,8 +231,65 @@ __device__ int sat_select(const SatSegArgs& a, int64_t start, int32_t anode, int
     uint64_t* t = lin;
     lin = lout;
     lout = t;
-    // every thread read scnt[c ^ 1] before the barrier of this step
-    if (threadIdx.x == 0) scnt[c ^ 1] = 0;
+    if (threadIdx.x == 0) scnt[(k + 2) % 3] = 0;
+  }
+  if (bk == PAD) return k;
+  // stage the open points
+  __shared__ int sib;
+  for (int i = threadIdx.x; i < L; i += NW * 32) {
+    const uint64_t e = lin[i];
+    sm.skey[i] = e;
+    sm.sl0[i] = i;
+    if (e == bk) sib = i;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < L * nch; idx += NW * 32) {
+    const int i = idx / nch, ch = idx - i * nch;
+    sm.rows[idx] =
+        __ldg(reinterpret_cast<const uint4*>(a.X + (int64_t)key_id(sm.skey[i]) * a.ld_bytes) +
+              ch);
+  }
+  __syncthreads();
+  int ib = sib;
+  int32_t* cl = sm.sl0;
+  int32_t* nl = sm.sl1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane / Ln::P, j = lane % Ln::P;
+  while (bk != PAD) {
+    const int32_t b = key_id(bk);
+    if (threadIdx.x == 0) {
+      a.kid[start + k] = b;
+      a.parent[tbase + b] = anode;
+    }
+    ++k;
+    const int c = k % 3;
+    const uint4* crow = sm.rows + (int64_t)ib * nch;
+    uint64_t lmin = PAD;
+    int li = -1;
+    for (int base = warp * Ln::CPW; base < L; base += NW * Ln::CPW) {  // warp-uniform
+      const int e = cl[min(base + g, L - 1)];
+      uint4 y[Ln::VL][K];
+      load_slots_smem<G, K>(sm.rows + (int64_t)e * nch, nch, j, y);
+      const float dd = slots_dist<METRIC, G, K>(crow, y, nch, a.d, j);
+      const uint64_t ek = sm.skey[e];
+      const bool keep = j == 0 && base + g < L && ek != bk && dd > key_dist(ek);
+      const uint32_t pos = warp_append(keep, scnt + c);
+      if (keep) {
+        nl[pos] = e;
+        if (ek < lmin) {
+          lmin = ek;
+          li = e;
+        }
+      }
+    }
+    bk = block_argmin64<NW>(lmin, li, rk, ri, parity);
+    parity ^= 1;
+    ib = li;
+    L = (int)scnt[c];
+    int32_t* t = cl;
+    cl = nl;
+    nl = t;
+    if (threadIdx.x == 0) scnt[(k + 2) % 3] = 0;
   }
   return k;
 }
@@ -241,31 +350,74 @@ __device__ __forceinline__ void sat_count(const SatSegArgs& a, int m, int k) {
   atomicAdd(a.ctr, (unsigned long long)(mm + kk * (kk - 1) / 2 + (mm - kk) * kk));
 }
 
+// Dynamic shared memory of the SAT kernels: one row (the node's point, then
+// each new child), then a region used first by the selection (SelSmem) and
+// then by the assignment (kc staged children and their ids).
+__device__ __forceinline__ SelSmem sel_smem(const SatSegArgs& a, unsigned char* base) {
+  SelSmem sm;
+  const int64_t nch = a.nchunks;
+  sm.rows = reinterpret_cast<uint4*>(base) + nch;
+  sm.skey = reinterpret_cast<uint64_t*>(sm.rows + (int64_t)a.ls * nch);
+  sm.sl0 = reinterpret_cast<int32_t*>(sm.skey + a.ls);
+  sm.sl1 = sm.sl0 + a.ls;
+  sm.ls = a.ls;
+  return sm;
+}
+
 // A node with fewer points: one CTA runs the whole construction of its
 // children.
 template <int METRIC, int G, int K, int NW>
 __global__ void __launch_bounds__(NW * 32) sat_segment_kernel(const SatSegArgs a) {
   __shared__ uint64_t rk[2][NW];
-  __shared__ uint32_t scnt[2];
+  __shared__ int ri[2][NW];
+  __shared__ uint32_t scnt[3];
   extern __shared__ __align__(16) unsigned char ssat[];
   uint4* cvec = reinterpret_cast<uint4*>(ssat);  // the node's point, then each new child
   uint4* kvec = cvec + a.nchunks;               // children staged for the assignment
   int32_t* kids = reinterpret_cast<int32_t*>(kvec + (int64_t)a.kc * a.nchunks);
-  const int s = blockIdx.x;
+  const SelSmem sm = sel_smem(a, ssat);
+  const int64_t s = a.seg_off + blockIdx.x;
   const int64_t start = a.seg_start[s];
   const int m = a.seg_len[s];
   const int32_t anode = a.seg_node[s];
   const int64_t tbase = (int64_t)a.seg_tree[s] * a.n;
-  if (threadIdx.x == 0) scnt[0] = scnt[1] = 0;
+  if (threadIdx.x == 0) scnt[0] = scnt[1] = scnt[2] = 0;
   stage_row_cta(cvec, a.X + (int64_t)anode * a.ld_bytes, a.nchunks);
   __syncthreads();
   uint64_t* l0 = a.lst0 + start;
   const uint64_t lmin = sat_first<METRIC, G, K, NW>(a, start, 0, m, cvec, l0);
   const uint64_t bk = block_min64<NW>(lmin, rk, 0);
   const int k = sat_select<METRIC, G, K, NW>(a, start, anode, tbase, l0, a.lst1 + start, m, bk,
-                                             0, cvec, rk, scnt);
+                                             0, cvec, sm, rk, ri, scnt);
+  if (a.seg_k) {
+    if (threadIdx.x == 0) a.seg_k[s] = k;
+    return;
+  }
   sat_assign<METRIC, G, K, NW>(a, start, 0, m, k, tbase, kvec, kids);
   if (threadIdx.x == 0) sat_count(a, m, k);
+}
+
+// The assignment as its own launch, tiles of ASSIGN_TILE points of a node per
+// CTA: segment segs[y] (or seg_off + y without a list), its children counted
+// in seg_k.
+constexpr int ASSIGN_TILE = 256;
+constexpr int ASSIGN_NW = 8;
+
+template <int METRIC, int G, int K>
+__global__ void __launch_bounds__(ASSIGN_NW * 32)
+    sat_assign_kernel(const SatSegArgs a, const int32_t* segs, int32_t y_off) {
+  extern __shared__ __align__(16) unsigned char sasg[];
+  uint4* kvec = reinterpret_cast<uint4*>(sasg) + a.nchunks;
+  int32_t* kids = reinterpret_cast<int32_t*>(kvec + (int64_t)a.kc * a.nchunks);
+  const int y = blockIdx.y + y_off;
+  const int64_t s = segs ? (int64_t)segs[y] : a.seg_off + y;
+  const int m = a.seg_len[s];
+  const int t0 = blockIdx.x * ASSIGN_TILE;
+  if (t0 >= m) return;
+  const int k = a.seg_k[s];
+  sat_assign<METRIC, G, K, ASSIGN_NW>(a, a.seg_start[s], t0, min(m, t0 + ASSIGN_TILE), k,
+                                      (int64_t)a.seg_tree[s] * a.n, kvec, kids);
+  if (blockIdx.x == 0 && threadIdx.x == 0) sat_count(a, m, k);
 }
 
 // ---------------------------------------------------------------------------
@@ -277,7 +429,8 @@ __global__ void __launch_bounds__(NW * 32) sat_segment_kernel(const SatSegArgs a
 // waits for another.  Once the lists are short, one CTA per node finishes
 // the selection, and the assignment is again split into tiles.
 // ---------------------------------------------------------------------------
-constexpr int BIG_TILE = 2048;  // points per CTA
+constexpr int BIG_TILE = 512;   // points per CTA (modes 0 and 2)
+constexpr int STEP_TILE = 256;  // open entries per CTA (mode 1)
 constexpr int BIG_NW = 8;
 
 struct SatBigArgs {
@@ -297,17 +450,16 @@ struct SatBigArgs {
 
 // mode 0: keys of every point to the node's point, first minimum.
 // mode 1: one child selection, tiles of the open list across CTAs.
-// mode 3: the remaining selections, one CTA per node.
-// mode 2: closest child of every point, the assignment and the count.
+// mode 3: the remaining selections, one CTA per node; the assignment follows
+// as sat_assign_kernel.
 template <int METRIC, int G, int K>
 __global__ void __launch_bounds__(BIG_NW * 32) sat_big_kernel(const SatBigArgs A, int mode) {
   __shared__ uint64_t rk[2][BIG_NW];
-  __shared__ uint32_t scnt[2];
+  __shared__ int ri[2][BIG_NW];
+  __shared__ uint32_t scnt[3];
   extern __shared__ __align__(16) unsigned char sbig[];
   const SatSegArgs& a = A.s;
   uint4* cvec = reinterpret_cast<uint4*>(sbig);
-  uint4* kvec = cvec + a.nchunks;
-  int32_t* kids = reinterpret_cast<int32_t*>(kvec + (int64_t)a.kc * a.nchunks);
   const int y = blockIdx.y + A.y_off;
   const int sidx = A.big[y];
   const int64_t start = a.seg_start[sidx];
@@ -315,22 +467,15 @@ __global__ void __launch_bounds__(BIG_NW * 32) sat_big_kernel(const SatBigArgs A
   const int32_t anode = a.seg_node[sidx];
   const int64_t tbase = (int64_t)a.seg_tree[sidx] * a.n;
   if (mode == 3) {
-    if (threadIdx.x == 0) scnt[0] = scnt[1] = 0;
+    if (threadIdx.x == 0) scnt[0] = scnt[1] = scnt[2] = 0;
+    __syncthreads();
     const uint64_t bk = A.cur[y];
     int k = (int)A.kcount[y];
     if (bk != PAD)
       k = sat_select<METRIC, G, K, BIG_NW>(a, start, anode, tbase, A.lin + start,
-                                           A.lout + start, (int)A.curlen[y], bk, k, cvec, rk,
-                                           scnt);
-    if (threadIdx.x == 0) A.kcount[y] = (uint32_t)k;
-    return;
-  }
-  if (mode == 2) {
-    const int t0 = blockIdx.x * BIG_TILE;
-    if (t0 >= m) return;
-    const int k = (int)A.kcount[y];
-    sat_assign<METRIC, G, K, BIG_NW>(a, start, t0, min(m, t0 + BIG_TILE), k, tbase, kvec, kids);
-    if (blockIdx.x == 0 && threadIdx.x == 0) sat_count(a, m, k);
+                                           A.lout + start, (int)A.curlen[y], bk, k, cvec,
+                                           sel_smem(a, sbig), rk, ri, scnt);
+    if (threadIdx.x == 0) a.seg_k[sidx] = k;
     return;
   }
   if (mode == 0) {
@@ -361,12 +506,12 @@ __global__ void __launch_bounds__(BIG_NW * 32) sat_big_kernel(const SatBigArgs A
     A.kcount[y] = k + 1;
   }
   const int L = (int)A.curlen[y];
-  const int e0 = blockIdx.x * BIG_TILE;
+  const int e0 = blockIdx.x * STEP_TILE;
   if (e0 >= L) return;
   stage_row_cta(cvec, a.X + (int64_t)b * a.ld_bytes, a.nchunks);
   __syncthreads();
   uint64_t lmin = sat_step<METRIC, G, K, BIG_NW>(a, A.lin + start, A.lout + start, e0,
-                                                 min(L, e0 + BIG_TILE), bk, cvec, A.nxtlen + y);
+                                                 min(L, e0 + STEP_TILE), bk, cvec, A.nxtlen + y);
   lmin = warp_min64(lmin);
   if ((threadIdx.x & 31) == 0 && lmin != PAD)
     atomicMin(reinterpret_cast<unsigned long long*>(A.nxt + y), (unsigned long long)lmin);
@@ -375,12 +520,40 @@ __global__ void __launch_bounds__(BIG_NW * 32) sat_big_kernel(const SatBigArgs A
 using SatBigFn = void (*)(const SatBigArgs, int);
 
 using SatKernelFn = void (*)(const SatSegArgs);
-constexpr int SAT_NW = 8;
-constexpr int SAT_SMEM = 32768;
+constexpr int SAT_NW = 8;           // warps per CTA: nodes of more points, the big path
+constexpr int TINY_NW = 2;          // warps per CTA: nodes that fit in shared memory
+constexpr int SAT_SMEM = 96 * 1024; // dynamic shared memory per CTA, by CTA width
+constexpr int TINY_SMEM = 24 * 1024;
 
+template <int NW>
 static SatKernelFn sat_kernel_for(int metric, int G, int K) {
 #define SATX(M, GG, KK) \
-  if (metric == M && G == GG && K == KK) return sat_segment_kernel<M, GG, KK, SAT_NW>;
+  if (metric == M && G == GG && K == KK) return sat_segment_kernel<M, GG, KK, NW>;
+#define SATF(M) SATX(M, 4, 1) SATX(M, 8, 1) SATX(M, 16, 1) SATX(M, 32, 1) SATX(M, 32, 2) \
+  SATX(M, 32, 4) SATX(M, 32, 8)
+  SATF(0)
+  SATF(1)
+  SATX(2, 4, 1) SATX(2, 8, 1) SATX(2, 16, 1)
+#undef SATF
+#undef SATX
+  return nullptr;
+}
+
+// Shared-memory split for a CTA with `budget` bytes: open points staged by
+// the selection (a.ls) and children staged per assignment chunk (a.kc).
+// Returns the dynamic shared memory size.
+static size_t sat_smem_plan(SatSegArgs& a, int budget) {
+  const int row16 = a.nchunks * 16;
+  a.ls = std::max(1, std::min(4096, (budget - row16) / (row16 + 16)));
+  a.kc = std::max(1, std::min(256, (budget - row16) / (row16 + 4)));
+  return (size_t)row16 + std::max((size_t)a.ls * (row16 + 16), (size_t)a.kc * (row16 + 4));
+}
+
+using SatAssignFn = void (*)(const SatSegArgs, const int32_t*, int32_t);
+
+static SatAssignFn sat_assign_for(int metric, int G, int K) {
+#define SATX(M, GG, KK) \
+  if (metric == M && G == GG && K == KK) return sat_assign_kernel<M, GG, KK>;
 #define SATF(M) SATX(M, 4, 1) SATX(M, 8, 1) SATX(M, 16, 1) SATX(M, 32, 1) SATX(M, 32, 2) \
   SATX(M, 32, 4) SATX(M, 32, 8)
   SATF(0)
@@ -432,22 +605,28 @@ __global__ void sat_count_kernel(int64_t n, int64_t tot, const int32_t* node_of,
   }
 }
 
+// Segment lists of a level: nodes of at most tiny_max points fill the list
+// from the front (count nseg[0]), nodes of at least big_min points from
+// big_base on (nseg[1], with their indices in big_list), the others from the
+// top of the small-node region down (nseg[3]).
 __global__ void sat_segments_kernel(int64_t n, int64_t tot, const uint32_t* kcnt,
                                     const int64_t* kstart, int64_t* seg_start, int32_t* seg_len,
                                     int32_t* seg_node, int32_t* seg_tree, uint32_t* nseg,
-                                    int32_t big_min, int32_t* big_list, int64_t big_base) {
+                                    int32_t tiny_max, int32_t big_min, int32_t* big_list,
+                                    int64_t big_base) {
   for (int64_t key = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; key < tot;
        key += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t c = kcnt[key];
     if (c) {
-      // small nodes fill the list from the front, big ones from big_base on
-      uint32_t s;
+      int64_t s;
       if ((int32_t)c >= big_min) {
         const uint32_t j = atomicAdd(nseg + 1, 1u);
-        s = (uint32_t)(big_base + j);
+        s = big_base + j;
         big_list[j] = (int32_t)s;
-      } else {
+      } else if ((int32_t)c <= tiny_max) {
         s = atomicAdd(nseg, 1u);
+      } else {
+        s = tot - 1 - (int64_t)atomicAdd(nseg + 3, 1u);
       }
       seg_start[s] = kstart[key];
       seg_len[s] = (int32_t)c;
@@ -478,9 +657,11 @@ static int grid_for(int64_t tot) {
 
 int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* parents,
                SatScratch& S, unsigned long long* ctr_sat, cudaStream_t s) {
-  SatKernelFn kern = sat_kernel_for(L.metric, L.G, L.K);
+  SatKernelFn kern = sat_kernel_for<SAT_NW>(L.metric, L.G, L.K);
+  SatKernelFn tinyk = sat_kernel_for<TINY_NW>(L.metric, L.G, L.K);
   SatBigFn bigk = sat_big_for(L.metric, L.G, L.K);
-  if (!kern || !bigk) {
+  SatAssignFn asgk = sat_assign_for(L.metric, L.G, L.K);
+  if (!kern || !tinyk || !bigk || !asgk) {
     set_error(1, "no SAT kernel for this metric and dimension");
     return 1;
   }
@@ -503,40 +684,64 @@ int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* paren
   a.lst1 = S.lst + tot;
   a.best = S.best;
   a.kid = S.kid;
-  // children staged per assignment chunk: about 32 KB of shared memory per CTA
-  const int row16 = L.nchunks * 16;
-  a.kc = std::max(1, std::min(256, (SAT_SMEM - row16) / (row16 + 4)));
-  const size_t smem = (size_t)row16 * (1 + a.kc) + sizeof(int32_t) * a.kc;
   a.node_of = S.node_of;
   a.parent = parents;
   a.ctr = ctr_sat;
+  a.seg_off = 0;
+  a.seg_k = nullptr;
+  SatSegArgs at = a;
+  a.seg_k = S.seg_k;
+  const size_t smem = sat_smem_plan(a, SAT_SMEM);
+  const size_t smem_t = sat_smem_plan(at, TINY_SMEM);
+  FG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FG_CUDA(cudaFuncSetAttribute(bigk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FG_CUDA(cudaFuncSetAttribute(tinyk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t));
+  FG_CUDA(cudaFuncSetAttribute(asgk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // the assignment launches: tiles of one node per grid column, nodes in rows
+  // (grid.y is limited to 65535, so rows are covered in chunks)
+  auto assign_all = [&](const int32_t* segs, uint32_t nrows, int64_t max_m) {
+    const unsigned gxa = (unsigned)((max_m + ASSIGN_TILE - 1) / ASSIGN_TILE);
+    for (uint32_t y0 = 0; y0 < nrows; y0 += 65535u) {
+      const dim3 grid(gxa, std::min<uint32_t>(65535u, nrows - y0));
+      asgk<<<grid, ASSIGN_NW * 32, smem, s>>>(a, segs, (int32_t)y0);
+      note_launch();
+    }
+  };
+  const int32_t tiny_max = at.ls;  // such nodes are staged in shared memory whole
   std::vector<uint64_t> hkeys;
   std::vector<uint32_t> hlens;
   for (int64_t level = 0; level <= n; ++level) {
-    FG_CUDA(cudaMemsetAsync(S.nseg, 0, 3 * sizeof(uint32_t), s));
+    FG_CUDA(cudaMemsetAsync(S.nseg, 0, 4 * sizeof(uint32_t), s));
     sat_count_kernel<<<grid_for(tot), 256, 0, s>>>(n, tot, S.node_of, S.kcnt, S.nseg + 2);
     note_launch();
     int rc = scan_u32(S.kcnt, S.kstart, tot, S.scan_tmp, s);
     if (rc) return rc;
     sat_segments_kernel<<<grid_for(tot), 256, 0, s>>>(n, tot, S.kcnt, S.kstart, S.seg_start,
                                                       S.seg_len, S.seg_node, S.seg_tree, S.nseg,
-                                                      S.big_min, S.big_list, tot);
+                                                      tiny_max, S.big_min, S.big_list, tot);
     note_launch();
     sat_scatter_kernel<<<grid_for(tot), 256, 0, s>>>(n, tot, S.node_of, S.kcnt, S.kstart,
                                                      S.item_pt);
     note_launch();
     FG_CUDA(cudaGetLastError());
-    uint32_t cnts[3] = {0, 0, 0};
+    uint32_t cnts[4] = {0, 0, 0, 0};
     FG_CUDA(cudaMemcpyAsync(cnts, S.nseg, sizeof(cnts), cudaMemcpyDeviceToHost, s));
     FG_CUDA(cudaStreamSynchronize(s));
     if (cnts[2]) {
       set_error(3, "SAT: a point was assigned to an invalid node");
       return 3;
     }
-    const uint32_t nsmall = cnts[0], nbig = cnts[1];
-    if (nsmall == 0 && nbig == 0) return 0;
+    const uint32_t ntiny = cnts[0], nbig = cnts[1], nsmall = cnts[3];
+    if (ntiny == 0 && nsmall == 0 && nbig == 0) return 0;
     if (nsmall) {
+      a.seg_off = tot - nsmall;
       kern<<<nsmall, SAT_NW * 32, smem, s>>>(a);
+      note_launch();
+      assign_all(nullptr, nsmall, std::min<int64_t>(n, S.big_min));
+      FG_CUDA(cudaGetLastError());
+    }
+    if (ntiny) {
+      tinyk<<<ntiny, TINY_NW * 32, smem_t, s>>>(at);
       note_launch();
       FG_CUDA(cudaGetLastError());
     }
@@ -552,6 +757,7 @@ int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* paren
       FG_CUDA(cudaMemsetAsync(S.big_lens, 0, 3 * nbig * sizeof(uint32_t), s));
       FG_CUDA(cudaMemsetAsync(S.big_kcount, 0, nbig * sizeof(uint32_t), s));
       const unsigned gx = (unsigned)((n + BIG_TILE - 1) / BIG_TILE);
+      unsigned gx1 = (unsigned)((n + STEP_TILE - 1) / STEP_TILE);  // open lists only shrink
       int r = 0, par = 0;  // kb[r], lb[r], lists[par]: the current step's state
       // grid.y is limited to 65535: big nodes are covered in chunks
       auto launch_all = [&](int mode, unsigned gxm) {
@@ -578,7 +784,7 @@ int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* paren
       bool short_lists = false;
       for (int64_t it = 0; it <= n && !short_lists;) {
         for (int j = 0; j < 4; ++j, ++it) {
-          launch_all(1, gx);
+          launch_all(1, gx1);
           r = (r + 1) % 3;
           par ^= 1;
         }
@@ -589,15 +795,19 @@ int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* paren
                                 cudaMemcpyDeviceToHost, s));
         FG_CUDA(cudaStreamSynchronize(s));
         short_lists = true;
-        for (uint32_t i = 0; i < nbig; ++i)
+        uint32_t max_len = 1;
+        for (uint32_t i = 0; i < nbig; ++i) {
           short_lists &= (hkeys[i] == PAD || hlens[i] <= (uint32_t)S.finish_len);
+          if (hkeys[i] != PAD) max_len = std::max(max_len, hlens[i]);
+        }
+        gx1 = (max_len + STEP_TILE - 1) / STEP_TILE;
       }
       if (!short_lists) {
         set_error(1, "SAT child selection did not terminate");
         return 1;
       }
       launch_all(3, 1);
-      launch_all(2, gx);
+      assign_all(S.big_list, nbig, n);
       FG_CUDA(cudaGetLastError());
     }
   }

@@ -220,7 +220,7 @@ def test_sat_multi_cta_nodes(fg, split, finish):
         ix, ctr, st, fin, D, ref = _build_both(fg, ps, T=6, R=16, ef=32, B=2)
         _compare(ctr, st, fin, ref)
     finally:
-        fg.fgraft_tune_sat(16384, 2048)
+        fg.fgraft_tune_sat(16384, 512)
 
 
 def test_n20000_parity(fg):
