@@ -2,6 +2,8 @@
 // sequencing of the kernels (SAT levels, harvest blocks with their overflow
 // re-run and reverse-list update, final graph, search, dense blocks).
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -26,6 +28,20 @@ static std::atomic<uint64_t> g_launches{0};
 void note_launch(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 void set_launch_count(uint64_t v) { g_launches.store(v, std::memory_order_relaxed); }
+
+cudaError_t raise_smem_limit(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> limits;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  int& cur = limits[{dev, fn}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 
 int cuda_fail(cudaError_t e, const char* what) {
   set_error(FGRAFT_ECUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
@@ -229,7 +245,7 @@ int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStrea
   const int alive_bytes = (ecap / 8 + 15) / 16 * 16;  // kept a multiple of 16 (see beam.cuh)
   const int wbytes = vis_bytes + 8 * ecap + alive_bytes + 256 + qbytes;
   const int smem = wbytes * ix->wpc;
-  FG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(kern), smem));
   int per_sm = 0;
   FG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ix->wpc * 32, smem));
   if (per_sm < 1) return fail(FGRAFT_EINVAL, "harvest launch does not fit an SM");
@@ -305,8 +321,7 @@ int size_visited_bitmaps(fgraft_index* ix) {
     const int vis_bytes = bitmap ? (int)bm_bytes : 4 * nslots;
     const int wbytes =
         vis_bytes + 8 * ecap + (ecap / 8 + 15) / 16 * 16 + 256 + 16 * ix->L.nchunks;
-    FG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 wbytes * ix->wpc));
+    FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(kern), wbytes * ix->wpc));
     int per_sm = 0;
     FG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ix->wpc * 32,
                                                           wbytes * ix->wpc));
@@ -327,10 +342,11 @@ int size_visited_bitmaps(fgraft_index* ix) {
 }
 
 int check_err_flag(fgraft_index* ix, cudaStream_t s) {
-  uint32_t f = 0;
-  FG_CUDA(cudaMemcpyAsync(&f, ix->work + 3, sizeof(f), cudaMemcpyDeviceToHost, s));
+  uint32_t f[2] = {0, 0};
+  FG_CUDA(cudaMemcpyAsync(f, ix->work + 3, sizeof(f), cudaMemcpyDeviceToHost, s));
   FG_CUDA(cudaStreamSynchronize(s));
-  if (f) return fail(FGRAFT_EOVERFLOW, "a search outgrew its global-memory scratch");
+  if (f[0]) return fail(FGRAFT_EOVERFLOW, "a search outgrew its global-memory scratch");
+  if (f[1]) return fail(FGRAFT_ECUDA, "a tensor-core prune timed out waiting for its products");
   return 0;
 }
 
@@ -409,7 +425,7 @@ int harvest_block_impl(fgraft_index* ix, int32_t b, cudaStream_t s) {
   if (sep) {
     rc = harvest_prune(ix->L, ix->Eg, ix->Eg_cnt, ix->eg_ecap, a.nq, a.q_first,
                        a.q_step, ix->p.R, a.alpha2, ix->A, ix->cnt, ix->ctr + C_PRUNE,
-                       ix->num_sms, s);
+                       ix->num_sms, s, nullptr, nullptr, nullptr, nullptr, ix->work + 4);
     if (rc) return rc;
   }
   if (prof) FG_CUDA(record_event(ix->ev_pend[b], s));
@@ -608,7 +624,7 @@ fgraft_status fgraft_prune(fgraft_index* ix, fgraft_stream stream, fgraft_counte
   FGS(cudaMemsetAsync(ix->ctr + C_FINAL, 0, sizeof(unsigned long long), s));
   rc = final_graph(ix->L, ix->p.R, ix->p.alpha * ix->p.alpha, ix->A, ix->cnt, ix->r_off,
                    ix->r_ids, ix->parents, ix->f_off, &ix->f_ids, &ix->f_nnz, ix->scan_tmp,
-                   ix->ctr + C_FINAL, s);
+                   ix->ctr + C_FINAL, ix->num_sms, s);
   if (rc) return (fgraft_status)rc;
   if (needed) *needed = ix->f_nnz;
   if (out_offsets) {
@@ -871,6 +887,13 @@ fgraft_status fgraft_index_harvest_ms(fgraft_index* ix, fgraft_stream stream, do
 }
 
 uint64_t fgraft_kernel_launches(void) { return launch_count(); }
+
+fgraft_status fgraft_tune_prune(int32_t tensor_cores) {
+  if (tensor_cores != 0 && tensor_cores != 1)
+    return (fgraft_status)fail(FGRAFT_EINVAL, "tensor_cores must be 0 or 1");
+  g_prune_tc = tensor_cores;
+  return FGRAFT_OK;
+}
 
 fgraft_status fgraft_tune_sat(int32_t big_node_min, int32_t finish_len) {
   if (big_node_min == 1 || big_node_min < 0)

@@ -339,13 +339,49 @@ struct FinalArgs {
   uint32_t* nlong;
   uint64_t* gbuf;
   int32_t gcap;
-  int32_t mode;  // 0 final graph, 1 list prune
+  int32_t mode;  // 0 final graph, 1 list prune, 2 final rows after the CTA prune
   int32_t qbytes;  // bytes of one staged vector (16 * nchunks)
   unsigned long long* ctr;
+  // final graph rows handed to the CTA prune (def_keys null: none): rows
+  // with R < m <= def_cap write their sorted keys to def_keys + def_koff[u]
+  // and join the list def_rows / def_m (length *def_count); mode 2 then
+  // takes the kept keys (def_kept, R per listed row, def_kcnt of them)
+  uint64_t* def_keys;
+  const int64_t* def_koff;
+  int32_t* def_rows;
+  int32_t* def_m;
+  uint32_t* def_count;
+  int32_t def_cap;
+  const uint64_t* def_kept;
+  const int32_t* def_kcnt;
 };
+
+// Final row of u from its kept keys (sorted, kk of them, owner's vector
+// staged in us): the tree-0 spine members not yet in it are evaluated and
+// added, the row is sorted by (delta, id) and written out.
+template <int METRIC, int G, int K>
+__device__ void final_spine_out(const FinalArgs& a, int32_t u, const uint4* us, uint64_t* keys,
+                                int kk, int lane) {
+  const int32_t p0 = a.parent0[u];
+  const int32_t* ch = a.c0_ids + a.c0_off[u];
+  const int sdeg = (p0 >= 0 ? 1 : 0) + (int)(a.c0_off[u + 1] - a.c0_off[u]);
+  int add = 0;
+  for (int j = 0; j < sdeg; ++j) {
+    const int32_t v = (p0 >= 0) ? (j == 0 ? p0 : ch[j - 1]) : ch[j];
+    if (keys_contain(keys, kk, v, lane)) continue;
+    // evaluate delta(u, v) and append
+    eval_keys<METRIC, G, K>(a.V, us, &v, 1, nullptr, 0, keys, kk + add, lane);
+    ++add;
+  }
+  kk = sort_unique(keys, kk + add, lane);
+  int32_t* out = a.out_ids + a.out_cap_off[u];
+  for (int i = lane; i < kk; i += 32) out[i] = key_id(keys[i]);
+  if (lane == 0) a.out_cnt[u] = kk;
+}
 
 constexpr int FIN_WARPS = 4;
 constexpr int FIN_CAP = 1024;
+constexpr int FIN_DEF_CAP = 128;  // longest final row list the CTA prune takes
 
 // Shared memory per warp: key buffer and bit words (unless the row works in
 // global scratch), then two staged vectors (the row's owner, the kept c*).
@@ -378,6 +414,15 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
   unsigned long long ev = 0;
   for (int64_t w = gw; w < total; w += (int64_t)gridDim.x * FIN_WARPS) {
     const int64_t r = a.rowlist ? a.rowlist[w] : w;
+    if (a.mode == 2) {
+      const int32_t u2 = a.def_rows[r];
+      const int kk2 = a.def_kcnt[r];
+      for (int i = lane; i < kk2; i += 32) keys[i] = a.def_kept[r * a.R + i];
+      stage_row(us, a.V.X + (int64_t)u2 * a.V.ld_bytes, a.V.nchunks, lane);
+      final_spine_out<METRIC, G, K>(a, u2, us, keys, kk2, lane);
+      __syncwarp();
+      continue;
+    }
     int32_t u;
     const int32_t *seg0, *seg1;
     int len0, len1;
@@ -411,9 +456,7 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
     int m = sort_unique(keys, mraw, lane);
     if (m > 0 && __shfl_sync(FULL, keys[m - 1] == PAD ? 1 : 0, 0)) --m;  // dropped owner
     ev += (unsigned long long)m;
-    int32_t* out;
     if (a.mode == 0) {
-      out = a.out_ids + a.out_cap_off[u];
       // spine members not already candidates cost one evaluation each
       const int32_t p0 = a.parent0[u];
       const int32_t* ch = a.c0_ids + a.c0_off[u];
@@ -421,27 +464,28 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
         const int32_t v = (p0 >= 0) ? (j == 0 ? p0 : ch[j - 1]) : ch[j];
         if (!keys_contain(keys, m, v, lane)) ++ev;
       }
-    } else {
-      out = a.out_ids + r * a.R;
+      if (a.def_keys && !a.gbuf && m > a.R && m <= a.def_cap) {
+        // the prune of this row runs in the CTA prune kernel
+        uint32_t slot = 0;
+        if (lane == 0) slot = atomicAdd(a.def_count, 1u);
+        slot = __shfl_sync(FULL, slot, 0);
+        uint64_t* dst = a.def_keys + a.def_koff[u];
+        for (int i = lane; i < m; i += 32) dst[i] = keys[i];
+        if (lane == 0) {
+          a.def_rows[slot] = u;
+          a.def_m[slot] = m;
+        }
+        __syncwarp();
+        continue;
+      }
     }
     int kk = m;
     if (m > a.R || a.mode == 1)
       kk = prune_sorted<METRIC, G, K>(a.V, keys, m, a.alpha2, a.R, bits, cs, &ev, lane);
     if (a.mode == 0) {
-      const int32_t p0 = a.parent0[u];
-      const int32_t* ch = a.c0_ids + a.c0_off[u];
-      int add = 0;
-      for (int j = 0; j < sdeg; ++j) {
-        const int32_t v = (p0 >= 0) ? (j == 0 ? p0 : ch[j - 1]) : ch[j];
-        if (keys_contain(keys, kk, v, lane)) continue;
-        // evaluate delta(u, v) and append
-        eval_keys<METRIC, G, K>(a.V, us, &v, 1, nullptr, 0, keys, kk + add, lane);
-        ++add;
-      }
-      kk = sort_unique(keys, kk + add, lane);
-      for (int i = lane; i < kk; i += 32) out[i] = key_id(keys[i]);
-      if (lane == 0) a.out_cnt[u] = kk;
+      final_spine_out<METRIC, G, K>(a, u, us, keys, kk, lane);
     } else {
+      int32_t* out = a.out_ids + r * a.R;
       for (int i = lane; i < a.R; i += 32) out[i] = i < kk ? key_id(keys[i]) : -1;
       if (lane == 0) a.out_cnt[r] = kk;
     }
@@ -508,12 +552,12 @@ __global__ void max_final_need_kernel(int64_t n, const int32_t* rows, const uint
 static int fin_smem(FinalKernelFn kern, int qbytes, int* sm_shared, int* sm_global) {
   *sm_shared = FIN_WARPS * fin_warp_bytes(false, qbytes);
   *sm_global = FIN_WARPS * fin_warp_bytes(true, qbytes);
-  FG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               std::max(*sm_shared, *sm_global)));
+  FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(kern), std::max(*sm_shared, *sm_global)));
   return 0;
 }
 
-static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, cudaStream_t s) {
+static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, int num_sms,
+                          cudaStream_t s) {
   FinalKernelFn kern = final_kernel_for(L.metric, L.G, L.K);
   if (!kern) {
     set_error(1, "no row kernel for this metric and dimension");
@@ -565,19 +609,54 @@ static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, cudaSt
       cudaFreeAsync(gbuf, s);
     }
   }
+  if (!rc && a.def_keys) {
+    // rows deferred to the CTA prune, then their spine merge
+    rc = harvest_prune(L, a.def_keys, a.def_m, a.def_cap, 0, 0, 0, a.R, a.alpha2, nullptr,
+                       const_cast<int32_t*>(a.def_kcnt), a.ctr, num_sms, s, a.def_rows,
+                       a.def_koff, a.def_count, const_cast<uint64_t*>(a.def_kept),
+                       a.def_count + 1);
+    if (!rc) {
+      FinalArgs b = a;
+      b.mode = 2;
+      b.rowlist = nullptr;
+      b.rowlist_len = a.def_count;
+      b.gbuf = nullptr;
+      b.gcap = 0;
+      kern<<<grid1d(nrows * 32, FIN_WARPS * 32), FIN_WARPS * 32, sm0, s>>>(b);
+      note_launch();
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) rc = cuda_fail(e, "final_rows_kernel(merge)");
+    }
+  }
   cudaFreeAsync(long_rows, s);
   cudaFreeAsync(small, s);
   return rc;
 }
 
+// Key space of a final row that may go to the CTA prune: its raw candidate
+// count (row plus reverse list) when above R, capped at def_cap.
+__global__ void final_defcap_kernel(int64_t n, int R, int def_cap, const int32_t* cnt,
+                                    const int64_t* r_off, uint32_t* capd) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t mraw = cnt[i] + (r_off[i + 1] - r_off[i]);
+    capd[i] = mraw > R ? (uint32_t)std::min<int64_t>(mraw, def_cap) : 0u;
+  }
+}
+
 int final_graph(const VecLayout& L, int R, float alpha2, const int32_t* A, const int32_t* cnt,
                 const int64_t* r_off, const int32_t* r_ids, const int32_t* parent0,
                 int64_t* f_off, int32_t** f_ids, int64_t* f_nnz, int64_t* scan_tmp,
-                unsigned long long* ctr, cudaStream_t s) {
+                unsigned long long* ctr, int num_sms, cudaStream_t s) {
   const int64_t n = L.n;
   uint32_t *c0cnt = nullptr, *capc = nullptr;
   int64_t *c0_off = nullptr, *cap_off = nullptr;
   int32_t *c0_ids = nullptr, *tmp_ids = nullptr, *rowcnt = nullptr;
+  // rows pruned by the CTA prune kernel
+  int64_t* def_koff = nullptr;
+  uint64_t *def_keys = nullptr, *def_kept = nullptr;
+  int32_t *def_rows = nullptr, *def_m = nullptr, *def_kcnt = nullptr;
+  uint32_t* def_count = nullptr;
   int rc = 0;
   auto cleanup = [&]() {
     cudaFreeAsync(c0cnt, s);
@@ -587,6 +666,13 @@ int final_graph(const VecLayout& L, int R, float alpha2, const int32_t* A, const
     cudaFreeAsync(c0_ids, s);
     cudaFreeAsync(tmp_ids, s);
     cudaFreeAsync(rowcnt, s);
+    cudaFreeAsync(def_koff, s);
+    cudaFreeAsync(def_keys, s);
+    cudaFreeAsync(def_kept, s);
+    cudaFreeAsync(def_rows, s);
+    cudaFreeAsync(def_m, s);
+    cudaFreeAsync(def_kcnt, s);
+    cudaFreeAsync(def_count, s);
   };
 #define FG_TRY(call)                                \
   do {                                              \
@@ -619,7 +705,42 @@ int final_graph(const VecLayout& L, int R, float alpha2, const int32_t* A, const
   FG_TRY(cudaMemcpyAsync(&capn, cap_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   FG_TRY(cudaStreamSynchronize(s));
   FG_TRY(cudaMallocAsync(&tmp_ids, sizeof(int32_t) * std::max<int64_t>(capn, 1), s));
+  // rows of at most def_cap candidates go to the CTA prune, which stages
+  // them all in shared memory: def_cap is the largest power of two in
+  // [64, FIN_DEF_CAP] that fits an SM, or 0 (no such rows) for long vectors
+  int def_cap = 0;
+  {
+    int dev = 0, optin = 0;
+    FG_TRY(cudaGetDevice(&dev));
+    FG_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    for (int c = FIN_DEF_CAP; c >= 64 && !def_cap; c >>= 1)
+      if (harvest_prune_smem(c, L.nchunks) <= optin) def_cap = c;
+  }
+  // key space of the rows that may go to the CTA prune (capc is reused)
+  final_defcap_kernel<<<grid1d(n), 256, 0, s>>>(n, R, def_cap, cnt, r_off, capc);
+  note_launch();
+  FG_TRY(cudaMallocAsync(&def_koff, sizeof(int64_t) * (n + 1), s));
+  rc = scan_u32(capc, def_koff, n, scan_tmp, s);
+  if (rc) return cleanup(), rc;
+  int64_t defn = 0;
+  FG_TRY(cudaMemcpyAsync(&defn, def_koff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  FG_TRY(cudaStreamSynchronize(s));
+  FG_TRY(cudaMallocAsync(&def_keys, sizeof(uint64_t) * std::max<int64_t>(defn, 1), s));
+  FG_TRY(cudaMallocAsync(&def_kept, sizeof(uint64_t) * std::max<int64_t>(n * R, 1), s));
+  FG_TRY(cudaMallocAsync(&def_rows, sizeof(int32_t) * std::max<int64_t>(n, 1), s));
+  FG_TRY(cudaMallocAsync(&def_m, sizeof(int32_t) * std::max<int64_t>(n, 1), s));
+  FG_TRY(cudaMallocAsync(&def_kcnt, sizeof(int32_t) * std::max<int64_t>(n, 1), s));
+  FG_TRY(cudaMallocAsync(&def_count, 2 * sizeof(uint32_t), s));  // count, timeout flag
+  FG_TRY(cudaMemsetAsync(def_count, 0, 2 * sizeof(uint32_t), s));
   FinalArgs a{};
+  a.def_keys = def_cap ? def_keys : nullptr;
+  a.def_koff = def_koff;
+  a.def_rows = def_rows;
+  a.def_m = def_m;
+  a.def_count = def_count;
+  a.def_cap = def_cap;
+  a.def_kept = def_kept;
+  a.def_kcnt = def_kcnt;
   a.V = RowVec{L.X, L.ld_bytes, L.d, L.nchunks};
   a.n = n;
   a.R = R;
@@ -636,14 +757,21 @@ int final_graph(const VecLayout& L, int R, float alpha2, const int32_t* A, const
   a.out_cnt = rowcnt;
   a.mode = 0;
   a.ctr = ctr;
-  rc = run_final_rows(a, L, n, s);
+  rc = run_final_rows(a, L, n, num_sms, s);
   if (rc) return cleanup(), rc;
   // final CSR
   rc = scan_u32(reinterpret_cast<const uint32_t*>(rowcnt), f_off, n, scan_tmp, s);
   if (rc) return cleanup(), rc;
   int64_t nnz = 0;
+  uint32_t tc_err = 0;
   FG_TRY(cudaMemcpyAsync(&nnz, f_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  FG_TRY(cudaMemcpyAsync(&tc_err, def_count + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   FG_TRY(cudaStreamSynchronize(s));
+  if (tc_err) {
+    set_error(3, "a tensor-core prune timed out waiting for its products");
+    cleanup();
+    return 3;
+  }
   if (*f_ids) {
     cudaFree(*f_ids);
     *f_ids = nullptr;
@@ -673,7 +801,7 @@ int prune_lists(const VecLayout& L, const int32_t* owner, const int64_t* l_off,
   a.out_cnt = out_cnt;
   a.mode = 1;
   a.ctr = ctr;
-  return run_final_rows(a, L, nlists, s);
+  return run_final_rows(a, L, nlists, 0, s);
 }
 
 // ---------------------------------------------------------------------------

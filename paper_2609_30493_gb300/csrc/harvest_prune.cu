@@ -7,9 +7,14 @@
 // prune itself -- keep the first alive c*, remove the alive candidates it
 // dominates, stop at R -- is then a walk over bit words.  The evaluation
 // count is the prune's own (the alive candidates each removal pass
-// examines), not the number of pairs computed here.
+// examines), not the number of pairs computed here.  The final graph's rows
+// that need a prune take the same kernel (lists given by row, kept keys out).
+#include <algorithm>
+#include <cmath>
+
 #include "beam.cuh"
 #include "internal.h"
+#include "tc.cuh"
 
 namespace fg {
 
@@ -30,9 +35,23 @@ struct HPruneArgs {
   int32_t* A_out;
   int32_t* cnt_out;
   unsigned long long* prune_ctr;
+  // the final graph's rows (all null for the harvest): point of list qidx,
+  // start of its keys in Eg by point, list count on the device, and kept
+  // keys out (R per list, count in cnt_out[qidx]) instead of rows of A_out
+  const int32_t* rows;
+  const int64_t* Eg_off;
+  const uint32_t* nq_dev;
+  uint64_t* K_out;
+  // tensor-core variant: error bound coefficients and the timeout flag
+  float tc_e1;
+  float tc_e0;
+  uint32_t* err;
 };
 
 constexpr int HP_WARPS = 4;
+// tensor-core dominance bits on (1) or off (0, the lane-group kernel for all
+// lists); results do not depend on it
+int g_prune_tc = 1;
 
 // shared layout: keys[ecap] | dom[ecap][ecap/32] | alive[ecap/32] + m | Cs[ecap][nchunks]
 __host__ __device__ inline int hp_dom_off(int ecap) { return 8 * ecap; }
@@ -60,12 +79,13 @@ __global__ void __launch_bounds__(HP_WARPS * 32) harvest_prune_kernel(const HPru
   // lane groups of a warp run different column counts below: shuffles use the
   // group's own lanes
   const unsigned gmask = L::P == 32 ? FULL : (((1u << L::P) - 1u) << (g * L::P));
-  for (int64_t qidx = blockIdx.x; qidx < a.nq; qidx += gridDim.x) {
+  const int64_t nq = a.nq_dev ? (int64_t)*a.nq_dev : a.nq;
+  for (int64_t qidx = blockIdx.x; qidx < nq; qidx += gridDim.x) {
     const int ne = a.Eg_cnt[qidx];
     if (ne < 0) continue;  // pruned by the re-run pass (uniform over the CTA)
-    const int64_t p = a.q_first + qidx * a.q_step;
+    const int64_t p = a.rows ? (int64_t)a.rows[qidx] : a.q_first + qidx * a.q_step;
     if (warp == 0) {
-      const uint64_t* src = a.Eg + qidx * (int64_t)a.ecap;
+      const uint64_t* src = a.Eg_off ? a.Eg + a.Eg_off[p] : a.Eg + qidx * (int64_t)a.ecap;
       int NE2 = 32;
       while (NE2 < ne) NE2 <<= 1;
       int m = 0;
@@ -138,7 +158,8 @@ __global__ void __launch_bounds__(HP_WARPS * 32) harvest_prune_kernel(const HPru
       uint32_t al = lane < W ? (lane * 32 + 32 <= m ? FULL
                                                     : (lane * 32 < m ? ((1u << (m - lane * 32)) - 1u) : 0u))
                              : 0u;
-      int32_t* row = a.A_out + p * a.R;
+      int32_t* row = a.K_out ? nullptr : a.A_out + p * a.R;
+      uint64_t* krow = a.K_out ? a.K_out + qidx * a.R : nullptr;
       int kept = 0;
       unsigned long long q_pe = 0;
       while (kept < a.R) {
@@ -147,7 +168,12 @@ __global__ void __launch_bounds__(HP_WARPS * 32) harvest_prune_kernel(const HPru
         const int w0 = __ffs(nz) - 1;
         const uint32_t bw = __shfl_sync(FULL, al, w0);
         const int cur = w0 * 32 + __ffs(bw) - 1;
-        if (lane == 0) row[kept] = key_id(keys[cur]);
+        if (lane == 0) {
+          if (krow)
+            krow[kept] = keys[cur];
+          else
+            row[kept] = key_id(keys[cur]);
+        }
         ++kept;
         if (lane == w0) al &= ~(1u << (cur % 32));
         if (kept == a.R) break;
@@ -156,8 +182,12 @@ __global__ void __launch_bounds__(HP_WARPS * 32) harvest_prune_kernel(const HPru
         q_pe += (unsigned long long)__reduce_add_sync(FULL, __popc(al));
         if (lane < W) al &= ~dom[cur * W + lane];
       }
-      for (int r = kept + lane; r < a.R; r += 32) row[r] = -1;
-      if (lane == 0) a.cnt_out[p] = kept;
+      if (krow) {
+        if (lane == 0) a.cnt_out[qidx] = kept;
+      } else {
+        for (int r = kept + lane; r < a.R; r += 32) row[r] = -1;
+        if (lane == 0) a.cnt_out[p] = kept;
+      }
       ev += q_pe;
     }
     __syncthreads();
@@ -165,7 +195,297 @@ __global__ void __launch_bounds__(HP_WARPS * 32) harvest_prune_kernel(const HPru
   if (threadIdx.x == 0 && ev) atomicAdd(a.prune_ctr, ev);
 }
 
+
+// ---------------------------------------------------------------------------
+// Tensor-core variant for the float32 metrics and lists of at most 128.
+//
+// The candidates are staged once, as float32, in the canonical K-major
+// operand layout of tcgen05 (core matrices of 8 rows x 16 bytes); their Gram
+// matrix C C^T is one chain of kind::tf32 MMAs (M = N = 128, 128 TMEM
+// columns), which reads the same float32 words with the low mantissa bits
+// ignored.  Thread i then reads row i of the Gram matrix from TMEM and
+// decides each bit j > i from the approximate distance when the decision is
+// certain: with |approx - canonical| <= eps (input rounding to 10 mantissa
+// bits, float32 accumulation in any order, the canonical sum's own rounding,
+// times 2), the canonical test fl(alpha2 * delta) <= delta(p, c_j) has the
+// same outcome whenever alpha2 * (approx +- eps) lies on one side of
+// delta(p, c_j) with a margin for the rounding of the test.  Otherwise the
+// thread computes the canonical float32 distance itself, in the same order
+// as the lane-group kernels (virtual lane l sums elements 128k + 4l + c by
+// fused multiply-adds, then the pairwise tree over the lanes).  The bits,
+// and so the prune, are identical to the float32 path.
+// ---------------------------------------------------------------------------
+constexpr int TCP_M = 128;  // candidates of one tile: TMEM lanes and columns
+constexpr int TCP_W = TCP_M / 32;
+__host__ __device__ inline int tcp_nq(int nchunks) { return (nchunks + 1) & ~1; }
+// shared layout: keys[128] | dom[128][4] | m | nrm[128] | mbarrier | tmem slot | Cs
+constexpr int TCP_DOM = 8 * TCP_M;
+constexpr int TCP_M_OFF = TCP_DOM + 4 * TCP_M * TCP_W;
+constexpr int TCP_NRM = TCP_M_OFF + 16;
+constexpr int TCP_BAR = TCP_NRM + 4 * TCP_M;
+constexpr int TCP_SLOT = TCP_BAR + 8;
+constexpr int TCP_CS = (TCP_SLOT + 8 + 127) & ~127;
+int harvest_prune_tc_smem(int nchunks) { return TCP_CS + TCP_M * tcp_nq(nchunks) * 16; }
+
+// Chunk q of staged row r in the canonical operand layout.
+__device__ __forceinline__ int tcp_at(int r, int q, int NQ) {
+  return (r >> 3) * 8 * NQ + q * 8 + (r & 7);
+}
+
+// Canonical float32 distance of staged rows ri and rj, one thread.
+template <int METRIC, int G, int K>
+__device__ float canon_dist_thread(const uint4* Cs, int NQ, int ri, int rj, int nch, int d) {
+  float v[G];
+#pragma unroll
+  for (int l = 0; l < G; ++l) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int c = 32 * k + l;
+      if (c < nch) {
+        const uint4 xa = Cs[tcp_at(ri, c, NQ)], ya = Cs[tcp_at(rj, c, NQ)];
+        const float x[4] = {__uint_as_float(xa.x), __uint_as_float(xa.y), __uint_as_float(xa.z),
+                            __uint_as_float(xa.w)};
+        const float y[4] = {__uint_as_float(ya.x), __uint_as_float(ya.y), __uint_as_float(ya.z),
+                            __uint_as_float(ya.w)};
+        const int nv = d - 4 * c;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (nv > e) {
+            if constexpr (METRIC == ANGULAR_F32) {
+              acc = __fmaf_rn(x[e], y[e], acc);
+            } else {
+              const float t = __fsub_rn(x[e], y[e]);
+              acc = __fmaf_rn(t, t, acc);
+            }
+          }
+        }
+      }
+    }
+    v[l] = acc;
+  }
+#pragma unroll
+  for (int sh = G / 2; sh >= 1; sh >>= 1) {
+#pragma unroll
+    for (int l = 0; l < sh; ++l) v[l] = __fadd_rn(v[l], v[l + sh]);
+  }
+  if constexpr (METRIC == ANGULAR_F32) return __fsub_rn(1.0f, v[0]);
+  return v[0];
+}
+
+template <int METRIC, int G, int K>
+__global__ void __launch_bounds__(TCP_M) harvest_prune_tc_kernel(const HPruneArgs a) {
+  extern __shared__ __align__(128) unsigned char psm[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nch = a.nchunks, NQ = tcp_nq(nch);
+  uint64_t* keys = reinterpret_cast<uint64_t*>(psm);
+  uint32_t* dom = reinterpret_cast<uint32_t*>(psm + TCP_DOM);
+  int* mshared = reinterpret_cast<int*>(psm + TCP_M_OFF);
+  float* nrm = reinterpret_cast<float*>(psm + TCP_NRM);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(psm + TCP_BAR);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(psm + TCP_SLOT);
+  uint4* Cs = reinterpret_cast<uint4*>(psm + TCP_CS);
+  // rows no list fills stay zero
+  for (int idx = tid; idx < TCP_M * NQ; idx += TCP_M) Cs[idx] = make_uint4(0u, 0u, 0u, 0u);
+  if (warp == 0) {
+    tmem_alloc(tslot, TCP_M);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = idesc_tf32(TCP_M, TCP_M);
+  const uint32_t cs0 = smem_u32(Cs);
+  const uint32_t sbo = (uint32_t)NQ * 128u;
+  uint32_t phase = 0;
+  bool ok = true;
+  unsigned long long ev = 0;
+  const int64_t nq = a.nq_dev ? (int64_t)*a.nq_dev : a.nq;
+  for (int64_t qidx = blockIdx.x; qidx < nq; qidx += gridDim.x) {
+    const int ne = a.Eg_cnt[qidx];
+    if (ne < 0) continue;  // pruned by the re-run pass (uniform over the CTA)
+    const int64_t p = a.rows ? (int64_t)a.rows[qidx] : a.q_first + qidx * a.q_step;
+    if (warp == 0) {
+      const uint64_t* src = a.Eg_off ? a.Eg + a.Eg_off[p] : a.Eg + qidx * (int64_t)a.ecap;
+      int NE2 = 32;
+      while (NE2 < ne) NE2 <<= 1;
+      int m = 0;
+      for (int i0 = 0; i0 < NE2; i0 += 32) {
+        const int i = i0 + lane;
+        uint64_t kk = i < ne ? src[i] : PAD;
+        if (kk != PAD && key_id(kk) == (int32_t)p) kk = PAD;
+        keys[i] = kk;
+        m += __popc(__ballot_sync(FULL, kk != PAD));
+      }
+      __syncwarp();
+      if (!a.rows) warp_sort_mem(keys, NE2, lane);  // the final graph's lists come sorted
+      if (lane == 0) *mshared = m;
+    }
+    __syncthreads();
+    const int m = *mshared;
+    // stage the candidates (element tails past d zeroed)
+    for (int idx = tid; idx < m * NQ; idx += TCP_M) {
+      const int r = idx / NQ, q = idx - r * NQ;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (q < nch) {
+        v = __ldg(reinterpret_cast<const uint4*>(a.X + (int64_t)key_id(keys[r]) * a.ld_bytes) + q);
+        const int rem = a.d - 4 * q;
+        if (rem < 4) v.w = 0u;
+        if (rem < 3) v.z = 0u;
+        if (rem < 2) v.y = 0u;
+      }
+      Cs[tcp_at(r, q, NQ)] = v;
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      for (int kk = 0; kk < NQ / 2; ++kk) {
+        // a K = 8 step spans two core matrices along K (2 x 128 bytes)
+        const uint64_t desc = smem_desc(cs0 + kk * 256, 128, sbo);
+        mma_tf32(tmem, desc, desc, idesc, kk > 0 ? 1u : 0u);
+      }
+      mma_commit(bar);
+    }
+    if (tid < m) {
+      float sq = 0.0f;
+      for (int q = 0; q < nch; ++q) {
+        const uint4 v = Cs[tcp_at(tid, q, NQ)];
+        sq = fmaf(__uint_as_float(v.x), __uint_as_float(v.x), sq);
+        sq = fmaf(__uint_as_float(v.y), __uint_as_float(v.y), sq);
+        sq = fmaf(__uint_as_float(v.z), __uint_as_float(v.z), sq);
+        sq = fmaf(__uint_as_float(v.w), __uint_as_float(v.w), sq);
+      }
+      nrm[tid] = sq;
+    }
+    // wait (bounded) for the Gram matrix; every thread takes the same decision
+    bool done = false;
+    for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(bar, phase);
+    done = __syncthreads_and(done);
+    if (!done) {
+      ok = false;
+      if (tid == 0) atomicOr(a.err, 1u);
+      break;
+    }
+    phase ^= 1u;
+    tc_fence_after();
+    // dominance bits of row i = tid, one word per 32 columns
+    const int i = tid;
+    const float ni = i < m ? nrm[i] : 0.0f;
+    for (int cb = 0; cb < TCP_W && 32 * cb < m; ++cb) {
+      if (32 * cb + 31 <= 32 * warp) {  // every column of the block is at or left of i
+        if (i < m) dom[i * TCP_W + cb] = 0u;
+        continue;
+      }
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * cb), v);
+      if (i < m) {
+        uint32_t word = 0, unsure = 0;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          const int jj = 32 * cb + t;
+          if (jj <= i || jj >= m) continue;
+          const float g = __uint_as_float(v[t]);
+          const float nj = nrm[jj];
+          float dt, eps;
+          if constexpr (METRIC == ANGULAR_F32) {
+            dt = 1.0f - g;
+            eps = a.tc_e1 * 0.5f * (ni + nj) + a.tc_e0;
+          } else {
+            dt = (ni + nj) - 2.0f * g;
+            eps = a.tc_e1 * (ni + nj) + a.tc_e0;
+          }
+          const float dp = key_dist(keys[jj]);
+          float up = a.alpha2 * (dt + eps);
+          up += fabsf(up) * 4.76837158e-7f + 1e-30f;  // 2^-21
+          float lo = a.alpha2 * (dt - eps);
+          lo -= fabsf(lo) * 4.76837158e-7f + 1e-30f;
+          if (up <= dp)
+            word |= 1u << t;
+          else if (!(lo > dp))
+            unsure |= 1u << t;
+        }
+        // the tests the Gram value cannot decide, in canonical float32
+        while (unsure) {
+          const int t = __ffs(unsure) - 1;
+          unsure &= unsure - 1u;
+          const int jj = 32 * cb + t;
+          const float dd = canon_dist_thread<METRIC, G, K>(Cs, NQ, i, jj, nch, a.d);
+          if (__fmul_rn(a.alpha2, dd) <= key_dist(keys[jj])) word |= 1u << t;
+        }
+        dom[i * TCP_W + cb] = word;
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+      // the prune as a walk over bit words; lane w holds alive word w
+      uint32_t al = lane < TCP_W ? (lane * 32 + 32 <= m
+                                        ? FULL
+                                        : (lane * 32 < m ? ((1u << (m - lane * 32)) - 1u) : 0u))
+                                 : 0u;
+      int32_t* row = a.K_out ? nullptr : a.A_out + p * a.R;
+      uint64_t* krow = a.K_out ? a.K_out + qidx * a.R : nullptr;
+      int kept = 0;
+      unsigned long long q_pe = 0;
+      while (kept < a.R) {
+        const unsigned nz = __ballot_sync(FULL, al != 0u);
+        if (nz == 0u) break;
+        const int w0 = __ffs(nz) - 1;
+        const uint32_t bw = __shfl_sync(FULL, al, w0);
+        const int cur = w0 * 32 + __ffs(bw) - 1;
+        if (lane == 0) {
+          if (krow)
+            krow[kept] = keys[cur];
+          else
+            row[kept] = key_id(keys[cur]);
+        }
+        ++kept;
+        if (lane == w0) al &= ~(1u << (cur % 32));
+        if (kept == a.R) break;
+        // the removal pass examines every alive candidate after c*
+        q_pe += (unsigned long long)__reduce_add_sync(FULL, __popc(al));
+        if (lane < TCP_W) al &= ~dom[cur * TCP_W + lane];
+      }
+      if (krow) {
+        if (lane == 0) a.cnt_out[qidx] = kept;
+      } else {
+        for (int r = kept + lane; r < a.R; r += 32) row[r] = -1;
+        if (lane == 0) a.cnt_out[p] = kept;
+      }
+      ev += q_pe;
+    }
+    __syncthreads();
+  }
+  if (!ok) {
+    // let the products in flight land before the tensor memory is released
+    for (int it = 0; it < (1 << 22); ++it)
+      if (mbar_try_wait(bar, phase)) break;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, TCP_M);
+  if (tid == 0 && ev) atomicAdd(a.prune_ctr, ev);
+}
+
 using HPruneFn = void (*)(const HPruneArgs);
+
+static HPruneFn hprune_tc_kernel_for(int metric, int G, int K) {
+#define HX(M, GG, KK) \
+  if (metric == M && G == GG && K == KK) return harvest_prune_tc_kernel<M, GG, KK>;
+#define HF(M) HX(M, 4, 1) HX(M, 8, 1) HX(M, 16, 1) HX(M, 32, 1) HX(M, 32, 2) HX(M, 32, 4) \
+  HX(M, 32, 8)
+  HF(0)
+  HF(1)
+#undef HF
+#undef HX
+  return nullptr;
+}
 
 static HPruneFn hprune_kernel_for(int metric, int G, int K) {
 #define HX(M, GG, KK) \
@@ -186,7 +506,8 @@ int harvest_prune_smem(int ecap, int nchunks) { return hp_cs_off(ecap) + 16 * nc
 int harvest_prune(const VecLayout& L, const uint64_t* Eg, const int32_t* Eg_cnt, int ecap,
                   int64_t nq, int64_t q_first, int64_t q_step, int R, float alpha2,
                   int32_t* A_out, int32_t* cnt_out, unsigned long long* prune_ctr, int num_sms,
-                  cudaStream_t s) {
+                  cudaStream_t s, const int32_t* rows, const int64_t* Eg_off,
+                  const uint32_t* nq_dev, uint64_t* K_out, uint32_t* err) {
   HPruneFn kern = hprune_kernel_for(L.metric, L.G, L.K);
   if (!kern) {
     set_error(1, "no prune kernel for this metric and dimension");
@@ -194,15 +515,46 @@ int harvest_prune(const VecLayout& L, const uint64_t* Eg, const int32_t* Eg_cnt,
   }
   HPruneArgs a{L.X, L.ld_bytes, L.d, L.nchunks, Eg, Eg_cnt, ecap,
                harvest_prune_smem(ecap, L.nchunks), nq, q_first, q_step, R, alpha2,
-               A_out, cnt_out, prune_ctr};
-  FG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem));
+               A_out, cnt_out, prune_ctr, rows, Eg_off, nq_dev, K_out, 0.0f, 0.0f, err};
+  int threads = HP_WARPS * 32;
+  int max_per_sm = 1 << 20;
+  HPruneFn tck = hprune_tc_kernel_for(L.metric, L.G, L.K);
+  int optin = 0, dev = 0;
+  FG_CUDA(cudaGetDevice(&dev));
+  FG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (tck && err && g_prune_tc && ecap <= TCP_M && harvest_prune_tc_smem(L.nchunks) <= optin) {
+    // tensor-core Gram: error bound of |approx - canonical| (see the kernel)
+    const double D = 4.0 * tcp_nq(L.nchunks);
+    const double ut = std::ldexp(1.0, -10), u22 = std::ldexp(1.0, -22);
+    if (L.metric == ANGULAR_F32) {
+      a.tc_e1 = (float)(2.0 * (2.01 * ut + (1.25 * D + 1.0) * u22));
+      a.tc_e0 = (float)(2.0 * u22);
+    } else {
+      a.tc_e1 = (float)(2.0 * (2.01 * ut + (1.75 * D + 2.0) * u22));
+      a.tc_e0 = 0.0f;
+    }
+    kern = tck;
+    threads = TCP_M;
+    // at most 512 / 128 CTAs on an SM (its tensor memory columns): the
+    // shared memory request is raised so that no more can be resident
+    int sm_bytes = 0;
+    FG_CUDA(cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    const int tc_ctas = 512 / TCP_M;
+    a.smem = std::max(harvest_prune_tc_smem(L.nchunks), sm_bytes / (tc_ctas + 1));
+    max_per_sm = std::min(tc_ctas, sm_bytes / (a.smem + 1024));
+  }
+  FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(kern), a.smem));
   int per_sm = 0;
-  FG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, HP_WARPS * 32, a.smem));
+  if (kern == tck) {
+    per_sm = max_per_sm;  // the occupancy query does not see tensor memory
+  } else {
+    FG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, a.smem));
+  }
   if (per_sm < 1) {
     set_error(1, "prune launch does not fit an SM");
     return 1;
   }
-  kern<<<per_sm * num_sms, HP_WARPS * 32, a.smem, s>>>(a);
+  kern<<<per_sm * num_sms, threads, a.smem, s>>>(a);
   note_launch();
   FG_CUDA(cudaGetLastError());
   return 0;

@@ -20,6 +20,10 @@ void note_launch(uint64_t k = 1);
 uint64_t launch_count();
 void set_launch_count(uint64_t v);
 int cuda_fail(cudaError_t e, const char* what);
+// Raises the dynamic shared memory limit of kernel fn on the current device
+// to at least bytes; never lowers it, since a graph captured earlier may
+// launch the same kernel with more.
+cudaError_t raise_smem_limit(const void* fn, int bytes);
 
 #define FG_STR2(x) #x
 #define FG_STR(x) FG_STR2(x)
@@ -91,7 +95,7 @@ int reverse_rows(int64_t n, int R, int nb, int b, const int32_t* A, const int32_
 int final_graph(const VecLayout& L, int R, float alpha2, const int32_t* A, const int32_t* cnt,
                 const int64_t* r_off, const int32_t* r_ids, const int32_t* parent0,
                 int64_t* f_off, int32_t** f_ids, int64_t* f_nnz, int64_t* scan_tmp,
-                unsigned long long* ctr, cudaStream_t s);
+                unsigned long long* ctr, int num_sms, cudaStream_t s);
 
 // Batched occlusion prune of explicit candidate lists.
 int prune_lists(const VecLayout& L, const int32_t* owner, const int64_t* l_off,
@@ -106,11 +110,21 @@ int64_t prune_lists_static_max_lists();
 int prune_lists_static_max_len();
 
 // Harvest prune as its own kernel over the expanded lists the search wrote.
+// With rows non-null the lists are the final graph's: list qidx belongs to
+// point rows[qidx], its keys start at Eg + Eg_off[point], the list count is
+// read from *nq_dev, and the kept keys go to K_out[qidx * R ...] with their
+// count in cnt_out[qidx].
 int harvest_prune_smem(int ecap, int nchunks);
 int harvest_prune(const VecLayout& L, const uint64_t* Eg, const int32_t* Eg_cnt, int ecap,
                   int64_t nq, int64_t q_first, int64_t q_step, int R, float alpha2,
                   int32_t* A_out, int32_t* cnt_out, unsigned long long* prune_ctr, int num_sms,
-                  cudaStream_t s);
+                  cudaStream_t s, const int32_t* rows = nullptr, const int64_t* Eg_off = nullptr,
+                  const uint32_t* nq_dev = nullptr, uint64_t* K_out = nullptr,
+                  uint32_t* err = nullptr);
+// Dominance bits of the prune on the tensor cores (1, the default, for the
+// float32 metrics and lists of at most 128 when err is given) or on the lane
+// groups (0).  The pruned lists are the same either way.
+extern int g_prune_tc;
 
 // Dense-block top-k with the BF16 tensor-core filter and canonical rerank;
 // stats (host, optional): rerank fraction, Gram ms, select ms, prep ms.

@@ -693,10 +693,10 @@ int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* paren
   a.seg_k = S.seg_k;
   const size_t smem = sat_smem_plan(a, SAT_SMEM);
   const size_t smem_t = sat_smem_plan(at, TINY_SMEM);
-  FG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  FG_CUDA(cudaFuncSetAttribute(bigk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  FG_CUDA(cudaFuncSetAttribute(tinyk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t));
-  FG_CUDA(cudaFuncSetAttribute(asgk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(kern), (int)smem));
+  FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(bigk), (int)smem));
+  FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(tinyk), (int)smem_t));
+  FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(asgk), (int)smem));
   // the assignment launches: tiles of one node per grid column, nodes in rows
   // (grid.y is limited to 65535, so rows are covered in chunks)
   auto assign_all = [&](const int32_t* segs, uint32_t nrows, int64_t max_m) {

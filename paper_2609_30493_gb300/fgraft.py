@@ -42,7 +42,7 @@ EXPORTS = ["fgraft_build_scaffold", "fgraft_harvest_block", "fgraft_harvest_all"
            "fgraft_prune_lists", "fgraft_search", "fgraft_dense_block_dist", "fgraft_index_copy",
            "fgraft_index_sizes", "fgraft_index_counters", "fgraft_index_tune",
            "fgraft_index_profile", "fgraft_index_harvest_ms", "fgraft_kernel_launches",
-           "fgraft_tune_sat", "fgraft_prune_lists_noalloc",
+           "fgraft_tune_sat", "fgraft_tune_prune", "fgraft_prune_lists_noalloc",
            "fgraft_index_destroy", "fgraft_last_error"]
 
 
@@ -192,6 +192,10 @@ def fgraft_index_harvest_ms(ix: Index, with_prune: bool = False):
     _check(load().fgraft_index_harvest_ms(ix.handle, _stream(ix.X.device), C.byref(ms),
                                           C.byref(nl), C.byref(pm)))
     return (ms.value, nl.value, pm.value) if with_prune else (ms.value, nl.value)
+
+
+def fgraft_tune_prune(tensor_cores: bool = True):
+    _check(load().fgraft_tune_prune(C.c_int32(1 if tensor_cores else 0)))
 
 
 def fgraft_tune_sat(big_node_min: int = 0, finish_len: int = 0):

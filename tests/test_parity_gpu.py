@@ -107,6 +107,32 @@ def test_shapes_parity(fg, case):
     _compare(ctr, st, fin, ref)
 
 
+@pytest.mark.parametrize("case", [
+    dict(kind="vmf", n=3000, d=100, k=16, T=8, R=32, ef=64, B=8),
+    dict(kind="gauss", n=1300, d=129, k=4, T=4, R=12, ef=40, B=2),
+    dict(kind="gauss", n=1200, d=3, k=4, T=3, R=8, ef=16, B=3),
+])
+def test_prune_lane_groups_parity(fg, case):
+    # the prune with every dominance test on the lane groups (no tensor-core
+    # Gram) gives the same graphs
+    try:
+        fg.fgraft_tune_prune(False)
+        if case["kind"] == "vmf":
+            ps = synth.vmf_like(case["n"], case["d"], case["k"], seed=4)
+        else:
+            ps = synth.gaussian_mixture(case["n"], case["d"], case["k"], seed=4)
+        ix, ctr, st, fin, D, ref = _build_both(fg, ps, case["T"], case["R"], case["ef"],
+                                               case["B"])
+        _compare(ctr, st, fin, ref)
+    finally:
+        fg.fgraft_tune_prune(True)
+
+
+def test_prune_tune_rejects(fg):
+    with pytest.raises(fg.FgraftError):
+        fg._check(fg.load().fgraft_tune_prune(2))
+
+
 @pytest.mark.parametrize("mode", [1, 2])
 def test_overflow_is_exact(fg, mode):
     # a 128-slot visited set overflows for most queries; moving to the global
