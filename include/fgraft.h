@@ -242,13 +242,14 @@ fgraft_status fgraft_index_counters(fgraft_index* ix, fgraft_stream stream,
 fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t warps_per_cta,
                                 int32_t overflow_mode);
 
-/* Occlusion prune configuration for later harvests and final graphs in this
- * process (tuning; results do not depend on it).  With tensor_cores = 1 (the
- * default) the dominance tests of a list of at most 128 candidates under a
- * float32 metric are decided from a TF32 Gram matrix computed by tcgen05.mma,
- * and every test whose outcome the Gram value cannot fix within its error
- * bound is recomputed in canonical float32 (Section 3's prune is unchanged);
- * with 0 every test is computed in canonical float32 by lane groups.
+/* Tensor-core configuration for later builds, harvests and final graphs in
+ * this process (tuning; results do not depend on it).  With tensor_cores = 1
+ * (the default), under a float32 metric, the dominance tests of an occlusion
+ * prune of at most 128 candidates and the SAT's closest-child choices are
+ * decided from TF32 Gram tiles computed by tcgen05.mma, and every decision
+ * the Gram value cannot fix within its error bound is recomputed in canonical
+ * float32 (the prune of Section 3 and the tree of Section 1 are unchanged);
+ * with 0 every distance is computed in canonical float32 by lane groups.
  * FGRAFT_EINVAL for other values. */
 fgraft_status fgraft_tune_prune(int32_t tensor_cores);
 

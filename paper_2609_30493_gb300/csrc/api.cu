@@ -543,7 +543,7 @@ fgraft_status fgraft_build_scaffold(const void* X, int64_t n, int32_t d, int64_t
   rc = rc ? rc : dalloc(&S.seg_node, tot + nbig_max);
   rc = rc ? rc : dalloc(&S.seg_tree, tot + nbig_max);
   rc = rc ? rc : dalloc(&S.seg_k, tot + nbig_max);
-  rc = rc ? rc : dalloc(&S.nseg, 4);
+  rc = rc ? rc : dalloc(&S.nseg, 5);
   rc = rc ? rc : dalloc(&S.big_list, nbig_max);
   rc = rc ? rc : dalloc(&S.big_keys, 3 * nbig_max);
   rc = rc ? rc : dalloc(&S.big_kcount, nbig_max);
@@ -892,6 +892,7 @@ fgraft_status fgraft_tune_prune(int32_t tensor_cores) {
   if (tensor_cores != 0 && tensor_cores != 1)
     return (fgraft_status)fail(FGRAFT_EINVAL, "tensor_cores must be 0 or 1");
   g_prune_tc = tensor_cores;
+  g_sat_tc = tensor_cores;
   return FGRAFT_OK;
 }
 

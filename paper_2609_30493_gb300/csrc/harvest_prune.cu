@@ -14,7 +14,7 @@
 
 #include "beam.cuh"
 #include "internal.h"
-#include "tc.cuh"
+#include "tcdist.cuh"
 
 namespace fg {
 
@@ -217,7 +217,6 @@ __global__ void __launch_bounds__(HP_WARPS * 32) harvest_prune_kernel(const HPru
 // ---------------------------------------------------------------------------
 constexpr int TCP_M = 128;  // candidates of one tile: TMEM lanes and columns
 constexpr int TCP_W = TCP_M / 32;
-__host__ __device__ inline int tcp_nq(int nchunks) { return (nchunks + 1) & ~1; }
 // shared layout: keys[128] | dom[128][4] | m | nrm[128] | mbarrier | tmem slot | Cs
 constexpr int TCP_DOM = 8 * TCP_M;
 constexpr int TCP_M_OFF = TCP_DOM + 4 * TCP_M * TCP_W;
@@ -226,52 +225,6 @@ constexpr int TCP_BAR = TCP_NRM + 4 * TCP_M;
 constexpr int TCP_SLOT = TCP_BAR + 8;
 constexpr int TCP_CS = (TCP_SLOT + 8 + 127) & ~127;
 int harvest_prune_tc_smem(int nchunks) { return TCP_CS + TCP_M * tcp_nq(nchunks) * 16; }
-
-// Chunk q of staged row r in the canonical operand layout.
-__device__ __forceinline__ int tcp_at(int r, int q, int NQ) {
-  return (r >> 3) * 8 * NQ + q * 8 + (r & 7);
-}
-
-// Canonical float32 distance of staged rows ri and rj, one thread.
-template <int METRIC, int G, int K>
-__device__ float canon_dist_thread(const uint4* Cs, int NQ, int ri, int rj, int nch, int d) {
-  float v[G];
-#pragma unroll
-  for (int l = 0; l < G; ++l) {
-    float acc = 0.0f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int c = 32 * k + l;
-      if (c < nch) {
-        const uint4 xa = Cs[tcp_at(ri, c, NQ)], ya = Cs[tcp_at(rj, c, NQ)];
-        const float x[4] = {__uint_as_float(xa.x), __uint_as_float(xa.y), __uint_as_float(xa.z),
-                            __uint_as_float(xa.w)};
-        const float y[4] = {__uint_as_float(ya.x), __uint_as_float(ya.y), __uint_as_float(ya.z),
-                            __uint_as_float(ya.w)};
-        const int nv = d - 4 * c;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          if (nv > e) {
-            if constexpr (METRIC == ANGULAR_F32) {
-              acc = __fmaf_rn(x[e], y[e], acc);
-            } else {
-              const float t = __fsub_rn(x[e], y[e]);
-              acc = __fmaf_rn(t, t, acc);
-            }
-          }
-        }
-      }
-    }
-    v[l] = acc;
-  }
-#pragma unroll
-  for (int sh = G / 2; sh >= 1; sh >>= 1) {
-#pragma unroll
-    for (int l = 0; l < sh; ++l) v[l] = __fadd_rn(v[l], v[l + sh]);
-  }
-  if constexpr (METRIC == ANGULAR_F32) return __fsub_rn(1.0f, v[0]);
-  return v[0];
-}
 
 template <int METRIC, int G, int K>
 __global__ void __launch_bounds__(TCP_M) harvest_prune_tc_kernel(const HPruneArgs a) {
@@ -331,15 +284,8 @@ __global__ void __launch_bounds__(TCP_M) harvest_prune_tc_kernel(const HPruneArg
     // stage the candidates (element tails past d zeroed)
     for (int idx = tid; idx < m * NQ; idx += TCP_M) {
       const int r = idx / NQ, q = idx - r * NQ;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (q < nch) {
-        v = __ldg(reinterpret_cast<const uint4*>(a.X + (int64_t)key_id(keys[r]) * a.ld_bytes) + q);
-        const int rem = a.d - 4 * q;
-        if (rem < 4) v.w = 0u;
-        if (rem < 3) v.z = 0u;
-        if (rem < 2) v.y = 0u;
-      }
-      Cs[tcp_at(r, q, NQ)] = v;
+      Cs[tcp_at(r, q, NQ)] =
+          tc_chunk(a.X + (int64_t)key_id(keys[r]) * a.ld_bytes, q, nch, a.d);
     }
     fence_proxy_async();
     __syncthreads();
@@ -352,17 +298,7 @@ __global__ void __launch_bounds__(TCP_M) harvest_prune_tc_kernel(const HPruneArg
       }
       mma_commit(bar);
     }
-    if (tid < m) {
-      float sq = 0.0f;
-      for (int q = 0; q < nch; ++q) {
-        const uint4 v = Cs[tcp_at(tid, q, NQ)];
-        sq = fmaf(__uint_as_float(v.x), __uint_as_float(v.x), sq);
-        sq = fmaf(__uint_as_float(v.y), __uint_as_float(v.y), sq);
-        sq = fmaf(__uint_as_float(v.z), __uint_as_float(v.z), sq);
-        sq = fmaf(__uint_as_float(v.w), __uint_as_float(v.w), sq);
-      }
-      nrm[tid] = sq;
-    }
+    if (tid < m) nrm[tid] = tc_norm2(Cs, tid, NQ, nch);
     // wait (bounded) for the Gram matrix; every thread takes the same decision
     bool done = false;
     for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(bar, phase);
@@ -390,16 +326,8 @@ __global__ void __launch_bounds__(TCP_M) harvest_prune_tc_kernel(const HPruneArg
         for (int t = 0; t < 32; ++t) {
           const int jj = 32 * cb + t;
           if (jj <= i || jj >= m) continue;
-          const float g = __uint_as_float(v[t]);
-          const float nj = nrm[jj];
           float dt, eps;
-          if constexpr (METRIC == ANGULAR_F32) {
-            dt = 1.0f - g;
-            eps = a.tc_e1 * 0.5f * (ni + nj) + a.tc_e0;
-          } else {
-            dt = (ni + nj) - 2.0f * g;
-            eps = a.tc_e1 * (ni + nj) + a.tc_e0;
-          }
+          tc_approx<METRIC>(__uint_as_float(v[t]), ni, nrm[jj], a.tc_e1, a.tc_e0, &dt, &eps);
           const float dp = key_dist(keys[jj]);
           float up = a.alpha2 * (dt + eps);
           up += fabsf(up) * 4.76837158e-7f + 1e-30f;  // 2^-21
@@ -415,7 +343,7 @@ __global__ void __launch_bounds__(TCP_M) harvest_prune_tc_kernel(const HPruneArg
           const int t = __ffs(unsure) - 1;
           unsure &= unsure - 1u;
           const int jj = 32 * cb + t;
-          const float dd = canon_dist_thread<METRIC, G, K>(Cs, NQ, i, jj, nch, a.d);
+          const float dd = canon_dist_thread<METRIC, G, K>(Cs, i, Cs, jj, NQ, nch, a.d);
           if (__fmul_rn(a.alpha2, dd) <= key_dist(keys[jj])) word |= 1u << t;
         }
         dom[i * TCP_W + cb] = word;
@@ -523,16 +451,7 @@ int harvest_prune(const VecLayout& L, const uint64_t* Eg, const int32_t* Eg_cnt,
   FG_CUDA(cudaGetDevice(&dev));
   FG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   if (tck && err && g_prune_tc && ecap <= TCP_M && harvest_prune_tc_smem(L.nchunks) <= optin) {
-    // tensor-core Gram: error bound of |approx - canonical| (see the kernel)
-    const double D = 4.0 * tcp_nq(L.nchunks);
-    const double ut = std::ldexp(1.0, -10), u22 = std::ldexp(1.0, -22);
-    if (L.metric == ANGULAR_F32) {
-      a.tc_e1 = (float)(2.0 * (2.01 * ut + (1.25 * D + 1.0) * u22));
-      a.tc_e0 = (float)(2.0 * u22);
-    } else {
-      a.tc_e1 = (float)(2.0 * (2.01 * ut + (1.75 * D + 2.0) * u22));
-      a.tc_e0 = 0.0f;
-    }
+    tc_error_bound(L.metric, L.nchunks, &a.tc_e1, &a.tc_e0);
     kern = tck;
     threads = TCP_M;
     // at most 512 / 128 CTAs on an SM (its tensor memory columns): the

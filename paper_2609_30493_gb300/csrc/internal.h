@@ -66,7 +66,8 @@ struct SatScratch {
   int32_t* seg_len;     // same
   int32_t* seg_node;    // same
   int32_t* seg_tree;    // same
-  uint32_t* nseg;       // 4: tiny, big nodes of the level, error flag, other nodes
+  uint32_t* nseg;       // 5: tiny, big nodes of the level, error flag, other nodes,
+                        //    tensor-core timeout flag
   int64_t* scan_tmp;
   int32_t big_min;      // nodes with at least this many points use the multi-CTA path
   int32_t* big_list;    // segment index of each big node
@@ -125,6 +126,8 @@ int harvest_prune(const VecLayout& L, const uint64_t* Eg, const int32_t* Eg_cnt,
 // float32 metrics and lists of at most 128 when err is given) or on the lane
 // groups (0).  The pruned lists are the same either way.
 extern int g_prune_tc;
+// The same for the SAT's closest-child assignment.
+extern int g_sat_tc;
 
 // Dense-block top-k with the BF16 tensor-core filter and canonical rerank;
 // stats (host, optional): rerank fraction, Gram ms, select ms, prep ms.

@@ -21,6 +21,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tcdist.cuh"
 
 namespace fg {
 
@@ -420,6 +421,159 @@ __global__ void __launch_bounds__(ASSIGN_NW * 32)
   if (blockIdx.x == 0 && threadIdx.x == 0) sat_count(a, m, k);
 }
 
+// The assignment on the tensor cores (float32 metrics).  A CTA takes 128
+// points of a node (A) and the node's children 128 at a time (B), both staged
+// in the canonical operand layout, and computes their Gram tile with
+// kind::tf32 MMAs into 128 TMEM columns.  Thread i reads its point's row
+// twice: first the bound ub = min over children of (approx + eps), then the
+// candidates, the children with approx - eps <= ub; the canonical distance
+// of the closest child is at most ub and every other child's at least its
+// approx - eps, so the closest by (delta, id) is among the candidates, and
+// only they are evaluated in canonical float32 (bound: tcdist.cuh).
+constexpr int AT_M = 128;
+struct AtSmem {
+  int nq;
+  __host__ __device__ int b_off() const { return AT_M * nq * 16; }
+  __host__ __device__ int kid_off() const { return 2 * AT_M * nq * 16; }
+  __host__ __device__ int na_off() const { return kid_off() + 4 * AT_M; }
+  __host__ __device__ int nb_off() const { return na_off() + 4 * AT_M; }
+  __host__ __device__ int bar_off() const { return nb_off() + 4 * AT_M; }
+  __host__ __device__ int bytes() const { return bar_off() + 16; }
+};
+
+template <int METRIC, int G, int K>
+__global__ void __launch_bounds__(AT_M)
+    sat_assign_tc_kernel(const SatSegArgs a, const int32_t* segs, int32_t y_off, float e1,
+                         float e0, uint32_t* err) {
+  extern __shared__ __align__(128) unsigned char atsm[];
+  const int y = blockIdx.y + y_off;
+  const int64_t s = segs ? (int64_t)segs[y] : a.seg_off + y;
+  const int m = a.seg_len[s];
+  const int t0 = blockIdx.x * AT_M;
+  if (t0 >= m) return;  // before any tensor memory is taken
+  const int na = min(AT_M, m - t0);
+  const int k = a.seg_k[s];
+  const int64_t start = a.seg_start[s];
+  const int64_t tbase = (int64_t)a.seg_tree[s] * a.n;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int nch = a.nchunks;
+  const AtSmem L{tcp_nq(nch)};
+  const int NQ = L.nq;
+  uint4* As = reinterpret_cast<uint4*>(atsm);
+  uint4* Bs = reinterpret_cast<uint4*>(atsm + L.b_off());
+  int32_t* kids = reinterpret_cast<int32_t*>(atsm + L.kid_off());
+  float* nra = reinterpret_cast<float*>(atsm + L.na_off());
+  float* nrb = reinterpret_cast<float*>(atsm + L.nb_off());
+  uint64_t* bar = reinterpret_cast<uint64_t*>(atsm + L.bar_off());
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(atsm + L.bar_off() + 8);
+  // stage the points (rows past na zero)
+  for (int idx = tid; idx < AT_M * NQ; idx += AT_M) {
+    const int r = idx / NQ, q = idx - r * NQ;
+    As[tcp_at(r, q, NQ)] =
+        r < na ? tc_chunk(a.X + (int64_t)a.item_pt[start + t0 + r] * a.ld_bytes, q, nch, a.d)
+               : make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (warp == 0) {
+    tmem_alloc(tslot, AT_M);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+  const int i = tid;
+  const float ni = i < na ? tc_norm2(As, i, NQ, nch) : 0.0f;
+  const int32_t pt = i < na ? a.item_pt[start + t0 + i] : -1;
+  uint64_t best = PAD;
+  bool self = false, ok = true;
+  uint32_t phase = 0;
+  const uint32_t idesc = idesc_tf32(AT_M, AT_M);
+  const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs), sbo = (uint32_t)NQ * 128u;
+  for (int c0 = 0; c0 < k; c0 += AT_M) {
+    const int kn = min(AT_M, k - c0);
+    if (c0 > 0) {  // the previous chunk's MMAs and TMEM reads are done
+      tc_fence_before();
+      __syncthreads();
+    }
+    for (int idx = tid; idx < AT_M * NQ; idx += AT_M) {
+      const int r = idx / NQ, q = idx - r * NQ;
+      Bs[tcp_at(r, q, NQ)] =
+          r < kn ? tc_chunk(a.X + (int64_t)a.kid[start + c0 + r] * a.ld_bytes, q, nch, a.d)
+                 : make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (tid < kn) kids[tid] = a.kid[start + c0 + tid];
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      for (int kk = 0; kk < NQ / 2; ++kk)
+        mma_tf32(tmem, smem_desc(a0 + kk * 256, 128, sbo), smem_desc(b0 + kk * 256, 128, sbo),
+                 idesc, kk > 0 ? 1u : 0u);
+      mma_commit(bar);
+    }
+    if (tid < kn) nrb[tid] = tc_norm2(Bs, tid, NQ, nch);
+    bool done = false;
+    for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(bar, phase);
+    done = __syncthreads_and(done);  // also publishes nrb
+    if (!done) {
+      ok = false;
+      if (tid == 0) atomicOr(err, 1u);
+      break;
+    }
+    phase ^= 1u;
+    tc_fence_after();
+    const int nb = (kn + 31) / 32;
+    float ub = INFINITY;
+    for (int cb = 0; cb < nb; ++cb) {  // uniform
+      uint32_t v[32];
+      tmem_ld32(trow + (uint32_t)(32 * cb), v);
+#pragma unroll
+      for (int t = 0; t < 32; ++t) {
+        const int c = 32 * cb + t;
+        float dt, eps;
+        tc_approx<METRIC>(__uint_as_float(v[t]), ni, nrb[min(c, kn - 1)], e1, e0, &dt, &eps);
+        if (c < kn) ub = fminf(ub, dt + eps);
+      }
+    }
+    for (int cb = 0; cb < nb; ++cb) {
+      uint32_t v[32];
+      tmem_ld32(trow + (uint32_t)(32 * cb), v);
+      uint32_t cand = 0;
+#pragma unroll
+      for (int t = 0; t < 32; ++t) {
+        const int c = 32 * cb + t;
+        float dt, eps;
+        tc_approx<METRIC>(__uint_as_float(v[t]), ni, nrb[min(c, kn - 1)], e1, e0, &dt, &eps);
+        if (c < kn && dt - eps <= ub) cand |= 1u << t;
+      }
+      if (i < na) {
+        while (cand) {
+          const int t = __ffs(cand) - 1;
+          cand &= cand - 1u;
+          const int c = 32 * cb + t;
+          const float dd = canon_dist_thread<METRIC, G, K>(As, i, Bs, c, NQ, nch, a.d);
+          best = umin64(best, make_key(dd, kids[c]));
+        }
+        for (int t = 0; t < 32 && 32 * cb + t < kn; ++t) self |= kids[32 * cb + t] == pt;
+      }
+    }
+  }
+  if (ok && i < na) a.node_of[tbase + pt] = self ? -1 : key_id(best);
+  if (!ok) {
+    for (int it = 0; it < (1 << 22); ++it)
+      if (mbar_try_wait(bar, phase)) break;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, AT_M);
+  if (blockIdx.x == 0 && tid == 0) sat_count(a, m, k);
+}
+
 // ---------------------------------------------------------------------------
 // Nodes with many points.  While a node's open list is long, every CTA of a
 // launch owns a tile of it and one launch performs one child selection for
@@ -520,6 +674,7 @@ __global__ void __launch_bounds__(BIG_NW * 32) sat_big_kernel(const SatBigArgs A
 using SatBigFn = void (*)(const SatBigArgs, int);
 
 using SatKernelFn = void (*)(const SatSegArgs);
+int g_sat_tc = 1;  // closest-child assignment on the tensor cores where possible
 constexpr int SAT_NW = 8;           // warps per CTA: nodes of more points, the big path
 constexpr int TINY_NW = 2;          // warps per CTA: nodes that fit in shared memory
 constexpr int SAT_SMEM = 96 * 1024; // dynamic shared memory per CTA, by CTA width
@@ -559,6 +714,21 @@ static SatAssignFn sat_assign_for(int metric, int G, int K) {
   SATF(0)
   SATF(1)
   SATX(2, 4, 1) SATX(2, 8, 1) SATX(2, 16, 1)
+#undef SATF
+#undef SATX
+  return nullptr;
+}
+
+using SatAssignTcFn = void (*)(const SatSegArgs, const int32_t*, int32_t, float, float,
+                              uint32_t*);
+
+static SatAssignTcFn sat_assign_tc_for(int metric, int G, int K) {
+#define SATX(M, GG, KK) \
+  if (metric == M && G == GG && K == KK) return sat_assign_tc_kernel<M, GG, KK>;
+#define SATF(M) SATX(M, 4, 1) SATX(M, 8, 1) SATX(M, 16, 1) SATX(M, 32, 1) SATX(M, 32, 2) \
+  SATX(M, 32, 4) SATX(M, 32, 8)
+  SATF(0)
+  SATF(1)
 #undef SATF
 #undef SATX
   return nullptr;
@@ -666,6 +836,7 @@ int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* paren
     return 1;
   }
   const int64_t n = L.n, tot = (int64_t)T * n;
+  FG_CUDA(cudaMemsetAsync(S.nseg + 4, 0, sizeof(uint32_t), s));
   sat_init_kernel<<<grid_for(tot), 256, 0, s>>>(n, T, roots_d, S.node_of, parents);
   note_launch();
   FG_CUDA(cudaGetLastError());
@@ -699,11 +870,33 @@ int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* paren
   FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(asgk), (int)smem));
   // the assignment launches: tiles of one node per grid column, nodes in rows
   // (grid.y is limited to 65535, so rows are covered in chunks)
+  // on the tensor cores where the metric and the shared memory allow
+  SatAssignTcFn asgtc = g_sat_tc ? sat_assign_tc_for(L.metric, L.G, L.K) : nullptr;
+  size_t smem_tc = 0;
+  float tc_e1 = 0.0f, tc_e0 = 0.0f;
+  if (asgtc) {
+    int dev = 0, optin = 0, sm_bytes = 0;
+    FG_CUDA(cudaGetDevice(&dev));
+    FG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    FG_CUDA(cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    // at most 512 / 128 CTAs on an SM (its tensor memory columns)
+    smem_tc = std::max<size_t>(AtSmem{tcp_nq(L.nchunks)}.bytes(), sm_bytes / 5);
+    if (smem_tc > (size_t)optin) {
+      asgtc = nullptr;
+    } else {
+      FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(asgtc), (int)smem_tc));
+      tc_error_bound(L.metric, L.nchunks, &tc_e1, &tc_e0);
+    }
+  }
   auto assign_all = [&](const int32_t* segs, uint32_t nrows, int64_t max_m) {
-    const unsigned gxa = (unsigned)((max_m + ASSIGN_TILE - 1) / ASSIGN_TILE);
+    const int tile = asgtc ? AT_M : ASSIGN_TILE;
+    const unsigned gxa = (unsigned)((max_m + tile - 1) / tile);
     for (uint32_t y0 = 0; y0 < nrows; y0 += 65535u) {
       const dim3 grid(gxa, std::min<uint32_t>(65535u, nrows - y0));
-      asgk<<<grid, ASSIGN_NW * 32, smem, s>>>(a, segs, (int32_t)y0);
+      if (asgtc)
+        asgtc<<<grid, AT_M, smem_tc, s>>>(a, segs, (int32_t)y0, tc_e1, tc_e0, S.nseg + 4);
+      else
+        asgk<<<grid, ASSIGN_NW * 32, smem, s>>>(a, segs, (int32_t)y0);
       note_launch();
     }
   };
@@ -724,11 +917,15 @@ int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* paren
                                                      S.item_pt);
     note_launch();
     FG_CUDA(cudaGetLastError());
-    uint32_t cnts[4] = {0, 0, 0, 0};
+    uint32_t cnts[5] = {0, 0, 0, 0, 0};
     FG_CUDA(cudaMemcpyAsync(cnts, S.nseg, sizeof(cnts), cudaMemcpyDeviceToHost, s));
     FG_CUDA(cudaStreamSynchronize(s));
     if (cnts[2]) {
       set_error(3, "SAT: a point was assigned to an invalid node");
+      return 3;
+    }
+    if (cnts[4]) {
+      set_error(3, "SAT: a tensor-core assignment timed out waiting for its products");
       return 3;
     }
     const uint32_t ntiny = cnts[0], nbig = cnts[1], nsmall = cnts[3];
