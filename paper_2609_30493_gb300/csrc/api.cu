@@ -374,6 +374,35 @@ int dalloc(T** p, int64_t count) {
   return 0;
 }
 
+// Stream-ordered scratch: the device's default memory pool keeps what it has
+// reserved (release threshold raised once per device), so the scratch of a
+// repeated build or prune is served without new mappings or device syncs.
+static void keep_pool_reserved() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done[dev] = true;
+}
+
+template <typename T>
+int dalloc_async(T** p, int64_t count, cudaStream_t s) {
+  cudaError_t e = cudaMallocAsync(p, sizeof(T) * (size_t)std::max<int64_t>(count, 1), s);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    set_error(FGRAFT_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+    return FGRAFT_ENOMEM;
+  }
+  return 0;
+}
+
 void free_index(fgraft_index* ix) {
   if (!ix) return;
   if (ix->graph_exec) cudaGraphExecDestroy(ix->graph_exec);
@@ -526,28 +555,29 @@ fgraft_status fgraft_build_scaffold(const void* X, int64_t n, int32_t d, int64_t
   FAILX(cudaMemsetAsync(ix->cnt, 0, sizeof(int32_t) * n, s));
   FAILX(cudaMemsetAsync(ix->A, 0xFF, sizeof(int32_t) * n * p.R, s));
 
-  // SAT forest
+  // SAT forest (stream-ordered scratch)
+  keep_pool_reserved();
   SatScratch S{};
   rc = 0;
-  rc = rc ? rc : dalloc(&S.node_of, tot);
-  rc = rc ? rc : dalloc(&S.kcnt, tot);
-  rc = rc ? rc : dalloc(&S.kstart, tot + 1);
-  rc = rc ? rc : dalloc(&S.item_pt, tot);
-  rc = rc ? rc : dalloc(&S.lst, 2 * tot);
-  rc = rc ? rc : dalloc(&S.best, tot);
-  rc = rc ? rc : dalloc(&S.kid, tot);
+  rc = rc ? rc : dalloc_async(&S.node_of, tot, s);
+  rc = rc ? rc : dalloc_async(&S.kcnt, tot, s);
+  rc = rc ? rc : dalloc_async(&S.kstart, tot + 1, s);
+  rc = rc ? rc : dalloc_async(&S.item_pt, tot, s);
+  rc = rc ? rc : dalloc_async(&S.lst, 2 * tot, s);
+  rc = rc ? rc : dalloc_async(&S.best, tot, s);
+  rc = rc ? rc : dalloc_async(&S.kid, tot, s);
   S.big_min = g_sat_big_min;
   const int64_t nbig_max = tot / S.big_min + 1;
-  rc = rc ? rc : dalloc(&S.seg_start, tot + nbig_max);
-  rc = rc ? rc : dalloc(&S.seg_len, tot + nbig_max);
-  rc = rc ? rc : dalloc(&S.seg_node, tot + nbig_max);
-  rc = rc ? rc : dalloc(&S.seg_tree, tot + nbig_max);
-  rc = rc ? rc : dalloc(&S.seg_k, tot + nbig_max);
-  rc = rc ? rc : dalloc(&S.nseg, 5);
-  rc = rc ? rc : dalloc(&S.big_list, nbig_max);
-  rc = rc ? rc : dalloc(&S.big_keys, 3 * nbig_max);
-  rc = rc ? rc : dalloc(&S.big_kcount, nbig_max);
-  rc = rc ? rc : dalloc(&S.big_lens, 3 * nbig_max);
+  rc = rc ? rc : dalloc_async(&S.seg_start, tot + nbig_max, s);
+  rc = rc ? rc : dalloc_async(&S.seg_len, tot + nbig_max, s);
+  rc = rc ? rc : dalloc_async(&S.seg_node, tot + nbig_max, s);
+  rc = rc ? rc : dalloc_async(&S.seg_tree, tot + nbig_max, s);
+  rc = rc ? rc : dalloc_async(&S.seg_k, tot + nbig_max, s);
+  rc = rc ? rc : dalloc_async(&S.nseg, 7, s);
+  rc = rc ? rc : dalloc_async(&S.big_list, nbig_max, s);
+  rc = rc ? rc : dalloc_async(&S.big_keys, 3 * nbig_max, s);
+  rc = rc ? rc : dalloc_async(&S.big_kcount, nbig_max, s);
+  rc = rc ? rc : dalloc_async(&S.big_lens, 3 * nbig_max, s);
   S.finish_len = g_sat_finish_len;
   S.scan_tmp = ix->scan_tmp;
   auto free_sat = [&]() {
@@ -555,7 +585,7 @@ fgraft_status fgraft_build_scaffold(const void* X, int64_t n, int32_t d, int64_t
                   S.seg_start, S.seg_len, S.seg_node, S.seg_tree, S.seg_k, S.nseg,
                   S.big_list, S.big_keys, S.big_kcount, S.big_lens};
     for (void* q : ps)
-      if (q) cudaFree(q);
+      if (q) cudaFreeAsync(q, s);
   };
   if (!rc) {
     cudaError_t e = cudaMemsetAsync(S.kcnt, 0, sizeof(uint32_t) * tot, s);
@@ -572,16 +602,16 @@ fgraft_status fgraft_build_scaffold(const void* X, int64_t n, int32_t d, int64_t
   int64_t* tmp_off = nullptr;
   int32_t* tmp_ids = nullptr;
   rc = 0;
-  rc = rc ? rc : dalloc(&deg, n);
-  rc = rc ? rc : dalloc(&tmp_off, n + 1);
-  rc = rc ? rc : dalloc(&tmp_ids, 2 * tot);
+  rc = rc ? rc : dalloc_async(&deg, n, s);
+  rc = rc ? rc : dalloc_async(&tmp_off, n + 1, s);
+  rc = rc ? rc : dalloc_async(&tmp_ids, 2 * tot, s);
   if (!rc)
     rc = scaffold_csr(n, p.T, ix->parents, ix->s_off, &ix->s_ids, &ix->s_nnz, deg, tmp_off,
                       tmp_ids, ix->scan_tmp, s);
+  if (deg) cudaFreeAsync(deg, s);
+  if (tmp_off) cudaFreeAsync(tmp_off, s);
+  if (tmp_ids) cudaFreeAsync(tmp_ids, s);
   cudaStreamSynchronize(s);
-  if (deg) cudaFree(deg);
-  if (tmp_off) cudaFree(tmp_off);
-  if (tmp_ids) cudaFree(tmp_ids);
   if (rc) {
     free_index(ix);
     return (fgraft_status)rc;
@@ -622,6 +652,7 @@ fgraft_status fgraft_prune(fgraft_index* ix, fgraft_stream stream, fgraft_counte
   int rc = check_err_flag(ix, s);
   if (rc) return (fgraft_status)rc;
   FGS(cudaMemsetAsync(ix->ctr + C_FINAL, 0, sizeof(unsigned long long), s));
+  keep_pool_reserved();
   rc = final_graph(ix->L, ix->p.R, ix->p.alpha * ix->p.alpha, ix->A, ix->cnt, ix->r_off,
                    ix->r_ids, ix->parents, ix->f_off, &ix->f_ids, &ix->f_nnz, ix->scan_tmp,
                    ix->ctr + C_FINAL, ix->num_sms, s);

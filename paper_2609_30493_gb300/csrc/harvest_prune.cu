@@ -282,11 +282,7 @@ __global__ void __launch_bounds__(TCP_M) harvest_prune_tc_kernel(const HPruneArg
     __syncthreads();
     const int m = *mshared;
     // stage the candidates (element tails past d zeroed)
-    for (int idx = tid; idx < m * NQ; idx += TCP_M) {
-      const int r = idx / NQ, q = idx - r * NQ;
-      Cs[tcp_at(r, q, NQ)] =
-          tc_chunk(a.X + (int64_t)key_id(keys[r]) * a.ld_bytes, q, nch, a.d);
-    }
+    if (tid < m) tc_stage_row(Cs, tid, a.X + (int64_t)key_id(keys[tid]) * a.ld_bytes, NQ, nch, a.d);
     fence_proxy_async();
     __syncthreads();
     if (tid == 0) {

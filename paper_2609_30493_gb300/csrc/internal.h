@@ -66,8 +66,8 @@ struct SatScratch {
   int32_t* seg_len;     // same
   int32_t* seg_node;    // same
   int32_t* seg_tree;    // same
-  uint32_t* nseg;       // 5: tiny, big nodes of the level, error flag, other nodes,
-                        //    tensor-core timeout flag
+  uint32_t* nseg;       // 7: tiny, big nodes of the level, error flag, other nodes,
+                        //    tensor-core timeout flag, most points of other / big nodes
   int64_t* scan_tmp;
   int32_t big_min;      // nodes with at least this many points use the multi-CTA path
   int32_t* big_list;    // segment index of each big node

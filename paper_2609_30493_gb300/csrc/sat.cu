@@ -196,6 +196,7 @@ struct SelSmem {
   uint64_t* skey;  // ls keys
   int32_t* sl0;    // ls indices
   int32_t* sl1;    // ls indices
+  int32_t* krow;   // ls: staged row of the t-th child (while t < ls)
   int32_t ls;      // capacity
 };
 
@@ -283,6 +284,7 @@ __device__ int sat_select(const SatSegArgs& a, int64_t start, int32_t anode, int
         }
       }
     }
+    if (threadIdx.x == 0 && k - 1 < sm.ls) sm.krow[k - 1] = ib;
     bk = block_argmin64<NW>(lmin, li, rk, ri, parity);
     parity ^= 1;
     ib = li;
@@ -361,8 +363,38 @@ __device__ __forceinline__ SelSmem sel_smem(const SatSegArgs& a, unsigned char* 
   sm.skey = reinterpret_cast<uint64_t*>(sm.rows + (int64_t)a.ls * nch);
   sm.sl0 = reinterpret_cast<int32_t*>(sm.skey + a.ls);
   sm.sl1 = sm.sl0 + a.ls;
+  sm.krow = sm.sl1 + a.ls;
   sm.ls = a.ls;
   return sm;
+}
+
+// Assignment of a node whose m points were all staged, in item order, when
+// its selection began (m <= ls): point i is staged row i and the t-th child
+// staged row krow[t], so no global memory is read.
+template <int METRIC, int G, int K, int NW>
+__device__ void sat_assign_staged(const SatSegArgs& a, const SelSmem& sm, int m, int k,
+                                  int64_t tbase) {
+  using L = Lanes<G, K>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane / L::P, j = lane % L::P;
+  const int nch = a.nchunks;
+  __syncthreads();  // krow of the last step
+  for (int base = warp * L::CPW; base < m; base += NW * L::CPW) {  // warp-uniform
+    const int i = min(base + g, m - 1);
+    uint4 xq[L::VL][K];
+    load_slots_smem<G, K>(sm.rows + (int64_t)i * nch, nch, j, xq);
+    uint64_t best = PAD;
+    bool self = false;
+    for (int t = 0; t < k; ++t) {
+      const int r = sm.krow[t];
+      uint4 y[L::VL][K];
+      load_slots_smem<G, K>(sm.rows + (int64_t)r * nch, nch, j, y);
+      const float dd = regs_dist<METRIC, G, K>(xq, y, nch, a.d, j, FULL);
+      best = umin64(best, make_key(dd, key_id(sm.skey[r])));
+      self |= r == i;
+    }
+    if (base + g < m && j == 0) a.node_of[tbase + key_id(sm.skey[i])] = self ? -1 : key_id(best);
+  }
 }
 
 // A node with fewer points: one CTA runs the whole construction of its
@@ -390,6 +422,14 @@ __global__ void __launch_bounds__(NW * 32) sat_segment_kernel(const SatSegArgs a
   const uint64_t bk = block_min64<NW>(lmin, rk, 0);
   const int k = sat_select<METRIC, G, K, NW>(a, start, anode, tbase, l0, a.lst1 + start, m, bk,
                                              0, cvec, sm, rk, ri, scnt);
+  if (m <= sm.ls) {  // staged whole from the start
+    sat_assign_staged<METRIC, G, K, NW>(a, sm, m, k, tbase);
+    if (threadIdx.x == 0) {
+      sat_count(a, m, k);
+      if (a.seg_k) a.seg_k[s] = -1;  // nothing left for the assignment launch
+    }
+    return;
+  }
   if (a.seg_k) {
     if (threadIdx.x == 0) a.seg_k[s] = k;
     return;
@@ -414,8 +454,8 @@ __global__ void __launch_bounds__(ASSIGN_NW * 32)
   const int64_t s = segs ? (int64_t)segs[y] : a.seg_off + y;
   const int m = a.seg_len[s];
   const int t0 = blockIdx.x * ASSIGN_TILE;
-  if (t0 >= m) return;
   const int k = a.seg_k[s];
+  if (t0 >= m || k < 0) return;  // k < 0: assigned by the node's own CTA
   sat_assign<METRIC, G, K, ASSIGN_NW>(a, a.seg_start[s], t0, min(m, t0 + ASSIGN_TILE), k,
                                       (int64_t)a.seg_tree[s] * a.n, kvec, kids);
   if (blockIdx.x == 0 && threadIdx.x == 0) sat_count(a, m, k);
@@ -450,9 +490,9 @@ __global__ void __launch_bounds__(AT_M)
   const int64_t s = segs ? (int64_t)segs[y] : a.seg_off + y;
   const int m = a.seg_len[s];
   const int t0 = blockIdx.x * AT_M;
-  if (t0 >= m) return;  // before any tensor memory is taken
-  const int na = min(AT_M, m - t0);
   const int k = a.seg_k[s];
+  if (t0 >= m || k < 0) return;  // before any tensor memory is taken; k < 0: assigned
+  const int na = min(AT_M, m - t0);
   const int64_t start = a.seg_start[s];
   const int64_t tbase = (int64_t)a.seg_tree[s] * a.n;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -466,13 +506,10 @@ __global__ void __launch_bounds__(AT_M)
   float* nrb = reinterpret_cast<float*>(atsm + L.nb_off());
   uint64_t* bar = reinterpret_cast<uint64_t*>(atsm + L.bar_off());
   uint32_t* tslot = reinterpret_cast<uint32_t*>(atsm + L.bar_off() + 8);
-  // stage the points (rows past na zero)
-  for (int idx = tid; idx < AT_M * NQ; idx += AT_M) {
-    const int r = idx / NQ, q = idx - r * NQ;
-    As[tcp_at(r, q, NQ)] =
-        r < na ? tc_chunk(a.X + (int64_t)a.item_pt[start + t0 + r] * a.ld_bytes, q, nch, a.d)
-               : make_uint4(0u, 0u, 0u, 0u);
-  }
+  // stage the points (rows past na zero), one row per thread
+  tc_stage_row(As, tid,
+               tid < na ? a.X + (int64_t)a.item_pt[start + t0 + tid] * a.ld_bytes : nullptr, NQ,
+               nch, a.d);
   if (warp == 0) {
     tmem_alloc(tslot, AT_M);
     tmem_relinquish();
@@ -500,13 +537,9 @@ __global__ void __launch_bounds__(AT_M)
       tc_fence_before();
       __syncthreads();
     }
-    for (int idx = tid; idx < AT_M * NQ; idx += AT_M) {
-      const int r = idx / NQ, q = idx - r * NQ;
-      Bs[tcp_at(r, q, NQ)] =
-          r < kn ? tc_chunk(a.X + (int64_t)a.kid[start + c0 + r] * a.ld_bytes, q, nch, a.d)
-                 : make_uint4(0u, 0u, 0u, 0u);
-    }
-    if (tid < kn) kids[tid] = a.kid[start + c0 + tid];
+    const int32_t kc = tid < kn ? a.kid[start + c0 + tid] : -1;
+    tc_stage_row(Bs, tid, kc >= 0 ? a.X + (int64_t)kc * a.ld_bytes : nullptr, NQ, nch, a.d);
+    if (tid < kn) kids[tid] = kc;
     fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
@@ -676,9 +709,9 @@ using SatBigFn = void (*)(const SatBigArgs, int);
 using SatKernelFn = void (*)(const SatSegArgs);
 int g_sat_tc = 1;  // closest-child assignment on the tensor cores where possible
 constexpr int SAT_NW = 8;           // warps per CTA: nodes of more points, the big path
-constexpr int TINY_NW = 2;          // warps per CTA: nodes that fit in shared memory
+constexpr int TINY_NW = 1;          // warps per CTA: nodes that fit in shared memory
 constexpr int SAT_SMEM = 96 * 1024; // dynamic shared memory per CTA, by CTA width
-constexpr int TINY_SMEM = 24 * 1024;
+constexpr int TINY_SMEM = 12 * 1024;
 
 template <int NW>
 static SatKernelFn sat_kernel_for(int metric, int G, int K) {
@@ -699,9 +732,9 @@ static SatKernelFn sat_kernel_for(int metric, int G, int K) {
 // Returns the dynamic shared memory size.
 static size_t sat_smem_plan(SatSegArgs& a, int budget) {
   const int row16 = a.nchunks * 16;
-  a.ls = std::max(1, std::min(4096, (budget - row16) / (row16 + 16)));
+  a.ls = std::max(1, std::min(4096, (budget - row16) / (row16 + 20)));
   a.kc = std::max(1, std::min(256, (budget - row16) / (row16 + 4)));
-  return (size_t)row16 + std::max((size_t)a.ls * (row16 + 16), (size_t)a.kc * (row16 + 4));
+  return (size_t)row16 + std::max((size_t)a.ls * (row16 + 20), (size_t)a.kc * (row16 + 4));
 }
 
 using SatAssignFn = void (*)(const SatSegArgs, const int32_t*, int32_t);
@@ -777,8 +810,9 @@ __global__ void sat_count_kernel(int64_t n, int64_t tot, const int32_t* node_of,
 
 // Segment lists of a level: nodes of at most tiny_max points fill the list
 // from the front (count nseg[0]), nodes of at least big_min points from
-// big_base on (nseg[1], with their indices in big_list), the others from the
-// top of the small-node region down (nseg[3]).
+// big_base on (nseg[1], with their indices in big_list, most points in
+// nseg[6]), the others from the top of the small-node region down (nseg[3],
+// most points in nseg[5]).
 __global__ void sat_segments_kernel(int64_t n, int64_t tot, const uint32_t* kcnt,
                                     const int64_t* kstart, int64_t* seg_start, int32_t* seg_len,
                                     int32_t* seg_node, int32_t* seg_tree, uint32_t* nseg,
@@ -793,10 +827,12 @@ __global__ void sat_segments_kernel(int64_t n, int64_t tot, const uint32_t* kcnt
         const uint32_t j = atomicAdd(nseg + 1, 1u);
         s = big_base + j;
         big_list[j] = (int32_t)s;
+        atomicMax(nseg + 6, c);
       } else if ((int32_t)c <= tiny_max) {
         s = atomicAdd(nseg, 1u);
       } else {
         s = tot - 1 - (int64_t)atomicAdd(nseg + 3, 1u);
+        atomicMax(nseg + 5, c);
       }
       seg_start[s] = kstart[key];
       seg_len[s] = (int32_t)c;
@@ -905,6 +941,7 @@ int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* paren
   std::vector<uint32_t> hlens;
   for (int64_t level = 0; level <= n; ++level) {
     FG_CUDA(cudaMemsetAsync(S.nseg, 0, 4 * sizeof(uint32_t), s));
+    FG_CUDA(cudaMemsetAsync(S.nseg + 5, 0, 2 * sizeof(uint32_t), s));
     sat_count_kernel<<<grid_for(tot), 256, 0, s>>>(n, tot, S.node_of, S.kcnt, S.nseg + 2);
     note_launch();
     int rc = scan_u32(S.kcnt, S.kstart, tot, S.scan_tmp, s);
@@ -917,7 +954,7 @@ int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* paren
                                                      S.item_pt);
     note_launch();
     FG_CUDA(cudaGetLastError());
-    uint32_t cnts[5] = {0, 0, 0, 0, 0};
+    uint32_t cnts[7] = {0, 0, 0, 0, 0, 0, 0};
     FG_CUDA(cudaMemcpyAsync(cnts, S.nseg, sizeof(cnts), cudaMemcpyDeviceToHost, s));
     FG_CUDA(cudaStreamSynchronize(s));
     if (cnts[2]) {
@@ -934,7 +971,7 @@ int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* paren
       a.seg_off = tot - nsmall;
       kern<<<nsmall, SAT_NW * 32, smem, s>>>(a);
       note_launch();
-      assign_all(nullptr, nsmall, std::min<int64_t>(n, S.big_min));
+      assign_all(nullptr, nsmall, cnts[5]);
       FG_CUDA(cudaGetLastError());
     }
     if (ntiny) {
@@ -1004,7 +1041,7 @@ int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* paren
         return 1;
       }
       launch_all(3, 1);
-      assign_all(S.big_list, nbig, n);
+      assign_all(S.big_list, nbig, cnts[6]);
       FG_CUDA(cudaGetLastError());
     }
   }

@@ -52,6 +52,21 @@ __device__ __forceinline__ uint4 tc_chunk(const char* __restrict__ row, int q, i
   return v;
 }
 
+// Stage a float32 row as staged row r, one thread, 16 chunks in flight at a
+// time (row == nullptr: zeros).
+__device__ __forceinline__ void tc_stage_row(uint4* C, int r, const char* __restrict__ row,
+                                             int NQ, int nch, int d) {
+  for (int q0 = 0; q0 < NQ; q0 += 16) {
+    uint4 v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+      v[u] = (row && q0 + u < NQ) ? tc_chunk(row, q0 + u, nch, d) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+      if (q0 + u < NQ) C[tcp_at(r, q0 + u, NQ)] = v[u];
+  }
+}
+
 // Squared norm of staged row r (float32, any order).
 __device__ __forceinline__ float tc_norm2(const uint4* C, int r, int NQ, int nch) {
   float sq = 0.0f;
