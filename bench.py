@@ -76,7 +76,20 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel_file: str):
+# the harvest search kernel's source: the kernel and the distance and merge code it uses
+BEAM_SOURCES = [os.path.join(ROOT, "paper_2609_30493_gb300", "csrc", f)
+                for f in ("beam.cuh", "common.cuh", "beam_ang.cu")]
+
+
+def kernel_source_sha256(files):
+    """One hash over the kernel's source files, in the order given."""
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
+def ncu_traffic(kernel_files):
     """DRAM bytes per harvest launch from the committed ncu summary, if it was
     taken on the current kernel source (hash match), else None."""
     prof = os.path.join(ROOT, "profiles", "harvest_beam_incache_n100k_d100.md")
@@ -87,8 +100,7 @@ def ncu_traffic(kernel_file: str):
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
     if not m or not h:
         return None
-    cur = hashlib.sha256(open(kernel_file, "rb").read()).hexdigest()
-    return float(m.group(1)) if h.group(1) == cur else None
+    return float(m.group(1)) if h.group(1) == kernel_source_sha256(kernel_files) else None
 
 
 class Clocks:
@@ -299,7 +311,7 @@ def run_ours(args):
     scanned = ctr_sum.get("ids_scanned", 0)
     alg_bytes = evals * line_bytes + scanned * 4
     achieved = alg_bytes / (harvest_ms / 1e3) / 1e9 if harvest_ms > 0 else 0.0
-    traffic = ncu_traffic(os.path.join(ROOT, "paper_2609_30493_gb300", "csrc", "beam.cuh"))
+    traffic = ncu_traffic(BEAM_SOURCES)
     dense_pairs = spec["dense_blocks"] * spec["block_size"] * (spec["block_size"] - 1)
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "pts/s", "n_gpus": world,

@@ -398,7 +398,33 @@ __device__ __forceinline__ void merge_into_pool(uint64_t (&pool)[S], uint64_t ca
   for (int s = 0; s < S; ++s)
     if (s == (ef - 1) / 32) worst = __shfl_sync(FULL, pool[s], (ef - 1) % 32);
   if (cand >= worst) cand = PAD;
-  if (__ballot_sync(FULL, cand != PAD) == 0) return;
+  unsigned bal = __ballot_sync(FULL, cand != PAD);
+  if (bal == 0) return;
+  if (__popc(bal) <= 4) {
+    // few survivors: insert one at a time (rank by ballots, shift by one)
+    while (bal) {
+      const int src = __ffs(bal) - 1;
+      bal &= bal - 1u;
+      const uint64_t c = __shfl_sync(FULL, cand, src);
+      int rank = 0;
+#pragma unroll
+      for (int s = 0; s < S; ++s) rank += __popc(__ballot_sync(FULL, pool[s] < c));
+      uint64_t prevlast = PAD;
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        uint64_t up = __shfl_up_sync(FULL, pool[s], 1);
+        const uint64_t last = __shfl_sync(FULL, pool[s], 31);
+        if (lane == 0) up = prevlast;
+        const int i = s * 32 + lane;
+        pool[s] = i < rank ? pool[s] : (i == rank ? c : up);
+        prevlast = last;
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+      if (s * 32 + lane >= ef) pool[s] = PAD;
+    return;
+  }
   cand = warp_sort32(cand, lane);
   uint64_t rev = __shfl_sync(FULL, cand, 31 - lane);
   pool[S - 1] = umin64(pool[S - 1], rev);
