@@ -234,31 +234,46 @@ __global__ void __launch_bounds__(SEL_WARPS * 32)
     int kk = 0;
     if (xi >= 0) {
       const float* lp = a.LP + (blk * TC_ROWS + i) * (int64_t)TC_ROWS;
-      for (int c = lane; c < TC_ROWS; c += 32) {
-        const bool valid = c < a.bs && c != i && ids[c] >= 0;
-        keys[c] = valid ? (((uint64_t)fkey(lp[c]) << 32) | (uint32_t)c) : PAD;
-      }
-      __syncwarp();
-      warp_sort_mem(keys, TC_ROWS, lane);
+      // lane holds columns lane + 32 t; invalid columns get the largest key
+      uint32_t u[TC_ROWS / 32];
       int nv = 0;
-      for (int base = 0; base < TC_ROWS; base += 32)
-        nv += __popc(__ballot_sync(FULL, keys[base + lane] != PAD));
+#pragma unroll
+      for (int t = 0; t < TC_ROWS / 32; ++t) {
+        const int c = lane + 32 * t;
+        const bool valid = c < a.bs && c != i && ids[c] >= 0;
+        u[t] = valid ? fkey(lp[c]) : 0xFFFFFFFFu;
+        nv += valid ? 1 : 0;
+      }
+      nv = __reduce_add_sync(FULL, nv);
       // eps for this row (see the file header)
       const float Ai = sqrtf(a.nrm[blk * TC_ROWS + i]), M = a.Mx[blk];
       float eps = 2.0f * ((4.0f * u_b + 6.0f * dk * gam) * Ai * M +
                           6.0f * dk * gam * (Ai * Ai + M * M));
       if (a.metric == ANGULAR_F32) eps = 0.5f * eps + 2.0f * (3.0f * dk * gam + 2.0f * gam);
-      int cand = nv;
+      // candidates: every valid column when there are at most k, else those
+      // with approx <= tau + 2 eps, tau the k-th smallest approximate value,
+      // found bit by bit (the largest t with fewer than k keys below t)
+      uint32_t lim = 0xFFFFFFFEu;
       if (nv > k) {
-        const float tau = fkey_inv((uint32_t)(keys[k - 1] >> 32));
-        const float theta = tau + 2.0f * eps;
-        cand = 0;
-        for (int base = 0; base < nv; base += 32) {
-          const int c = base + lane;
-          const bool in = c < nv && fkey_inv((uint32_t)(keys[c] >> 32)) <= theta;
-          cand += __popc(__ballot_sync(FULL, in));
+        uint32_t t = 0;
+        for (int bit = 31; bit >= 0; --bit) {
+          const uint32_t tt = t | (1u << bit);
+          int below = 0;
+#pragma unroll
+          for (int q = 0; q < TC_ROWS / 32; ++q) below += u[q] < tt ? 1 : 0;
+          if (__reduce_add_sync(FULL, below) < k) t = tt;
         }
+        lim = fkey(fkey_inv(t) + 2.0f * eps);
       }
+      int cand = 0;
+#pragma unroll
+      for (int q = 0; q < TC_ROWS / 32; ++q) {
+        const bool in = u[q] <= lim;
+        const unsigned m = __ballot_sync(FULL, in);
+        if (in) keys[cand + __popc(m & ((1u << lane) - 1u))] = (uint64_t)(lane + 32 * q);
+        cand += __popc(m);
+      }
+      __syncwarp();
       nre += (unsigned long long)cand;
       // canonical distances of the candidates, in place
       stage_row(qs, a.X + (int64_t)xi * a.ld_bytes, nch, lane);
