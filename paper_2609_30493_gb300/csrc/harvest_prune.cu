@@ -217,11 +217,16 @@ __global__ void __launch_bounds__(HP_WARPS * 32) harvest_prune_kernel(const HPru
 // ---------------------------------------------------------------------------
 constexpr int TCP_M = 128;  // candidates of one tile: TMEM lanes and columns
 constexpr int TCP_W = TCP_M / 32;
-// shared layout: keys[128] | dom[128][4] | m | nrm[128] | mbarrier | tmem slot | Cs
-constexpr int TCP_DOM = 8 * TCP_M;
-constexpr int TCP_M_OFF = TCP_DOM + 4 * TCP_M * TCP_W;
-constexpr int TCP_NRM = TCP_M_OFF + 16;
-constexpr int TCP_BAR = TCP_NRM + 4 * TCP_M;
+// shared layout: keys[128] (sorted) | kraw[128] (list order) | dom[128][4] |
+// col[128] (float4: norm, delta(p, c), rounding margin) | queue[1024] |
+// mbarrier | tmem slot (and the queue count) |
+// Cs (128 staged candidates, sorted order)
+constexpr int TCP_KRAW = 8 * TCP_M;
+constexpr int TCP_DOM = TCP_KRAW + 8 * TCP_M;
+constexpr int TCP_COL = TCP_DOM + 4 * TCP_M * TCP_W;
+constexpr int TCP_QCAP = 1024;  // queued tests the Gram value cannot decide
+constexpr int TCP_UQ = TCP_COL + 16 * TCP_M;
+constexpr int TCP_BAR = TCP_UQ + 4 * TCP_QCAP;
 constexpr int TCP_SLOT = TCP_BAR + 8;
 constexpr int TCP_CS = (TCP_SLOT + 8 + 127) & ~127;
 int harvest_prune_tc_smem(int nchunks) { return TCP_CS + TCP_M * tcp_nq(nchunks) * 16; }
@@ -233,8 +238,10 @@ __global__ void __launch_bounds__(TCP_M) harvest_prune_tc_kernel(const HPruneArg
   const int nch = a.nchunks, NQ = tcp_nq(nch);
   uint64_t* keys = reinterpret_cast<uint64_t*>(psm);
   uint32_t* dom = reinterpret_cast<uint32_t*>(psm + TCP_DOM);
-  int* mshared = reinterpret_cast<int*>(psm + TCP_M_OFF);
-  float* nrm = reinterpret_cast<float*>(psm + TCP_NRM);
+  uint64_t* kraw = reinterpret_cast<uint64_t*>(psm + TCP_KRAW);
+  float4* col = reinterpret_cast<float4*>(psm + TCP_COL);
+  uint32_t* uq = reinterpret_cast<uint32_t*>(psm + TCP_UQ);
+  uint32_t* qn = reinterpret_cast<uint32_t*>(psm + TCP_SLOT + 4);
   uint64_t* bar = reinterpret_cast<uint64_t*>(psm + TCP_BAR);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(psm + TCP_SLOT);
   uint4* Cs = reinterpret_cast<uint4*>(psm + TCP_CS);
@@ -247,6 +254,7 @@ __global__ void __launch_bounds__(TCP_M) harvest_prune_tc_kernel(const HPruneArg
   if (tid == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
+    *qn = 0u;
   }
   tc_fence_before();
   __syncthreads();
@@ -263,26 +271,22 @@ __global__ void __launch_bounds__(TCP_M) harvest_prune_tc_kernel(const HPruneArg
     const int ne = a.Eg_cnt[qidx];
     if (ne < 0) continue;  // pruned by the re-run pass (uniform over the CTA)
     const int64_t p = a.rows ? (int64_t)a.rows[qidx] : a.q_first + qidx * a.q_step;
-    if (warp == 0) {
-      const uint64_t* src = a.Eg_off ? a.Eg + a.Eg_off[p] : a.Eg + qidx * (int64_t)a.ecap;
-      int NE2 = 32;
-      while (NE2 < ne) NE2 <<= 1;
-      int m = 0;
-      for (int i0 = 0; i0 < NE2; i0 += 32) {
-        const int i = i0 + lane;
-        uint64_t kk = i < ne ? src[i] : PAD;
-        if (kk != PAD && key_id(kk) == (int32_t)p) kk = PAD;
-        keys[i] = kk;
-        m += __popc(__ballot_sync(FULL, kk != PAD));
-      }
-      __syncwarp();
-      if (!a.rows) warp_sort_mem(keys, NE2, lane);  // the final graph's lists come sorted
-      if (lane == 0) *mshared = m;
-    }
+    const uint64_t* src = a.Eg_off ? a.Eg + a.Eg_off[p] : a.Eg + qidx * (int64_t)a.ecap;
+    // keys: each thread ranks its own among the list (the point itself out)
+    uint64_t kt = tid < ne ? src[tid] : PAD;
+    if (kt != PAD && key_id(kt) == (int32_t)p) kt = PAD;
+    kraw[tid] = kt;
     __syncthreads();
-    const int m = *mshared;
-    // stage the candidates (element tails past d zeroed)
-    if (tid < m) tc_stage_row(Cs, tid, a.X + (int64_t)key_id(keys[tid]) * a.ld_bytes, NQ, nch, a.d);
+    if (kt != PAD) {
+      int r = 0;
+      for (int s2 = 0; s2 < ne; ++s2) r += kraw[s2] < kt ? 1 : 0;
+      keys[r] = kt;
+    }
+    const int m = __syncthreads_count(kt != PAD);
+    // stage the sorted candidates (element tails past d zeroed), one row per
+    // thread with its chunks in flight together
+    if (tid < m)
+      tc_stage_row(Cs, tid, a.X + (int64_t)key_id(keys[tid]) * a.ld_bytes, NQ, nch, a.d);
     fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
@@ -294,11 +298,15 @@ __global__ void __launch_bounds__(TCP_M) harvest_prune_tc_kernel(const HPruneArg
       }
       mma_commit(bar);
     }
-    if (tid < m) nrm[tid] = tc_norm2(Cs, tid, NQ, nch);
+    if (tid < m) {
+      const float dpt = key_dist(keys[tid]);
+      col[tid] = make_float4(tc_norm2(Cs, tid, NQ, nch), dpt,
+                             fabsf(dpt) * 4.76837158e-7f + 1e-30f, 0.0f);  // 2^-21 |dp|
+    }
     // wait (bounded) for the Gram matrix; every thread takes the same decision
     bool done = false;
     for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(bar, phase);
-    done = __syncthreads_and(done);
+    done = __syncthreads_and(done);  // also publishes col
     if (!done) {
       ok = false;
       if (tid == 0) atomicOr(a.err, 1u);
@@ -306,9 +314,22 @@ __global__ void __launch_bounds__(TCP_M) harvest_prune_tc_kernel(const HPruneArg
     }
     phase ^= 1u;
     tc_fence_after();
-    // dominance bits of row i = tid, one word per 32 columns
+    // dominance bits of row i = tid, one word per 32 columns.  With
+    // x = alpha2 * approx - delta(p, c_j) and
+    // B = alpha2 * eps + 2^-21 (alpha2 |approx| + |delta(p, c_j)|) + tiny,
+    // x <= -B means the canonical test certainly holds, x > B that it
+    // certainly fails (the margins cover the rounding of the test and of x).
     const int i = tid;
-    const float ni = i < m ? nrm[i] : 0.0f;
+    const float ni = i < m ? col[i].x : 0.0f;
+    float c1, c0;  // eps = c1 * n_j + c0 for this row
+    if constexpr (METRIC == ANGULAR_F32) {
+      c1 = 0.5f * a.tc_e1;
+      c0 = 0.5f * a.tc_e1 * ni + a.tc_e0;
+    } else {
+      c1 = a.tc_e1;
+      c0 = a.tc_e1 * ni + a.tc_e0;
+    }
+    const float a2 = a.alpha2, a2m = a.alpha2 * 4.76837158e-7f;
     for (int cb = 0; cb < TCP_W && 32 * cb < m; ++cb) {
       if (32 * cb + 31 <= 32 * warp) {  // every column of the block is at or left of i
         if (i < m) dom[i * TCP_W + cb] = 0u;
@@ -322,65 +343,94 @@ __global__ void __launch_bounds__(TCP_M) harvest_prune_tc_kernel(const HPruneArg
         for (int t = 0; t < 32; ++t) {
           const int jj = 32 * cb + t;
           if (jj <= i || jj >= m) continue;
-          float dt, eps;
-          tc_approx<METRIC>(__uint_as_float(v[t]), ni, nrm[jj], a.tc_e1, a.tc_e0, &dt, &eps);
-          const float dp = key_dist(keys[jj]);
-          float up = a.alpha2 * (dt + eps);
-          up += fabsf(up) * 4.76837158e-7f + 1e-30f;  // 2^-21
-          float lo = a.alpha2 * (dt - eps);
-          lo -= fabsf(lo) * 4.76837158e-7f + 1e-30f;
-          if (up <= dp)
+          const float4 cj = col[jj];
+          const float g = __uint_as_float(v[t]);
+          float dt;
+          if constexpr (METRIC == ANGULAR_F32)
+            dt = 1.0f - g;
+          else
+            dt = (ni + cj.x) - 2.0f * g;
+          const float eps = fmaf(c1, cj.x, c0);
+          const float x = fmaf(a2, dt, -cj.y);
+          const float B = fmaf(a2, eps, fmaf(a2m, fabsf(dt), cj.z));
+          if (x <= -B)
             word |= 1u << t;
-          else if (!(lo > dp))
+          else if (!(x > B))
             unsure |= 1u << t;
         }
-        // the tests the Gram value cannot decide, in canonical float32
+        // the tests the Gram value cannot decide go to a CTA-wide queue (a
+        // full queue leaves them to this thread)
         while (unsure) {
           const int t = __ffs(unsure) - 1;
           unsure &= unsure - 1u;
           const int jj = 32 * cb + t;
-          const float dd = canon_dist_thread<METRIC, G, K>(Cs, i, Cs, jj, NQ, nch, a.d);
-          if (__fmul_rn(a.alpha2, dd) <= key_dist(keys[jj])) word |= 1u << t;
+          const uint32_t slot = atomicAdd(qn, 1u);
+          if (slot < TCP_QCAP) {
+            uq[slot] = (uint32_t)(i << 8 | jj);
+          } else {
+            const float dd = canon_dist_thread<METRIC, G, K>(Cs, i, Cs, jj, NQ, nch, a.d);
+            if (__fmul_rn(a.alpha2, dd) <= key_dist(keys[jj])) word |= 1u << t;
+          }
         }
         dom[i * TCP_W + cb] = word;
       }
     }
+    __syncthreads();
+    // the queued tests in canonical float32, spread over the CTA
+    {
+      const int nu = min((int)*qn, TCP_QCAP);
+      for (int e = tid; e < nu; e += TCP_M) {
+        const int ii = (int)(uq[e] >> 8), jj = (int)(uq[e] & 255u);
+        const float dd = canon_dist_thread<METRIC, G, K>(Cs, ii, Cs, jj, NQ, nch, a.d);
+        if (__fmul_rn(a.alpha2, dd) <= key_dist(keys[jj]))
+          atomicOr(&dom[ii * TCP_W + (jj >> 5)], 1u << (jj & 31));
+      }
+    }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
-      // the prune as a walk over bit words; lane w holds alive word w
-      uint32_t al = lane < TCP_W ? (lane * 32 + 32 <= m
-                                        ? FULL
-                                        : (lane * 32 < m ? ((1u << (m - lane * 32)) - 1u) : 0u))
-                                 : 0u;
+    if (tid == 0) *qn = 0u;  // read by every thread before the barrier above
+    if (tid == 0) {
+      // the prune as a walk over the four bit words, one thread: keep the
+      // first alive candidate, remove the alive ones it dominates
+      uint32_t al0 = m >= 32 ? FULL : (m > 0 ? (1u << m) - 1u : 0u);
+      uint32_t al1 = m >= 64 ? FULL : (m > 32 ? (1u << (m - 32)) - 1u : 0u);
+      uint32_t al2 = m >= 96 ? FULL : (m > 64 ? (1u << (m - 64)) - 1u : 0u);
+      uint32_t al3 = m >= 128 ? FULL : (m > 96 ? (1u << (m - 96)) - 1u : 0u);
       int32_t* row = a.K_out ? nullptr : a.A_out + p * a.R;
       uint64_t* krow = a.K_out ? a.K_out + qidx * a.R : nullptr;
       int kept = 0;
       unsigned long long q_pe = 0;
       while (kept < a.R) {
-        const unsigned nz = __ballot_sync(FULL, al != 0u);
+        const uint32_t nz = (al0 ? 1u : 0u) | (al1 ? 2u : 0u) | (al2 ? 4u : 0u) | (al3 ? 8u : 0u);
         if (nz == 0u) break;
-        const int w0 = __ffs(nz) - 1;
-        const uint32_t bw = __shfl_sync(FULL, al, w0);
-        const int cur = w0 * 32 + __ffs(bw) - 1;
-        if (lane == 0) {
-          if (krow)
-            krow[kept] = keys[cur];
-          else
-            row[kept] = key_id(keys[cur]);
-        }
+        const int w = __ffs(nz) - 1;
+        const uint32_t aw = w == 0 ? al0 : (w == 1 ? al1 : (w == 2 ? al2 : al3));
+        const int cur = 32 * w + __ffs(aw) - 1;
+        const uint32_t cl = aw & (aw - 1u);  // the word without c*
+        al0 = w == 0 ? cl : al0;
+        al1 = w == 1 ? cl : al1;
+        al2 = w == 2 ? cl : al2;
+        al3 = w == 3 ? cl : al3;
+        if (krow)
+          krow[kept] = keys[cur];
+        else
+          row[kept] = key_id(keys[cur]);
         ++kept;
-        if (lane == w0) al &= ~(1u << (cur % 32));
         if (kept == a.R) break;
-        // the removal pass examines every alive candidate after c*
-        q_pe += (unsigned long long)__reduce_add_sync(FULL, __popc(al));
-        if (lane < TCP_W) al &= ~dom[cur * TCP_W + lane];
+        // the removal pass examines every alive candidate after c* (all alive
+        // ones are after it: c* was the first)
+        q_pe += (unsigned long long)(__popc(al0) + __popc(al1) + __popc(al2) + __popc(al3));
+        const uint4 dm = *reinterpret_cast<const uint4*>(dom + cur * TCP_W);
+        al0 &= ~dm.x;
+        al1 &= ~dm.y;
+        al2 &= ~dm.z;
+        al3 &= ~dm.w;
       }
       if (krow) {
-        if (lane == 0) a.cnt_out[qidx] = kept;
+        a.cnt_out[qidx] = kept;
       } else {
-        for (int r = kept + lane; r < a.R; r += 32) row[r] = -1;
-        if (lane == 0) a.cnt_out[p] = kept;
+        for (int r = kept; r < a.R; ++r) row[r] = -1;
+        a.cnt_out[p] = kept;
       }
       ev += q_pe;
     }
