@@ -141,6 +141,46 @@ __device__ __forceinline__ float group_reduce(float p) {
 // s < P use shuffles inside the group.  Result: bit-identical to the
 // canonical order at a fraction of the shuffles.
 // ---------------------------------------------------------------------------
+// One 16-byte chunk of two float32 rows into a virtual lane's accumulator,
+// elements in order by fused multiply-adds (L2: of the rounded difference
+// squared).  The partial form takes only the first nv < 4 elements.
+template <int METRIC>
+__device__ __forceinline__ float chunk_acc(const uint4 a, const uint4 b, float acc) {
+  const float x[4] = {__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z),
+                      __uint_as_float(a.w)};
+  const float y[4] = {__uint_as_float(b.x), __uint_as_float(b.y), __uint_as_float(b.z),
+                      __uint_as_float(b.w)};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if constexpr (METRIC == ANGULAR_F32) {
+      acc = __fmaf_rn(x[e], y[e], acc);
+    } else {
+      const float t = __fsub_rn(x[e], y[e]);
+      acc = __fmaf_rn(t, t, acc);
+    }
+  }
+  return acc;
+}
+template <int METRIC>
+__device__ __forceinline__ float chunk_acc_partial(const uint4 a, const uint4 b, float acc,
+                                                  int nv) {
+  const float x[4] = {__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z),
+                      __uint_as_float(a.w)};
+  const float y[4] = {__uint_as_float(b.x), __uint_as_float(b.y), __uint_as_float(b.z),
+                      __uint_as_float(b.w)};
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    if (e >= nv) break;
+    if constexpr (METRIC == ANGULAR_F32) {
+      acc = __fmaf_rn(x[e], y[e], acc);
+    } else {
+      const float t = __fsub_rn(x[e], y[e]);
+      acc = __fmaf_rn(t, t, acc);
+    }
+  }
+  return acc;
+}
+
 template <int G, int K>
 struct Lanes {
   static constexpr int P = G <= 8 ? 1 : (G == 16 ? 2 : 4 * K);  // lanes per vector
@@ -222,6 +262,7 @@ __device__ __forceinline__ float regs_dist(const uint4 (&xq)[Lanes<G, K>::VL][K]
     for (int off = L::P / 2; off >= 1; off >>= 1) t += __shfl_xor_sync(mask, t, off);
     return __uint2float_rn(t);
   } else {
+    const int nfull = d >> 2;
     float v[L::VL];
 #pragma unroll
     for (int i = 0; i < L::VL; ++i) {
@@ -229,24 +270,10 @@ __device__ __forceinline__ float regs_dist(const uint4 (&xq)[Lanes<G, K>::VL][K]
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int c = 32 * k + j + L::P * i;
-        if (c < nchunks) {
-          const int nv = d - 4 * c;
-          const float x[4] = {__uint_as_float(xq[i][k].x), __uint_as_float(xq[i][k].y),
-                              __uint_as_float(xq[i][k].z), __uint_as_float(xq[i][k].w)};
-          const float yy[4] = {__uint_as_float(y[i][k].x), __uint_as_float(y[i][k].y),
-                               __uint_as_float(y[i][k].z), __uint_as_float(y[i][k].w)};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            if (nv > e) {
-              if constexpr (METRIC == ANGULAR_F32) {
-                acc = __fmaf_rn(x[e], yy[e], acc);
-              } else {
-                const float t = __fsub_rn(x[e], yy[e]);
-                acc = __fmaf_rn(t, t, acc);
-              }
-            }
-          }
-        }
+        if (c < nfull)
+          acc = chunk_acc<METRIC>(xq[i][k], y[i][k], acc);
+        else if (c < nchunks)
+          acc = chunk_acc_partial<METRIC>(xq[i][k], y[i][k], acc, d - 4 * c);
       }
       v[i] = acc;
     }
@@ -301,6 +328,10 @@ __device__ __forceinline__ float slots_dist(const uint4* qs, const uint4 (&y)[La
     for (int off = L::P / 2; off >= 1; off >>= 1) t += __shfl_xor_sync(mask, t, off);
     return __uint2float_rn(t);
   } else {
+    // full chunks (4 elements inside the row) need no element test; a row
+    // whose d is not a multiple of 4 has one partial chunk, the last chunk of
+    // its virtual lane, handled apart
+    const int nfull = d >> 2;
     float v[L::VL];
 #pragma unroll
     for (int i = 0; i < L::VL; ++i) {
@@ -308,24 +339,11 @@ __device__ __forceinline__ float slots_dist(const uint4* qs, const uint4 (&y)[La
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int c = 32 * k + j + L::P * i;
-        if (c < nchunks) {
+        if (c < nfull) {
           const uint4 xq = qs[c];
-          const int nv = d - 4 * c;
-          const float x[4] = {__uint_as_float(xq.x), __uint_as_float(xq.y),
-                              __uint_as_float(xq.z), __uint_as_float(xq.w)};
-          const float yy[4] = {__uint_as_float(y[i][k].x), __uint_as_float(y[i][k].y),
-                               __uint_as_float(y[i][k].z), __uint_as_float(y[i][k].w)};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            if (nv > e) {
-              if constexpr (METRIC == ANGULAR_F32) {
-                acc = __fmaf_rn(x[e], yy[e], acc);
-              } else {
-                const float t = __fsub_rn(x[e], yy[e]);
-                acc = __fmaf_rn(t, t, acc);
-              }
-            }
-          }
+          acc = chunk_acc<METRIC>(xq, y[i][k], acc);
+        } else if (c < nchunks) {
+          acc = chunk_acc_partial<METRIC>(qs[c], y[i][k], acc, d - 4 * c);
         }
       }
       v[i] = acc;
