@@ -97,6 +97,10 @@ struct Beam {
     using L = Lanes<G, K>;
     const int g = lane / L::P, j = lane % L::P;
     uint64_t mykey = PAD;
+    // float32 metrics keep this lane's query chunks in registers for the
+    // whole batch (uint8 rows read them from shared memory)
+    uint4 qr[L::VL][K];
+    if constexpr (METRIC != L2_U8) load_slots_smem<G, K>(qs, a.nchunks, j, qr);
     for (int base = 0; base < cnt; base += L::CPW * L::UW) {
       uint4 y[L::UW][L::VL][K];
 #pragma unroll
@@ -107,7 +111,11 @@ struct Beam {
       }
 #pragma unroll
       for (int u = 0; u < L::UW; ++u) {
-        const float dd = slots_dist<METRIC, G, K>(qs, y[u], a.nchunks, a.d, j);
+        float dd;
+        if constexpr (METRIC != L2_U8)
+          dd = regs_dist<METRIC, G, K>(qr, y[u], a.nchunks, a.d, j, FULL);
+        else
+          dd = slots_dist<METRIC, G, K>(qs, y[u], a.nchunks, a.d, j);
         const int rel = lane - base - u * L::CPW;
         const float got = __shfl_sync(FULL, dd, (rel & (L::CPW - 1)) * L::P);
         if (rel >= 0 && rel < L::CPW && lane < cnt) mykey = make_key(got, queue[lane]);
@@ -428,7 +436,7 @@ struct Beam {
 };
 
 template <int METRIC, int G, int K, int S>
-__global__ void __launch_bounds__(128) beam_kernel(const BeamArgs a) {
+__global__ void __launch_bounds__(128, METRIC == L2_U8 ? 1 : 4) beam_kernel(const BeamArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   Beam<METRIC, G, K, S>::run(a, smem);
 }
