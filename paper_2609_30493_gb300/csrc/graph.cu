@@ -447,15 +447,47 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
       if (lane == 0) a.long_rows[atomicAdd(a.nlong, 1u)] = (int32_t)r;
       continue;
     }
+    // the distinct candidate ids first, then their keys
+    int m;
+    if (a.mode == 0) {
+      // C(u) = A[u] u rev(u): neither list repeats an id or holds u, so only
+      // the reverse ids that also sit in A[u] are dropped
+      for (int i = lane; i < len0; i += 32) keys[i] = (uint64_t)(uint32_t)seg0[i] << 1;
+      __syncwarp();
+      m = len0;
+      for (int base = 0; base < len1; base += 32) {
+        const int i = base + lane;
+        const int32_t v = i < len1 ? seg1[i] : -1;
+        bool dup = v < 0;
+        for (int x = 0; x < len0; ++x) dup |= key_id(keys[x]) == v;
+        const unsigned keep = __ballot_sync(FULL, !dup);
+        if (!dup) keys[m + __popc(keep & ((1u << lane) - 1u))] = (uint64_t)(uint32_t)v << 1;
+        m += __popc(keep);
+      }
+      __syncwarp();
+    } else {
+      // a list may repeat ids and hold its owner
+      for (int i = lane; i < mraw; i += 32) {
+        const int32_t v = seg0[i];
+        keys[i] = v == u ? PAD : ((uint64_t)(uint32_t)v << 1);
+      }
+      __syncwarp();
+      m = sort_unique(keys, mraw, lane);
+      if (m > 0 && __shfl_sync(FULL, keys[m - 1] == PAD ? 1 : 0, 0)) --m;  // dropped owner
+    }
     stage_row(us, a.V.X + (int64_t)u * a.V.ld_bytes, a.V.nchunks, lane);
-    eval_keys<METRIC, G, K>(a.V, us, seg0, len0, seg1, len1, keys, 0, lane);
-    // the owner itself is not a candidate (list prune may contain it)
-    for (int i = lane; i < mraw; i += 32)
-      if (key_id(keys[i]) == u) keys[i] = PAD;
-    __syncwarp();
-    int m = sort_unique(keys, mraw, lane);
-    if (m > 0 && __shfl_sync(FULL, keys[m - 1] == PAD ? 1 : 0, 0)) --m;  // dropped owner
+    if (m > 0) eval_keys_inplace<METRIC, G, K>(a.V, us, keys, m, lane);
     ev += (unsigned long long)m;
+    // rows the CTA prune takes stay unsorted (that kernel orders them)
+    const bool defer =
+        a.mode == 0 && a.def_keys && !a.gbuf && m > a.R && m <= a.def_cap;
+    if (!defer) {
+      int N2 = 32;
+      while (N2 < m) N2 <<= 1;
+      for (int i = m + lane; i < N2; i += 32) keys[i] = PAD;
+      __syncwarp();
+      warp_sort_mem(keys, N2, lane);
+    }
     if (a.mode == 0) {
       // spine members not already candidates cost one evaluation each
       const int32_t p0 = a.parent0[u];
@@ -464,7 +496,7 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
         const int32_t v = (p0 >= 0) ? (j == 0 ? p0 : ch[j - 1]) : ch[j];
         if (!keys_contain(keys, m, v, lane)) ++ev;
       }
-      if (a.def_keys && !a.gbuf && m > a.R && m <= a.def_cap) {
+      if (defer) {
         // the prune of this row runs in the CTA prune kernel
         uint32_t slot = 0;
         if (lane == 0) slot = atomicAdd(a.def_count, 1u);

@@ -50,6 +50,33 @@ __device__ void eval_keys(const RowVec& V, const uint4* us, const int32_t* seg0,
   __syncwarp();
 }
 
+// keys[0..m) hold distinct ids (id << 1); each becomes the key
+// (delta(us, id), id), two candidates per lane group in flight.
+template <int METRIC, int G, int K>
+__device__ void eval_keys_inplace(const RowVec& V, const uint4* us, uint64_t* keys, int m,
+                                  int lane) {
+  using L = Lanes<G, K>;
+  constexpr int NU = 2;
+  const int g = lane / L::P, j = lane % L::P;
+  for (int base = 0; base < m; base += L::CPW * NU) {
+    uint4 y[NU][L::VL][K];
+    int32_t id[NU];
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+      const int i = min(base + u * L::CPW + g, m - 1);
+      id[u] = key_id(keys[i]);
+      load_slots<G, K>(V.X + (int64_t)id[u] * V.ld_bytes, V.nchunks, j, y[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+      const float dd = slots_dist<METRIC, G, K>(us, y[u], V.nchunks, V.d, j);
+      const int i = base + u * L::CPW + g;
+      if (i < m && j == 0) keys[i] = make_key(dd, id[u]);
+    }
+  }
+  __syncwarp();
+}
+
 // Sorts keys[0..len) (padding to a power of two >= 32 with PAD, which must
 // fit the buffer) and removes repeated keys; returns the distinct count.
 __device__ inline int sort_unique(uint64_t* keys, int len, int lane) {
