@@ -158,6 +158,50 @@ def recall_at_10(X, Q, ids):
     return hits / (Q.shape[0] * 10)
 
 
+EF_LADDER = (10, 16, 24, 32, 48, 64, 96, 128)
+
+
+def quality_report(fg, ix, ps, Q_d, spec, r_target=0.95):
+    """Measurement only (outside the timed region): recall@10 and evaluations
+    per query along the ef_s ladder, d@r (the evaluations per query of the
+    first ef_s reaching recall r), and local completeness (the fraction of each
+    point's 10 nearest neighbours that sit in its final adjacency row).  The
+    ground truth is a float32 brute force with PyTorch on the device."""
+    import torch
+    X = torch.from_numpy(ps.X[:, :spec["d"]]).cuda()
+    Q = Q_d[:, :spec["d"]]
+    gtq = []
+    for s in range(0, Q.shape[0], 2048):
+        gtq.append(torch.topk(Q[s:s + 2048] @ X.T, 10, dim=1).indices)
+    gtq = torch.cat(gtq)
+    ladder = []
+    d_at_r = None
+    for ef in EF_LADDER:
+        ids, _, ev = fg.fgraft_search(ix, Q_d, 10, ef)
+        hit = (ids.long().unsqueeze(2) == gtq.unsqueeze(1)).any(dim=2).sum().item()
+        rec = hit / (Q.shape[0] * 10)
+        epq = float(ev.double().mean().item())
+        ladder.append({"ef_s": ef, "recall_at_10": round(rec, 4), "evals_per_query": round(epq, 1)})
+        if d_at_r is None and rec >= r_target:
+            d_at_r = round(epq, 1)
+    # local completeness over every point
+    n = X.shape[0]
+    off, fids = fg.fgraft_prune(ix)
+    rows = torch.repeat_interleave(torch.arange(n, device=X.device), off[1:] - off[:-1])
+    edge_keys = torch.sort(rows * n + fids.long()).values
+    hits = 0
+    for s in range(0, n, 4096):
+        dots = X[s:s + 4096] @ X.T
+        dots[torch.arange(dots.shape[0], device=X.device),
+             torch.arange(s, s + dots.shape[0], device=X.device)] = -float("inf")
+        gt = torch.topk(dots, 10, dim=1).indices
+        keys = (torch.arange(s, s + gt.shape[0], device=X.device).unsqueeze(1) * n + gt).reshape(-1)
+        pos = torch.searchsorted(edge_keys, keys).clamp(max=edge_keys.numel() - 1)
+        hits += int((edge_keys[pos] == keys).sum().item())
+    return {"recall_ladder": ladder, f"d_at_r{r_target}": d_at_r,
+            "local_completeness_at_10": round(hits / (n * 10), 4)}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -267,7 +311,28 @@ def run_ours(args):
     breakdown["harvest_graph_plus_final"] = round(g0.elapsed_time(g1), 3)
     breakdown["harvest_plain_plus_final"] = round(breakdown["harvest_blocks_no_graph"]
                                                   + breakdown["final_prune"], 3)
+    # the graph-replayed and the plain build give the same final graph
+    fa, fb = fg.fgraft_prune(ix), fg.fgraft_prune(ixg)
+    graph_hash = hashlib.sha256(fa[0].cpu().numpy().tobytes() + fa[1].cpu().numpy().tobytes()
+                                ).hexdigest()[:16]
+    graph_same = bool(torch.equal(fa[0], fb[0]) and torch.equal(fa[1], fb[1]))
     del ixg
+
+    # ---- dense blocks in the other two precisions (untimed, same blocks) ----
+    dense_other = {}
+    for prec, name in ((0, "fp32_cuda_cores"), (2, "fp8_e4m3")):
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        pi, pd, pst = fg.fgraft_dense_block_dist(X_d, d, fg.ANGULAR_F32, B_d, spec["dense_k"],
+                                                 precision=prec, stats=True)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(pi, di) and torch.equal(pd, dd))
+        dense_other[name] = {"ms": round(q0.elapsed_time(q1), 3), "same_top_k_as_bf16": same}
+        if prec == 2:
+            dense_other[name]["rerank_fraction"] = round(pst[0], 5)
+            dense_other[name]["gram_ms"] = round(pst[1], 4)
+    quality = quality_report(fg, ix, ps, Q_d, spec)
 
     # ---- end to end through the public API, host buffers ----
     Xh = torch.from_numpy(ps.X).pin_memory()
@@ -346,6 +411,10 @@ def run_ours(args):
         "dense_gram_pairs_per_s": round(dense_pairs / (dst[1] / 1e3), 1) if dst[1] else None,
         "dense_gram_tflops": round(2 * d * dense_pairs / (dst[1] / 1e3) / 1e12, 2) if dst[1] else None,
         "dense_rerank_fraction": round(dst[0], 5),
+        "dense_other_precisions": dense_other,
+        "graph_replay_same_graph": graph_same,
+        "final_graph_sha256_16": graph_hash,
+        "quality": quality,
         "breakdown_ms": breakdown,
         "e2e": {"value": round(e2e_value, 1), "unit": "pts/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

@@ -200,11 +200,14 @@ fgraft_status fgraft_search(fgraft_index* ix, const void* Q, int64_t nq, int64_t
  *   precision 1  BF16 tensor-core filter (tcgen05, FP32 accumulation) on the
  *                block centred on its mean, then every pair within twice a
  *                rounding-error bound of the k-th approximate distance is
- *                recomputed in the canonical order.
+ *                recomputed in the canonical order;
+ *   precision 2  the same with an FP8 (E4M3) filter, each centred row scaled
+ *                so that its largest magnitude is 448 (kind::f8f6f4); the
+ *                bound is 16 times wider, so more pairs are recomputed.
  * stats (host, optional, 4 doubles; the call then synchronises `stream`):
  * fraction of pairs recomputed, Gram-kernel ms, select ms, prep ms
- * (precision 1; zeros for precision 0).  Float32 metrics only; bs <= 1024,
- * k <= 64, nb <= 65535.  Precision 1 allocates its scratch stream-ordered and
+ * (precisions 1 and 2; zeros for precision 0).  Float32 metrics only; bs <= 1024,
+ * k <= 64, nb <= 65535.  Precisions 1 and 2 allocate their scratch stream-ordered and
  * synchronises `stream` to check its bounded waits (FGRAFT_ETIMEOUT). */
 fgraft_status fgraft_dense_block_dist(const void* X, int64_t n, int32_t d, int64_t ld,
                                       int32_t metric, const int32_t* block_ids, int64_t nb,

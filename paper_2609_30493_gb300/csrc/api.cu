@@ -795,16 +795,18 @@ fgraft_status fgraft_dense_block_dist(const void* X, int64_t n, int32_t d, int64
   int rc = check_vectors(X, n, d, ld, metric, &L);
   if (rc) return (fgraft_status)rc;
   if (metric == L2_U8) return (fgraft_status)fail(FGRAFT_EINVAL, "dense blocks take float32 metrics");
-  if (precision != 0 && precision != 1)
-    return (fgraft_status)fail(FGRAFT_EINVAL, "precision must be 0 (float32) or 1 (BF16 filter)");
+  if (precision < 0 || precision > 2)
+    return (fgraft_status)fail(FGRAFT_EINVAL,
+                               "precision must be 0 (float32), 1 (BF16 filter) or 2 (FP8 filter)");
   if (nb < 0 || nb > 65535 || bs < 1 || bs > 1024 || k < 1 || k > 64)
     return (fgraft_status)fail(FGRAFT_EINVAL, "need nb <= 65535, bs in [1,1024], k in [1,64]");
   if (stats)
     for (int i = 0; i < 4; ++i) stats[i] = 0.0;
   if (nb == 0) return FGRAFT_OK;
   if (!block_ids || !out_ids || !out_dist) return (fgraft_status)fail(FGRAFT_EINVAL, "NULL pointer");
-  if (precision == 1)
-    return (fgraft_status)dense_block_tc(L, block_ids, nb, bs, k, out_ids, out_dist, stats, s);
+  if (precision >= 1)
+    return (fgraft_status)dense_block_tc(L, block_ids, nb, bs, k, precision == 2, out_ids,
+                                         out_dist, stats, s);
   rc = dense_block(L, block_ids, nb, bs, k, out_ids, out_dist, s);
   if (!rc && stats) FGS(cudaStreamSynchronize(s));
   return (fgraft_status)rc;

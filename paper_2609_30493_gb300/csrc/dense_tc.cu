@@ -13,6 +13,7 @@
 // approx <= canonical + eps <= k-th canonical + eps <= k-th approx + 2 eps, so
 // the result equals the canonical float32 top-k.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 
@@ -26,14 +27,15 @@ namespace fg {
 constexpr int TC_ROWS = 1024;  // rows of a block after padding
 constexpr int TC_M = 128;      // rows per CTA (one per TMEM lane)
 constexpr int TC_N = 256;      // columns per CTA (TMEM columns)
-constexpr int TC_K = 64;       // K elements per staged slice (8 core matrices)
+constexpr int TC_KB = 128;     // K bytes per staged slice (8 core matrices of 16 bytes)
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_TMEM_COLS = 256;
 
-// Byte offset of element (row r, k) of a staged K-slice: core matrix
-// (r/8, k/8) at (r/8)*1024 + (k/8)*128, row r%8 at +16*(r%8).
-__host__ __device__ constexpr uint32_t tile_off(int r, int k) {
-  return (uint32_t)((r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+// Byte offset of the 16-byte unit (row r, byte kb) of a staged K-slice: core
+// matrix (r/8, kb/16) at (r/8)*1024 + (kb/16)*128, row r%8 at +16*(r%8).
+// A slice is 64 BF16 or 128 E4M3 elements per row.
+__host__ __device__ constexpr uint32_t tile_off(int r, int kb) {
+  return (uint32_t)((r >> 3) * 1024 + (kb >> 4) * 128 + (r & 7) * 16);
 }
 
 // --------------------------------------------------------------------------
@@ -43,12 +45,16 @@ struct TcArgs {
   const char* X;
   int64_t ld_bytes;
   int32_t d;
-  int32_t dpad;  // d rounded up to TC_K
+  int32_t dpad;  // d rounded up to a whole slice (64 BF16 or 128 E4M3 elements)
+  int32_t rowb;  // bytes of a rounded row (2 dpad or dpad)
+  int32_t fp8;   // 0: BF16, 1: E4M3 with a scale per row
+  float u_in;    // unit roundoff of the input rounding (with the E4M3 subnormal term)
   int32_t metric;
   const int32_t* block_ids;
   int64_t nb;
   int32_t bs;
-  __nv_bfloat16* Xb;  // [nb][1024][dpad]
+  unsigned char* Xb;  // [nb][1024][rowb]
+  float* sc;          // [nb][1024] E4M3 row scale (the row is sc * its codes)
   float* nrm;         // [nb][1024] squared norm of the centred float32 row
   float* cc;          // [nb][1024] angular: (1 - |x|^2) / 2
   float* Mx;          // [nb] largest centred norm
@@ -83,10 +89,22 @@ __global__ void __launch_bounds__(256) dense_prep_kernel(const TcArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int r = warp; r < TC_ROWS; r += 8) {
     const int32_t id = r < a.bs ? ids[r] : -1;
-    __nv_bfloat16* dst = a.Xb + (blk * TC_ROWS + r) * (int64_t)a.dpad;
+    unsigned char* dst = a.Xb + (blk * TC_ROWS + r) * (int64_t)a.rowb;
     float s2 = 0.0f, x2 = 0.0f;
     const float* xr = id >= 0 ? reinterpret_cast<const float*>(a.X + (int64_t)id * a.ld_bytes)
                               : nullptr;
+    // E4M3: the row's largest centred magnitude maps to 448, the largest
+    // finite E4M3 value
+    float scale = 1.0f;
+    if (a.fp8) {
+      float mx = 0.0f;
+      for (int j = lane; j < a.d; j += 32)
+        if (id >= 0) mx = fmaxf(mx, fabsf(xr[j] - mu[j]));
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, off));
+      scale = mx > 0.0f ? mx / 448.0f : 1.0f;
+    }
+    const float rs = 1.0f / scale;
     for (int j = lane; j < a.dpad; j += 32) {
       float v = 0.0f;
       if (id >= 0 && j < a.d) {
@@ -95,8 +113,12 @@ __global__ void __launch_bounds__(256) dense_prep_kernel(const TcArgs a) {
         x2 = __fmaf_rn(x, x, x2);
       }
       s2 = __fmaf_rn(v, v, s2);
-      dst[j] = __float2bfloat16_rn(v);
+      if (a.fp8)
+        dst[j] = (unsigned char)__nv_cvt_float_to_fp8(v * rs, __NV_SATFINITE, __NV_E4M3);
+      else
+        reinterpret_cast<__nv_bfloat16*>(dst)[j] = __float2bfloat16_rn(v);
     }
+    if (lane == 0) a.sc[blk * TC_ROWS + r] = scale;
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) {
       s2 += __shfl_xor_sync(FULL, s2, off);
@@ -115,9 +137,9 @@ __global__ void __launch_bounds__(256) dense_prep_kernel(const TcArgs a) {
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(TC_THREADS) dense_gram_kernel(const TcArgs a) {
   extern __shared__ __align__(1024) unsigned char tsm[];
-  unsigned char* As = tsm;                      // 128 x 64 BF16 = 16 KB
-  unsigned char* Bs = tsm + TC_M * TC_K * 2;    // 256 x 64 BF16 = 32 KB
-  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + TC_N * TC_K * 2);
+  unsigned char* As = tsm;                      // 128 rows x 128 bytes = 16 KB
+  unsigned char* Bs = tsm + TC_M * TC_KB;       // 256 rows x 128 bytes = 32 KB
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + TC_N * TC_KB);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
   const int rt = blockIdx.x, ct = blockIdx.y;
   const int64_t blk = blockIdx.z;
@@ -136,23 +158,23 @@ __global__ void __launch_bounds__(TC_THREADS) dense_gram_kernel(const TcArgs a) 
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  const __nv_bfloat16* Ag = a.Xb + (blk * TC_ROWS + rt * TC_M) * (int64_t)a.dpad;
-  const __nv_bfloat16* Bg = a.Xb + (blk * TC_ROWS + ct * TC_N) * (int64_t)a.dpad;
-  constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
+  const unsigned char* Ag = a.Xb + (blk * TC_ROWS + rt * TC_M) * (int64_t)a.rowb;
+  const unsigned char* Bg = a.Xb + (blk * TC_ROWS + ct * TC_N) * (int64_t)a.rowb;
+  const uint32_t idesc = a.fp8 ? idesc_e4m3(TC_M, TC_N) : idesc_bf16(TC_M, TC_N);
   bool ok = true;
-  const int nslices = a.dpad / TC_K;
+  const int nslices = a.rowb / TC_KB;
   for (int sl = 0; sl < nslices; ++sl) {
-    const int k0 = sl * TC_K;
-    // stage the slices: 16-byte units (row, 8 K elements), 8 per row
+    const int k0 = sl * TC_KB;
+    // stage the slices: 16-byte units (row, 16 K bytes), 8 per row
     for (int u = tid; u < TC_M * 8; u += TC_THREADS) {
       const int r = u >> 3, kc = u & 7;
-      *reinterpret_cast<uint4*>(As + tile_off(r, kc * 8)) =
-          *reinterpret_cast<const uint4*>(Ag + (int64_t)r * a.dpad + k0 + kc * 8);
+      *reinterpret_cast<uint4*>(As + tile_off(r, kc * 16)) =
+          *reinterpret_cast<const uint4*>(Ag + (int64_t)r * a.rowb + k0 + kc * 16);
     }
     for (int u = tid; u < TC_N * 8; u += TC_THREADS) {
       const int r = u >> 3, kc = u & 7;
-      *reinterpret_cast<uint4*>(Bs + tile_off(r, kc * 8)) =
-          *reinterpret_cast<const uint4*>(Bg + (int64_t)r * a.dpad + k0 + kc * 8);
+      *reinterpret_cast<uint4*>(Bs + tile_off(r, kc * 16)) =
+          *reinterpret_cast<const uint4*>(Bg + (int64_t)r * a.rowb + k0 + kc * 16);
     }
     fence_proxy_async();
     __syncthreads();
@@ -160,10 +182,15 @@ __global__ void __launch_bounds__(TC_THREADS) dense_gram_kernel(const TcArgs a) 
       tc_fence_after();
       const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
 #pragma unroll
-      for (int kk = 0; kk < TC_K / 16; ++kk) {
-        // a K=16 step spans two core matrices along K (2 x 128 bytes)
-        mma_bf16(tmem, smem_desc(a0 + kk * 256, 128, 1024), smem_desc(b0 + kk * 256, 128, 1024),
-                 idesc, (sl > 0 || kk > 0) ? 1u : 0u);
+      for (int kk = 0; kk < 4; ++kk) {
+        // one MMA takes 32 K bytes (16 BF16 or 32 E4M3 elements): two core
+        // matrices along K (2 x 128 bytes of shared memory)
+        const uint64_t ad = smem_desc(a0 + kk * 256, 128, 1024);
+        const uint64_t bd = smem_desc(b0 + kk * 256, 128, 1024);
+        if (a.fp8)
+          mma_e4m3(tmem, ad, bd, idesc, (sl > 0 || kk > 0) ? 1u : 0u);
+        else
+          mma_bf16(tmem, ad, bd, idesc, (sl > 0 || kk > 0) ? 1u : 0u);
       }
       mma_commit(bar);
     }
@@ -186,6 +213,7 @@ __global__ void __launch_bounds__(TC_THREADS) dense_gram_kernel(const TcArgs a) 
     const int64_t rowbase = blk * TC_ROWS;
     const float ni = a.nrm[rowbase + i];
     const float ci = a.cc[rowbase + i];
+    const float si = a.fp8 ? a.sc[rowbase + i] : 1.0f;
     float* out = a.LP + (rowbase + i) * (int64_t)TC_ROWS + ct * TC_N;
     for (int c0 = 0; c0 < TC_N; c0 += 32) {
       uint32_t v[32];
@@ -193,7 +221,8 @@ __global__ void __launch_bounds__(TC_THREADS) dense_gram_kernel(const TcArgs a) 
 #pragma unroll
       for (int t = 0; t < 32; ++t) {
         const int j = ct * TC_N + c0 + t;
-        const float g = __uint_as_float(v[t]);
+        const float g = a.fp8 ? __uint_as_float(v[t]) * (si * a.sc[rowbase + j])
+                              : __uint_as_float(v[t]);
         const float s = a.nrm[rowbase + j] + ni - 2.0f * g;
         out[c0 + t] = a.metric == ANGULAR_F32 ? 0.5f * s + ci + a.cc[rowbase + j] : s;
       }
@@ -222,7 +251,7 @@ __global__ void __launch_bounds__(SEL_WARPS * 32)
   uint64_t* keys = reinterpret_cast<uint64_t*>(ssm + warp * wbytes);
   uint4* qs = reinterpret_cast<uint4*>(ssm + warp * wbytes + 8 * TC_ROWS);
   const int64_t rows = a.nb * a.bs;
-  const float u_b = 1.0f / 256.0f, gam = 1.0f / 16777216.0f;
+  const float u_b = a.u_in, gam = 1.0f / 16777216.0f;
   const float dk = (float)(a.d + 8);
   unsigned long long nre = 0;
   for (int64_t r = (int64_t)blockIdx.x * SEL_WARPS + warp; r < rows;
@@ -316,7 +345,7 @@ static SelectFn select_kernel_for(int metric, int G, int K) {
 }
 
 int dense_block_tc(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs, int k,
-                   int32_t* out_ids, float* out_dist, double* stats, cudaStream_t s) {
+                   int fp8, int32_t* out_ids, float* out_dist, double* stats, cudaStream_t s) {
   SelectFn sel = select_kernel_for(L.metric, L.G, L.K);
   if (!sel || L.metric == L2_U8) {
     set_error(1, "tensor-core dense blocks take float32 metrics");
@@ -330,20 +359,28 @@ int dense_block_tc(const VecLayout& L, const int32_t* block_ids, int64_t nb, int
   a.X = L.X;
   a.ld_bytes = L.ld_bytes;
   a.d = L.d;
-  a.dpad = (L.d + TC_K - 1) / TC_K * TC_K;
+  a.fp8 = fp8 ? 1 : 0;
+  const int slice = a.fp8 ? TC_KB : TC_KB / 2;  // elements per slice
+  a.dpad = (L.d + slice - 1) / slice * slice;
+  a.rowb = a.fp8 ? a.dpad : 2 * a.dpad;
+  // input rounding: BF16 2^-8; E4M3 2^-4 plus its subnormal spacing, at most
+  // 2^-10 of a code, summed over d elements of a row scaled to 448
+  a.u_in = a.fp8 ? 0.0625f + sqrtf((float)L.d) * (1.0f / 1024.0f) / 448.0f : 1.0f / 256.0f;
   a.metric = L.metric;
   a.block_ids = block_ids;
   a.nb = nb;
   a.bs = bs;
   char* scratch = nullptr;
-  const size_t xb = sizeof(__nv_bfloat16) * nb * TC_ROWS * (size_t)a.dpad;
+  const size_t xb = (size_t)nb * TC_ROWS * (size_t)a.rowb;
   const size_t vec = sizeof(float) * nb * TC_ROWS;
   const size_t lp = sizeof(float) * nb * (size_t)TC_ROWS * TC_ROWS;
-  const size_t total = xb + 2 * vec + 256 * ((nb * 4 + 255) / 256 + 1) + lp + 256;
+  const size_t total = xb + 3 * vec + 256 * ((nb * 4 + 255) / 256 + 1) + lp + 512;
   FG_CUDA(cudaMallocAsync(&scratch, total, s));
   size_t off = 0;
-  a.Xb = reinterpret_cast<__nv_bfloat16*>(scratch + off);
+  a.Xb = reinterpret_cast<unsigned char*>(scratch + off);
   off += (xb + 255) / 256 * 256;
+  a.sc = reinterpret_cast<float*>(scratch + off);
+  off += (vec + 255) / 256 * 256;
   a.nrm = reinterpret_cast<float*>(scratch + off);
   off += (vec + 255) / 256 * 256;
   a.cc = reinterpret_cast<float*>(scratch + off);

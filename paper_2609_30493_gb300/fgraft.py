@@ -271,7 +271,8 @@ def fgraft_prune_lists_noalloc(X: torch.Tensor, d: int, metric: int, owner: torc
 def fgraft_dense_block_dist(X: torch.Tensor, d: int, metric: int, block_ids: torch.Tensor, k: int,
                             precision: int = 0, stats: bool = False):
     """Per-row top-k of every block's pairs.  precision 0: float32 on CUDA cores;
-    1: BF16 tensor-core filter and exact float32 rerank.  With stats=True also
+    1: BF16 tensor-core filter and exact float32 rerank; 2: the same with an
+    FP8 (E4M3, per-row scale) filter.  With stats=True also
     returns (rerank fraction, Gram ms, select ms, prep ms)."""
     nb, bs = block_ids.shape
     ids = torch.empty((nb, bs, k), dtype=torch.int32, device=X.device)
