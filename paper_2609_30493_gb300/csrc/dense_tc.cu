@@ -214,7 +214,10 @@ __global__ void __launch_bounds__(TC_THREADS) dense_gram_kernel(const TcArgs a) 
     const float ni = a.nrm[rowbase + i];
     const float ci = a.cc[rowbase + i];
     const float si = a.fp8 ? a.sc[rowbase + i] : 1.0f;
-    float* out = a.LP + (rowbase + i) * (int64_t)TC_ROWS + ct * TC_N;
+    // each warp passes its 32 x 32 blocks through shared memory (the staging
+    // buffers are free now) so that every store writes one 128-byte row piece
+    float* stg = reinterpret_cast<float*>(tsm) + warp * 32 * 33;
+    float* out0 = a.LP + (rowbase + rt * TC_M + warp * 32) * (int64_t)TC_ROWS + ct * TC_N;
     for (int c0 = 0; c0 < TC_N; c0 += 32) {
       uint32_t v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
@@ -224,8 +227,11 @@ __global__ void __launch_bounds__(TC_THREADS) dense_gram_kernel(const TcArgs a) 
         const float g = a.fp8 ? __uint_as_float(v[t]) * (si * a.sc[rowbase + j])
                               : __uint_as_float(v[t]);
         const float s = a.nrm[rowbase + j] + ni - 2.0f * g;
-        out[c0 + t] = a.metric == ANGULAR_F32 ? 0.5f * s + ci + a.cc[rowbase + j] : s;
+        stg[lane * 33 + t] = a.metric == ANGULAR_F32 ? 0.5f * s + ci + a.cc[rowbase + j] : s;
       }
+      __syncwarp();
+      for (int rr = 0; rr < 32; ++rr) out0[(int64_t)rr * TC_ROWS + c0 + lane] = stg[rr * 33 + lane];
+      __syncwarp();
     }
   }
   tc_fence_before();
