@@ -47,9 +47,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="override n (smaller runs)")
-    ap.add_argument("--mode", default="step", choices=["step", "dims", "paper"],
+    ap.add_argument("--batch", type=int, default=64, help="builds of --mode batched")
+    ap.add_argument("--mode", default="step", choices=["step", "dims", "paper", "batched"],
                     help="step: the benchmark line; dims: adaptive vs dense cost per evaluation "
-                         "across d; paper: the paper-scale angular arms")
+                         "across d; paper: the paper-scale angular arms; batched: many "
+                         "independent builds harvested together")
     return ap.parse_args()
 
 
@@ -638,6 +640,108 @@ def run_paper(args):
         torch.cuda.empty_cache()
 
 
+def batched_inputs(i, n, d, device):
+    """Build i of the batched configuration, generated on the device with a
+    torch generator seeded by i: d = 64 or 960, unit vectors from 64
+    vMF-like clusters (kappa = 20, equal sizes); d = 128, uint8 from a mixture
+    of 128 Gaussian clusters (centres N(0, 25 I), unit noise) mapped by
+    clip(round(60 + 30 z / sqrt(26)), 0, 255).  Rows padded to 16 bytes."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(1000 + i)
+    if d == 128:
+        cent = 5.0 * torch.randn(128, d, generator=g, device=device)
+        lab = torch.randint(0, 128, (n,), generator=g, device=device)
+        z = cent[lab] + torch.randn(n, d, generator=g, device=device)
+        return torch.clamp(torch.round(60.0 + 30.0 * z / 26.0 ** 0.5), 0, 255).to(torch.uint8)
+    mu = torch.nn.functional.normalize(torch.randn(64, d, generator=g, device=device), dim=1)
+    lab = torch.randperm(n, generator=g, device=device) % 64
+    x = mu[lab] + torch.randn(n, d, generator=g, device=device) / 20.0 ** 0.5
+    return torch.nn.functional.normalize(x, dim=1).contiguous()
+
+
+def run_batched(args):
+    """Many independent builds at once (64 by default): n log-uniform in
+    [10^4, 5 * 10^5], d from {64, 128, 960}; T = 8, B = 8, R = 32, ef_h = 64.
+    Timed: every scaffold, then block by block all indices together through
+    fgraft_harvest_block_multi, then every final graph.  Untimed comparison:
+    the same builds one after another."""
+    import torch
+    from paper_2609_30493_gb300 import build as fgbuild
+    from paper_2609_30493_gb300 import fgraft as fg
+    fgbuild.build()
+    fg.load()
+    nbuild = args.batch
+    rng = np.random.default_rng(5)
+    ns = np.floor(np.exp(rng.uniform(np.log(1e4), np.log(5e5), nbuild))).astype(np.int64)
+    ds = rng.choice([64, 128, 960], nbuild)
+    data = [batched_inputs(i, int(ns[i]), int(ds[i]), "cuda") for i in range(nbuild)]
+    torch.cuda.synchronize()
+
+    def params(d):
+        return fg.Params(T=8, R=32, ef_h=64, B=8, alpha=1.2, seed=0,
+                         metric=fg.L2_U8 if d == 128 else fg.ANGULAR_F32)
+
+    def batched():
+        ixs = [fg.fgraft_build_scaffold(data[i], int(ds[i]), params(int(ds[i])))
+               for i in range(nbuild)]
+        for b in range(8):
+            fg.fgraft_harvest_block_multi(ixs, b)
+        for ix in ixs:
+            fg.fgraft_prune(ix)
+        return ixs
+
+    def one_by_one():
+        out = []
+        for i in range(nbuild):
+            ix = fg.fgraft_build_scaffold(data[i], int(ds[i]), params(int(ds[i])))
+            fg.fgraft_harvest_all(ix, use_graph=False)
+            out.append(ix)
+        return out
+
+    for _ in range(max(args.warmup, 1)):
+        del_ = batched()
+        del del_
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(args.steps):
+        t0.record()
+        ixs = batched()
+        t1.record()
+        torch.cuda.synchronize()
+        times.append(t0.elapsed_time(t1))
+        del ixs
+    clk = clocks.stop()
+    t0.record()
+    seq = one_by_one()
+    t1.record()
+    torch.cuda.synchronize()
+    seq_ms = t0.elapsed_time(t1)
+    same = True
+    ixs = batched()
+    for a_, b_ in zip(ixs, seq):
+        oa, ob = fg.fgraft_prune(a_), fg.fgraft_prune(b_)
+        same &= bool(torch.equal(oa[0], ob[0]) and torch.equal(oa[1], ob[1]))
+    ms = float(np.mean(times))
+    total_n = int(ns.sum())
+    print(json.dumps({
+        "metric": "batched FGraft builds pts/s, 1 GB300", "mode": "batched",
+        "value": round(total_n / (ms / 1e3), 1), "unit": "pts/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "dtype": "f32 and u8", "data": "synthetic (device generator)",
+        "config": {"workload": f"batched-{nbuild}-builds", "builds": nbuild, "sum_n": total_n,
+                   "n_min": int(ns.min()), "n_max": int(ns.max()),
+                   "builds_by_d": {str(k): int((ds == k).sum()) for k in (64, 128, 960)},
+                   "T": 8, "B": 8, "R": 32, "ef_h": 64},
+        "one_by_one_ms": round(seq_ms, 3),
+        "batched_vs_one_by_one": round(seq_ms / ms, 3),
+        "same_graphs_as_one_by_one": same,
+        "clocks": clk}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -646,6 +750,8 @@ def main():
         run_dims(args)
     elif args.mode == "paper":
         run_paper(args)
+    elif args.mode == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -127,6 +127,17 @@ fgraft_status fgraft_build_scaffold(const void* X, int64_t n, int32_t d, int64_t
 fgraft_status fgraft_harvest_block(fgraft_index* ix, int32_t b, fgraft_stream stream,
                                    fgraft_counters* counters);
 
+/* Block b of several independent indices at once (many builds of the same
+ * schedule, for example one per data shard or tenant): every index must be
+ * at block b (0..B-1 in order, as for fgraft_harvest_block) and appear once.
+ * The harvests are issued on internal side streams that wait for `stream`,
+ * so the kernels of different indices overlap on the GPU, and `stream`
+ * waits for all of them on return (nothing is synchronised on the host).
+ * Each index's rows equal those of its own fgraft_harvest_block call.  The
+ * paper has no counterpart; it runs one build at a time. */
+fgraft_status fgraft_harvest_block_multi(fgraft_index* const* ixs, int32_t nix, int32_t b,
+                                         fgraft_stream stream);
+
 /* All blocks in order, then the final graph; with use_graph != 0 the block
  * loop is captured once as a CUDA graph and replayed.  Equivalent to B calls
  * of fgraft_harvest_block followed by fgraft_prune with no outputs. */

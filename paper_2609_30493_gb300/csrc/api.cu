@@ -465,6 +465,38 @@ int harvest_block_impl(fgraft_index* ix, int32_t b, cudaStream_t s) {
   return 0;
 }
 
+// Side streams of a device for fgraft_harvest_block_multi, created on first
+// use and kept for the process.
+struct MultiStreams {
+  static constexpr int kStreams = 8;
+  cudaStream_t st[kStreams];
+  cudaEvent_t fork;
+  cudaEvent_t join[kStreams];
+  std::mutex mu;
+};
+
+int multi_streams(MultiStreams** out) {
+  static std::mutex mu;
+  static MultiStreams* per_dev[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return fail(FGRAFT_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!per_dev[dev]) {
+    MultiStreams* m = new MultiStreams();
+    e = cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming);
+    for (int k = 0; k < MultiStreams::kStreams && e == cudaSuccess; ++k) {
+      e = cudaStreamCreateWithFlags(&m->st[k], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->join[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "side streams");
+    per_dev[dev] = m;
+  }
+  *out = per_dev[dev];
+  return 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -667,6 +699,37 @@ fgraft_status fgraft_prune(fgraft_index* ix, fgraft_stream stream, fgraft_counte
   }
   if (counters) return (fgraft_status)read_counters(ix, s, counters);
   return FGRAFT_OK;
+}
+
+fgraft_status fgraft_harvest_block_multi(fgraft_index* const* ixs, int32_t nix, int32_t b,
+                                         fgraft_stream stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (nix < 0 || (nix > 0 && !ixs)) return (fgraft_status)fail(FGRAFT_EINVAL, "bad index list");
+  for (int32_t i = 0; i < nix; ++i) {
+    const fgraft_index* ix = ixs[i];
+    if (!ix) return (fgraft_status)fail(FGRAFT_EINVAL, "index is NULL");
+    if (b < 0 || b >= ix->nb) return (fgraft_status)fail(FGRAFT_EINVAL, "block index out of range");
+    if (b != ix->blocks_done)
+      return (fgraft_status)fail(FGRAFT_EINVAL, "blocks must be harvested in order 0..B-1");
+    for (int32_t j = 0; j < i; ++j)
+      if (ixs[j] == ix) return (fgraft_status)fail(FGRAFT_EINVAL, "an index is listed twice");
+  }
+  if (nix == 0) return FGRAFT_OK;
+  // fan out over the device's side streams (they wait for `stream`), join back
+  MultiStreams* ms = nullptr;
+  int rc = multi_streams(&ms);
+  if (rc) return (fgraft_status)rc;
+  std::lock_guard<std::mutex> lock(ms->mu);
+  FGS(cudaEventRecord(ms->fork, s));
+  const int ns = std::min<int>(nix, MultiStreams::kStreams);
+  for (int k = 0; k < ns; ++k) FGS(cudaStreamWaitEvent(ms->st[k], ms->fork, 0));
+  for (int32_t i = 0; i < nix && !rc; ++i) rc = harvest_block_impl(ixs[i], b, ms->st[i % ns]);
+  for (int k = 0; k < ns; ++k) {
+    cudaError_t e = cudaEventRecord(ms->join[k], ms->st[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ms->join[k], 0);
+    if (e != cudaSuccess && !rc) rc = cuda_fail(e, "multi-index join");
+  }
+  return (fgraft_status)rc;
 }
 
 fgraft_status fgraft_harvest_all(fgraft_index* ix, int32_t use_graph, fgraft_stream stream,

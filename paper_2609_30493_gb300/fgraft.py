@@ -43,6 +43,7 @@ EXPORTS = ["fgraft_build_scaffold", "fgraft_harvest_block", "fgraft_harvest_all"
            "fgraft_index_sizes", "fgraft_index_counters", "fgraft_index_tune",
            "fgraft_index_profile", "fgraft_index_harvest_ms", "fgraft_kernel_launches",
            "fgraft_tune_sat", "fgraft_tune_prune", "fgraft_prune_lists_noalloc",
+           "fgraft_harvest_block_multi",
            "fgraft_index_destroy", "fgraft_last_error"]
 
 
@@ -151,6 +152,14 @@ def fgraft_harvest_all(ix: Index, use_graph: bool = True, counters: bool = False
     _check(load().fgraft_harvest_all(ix.handle, C.c_int32(1 if use_graph else 0),
                                      _stream(ix.X.device), C.byref(ctr) if counters else None))
     return _counters_dict(ctr) if counters else None
+
+
+def fgraft_harvest_block_multi(ixs, b: int):
+    """Block b of every index in ixs, their kernels overlapping on side streams."""
+    arr = (C.c_void_p * max(len(ixs), 1))(*[ix.handle for ix in ixs])
+    dev = ixs[0].X.device if ixs else None
+    _check(load().fgraft_harvest_block_multi(arr, C.c_int32(len(ixs)), C.c_int32(b),
+                                             _stream(dev)))
 
 
 def fgraft_prune(ix: Index, counters: bool = False):

@@ -254,3 +254,29 @@ def test_n20000_parity(fg):
     ps = synth.vmf_like(20000, 100, 32, seed=9)
     ix, ctr, st, fin, D, ref = _build_both(fg, ps, T=8, R=32, ef=64, B=8)
     _compare(ctr, st, fin, ref)
+
+
+def test_harvest_block_multi_equals_single(fg):
+    # three independent builds harvested block by block together give the
+    # rows and final graphs of their separate builds
+    sets = [(synth.gaussian_mixture(1500, 16, 4, seed=11), 16, fg.L2_F32),
+            (synth.vmf_like(1800, 100, 6, seed=12), 100, fg.ANGULAR_F32),
+            (synth.gaussian_mixture(900, 33, 3, seed=13), 33, fg.L2_F32)]
+    p = dict(T=4, R=16, ef_h=32, B=4, alpha=1.2)
+    multi, single = [], []
+    for ps, d, metric in sets:
+        X = _dev(ps.X)
+        multi.append(fg.fgraft_build_scaffold(X, d, fg.Params(metric=metric, **p)))
+        single.append(fg.fgraft_build_scaffold(X, d, fg.Params(metric=metric, **p)))
+    for b in range(4):
+        fg.fgraft_harvest_block_multi(multi, b)
+    for ix in single:
+        for b in range(4):
+            fg.fgraft_harvest_block(ix, b)
+    for im, is_ in zip(multi, single):
+        cm, cs = fg.fgraft_index_copy(im), fg.fgraft_index_copy(is_)
+        assert torch.equal(cm["rows"], cs["rows"]) and torch.equal(cm["counts"], cs["counts"])
+        om, os_ = fg.fgraft_prune(im), fg.fgraft_prune(is_)
+        assert torch.equal(om[0], os_[0]) and torch.equal(om[1], os_[1])
+    with pytest.raises(fg.FgraftError, match="EINVAL"):
+        fg.fgraft_harvest_block_multi(multi, 0)  # already past block 0
