@@ -184,6 +184,29 @@ def beam(D: Data, off: np.ndarray, ids: np.ndarray, rts: np.ndarray, q: np.ndarr
             int(nev.value))
 
 
+def visited(D: Data, off: np.ndarray, ids: np.ndarray, rts: np.ndarray, q: np.ndarray, ef: int):
+    """The visited set of one beam search (ids in visiting order)."""
+    off = np.ascontiguousarray(off, np.int64)
+    ids = np.ascontiguousarray(ids, np.int32)
+    rts = np.ascontiguousarray(rts, np.int32)
+    q = np.ascontiguousarray(q, dtype=D.X.dtype)
+    out = np.empty(D.n, np.int32)
+    nv = C.c_int64(0)
+    _load().fgo_visited(D.ref, _p(off), _p(ids), _p(rts), C.c_int32(len(rts)), _p(q),
+                        C.c_int32(ef), _p(out), C.byref(nv))
+    return out[: nv.value].copy()
+
+
+def lockstep_density(sets):
+    """Lockstep density of a group of queries searched together (Section 6,
+    Table 6): the visited sets' summed sizes over (group size x the size of
+    their union).  1 when every query visits the same vertices, 1/|group|
+    when no vertex is shared."""
+    union = np.unique(np.concatenate(sets)) if sets else np.empty(0, np.int32)
+    total = sum(len(v) for v in sets)
+    return total / (len(sets) * max(len(union), 1))
+
+
 def prune_list(D: Data, p: int, cand: np.ndarray, alpha: float, R: int):
     """Occlusion prune of an explicit candidate list; returns (kept ids, evals)."""
     cand = np.ascontiguousarray(cand, np.int32)

@@ -465,6 +465,30 @@ int fgo_beam(const fgo_data* D, const int64_t* off, const int32_t* ids, const in
   return 0;
 }
 
+/* The visited set V of one beam search, in visiting order (Section 6 and
+ * Table 6 measure how much the V of queries searched together overlap). */
+int fgo_visited(const fgo_data* D, const int64_t* off, const int32_t* ids, const int32_t* roots,
+                int32_t T, const void* q, int32_t ef, int32_t* out_ids, int64_t* out_n) {
+  beam_scratch S;
+  int64_t maxdeg = csr_maxdeg(D->n, off);
+  S.visited = (uint8_t*)calloc((size_t)D->n, 1);
+  S.vlist = (int32_t*)malloc(sizeof(int32_t) * (size_t)D->n);
+  S.pool_cap = ef + maxdeg + T;
+  S.pool = (ent*)malloc(sizeof(ent) * (size_t)S.pool_cap);
+  int32_t* E_ids = (int32_t*)malloc(sizeof(int32_t) * (size_t)D->n);
+  float* E_d = (float*)malloc(sizeof(float) * (size_t)D->n);
+  int64_t nev = 0, pl = 0;
+  beam_run(D, off, ids, roots, T, q, ef, &S, E_ids, E_d, &nev, &pl);
+  for (int64_t i = 0; i < nev; ++i) out_ids[i] = S.vlist[i];
+  *out_n = nev;
+  free(S.visited);
+  free(S.vlist);
+  free(S.pool);
+  free(E_ids);
+  free(E_d);
+  return 0;
+}
+
 /* ------------------------------------------------------------------------ *
  * Occlusion prune (Section 3, after FANNG and DiskANN's RobustPrune).
  * Input: candidates of point p with their delta(p, .), p already removed.
