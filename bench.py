@@ -322,6 +322,12 @@ def run_ours(args):
 
     # ---- dense blocks in the other two precisions (untimed, same blocks) ----
     dense_other = {}
+    for prec, name in ((1, "bf16"), (2, "fp8_e4m3")):
+        # the filter's error against float64 on the reranked pairs (slow, separate call)
+        _, _, est = fg.fgraft_dense_block_dist(X_d, d, fg.ANGULAR_F32, B_d, spec["dense_k"],
+                                               precision=prec, stats=True, err64=True)
+        dense_other[name + "_error_check"] = {"max_err_over_bound": round(est[4], 5),
+                                              "max_canonical_err": est[5]}
     for prec, name in ((0, "fp32_cuda_cores"), (2, "fp8_e4m3")):
         q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         q0.record(stream)

@@ -215,9 +215,12 @@ fgraft_status fgraft_search(fgraft_index* ix, const void* Q, int64_t nq, int64_t
  *   precision 2  the same with an FP8 (E4M3) filter, each centred row scaled
  *                so that its largest magnitude is 448 (kind::f8f6f4); the
  *                bound is 16 times wider, so more pairs are recomputed.
- * stats (host, optional, 4 doubles; the call then synchronises `stream`):
+ * stats (host, optional, 6 doubles; the call then synchronises `stream`):
  * fraction of pairs recomputed, Gram-kernel ms, select ms, prep ms
- * (precisions 1 and 2; zeros for precision 0).  Float32 metrics only; bs <= 1024,
+ * (precisions 1 and 2; zeros for precision 0).  When stats[4] is nonzero on
+ * entry, stats[4] and stats[5] return, over the recomputed pairs, the largest
+ * |approximate - float64| as a fraction of the row's bound and the largest
+ * |canonical float32 - float64| (the float64 check slows the select).  Float32 metrics only; bs <= 1024,
  * k <= 64, nb <= 65535.  Precisions 1 and 2 allocate their scratch stream-ordered and
  * synchronises `stream` to check its bounded waits (FGRAFT_ETIMEOUT). */
 fgraft_status fgraft_dense_block_dist(const void* X, int64_t n, int32_t d, int64_t ld,

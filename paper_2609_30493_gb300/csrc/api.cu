@@ -863,13 +863,14 @@ fgraft_status fgraft_dense_block_dist(const void* X, int64_t n, int32_t d, int64
                                "precision must be 0 (float32), 1 (BF16 filter) or 2 (FP8 filter)");
   if (nb < 0 || nb > 65535 || bs < 1 || bs > 1024 || k < 1 || k > 64)
     return (fgraft_status)fail(FGRAFT_EINVAL, "need nb <= 65535, bs in [1,1024], k in [1,64]");
+  const bool err64 = stats && stats[4] != 0.0;  // float64 error maxima requested
   if (stats)
-    for (int i = 0; i < 4; ++i) stats[i] = 0.0;
+    for (int i = 0; i < 6; ++i) stats[i] = 0.0;
   if (nb == 0) return FGRAFT_OK;
   if (!block_ids || !out_ids || !out_dist) return (fgraft_status)fail(FGRAFT_EINVAL, "NULL pointer");
   if (precision >= 1)
-    return (fgraft_status)dense_block_tc(L, block_ids, nb, bs, k, precision == 2, out_ids,
-                                         out_dist, stats, s);
+    return (fgraft_status)dense_block_tc(L, block_ids, nb, bs, k, precision == 2, err64,
+                                         out_ids, out_dist, stats, s);
   rc = dense_block(L, block_ids, nb, bs, k, out_ids, out_dist, s);
   if (!rc && stats) FGS(cudaStreamSynchronize(s));
   return (fgraft_status)rc;

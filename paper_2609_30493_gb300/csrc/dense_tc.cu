@@ -16,6 +16,7 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "common.cuh"
 #include "internal.h"
@@ -59,8 +60,9 @@ struct TcArgs {
   float* cc;          // [nb][1024] angular: (1 - |x|^2) / 2
   float* Mx;          // [nb] largest centred norm
   float* LP;          // [nb][1024][1024] approximate distances
-  uint32_t* err;
+  uint32_t* err;  // [0] timeout flag, [8] and [9] error maxima (float bits)
   unsigned long long* pairs;  // valid ordered pairs over all blocks
+  int32_t errstat;  // measure the filter's error against float64 on the reranked pairs
 };
 
 __global__ void __launch_bounds__(256) dense_prep_kernel(const TcArgs a) {
@@ -321,7 +323,30 @@ __global__ void __launch_bounds__(SEL_WARPS * 32)
         load_slots<G, K>(a.X + (int64_t)cid * a.ld_bytes, nch, j, y);
         const float dd = slots_dist<METRIC, G, K>(qs, y, nch, a.d, j);
         __syncwarp();
-        if (c < cand && j == 0) keys[c] = make_key(dd, cid);
+        if (c < cand && j == 0) {
+          if (a.errstat) {
+            // the same pair in float64 (plain order): the filter's error
+            // relative to the bound used, the canonical value's absolute error
+            const float* xa = reinterpret_cast<const float*>(a.X + (int64_t)xi * a.ld_bytes);
+            const float* xb = reinterpret_cast<const float*>(a.X + (int64_t)cid * a.ld_bytes);
+            double acc = 0.0;
+            for (int e = 0; e < a.d; ++e) {
+              if (METRIC == ANGULAR_F32) {
+                acc += (double)xa[e] * (double)xb[e];
+              } else {
+                const double t = (double)xa[e] - (double)xb[e];
+                acc += t * t;
+              }
+            }
+            const double d64 = METRIC == ANGULAR_F32 ? 1.0 - acc : acc;
+            const int col = (int)(uint32_t)keys[c];
+            const float e1 = (float)(fabs((double)lp[col] - d64) / (double)eps);
+            const float e2 = (float)fabs((double)dd - d64);
+            atomicMax(a.err + 8, __float_as_uint(e1));
+            atomicMax(a.err + 9, __float_as_uint(e2));
+          }
+          keys[c] = make_key(dd, cid);
+        }
         __syncwarp();
       }
       kk = sort_unique(keys, cand, lane);
@@ -351,7 +376,8 @@ static SelectFn select_kernel_for(int metric, int G, int K) {
 }
 
 int dense_block_tc(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs, int k,
-                   int fp8, int32_t* out_ids, float* out_dist, double* stats, cudaStream_t s) {
+                   int fp8, bool err64, int32_t* out_ids, float* out_dist, double* stats,
+                   cudaStream_t s) {
   SelectFn sel = select_kernel_for(L.metric, L.G, L.K);
   if (!sel || L.metric == L2_U8) {
     set_error(1, "tensor-core dense blocks take float32 metrics");
@@ -366,6 +392,7 @@ int dense_block_tc(const VecLayout& L, const int32_t* block_ids, int64_t nb, int
   a.ld_bytes = L.ld_bytes;
   a.d = L.d;
   a.fp8 = fp8 ? 1 : 0;
+  a.errstat = stats && err64 ? 1 : 0;
   const int slice = a.fp8 ? TC_KB : TC_KB / 2;  // elements per slice
   a.dpad = (L.d + slice - 1) / slice * slice;
   a.rowb = a.fp8 ? a.dpad : 2 * a.dpad;
@@ -438,8 +465,8 @@ int dense_block_tc(const VecLayout& L, const int32_t* block_ids, int64_t nb, int
       rc = cuda_fail(e, "dense tensor-core kernels");
       break;
     }
-    uint32_t h[6] = {};
-    if ((e = cudaMemcpyAsync(h, a.err, 24, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+    uint32_t h[10] = {};
+    if ((e = cudaMemcpyAsync(h, a.err, 40, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess) {
       rc = cuda_fail(e, "dense tensor-core status");
       break;
@@ -460,6 +487,11 @@ int dense_block_tc(const VecLayout& L, const int32_t* block_ids, int64_t nb, int
       stats[1] = t2;
       stats[2] = t3;
       stats[3] = t1;
+      float m1, m2;
+      std::memcpy(&m1, &h[8], 4);
+      std::memcpy(&m2, &h[9], 4);
+      stats[4] = m1;
+      stats[5] = m2;
     }
   } while (0);
   for (int i = 0; i < 4 && stats; ++i) cudaEventDestroy(ev[i]);

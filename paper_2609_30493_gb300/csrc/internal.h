@@ -129,10 +129,12 @@ extern int g_prune_tc;
 // The same for the SAT's closest-child assignment.
 extern int g_sat_tc;
 
-// Dense-block top-k with the BF16 tensor-core filter and canonical rerank;
-// stats (host, optional): rerank fraction, Gram ms, select ms, prep ms.
+// Dense-block top-k with the BF16 or FP8 tensor-core filter and canonical
+// rerank; stats (host, optional): rerank fraction, Gram ms, select ms, prep
+// ms, and with err64 the float64 error maxima over the reranked pairs.
 int dense_block_tc(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs, int k,
-                   int fp8, int32_t* out_ids, float* out_dist, double* stats, cudaStream_t s);
+                   int fp8, bool err64, int32_t* out_ids, float* out_dist, double* stats,
+                   cudaStream_t s);
 
 // Dense-block top-k (canonical float32 distances of every pair of a block).
 int dense_block(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs, int k,

@@ -278,15 +278,17 @@ def fgraft_prune_lists_noalloc(X: torch.Tensor, d: int, metric: int, owner: torc
 
 
 def fgraft_dense_block_dist(X: torch.Tensor, d: int, metric: int, block_ids: torch.Tensor, k: int,
-                            precision: int = 0, stats: bool = False):
+                            precision: int = 0, stats: bool = False, err64: bool = False):
     """Per-row top-k of every block's pairs.  precision 0: float32 on CUDA cores;
     1: BF16 tensor-core filter and exact float32 rerank; 2: the same with an
     FP8 (E4M3, per-row scale) filter.  With stats=True also
-    returns (rerank fraction, Gram ms, select ms, prep ms)."""
+    returns (rerank fraction, Gram ms, select ms, prep ms, max |approx - f64| / bound,
+    max |canonical - f64|); the last two only with err64=True (slower)."""
     nb, bs = block_ids.shape
     ids = torch.empty((nb, bs, k), dtype=torch.int32, device=X.device)
     dist = torch.empty((nb, bs, k), dtype=torch.float32, device=X.device)
-    st = (C.c_double * 4)()
+    st = (C.c_double * 6)()
+    st[4] = 1.0 if err64 else 0.0
     _check(load().fgraft_dense_block_dist(_ptr(X), C.c_int64(X.shape[0]), C.c_int32(d),
                                           C.c_int64(X.shape[1]), C.c_int32(metric),
                                           _ptr(block_ids), C.c_int64(nb), C.c_int32(bs),

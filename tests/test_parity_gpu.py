@@ -196,13 +196,17 @@ def test_dense_block_parity(fg, metric, d, k, precision):
     blocks = synth.intra_cluster_blocks(ps.labels, 3, 1000, seed=1)
     blocks[2, -7:] = -1
     gi, gd, st = fg.fgraft_dense_block_dist(_dev(ps.X), d, metric, _dev(blocks), k,
-                                            precision=precision, stats=True)
+                                            precision=precision, stats=True,
+                                            err64=precision >= 1)
     D = oracle.Data(ps.X, d, metric)
     oi, od, _ = oracle.dense_block(D, blocks, k)
     assert np.array_equal(_np(gi), oi)
     assert np.array_equal(_np(gd), od)
     if precision >= 1:
         assert 0.0 < st[0] <= 1.0 and st[1] > 0.0
+        # the filter's error stays inside its bound on every recomputed pair
+        assert 0.0 < st[4] <= 1.0
+        assert st[5] >= 0.0
 
 
 def test_api_rejects_bad_arguments(fg):
