@@ -99,7 +99,7 @@ def ncu_traffic(kernel_files):
         return None
     txt = open(prof).read()
     m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
+    h = re.search(r"kernel_source_sha256[^:\n]*:\s*([0-9a-f]+)", txt)
     if not m or not h:
         return None
     return float(m.group(1)) if h.group(1) == kernel_source_sha256(kernel_files) else None
@@ -115,7 +115,7 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={idx}", f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
