@@ -198,7 +198,7 @@ def visited(D: Data, off: np.ndarray, ids: np.ndarray, rts: np.ndarray, q: np.nd
 
 
 def lockstep_density(sets):
-    """Lockstep density of a group of queries searched together (Section 6,
+    """Lockstep density of a group of queries searched together (Section 5.5,
     Table 6): the visited sets' summed sizes over (group size x the size of
     their union).  1 when every query visits the same vertices, 1/|group|
     when no vertex is shared."""

@@ -465,7 +465,7 @@ int fgo_beam(const fgo_data* D, const int64_t* off, const int32_t* ids, const in
   return 0;
 }
 
-/* The visited set V of one beam search, in visiting order (Section 6 and
+/* The visited set V of one beam search, in visiting order (Section 5.5 and
  * Table 6 measure how much the V of queries searched together overlap). */
 int fgo_visited(const fgo_data* D, const int64_t* off, const int32_t* ids, const int32_t* roots,
                 int32_t T, const void* q, int32_t ef, int32_t* out_ids, int64_t* out_n) {

@@ -1,4 +1,4 @@
-"""Lockstep density (Section 6, Table 6): how much the visited sets of the
+"""Lockstep density (Section 5.5, Table 6): how much the visited sets of the
 queries of one group overlap, the sum of their sizes over (group size x the
 size of their union).
 
