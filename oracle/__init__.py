@@ -166,6 +166,20 @@ def scaffold(n: int, parents: np.ndarray):
     return off, ids[: nnz.value]
 
 
+def scaffold_cap(D: Data, off: np.ndarray, ids: np.ndarray, K: int):
+    """Section 6's ablation: every scaffold row longer than K keeps its K
+    nearest entries by (delta, id); rows stay sorted by id."""
+    off = np.ascontiguousarray(off, np.int64)
+    ids = np.ascontiguousarray(ids, np.int32)
+    nnz = C.c_int64(0)
+    lib = _load()
+    lib.fgo_scaffold_cap(D.ref, _p(off), _p(ids), C.c_int32(K), None, None, C.byref(nnz))
+    o = np.empty(D.n + 1, np.int64)
+    out = np.empty(max(nnz.value, 1), np.int32)
+    lib.fgo_scaffold_cap(D.ref, _p(off), _p(ids), C.c_int32(K), _p(o), _p(out), C.byref(nnz))
+    return o, out[: nnz.value]
+
+
 def beam(D: Data, off: np.ndarray, ids: np.ndarray, rts: np.ndarray, q: np.ndarray, ef: int):
     """One beam search; returns (E_ids, E_d, pool_ids, pool_d, n_eval)."""
     off = np.ascontiguousarray(off, np.int64)
@@ -308,10 +322,13 @@ def dense_block(D: Data, block_ids: np.ndarray, k: int, use_f64: bool = False,
 
 
 def build_graph(D: Data, T: int, R: int, ef_h: int, B: int, alpha: float, seed: int,
-                nthreads: int = 0):
-    """The whole FGraft pipeline: SAT forest, scaffold, B harvest blocks, final graph."""
+                nthreads: int = 0, cap: int = 0):
+    """The whole FGraft pipeline: SAT forest, scaffold (rows capped at `cap`
+    nearest when cap > 0, Section 6), B harvest blocks, final graph."""
     rts, parents, sat_ev = sat_forest(D, T, seed)
     s_off, s_ids = scaffold(D.n, parents)
+    if cap > 0:
+        s_off, s_ids = scaffold_cap(D, s_off, s_ids, cap)
     A, cnt, ctr, per = fgraft(D, rts, s_off, s_ids, R, ef_h, B, alpha, nthreads)
     f_off, f_ids, fev = final(D, A, cnt, R, alpha, parents[0])
     ctr["sat_evals"] = sat_ev

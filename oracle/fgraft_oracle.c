@@ -367,6 +367,45 @@ int fgo_scaffold(int64_t n, int32_t T, const int32_t* parents, int64_t* off, int
 }
 
 /* ------------------------------------------------------------------------ *
+ * Scaffold degree cap (Section 6, an ablation the paper reports as negative):
+ * every row of S_0 longer than K keeps its K nearest entries by
+ * (delta(u, v), v); rows stay sorted by id.  Two calls as for fgo_scaffold.
+ * ------------------------------------------------------------------------ */
+int fgo_scaffold_cap(const fgo_data* D, const int64_t* off, const int32_t* ids, int32_t K,
+                     int64_t* out_off, int32_t* out_ids, int64_t* nnz) {
+  int64_t total = 0, maxlen = 0;
+  for (int64_t u = 0; u < D->n; ++u)
+    if (off[u + 1] - off[u] > maxlen) maxlen = off[u + 1] - off[u];
+  ent* e = (ent*)malloc(sizeof(ent) * (size_t)(maxlen > 0 ? maxlen : 1));
+  int32_t* keep = (int32_t*)malloc(sizeof(int32_t) * (size_t)(maxlen > 0 ? maxlen : 1));
+  for (int64_t u = 0; u < D->n; ++u) {
+    const int64_t len = off[u + 1] - off[u];
+    int64_t m = len;
+    if (len > K) {
+      for (int64_t i = 0; i < len; ++i) {
+        e[i].id = ids[off[u] + i];
+        e[i].d = dist_ptr(D, row_ptr(D, u), row_ptr(D, e[i].id));
+        e[i].expanded = 0;
+      }
+      qsort(e, (size_t)len, sizeof(ent), ent_cmp);
+      m = K;
+      for (int64_t i = 0; i < m; ++i) keep[i] = e[i].id;
+      qsort(keep, (size_t)m, sizeof(int32_t), i32_cmp);
+    } else {
+      for (int64_t i = 0; i < m; ++i) keep[i] = ids[off[u] + i];
+    }
+    if (out_off) out_off[u] = total;
+    if (out_ids) memcpy(out_ids + total, keep, sizeof(int32_t) * (size_t)m);
+    total += m;
+  }
+  if (out_off) out_off[D->n] = total;
+  if (nnz) *nnz = total;
+  free(e);
+  free(keep);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ *
  * Beam search (Section 3: "beam search of width ef_h from the tree roots").
  * visited = {}, pool = {}; each root not yet visited is evaluated, marked and
  * put in the pool; then, while the pool holds an unexpanded entry, the one
