@@ -48,10 +48,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="override n (smaller runs)")
     ap.add_argument("--batch", type=int, default=64, help="builds of --mode batched")
-    ap.add_argument("--mode", default="step", choices=["step", "dims", "paper", "batched"],
+    ap.add_argument("--mode", default="step", choices=["step", "dims", "paper", "batched", "cap"],
                     help="step: the benchmark line; dims: adaptive vs dense cost per evaluation "
                          "across d; paper: the paper-scale angular arms; batched: many "
-                         "independent builds harvested together")
+                         "independent builds harvested together; cap: the scaffold degree "
+                         "cap ablation")
     return ap.parse_args()
 
 
@@ -748,6 +749,47 @@ def run_batched(args):
         "clocks": clk}), flush=True)
 
 
+def run_cap(args):
+    """Section 6's negative result on the in-cache workload: the scaffold's
+    rows capped at K nearest (K = 0 is no cap); build time, work (distance
+    evaluations) and quality (recall ladder, local completeness) per K."""
+    import torch
+    from paper_2609_30493_gb300 import build as fgbuild
+    from paper_2609_30493_gb300 import fgraft as fg
+    fgbuild.build()
+    fg.load()
+    spec = dict(SPEC)
+    ps, Q, blocks = make_inputs(spec)
+    d = spec["d"]
+    X_d = torch.from_numpy(ps.X).cuda()
+    Q_d = torch.from_numpy(Q).cuda()
+    params = fg.Params(T=spec["T"], R=spec["R"], ef_h=spec["ef_h"], B=spec["B"],
+                       alpha=spec["alpha"], seed=spec["seed"], metric=fg.ANGULAR_F32)
+    for cap in (0, 64, 32, 16, 8):
+        fg.fgraft_tune_scaffold_cap(cap)
+        ts = []
+        for r in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ix = fg.fgraft_build_scaffold(X_d, d, params)
+            fg.fgraft_harvest_all(ix, use_graph=False)
+            torch.cuda.synchronize()
+            if r >= args.warmup:
+                ts.append(time.perf_counter() - t0)
+        c = fg.fgraft_index_counters(ix)
+        sizes = ix.sizes()
+        q = quality_report(fg, ix, ps, Q_d, spec)
+        work = c["harvest_evals"] + c["prune_evals"] + c["final_prune_evals"] + c["sat_evals"]
+        print(json.dumps({"mode": "cap", "cap": cap, "n": spec["n"], "build_ms": round(1e3 * float(np.median(ts)), 3),
+                          "scaffold_nnz": sizes["scaffold_nnz"], "counters": c, "work": work,
+                          "recall_at_10_ef64": next(x["recall_at_10"] for x in q["recall_ladder"] if x["ef_s"] == 64),
+                          "recall_at_10_ef128": next(x["recall_at_10"] for x in q["recall_ladder"] if x["ef_s"] == 128),
+                          "evals_per_query_ef128": next(x["evals_per_query"] for x in q["recall_ladder"] if x["ef_s"] == 128),
+                          "local_completeness_at_10": q["local_completeness_at_10"]}), flush=True)
+        del ix
+    fg.fgraft_tune_scaffold_cap(0)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -758,6 +800,8 @@ def main():
         run_paper(args)
     elif args.mode == "batched":
         run_batched(args)
+    elif args.mode == "cap":
+        run_cap(args)
     else:
         run_ours(args)
 

@@ -270,6 +270,14 @@ fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t war
  * FGRAFT_EINVAL for other values. */
 fgraft_status fgraft_tune_prune(int32_t tensor_cores);
 
+/* Scaffold degree cap for later fgraft_build_scaffold calls in this process
+ * (Section 6: the ablation the paper reports as negative).  With cap > 0
+ * every row of S_0 longer than cap keeps its cap nearest entries by
+ * (delta(u, v), v), rows sorted by id; the final graph's tree-0 spine and the
+ * entry roots are unchanged.  0 (the default) turns it off.  The distances
+ * the cap evaluates are not in any counter.  FGRAFT_EINVAL for cap < 0. */
+fgraft_status fgraft_tune_scaffold_cap(int32_t cap);
+
 /* SAT launch configuration for later fgraft_build_scaffold calls in this
  * process (tuning; results do not depend on it): tree nodes holding at least
  * big_node_min points are split across many CTAs, one launch per child

@@ -104,6 +104,7 @@ using namespace fg;
 // Nodes of at least this many points are built by the multi-CTA SAT path.
 static int32_t g_sat_big_min = 16384;
 static int32_t g_sat_finish_len = 512;
+static int32_t g_scaffold_cap = 0;  // 0: no degree cap
 
 #define FGS(call)                                                      \
   do {                                                                 \
@@ -639,7 +640,7 @@ fgraft_status fgraft_build_scaffold(const void* X, int64_t n, int32_t d, int64_t
   rc = rc ? rc : dalloc_async(&tmp_ids, 2 * tot, s);
   if (!rc)
     rc = scaffold_csr(n, p.T, ix->parents, ix->s_off, &ix->s_ids, &ix->s_nnz, deg, tmp_off,
-                      tmp_ids, ix->scan_tmp, s);
+                      tmp_ids, ix->scan_tmp, s, &ix->L, g_scaffold_cap);
   if (deg) cudaFreeAsync(deg, s);
   if (tmp_off) cudaFreeAsync(tmp_off, s);
   if (tmp_ids) cudaFreeAsync(tmp_ids, s);
@@ -990,6 +991,12 @@ fgraft_status fgraft_tune_prune(int32_t tensor_cores) {
     return (fgraft_status)fail(FGRAFT_EINVAL, "tensor_cores must be 0 or 1");
   g_prune_tc = tensor_cores;
   g_sat_tc = tensor_cores;
+  return FGRAFT_OK;
+}
+
+fgraft_status fgraft_tune_scaffold_cap(int32_t cap) {
+  if (cap < 0) return (fgraft_status)fail(FGRAFT_EINVAL, "cap must be >= 0");
+  g_scaffold_cap = cap;
   return FGRAFT_OK;
 }
 

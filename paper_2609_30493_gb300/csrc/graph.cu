@@ -237,9 +237,71 @@ static int sort_unique_all(int64_t n, const int64_t* off, int32_t* ids, uint32_t
   return rc;
 }
 
+// ---------------------------------------------------------------------------
+// Scaffold degree cap (Section 6, an ablation the paper reports as negative):
+// one warp per row longer than cap computes its keys (delta(u, v), v), finds
+// the cap-th smallest key by a 64-step bit search and keeps the entries at or
+// below it, in the row's id order.
+// ---------------------------------------------------------------------------
+constexpr int CAP_WARPS = 4;
+
+template <int METRIC, int G, int K>
+__global__ void __launch_bounds__(CAP_WARPS * 32)
+    cap_rows_kernel(const RowVec V, int64_t n, int cap, const int64_t* off, int32_t* ids,
+                    uint32_t* deg, uint64_t* kbuf) {
+  extern __shared__ __align__(16) uint4 cap_us[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint4* us = cap_us + (int64_t)warp * V.nchunks;
+  for (int64_t u = (int64_t)blockIdx.x * CAP_WARPS + warp; u < n;
+       u += (int64_t)gridDim.x * CAP_WARPS) {
+    const int len = (int)deg[u];
+    if (len <= cap) continue;  // uniform over the warp
+    const int64_t o = off[u];
+    uint64_t* kb = kbuf + o;
+    for (int i = lane; i < len; i += 32) kb[i] = (uint64_t)(uint32_t)ids[o + i] << 1;
+    __syncwarp();
+    stage_row(us, V.X + u * V.ld_bytes, V.nchunks, lane);
+    eval_keys_inplace<METRIC, G, K>(V, us, kb, len, lane);
+    uint64_t t = 0;  // the largest key value with fewer than cap keys below it
+    for (int bit = 63; bit >= 0; --bit) {
+      const uint64_t tt = t | (1ull << bit);
+      int below = 0;
+      for (int i = lane; i < len; i += 32) below += kb[i] < tt ? 1 : 0;
+      if (__reduce_add_sync(FULL, below) < cap) t = tt;
+    }
+    int pos = 0;
+    for (int i0 = 0; i0 < len; i0 += 32) {
+      const int i = i0 + lane;
+      const bool keep = i < len && kb[i] <= t;
+      const int32_t v = keep ? ids[o + i] : 0;
+      const unsigned bal = __ballot_sync(FULL, keep);
+      if (keep) ids[o + pos + __popc(bal & ((1u << lane) - 1u))] = v;
+      pos += __popc(bal);
+      __syncwarp();
+    }
+    if (lane == 0) deg[u] = (uint32_t)pos;
+  }
+}
+
+using CapKernelFn = void (*)(const RowVec, int64_t, int, const int64_t*, int32_t*, uint32_t*,
+                             uint64_t*);
+
+static CapKernelFn cap_kernel_for(int metric, int G, int K) {
+#define CX(M, GG, KK) \
+  if (metric == M && G == GG && K == KK) return cap_rows_kernel<M, GG, KK>;
+#define CF(M) CX(M, 4, 1) CX(M, 8, 1) CX(M, 16, 1) CX(M, 32, 1) CX(M, 32, 2) CX(M, 32, 4) \
+  CX(M, 32, 8)
+  CF(0)
+  CF(1)
+  CX(2, 4, 1) CX(2, 8, 1) CX(2, 16, 1)
+#undef CF
+#undef CX
+  return nullptr;
+}
+
 int scaffold_csr(int64_t n, int T, const int32_t* parents, int64_t* s_off, int32_t** s_ids,
                  int64_t* nnz_out, uint32_t* deg, int64_t* tmp_off, int32_t* tmp_ids,
-                 int64_t* scan_tmp, cudaStream_t s) {
+                 int64_t* scan_tmp, cudaStream_t s, const VecLayout* L, int cap) {
   const int64_t tot = (int64_t)T * n;
   FG_CUDA(cudaMemsetAsync(deg, 0, sizeof(uint32_t) * n, s));
   edge_count_kernel<<<grid1d(tot), 256, 0, s>>>(n, tot, parents, deg);
@@ -251,6 +313,22 @@ int scaffold_csr(int64_t n, int T, const int32_t* parents, int64_t* s_off, int32
   FG_CUDA(cudaGetLastError());
   rc = sort_unique_all(n, tmp_off, tmp_ids, deg, s);
   if (rc) return rc;
+  if (cap > 0) {
+    CapKernelFn ck = cap_kernel_for(L->metric, L->G, L->K);
+    if (!ck) {
+      set_error(1, "no scaffold cap kernel for this metric and dimension");
+      return 1;
+    }
+    uint64_t* kbuf = nullptr;
+    FG_CUDA(cudaMallocAsync(&kbuf, sizeof(uint64_t) * std::max<int64_t>(2 * tot, 1), s));
+    const int smem = CAP_WARPS * 16 * L->nchunks;
+    FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(ck), smem));
+    ck<<<grid1d(n * 32, CAP_WARPS * 32), CAP_WARPS * 32, smem, s>>>(
+        RowVec{L->X, L->ld_bytes, L->d, L->nchunks}, n, cap, tmp_off, tmp_ids, deg, kbuf);
+    note_launch();
+    FG_CUDA(cudaGetLastError());
+    FG_CUDA(cudaFreeAsync(kbuf, s));
+  }
   rc = scan_u32(deg, s_off, n, scan_tmp, s);
   if (rc) return rc;
   int64_t nnz = 0;

@@ -79,12 +79,13 @@ struct SatScratch {
 int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* parents,
                SatScratch& S, unsigned long long* ctr_sat, cudaStream_t s);
 
-// Scaffold CSR from the parents of T trees (rows sorted by id, no repeats).
-// tmp_off: n+1, tmp_ids: 2*T*n, ucnt: n, deg: n.  On return *nnz_out holds
-// the size and s_ids (allocated here with cudaMalloc) the ids.
+// Scaffold CSR from the parents of T trees (rows sorted by id, no repeats;
+// with cap > 0 a row longer than cap keeps its cap nearest entries, Section
+// 6).  tmp_off: n+1, tmp_ids: 2*T*n, ucnt: n, deg: n.  On return *nnz_out
+// holds the size and s_ids (allocated here with cudaMalloc) the ids.
 int scaffold_csr(int64_t n, int T, const int32_t* parents, int64_t* s_off, int32_t** s_ids,
                  int64_t* nnz_out, uint32_t* deg, int64_t* tmp_off, int32_t* tmp_ids,
-                 int64_t* scan_tmp, cudaStream_t s);
+                 int64_t* scan_tmp, cudaStream_t s, const VecLayout* L, int cap);
 
 // Reverse lists of the rows of blocks 0..b: r_off (n+1), r_ids (<= n*R).
 int reverse_rows(int64_t n, int R, int nb, int b, const int32_t* A, const int32_t* cnt,

@@ -43,7 +43,7 @@ EXPORTS = ["fgraft_build_scaffold", "fgraft_harvest_block", "fgraft_harvest_all"
            "fgraft_index_sizes", "fgraft_index_counters", "fgraft_index_tune",
            "fgraft_index_profile", "fgraft_index_harvest_ms", "fgraft_kernel_launches",
            "fgraft_tune_sat", "fgraft_tune_prune", "fgraft_prune_lists_noalloc",
-           "fgraft_harvest_block_multi",
+           "fgraft_harvest_block_multi", "fgraft_tune_scaffold_cap",
            "fgraft_index_destroy", "fgraft_last_error"]
 
 
@@ -205,6 +205,10 @@ def fgraft_index_harvest_ms(ix: Index, with_prune: bool = False):
 
 def fgraft_tune_prune(tensor_cores: bool = True):
     _check(load().fgraft_tune_prune(C.c_int32(1 if tensor_cores else 0)))
+
+
+def fgraft_tune_scaffold_cap(cap: int = 0):
+    _check(load().fgraft_tune_scaffold_cap(C.c_int32(cap)))
 
 
 def fgraft_tune_sat(big_node_min: int = 0, finish_len: int = 0):

@@ -34,7 +34,7 @@ def _np(t):
 
 
 def _build_both(fg, ps, T, R, ef, B, alpha=1.2, seed=0, use_graph=False, hash_log2=0,
-                overflow_mode=0):
+                overflow_mode=0, cap=0):
     X = _dev(ps.X)
     p = fg.Params(T=T, R=R, ef_h=ef, B=B, alpha=alpha, seed=seed, metric=ps.metric)
     ix, c0 = fg.fgraft_build_scaffold(X, ps.d, p, counters=True)
@@ -44,7 +44,7 @@ def _build_both(fg, ps, T, R, ef, B, alpha=1.2, seed=0, use_graph=False, hash_lo
     off, ids = fg.fgraft_prune(ix)
     st = fg.fgraft_index_copy(ix)
     D = oracle.Data(ps.X, ps.d, ps.metric)
-    ref = oracle.build_graph(D, T, R, ef, B, alpha, seed)
+    ref = oracle.build_graph(D, T, R, ef, B, alpha, seed, cap=cap)
     return ix, ctr, st, (off, ids), D, ref
 
 
@@ -284,3 +284,21 @@ def test_harvest_block_multi_equals_single(fg):
         assert torch.equal(om[0], os_[0]) and torch.equal(om[1], os_[1])
     with pytest.raises(fg.FgraftError, match="EINVAL"):
         fg.fgraft_harvest_block_multi(multi, 0)  # already past block 0
+
+
+@pytest.mark.parametrize("kind,cap", [("gauss", 3), ("vmf", 6), ("u8", 5)])
+def test_scaffold_cap_parity(fg, kind, cap):
+    # Section 6's ablation: scaffold rows capped at their cap nearest entries
+    if kind == "gauss":
+        ps = synth.gaussian_mixture(2000, 16, 8, seed=7)
+    elif kind == "vmf":
+        ps = synth.vmf_like(2500, 100, 8, seed=7)
+    else:
+        ps = synth.uint8_mixture(1500, 32, 6, seed=7)
+    try:
+        fg.fgraft_tune_scaffold_cap(cap)
+        ix, ctr, st, fin, D, ref = _build_both(fg, ps, T=6, R=16, ef=32, B=4, cap=cap)
+    finally:
+        fg.fgraft_tune_scaffold_cap(0)
+    assert int(np.diff(_np(st["s_off"])).max()) <= cap
+    _compare(ctr, st, fin, ref)
