@@ -161,6 +161,18 @@ def recall_at_10(X, Q, ids):
     return hits / (Q.shape[0] * 10)
 
 
+def job_rate(local_ms, steps, n_per_rank, world, dist_mod, device):
+    """Whole-job rate of a replicated run: the slowest rank's time decides
+    (max over ranks), every rank built n_per_rank points per step.  Returns
+    (ms per step, points per second over all ranks)."""
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    if dist_mod is not None:
+        dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    ms = float(t.item()) / steps
+    return ms, world * n_per_rank / (ms / 1e3)
+
+
 EF_LADDER = (10, 16, 24, 32, 48, 64, 96, 128)
 
 
@@ -275,12 +287,9 @@ def run_ours(args):
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_per_step = float(t.item()) / args.steps
     n = spec["n"]
-    value = world * n / (ms_per_step / 1e3)
+    ms_per_step, value = job_rate(total_ms, args.steps, n, world, dist if world > 1 else None,
+                                  "cuda")
 
     # ---- breakdown (one untimed profiled pass) ----
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
@@ -369,10 +378,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_ms += e0.elapsed_time(e1)
         d2h = sum(o.numel() * o.element_size() for o in outs)
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * n / (float(te.item()) / args.steps / 1e3)
+    _, e2e_value = job_rate(e2e_ms, args.steps, n, world, dist if world > 1 else None, "cuda")
 
     if rank != 0:
         if world > 1:

@@ -207,7 +207,8 @@ fgraft_status fgraft_search(fgraft_index* ix, const void* Q, int64_t nq, int64_t
  * out_ids/out_dist (nb*bs*k) receive the k smallest (delta, id) per row
  * (-1 / +inf fill).  The result is the canonical float32 top-k whatever the
  * precision:
- *   precision 0  every pair in the canonical float32 order (CUDA cores);
+ *   precision 0  every pair in the canonical float32 order (CUDA cores;
+ *                uint8 rows: exact integer distances);
  *   precision 1  BF16 tensor-core filter (tcgen05, FP32 accumulation) on the
  *                block centred on its mean, then every pair within twice a
  *                rounding-error bound of the k-th approximate distance is
@@ -220,7 +221,8 @@ fgraft_status fgraft_search(fgraft_index* ix, const void* Q, int64_t nq, int64_t
  * (precisions 1 and 2; zeros for precision 0).  When stats[4] is nonzero on
  * entry, stats[4] and stats[5] return, over the recomputed pairs, the largest
  * |approximate - float64| as a fraction of the row's bound and the largest
- * |canonical float32 - float64| (the float64 check slows the select).  Float32 metrics only; bs <= 1024,
+ * |canonical float32 - float64| (the float64 check slows the select).
+ * Precisions 1 and 2 take float32 metrics only; bs <= 1024,
  * k <= 64, nb <= 65535.  Precisions 1 and 2 allocate their scratch stream-ordered and
  * synchronises `stream` to check its bounded waits (FGRAFT_ETIMEOUT). */
 fgraft_status fgraft_dense_block_dist(const void* X, int64_t n, int32_t d, int64_t ld,

@@ -858,7 +858,8 @@ fgraft_status fgraft_dense_block_dist(const void* X, int64_t n, int32_t d, int64
   VecLayout L;
   int rc = check_vectors(X, n, d, ld, metric, &L);
   if (rc) return (fgraft_status)rc;
-  if (metric == L2_U8) return (fgraft_status)fail(FGRAFT_EINVAL, "dense blocks take float32 metrics");
+  if (metric == L2_U8 && precision != 0)
+    return (fgraft_status)fail(FGRAFT_EINVAL, "uint8 dense blocks take precision 0");
   if (precision < 0 || precision > 2)
     return (fgraft_status)fail(FGRAFT_EINVAL,
                                "precision must be 0 (float32), 1 (BF16 filter) or 2 (FP8 filter)");

@@ -1,7 +1,8 @@
 // Dense-block ceiling (Section 5.3, the blocked side of the two-ceiling model):
 // a pair set fixed in advance -- every
 // ordered pair of distinct members of a block -- evaluated in the canonical
-// float32 order, with the k smallest (delta, id) kept per row.  One warp owns
+// float32 order (exact integers for uint8 rows), with the k smallest
+// (delta, id) kept per row.  One warp owns
 // one row; the row's own vector sits in registers and the block's vectors
 // stream through L1/L2 in 16-byte chunks.
 #include <algorithm>
@@ -91,6 +92,7 @@ static DenseKernelFn dense_kernel_for(int metric, int G, int K, int S) {
   DX(M, 32, 8)
   DF(0)
   DF(1)
+  DX(2, 4, 1) DX(2, 8, 1) DX(2, 16, 1)
 #undef DF
 #undef DX
   return nullptr;

@@ -209,6 +209,17 @@ def test_dense_block_parity(fg, metric, d, k, precision):
         assert st[5] >= 0.0
 
 
+def test_dense_block_uint8_parity(fg):
+    ps = synth.uint8_mixture(3000, 128, 4, seed=5)
+    blocks = synth.intra_cluster_blocks(ps.labels, 3, 700, seed=2)
+    blocks[1, -9:] = -1
+    gi, gd = fg.fgraft_dense_block_dist(_dev(ps.X), 128, fg.L2_U8, _dev(blocks), 32)
+    oi, od, _ = oracle.dense_block(oracle.Data(ps.X, 128, fg.L2_U8), blocks, 32)
+    assert np.array_equal(_np(gi), oi) and np.array_equal(_np(gd), od)
+    with pytest.raises(fg.FgraftError, match="EINVAL"):
+        fg.fgraft_dense_block_dist(_dev(ps.X), 128, fg.L2_U8, _dev(blocks), 32, precision=1)
+
+
 def test_api_rejects_bad_arguments(fg):
     ps = synth.gaussian_mixture(100, 16, 2, seed=0)
     X = _dev(ps.X)
