@@ -48,6 +48,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="override n (smaller runs)")
     ap.add_argument("--batch", type=int, default=64, help="builds of --mode batched")
+    ap.add_argument("--arms", default="32x1,8x1,8x2,8x4,8x8,8x16",
+                    help="--mode paper: the TxB arms to build")
+    ap.add_argument("--tunes", default="0x0",
+                    help="--mode paper: harvest launch settings to try per arm, "
+                         "hash_log2 x warps per CTA (0 keeps the default)")
+    ap.add_argument("--no-ladder", action="store_true", help="--mode paper: skip recall")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "coherent", "id"],
+                    help="order in which each block's searches are claimed: tree-0 preorder "
+                         "(coherent), point id, or the preorder when X exceeds L2 (auto)")
     ap.add_argument("--mode", default="step", choices=["step", "dims", "paper", "batched", "cap"],
                     help="step: the benchmark line; dims: adaptive vs dense cost per evaluation "
                          "across d; paper: the paper-scale angular arms; batched: many "
@@ -403,7 +412,7 @@ def run_ours(args):
                    "ef_h": spec["ef_h"], "alpha": spec["alpha"], "nq": spec["nq"],
                    "ef_s": spec["ef_s"], "dense_blocks": spec["dense_blocks"],
                    "block_size": spec["block_size"], "dense_k": spec["dense_k"],
-                   "parallelism": f"replicas{world}",
+                   "parallelism": f"replicas{world}", "schedule": args.schedule,
                    "l2": "flushed before each timed step (256 MiB write); data 40 MB is L2-resident within a step"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                      "unit": "GB/s", "frac": round(achieved / hbm, 4),
@@ -611,11 +620,15 @@ def run_paper(args):
     for s0 in range(0, len(Q), 1024):
         gts.append(torch.topk(Qd[s0:s0 + 1024, :100] @ Xt.T, 10, dim=1).indices.cpu().numpy())
     gt = np.concatenate(gts)
-    for T, B in [(32, 1), (8, 1), (8, 2), (8, 4), (8, 8), (8, 16)]:
+    arms = [tuple(int(v) for v in a.split("x")) for a in args.arms.split(",")]
+    tunes = [tuple(int(v) for v in t.split("x")) for t in args.tunes.split(",")]
+    for (T, B), (hl2, wpc) in [(a, t) for a in arms for t in tunes]:
         p = fg.Params(T=T, R=64, ef_h=100, B=B, alpha=1.2, seed=0, metric=fg.ANGULAR_F32)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ix = fg.fgraft_build_scaffold(X, 100, p)
+        if hl2 or wpc:
+            fg.fgraft_index_tune(ix, hash_log2=hl2, warps_per_cta=wpc)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         fg.fgraft_index_profile(ix, True)
@@ -631,7 +644,7 @@ def run_paper(args):
         torch.cuda.synchronize()
         final_s = f0.elapsed_time(f1) / 1e3
         ladder = []
-        for ef in [10, 16, 24, 32, 48, 64, 96, 128]:
+        for ef in [] if args.no_ladder else [10, 16, 24, 32, 48, 64, 96, 128]:
             ids, dist, ev = fg.fgraft_search(ix, Qd, 10, ef)
             ids = ids.cpu().numpy()
             rec = float(np.mean([len(set(a.tolist()) & set(b.tolist())) / 10 for a, b in zip(ids, gt)]))
@@ -640,7 +653,8 @@ def run_paper(args):
         for (e0, r0, v0), (e1_, r1, v1) in zip(ladder, ladder[1:]):
             if r0 < 0.95 <= r1:
                 d95 = v0 + (0.95 - r0) * (v1 - v0) / (r1 - r0)
-        row = {"mode": "paper", "n": n, "T": T, "B": B, "R": 64, "ef_h": 100,
+        row = {"mode": "paper", "schedule": args.schedule, "hash_log2": hl2, "wpc": wpc,
+               "n": n, "T": T, "B": B, "R": 64, "ef_h": 100,
                "scaffold_s": round(t1 - t0, 3), "harvest_and_final_s": round(t2 - t1, 3),
                "final_s": round(final_s, 3),
                "build_s": round(t2 - t0, 3), "pts_per_s": round(n / (t2 - t0), 1),
@@ -798,6 +812,11 @@ def run_cap(args):
 
 def main():
     args = parse()
+    if args.impl != "reference" and args.schedule != "auto":
+        from paper_2609_30493_gb300 import build as fgbuild, fgraft as fg
+        fgbuild.build()
+        fg.load()
+        fg.fgraft_tune_schedule({"id": 0, "coherent": 1}[args.schedule])
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "dims":

@@ -290,6 +290,27 @@ fgraft_status fgraft_tune_scaffold_cap(int32_t cap);
  * value unchanged. */
 fgraft_status fgraft_tune_sat(int32_t big_node_min, int32_t finish_len);
 
+/* Harvest schedule for later fgraft_build_scaffold calls in this process
+ * (tuning; the rows of a block are independent given S_b, Section 4, so the
+ * graph does not depend on it).  With coherent = 1 the searches of each
+ * block are claimed in a preorder of SAT tree 0, so the searches in flight
+ * together are neighbours that evaluate many of the same targets (Section
+ * 5.5, Table 6) and share their loads through the L2 cache; with 0 they run
+ * in id order; with 2 (the default) the preorder is used when the vectors
+ * are larger than the device's L2 cache.  The schedule falls back to id
+ * order when B > 64 or tree 0 is deeper than 4096.  FGRAFT_EINVAL for other
+ * values. */
+fgraft_status fgraft_tune_schedule(int32_t coherent);
+
+/* The schedule of an index (inspection).  pre (device, n int32): the place
+ * of every point in the preorder of tree 0; qorder (device, n int32): for
+ * blocks b = 0..B-1 one after another, the indices i of the points
+ * b + i * B of block b in the order their searches are claimed.  Both are
+ * left untouched, and *coherent (host, optional) is 0, when the index runs
+ * in id order; otherwise *coherent is 1.  Any pointer may be NULL. */
+fgraft_status fgraft_index_schedule(const fgraft_index* ix, int32_t* pre, int32_t* qorder,
+                                    int32_t* coherent, fgraft_stream stream);
+
 /* Measurement hooks (results never depend on them).
  * fgraft_index_profile: with enable != 0, every later harvest of a block
  * records a CUDA event pair around its harvest kernel on the launching

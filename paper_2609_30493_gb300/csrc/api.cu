@@ -105,6 +105,7 @@ using namespace fg;
 static int32_t g_sat_big_min = 16384;
 static int32_t g_sat_finish_len = 512;
 static int32_t g_scaffold_cap = 0;  // 0: no degree cap
+static constexpr int kCoherentMaxDepth = 4096;
 
 #define FGS(call)                                                      \
   do {                                                                 \
@@ -157,6 +158,7 @@ struct fgraft_index {
   int32_t blocks_done = 0;
   int32_t hash_log2 = 12;
   bool bitmap_ok = true;
+  bool hash_auto = true;       // visited-set layout chosen by occupancy (no explicit hash size)
   int32_t overflow_mode = 1;   // 1: continue in a global bitmap, 2: abandon and re-run
   uint64_t* Eg = nullptr;      // expanded lists handed from the search to the prune kernel
   int32_t* Eg_cnt = nullptr;
@@ -172,6 +174,8 @@ struct fgraft_index {
   bool profile = false;
   std::vector<cudaEvent_t> ev_beg, ev_end;  // around the harvest kernel of each block
   std::vector<cudaEvent_t> ev_pend;         // after the prune kernel of each block
+  int32_t* pre = nullptr;     // place of each point in the preorder of tree 0 (coherent schedule)
+  int32_t* qorder = nullptr;  // query indices of every block in that preorder, block after block
 };
 
 namespace {
@@ -228,6 +232,66 @@ cudaError_t record_event(cudaEvent_t e, cudaStream_t s) {
   return cudaEventRecord(e, s);
 }
 
+// Visited-set layout, per-warp shared memory and CTAs per SM of the beam
+// kernel for a pool of S slots.  With an explicit hash size the n-bit bitmap
+// is used when it is no larger than the hash.  Otherwise the search prefers
+// the bitmap (exact, never full) when it keeps the CTAs per SM that the
+// smallest hash allows, else the largest hash of 2^7..2^12 slots that keeps
+// them: a search whose visited set outgrows the hash goes on in a global
+// bitmap, and the harvest is bound by the latency of its dependent loads, so
+// searches in flight matter more than hash hits (at n = 1.18M, d = 100 the
+// 2^12-slot hash allows 12 warps per SM and 2^11 the register limit of 16,
+// 27 % faster).
+struct BeamShape {
+  bool bitmap = false;
+  int nslots = 0, ecap = 0, vis_bytes = 0, wbytes = 0, per_sm = 0;
+};
+
+int beam_shape(fgraft_index* ix, BeamKernelFn kern, int S, BeamShape* out) {
+  const int64_t bm_bytes = ((ix->L.n + 127) / 128) * 16;
+  const int ecap = 1 << std::max(6, ceil_log2(2 * 32 * S));
+  const int fixed = 8 * ecap + (ecap / 8 + 15) / 16 * 16 + 256 + 16 * ix->L.nchunks;
+  int dev = 0, optin = 0;
+  FG_CUDA(cudaGetDevice(&dev));
+  FG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  auto eval = [&](bool bitmap, int nslots, BeamShape* sh) -> int {
+    sh->bitmap = bitmap;
+    sh->nslots = nslots;
+    sh->ecap = ecap;
+    sh->vis_bytes = bitmap ? (int)bm_bytes : 4 * nslots;
+    sh->wbytes = sh->vis_bytes + fixed;
+    sh->per_sm = 0;
+    if ((int64_t)sh->wbytes * ix->wpc > optin) return 0;
+    FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(kern), sh->wbytes * ix->wpc));
+    FG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->per_sm, kern, ix->wpc * 32,
+                                                          sh->wbytes * ix->wpc));
+    return 0;
+  };
+  int rc = 0;
+  if (!ix->hash_auto) {
+    const int nslots = 1 << ix->hash_log2;
+    return eval(ix->bitmap_ok && bm_bytes <= 4ll * nslots, nslots, out);
+  }
+  BeamShape best, c;
+  if ((rc = eval(false, 1 << 7, &best))) return rc;
+  if (bm_bytes <= optin) {
+    if ((rc = eval(true, 0, &c))) return rc;
+    if (c.per_sm >= best.per_sm && c.per_sm > 0) {
+      *out = c;
+      return 0;
+    }
+  }
+  for (int k = 12; k > 7; --k) {
+    if ((rc = eval(false, 1 << k, &c))) return rc;
+    if (c.per_sm >= best.per_sm && c.per_sm > 0) {
+      *out = c;
+      return 0;
+    }
+  }
+  *out = best;
+  return 0;
+}
+
 // Launch the beam over `nq` work items (shared-memory pass), then the
 // overflow list on global scratch.  `a` carries everything but the scratch.
 int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStream_t s,
@@ -235,20 +299,14 @@ int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStrea
   const int S = pool_slots(a.ef);
   BeamKernelFn kern = beam_kernel_for(ix->L.metric, ix->L.G, ix->L.K, S);
   if (!kern) return fail(FGRAFT_EINVAL, "no beam kernel for this metric and dimension");
-  const int ecap = 1 << std::max(6, ceil_log2(2 * 32 * S));
-  const int nslots = 1 << ix->hash_log2;
-  // an n-bit bitmap is exact and never overflows; use it when it is no
-  // larger than the hash would be
-  const int64_t bm_bytes = ((ix->L.n + 127) / 128) * 16;
-  const bool bitmap = ix->bitmap_ok && bm_bytes <= 4ll * nslots;
-  const int vis_bytes = bitmap ? (int)bm_bytes : 4 * nslots;
+  BeamShape sh;
+  int rc = beam_shape(ix, kern, S, &sh);
+  if (rc) return rc;
+  const int ecap = sh.ecap, nslots = sh.nslots, vis_bytes = sh.vis_bytes, wbytes = sh.wbytes;
+  const bool bitmap = sh.bitmap;
   const int qbytes = 16 * ix->L.nchunks;  // staged query (then c* in the prune)
-  const int alive_bytes = (ecap / 8 + 15) / 16 * 16;  // kept a multiple of 16 (see beam.cuh)
-  const int wbytes = vis_bytes + 8 * ecap + alive_bytes + 256 + qbytes;
   const int smem = wbytes * ix->wpc;
-  FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(kern), smem));
-  int per_sm = 0;
-  FG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ix->wpc * 32, smem));
+  const int per_sm = sh.per_sm;
   if (per_sm < 1) return fail(FGRAFT_EINVAL, "harvest launch does not fit an SM");
   a.counters = ctr;
   a.work = ix->work;
@@ -256,7 +314,7 @@ int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStrea
   a.ovf_count = ix->work + 2;
   a.ovf_cap = (uint32_t)ix->ovf_cap;
   a.err_flag = ix->work + 3;
-  a.hash_log2 = ix->hash_log2;
+  a.hash_log2 = ceil_log2(std::max(nslots, 1 << 7));
   a.bitmap = bitmap ? 1 : 0;
   a.vis_bytes = vis_bytes;
   a.vis_cap = bitmap ? INT32_MAX : (int32_t)(0.8 * nslots) - 32;
@@ -270,8 +328,6 @@ int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStrea
   a.wbytes = wbytes;
   a.qbytes = qbytes;
   a.global_scratch = 0;
-  a.qlist = nullptr;
-  a.qlist_len = nullptr;
   // the per-warp layout must be complete before any launch
   if (a.wbytes < a.vis_bytes + 8 * a.ecap + 256 + a.qbytes || a.qbytes < 16 * ix->L.nchunks)
     return fail(FGRAFT_EINVAL, "internal: harvest shared-memory layout incomplete");
@@ -312,21 +368,13 @@ int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStrea
 // tuning (and for the re-run pass).  Not called during stream capture.
 int size_visited_bitmaps(fgraft_index* ix) {
   int64_t need = ix->g_warps;
-  const int nslots = 1 << ix->hash_log2;
-  const int64_t bm_bytes = ((ix->L.n + 127) / 128) * 16;
   for (int S = 1; S <= 4; S *= 2) {
     BeamKernelFn kern = beam_kernel_for(ix->L.metric, ix->L.G, ix->L.K, S);
     if (!kern) continue;
-    const int ecap = 1 << std::max(6, ceil_log2(2 * 32 * S));
-    const bool bitmap = ix->bitmap_ok && bm_bytes <= 4ll * nslots;
-    const int vis_bytes = bitmap ? (int)bm_bytes : 4 * nslots;
-    const int wbytes =
-        vis_bytes + 8 * ecap + (ecap / 8 + 15) / 16 * 16 + 256 + 16 * ix->L.nchunks;
-    FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(kern), wbytes * ix->wpc));
-    int per_sm = 0;
-    FG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ix->wpc * 32,
-                                                          wbytes * ix->wpc));
-    need = std::max<int64_t>(need, (int64_t)per_sm * ix->num_sms * ix->wpc);
+    BeamShape sh;
+    const int rc = beam_shape(ix, kern, S, &sh);
+    if (rc) return rc;
+    need = std::max<int64_t>(need, (int64_t)sh.per_sm * ix->num_sms * ix->wpc);
   }
   if (need <= ix->gvbits_warps) return 0;
   if (ix->gvbits) cudaFree(ix->gvbits);
@@ -413,7 +461,7 @@ void free_index(fgraft_index* ix) {
   void* ptrs[] = {ix->roots, ix->parents, ix->s_off, ix->s_ids, ix->A,   ix->cnt,
                   ix->r_off, ix->r_ids,   ix->rcnt,  ix->rcur,  ix->f_off, ix->f_ids,
                   ix->scan_tmp, ix->work, ix->ovf_list, ix->gscratch, ix->ctr, ix->gvbits,
-                  ix->Eg, ix->Eg_cnt};
+                  ix->Eg, ix->Eg_cnt, ix->pre, ix->qorder};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete ix;
@@ -440,6 +488,10 @@ int harvest_block_impl(fgraft_index* ix, int32_t b, cudaStream_t s) {
   a.nq = (ix->L.n - b + ix->nb - 1) / ix->nb;
   a.q_first = b;
   a.q_step = ix->nb;
+  if (ix->qorder) {  // block b's searches in tree-0 preorder; blocks before b hold b*q + min(b, r)
+    const int64_t q = ix->L.n / ix->nb, r = ix->L.n % ix->nb;
+    a.qlist = ix->qorder + (int64_t)b * q + std::min<int64_t>(b, r);
+  }
   a.ef = ix->p.ef_h;
   a.mode = 0;
   a.alpha2 = ix->p.alpha * ix->p.alpha;
@@ -644,6 +696,26 @@ fgraft_status fgraft_build_scaffold(const void* X, int64_t n, int32_t d, int64_t
   if (deg) cudaFreeAsync(deg, s);
   if (tmp_off) cudaFreeAsync(tmp_off, s);
   if (tmp_ids) cudaFreeAsync(tmp_ids, s);
+  // coherent harvest schedule from tree 0 (the rows do not depend on it)
+  bool coherent = g_coherent == 1;
+  if (g_coherent == 2) {  // auto: only when the vectors do not fit in the L2 cache
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    coherent = n * L.ld_bytes > (int64_t)l2;
+  }
+  if (!rc && coherent) {
+    rc = rc ? rc : dalloc(&ix->pre, n);
+    rc = rc ? rc : dalloc(&ix->qorder, n);
+    bool ok = false;
+    if (!rc)
+      rc = coherent_schedule(n, ix->parents, ix->nb, kCoherentMaxDepth, ix->pre, ix->qorder, s,
+                             &ok);
+    if (!rc && !ok) {
+      cudaFree(ix->pre);
+      cudaFree(ix->qorder);
+      ix->pre = ix->qorder = nullptr;
+    }
+  }
   cudaStreamSynchronize(s);
   if (rc) {
     free_index(ix);
@@ -935,6 +1007,7 @@ fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t war
   if (hash_log2) {
     ix->hash_log2 = hash_log2;
     ix->bitmap_ok = false;  // an explicit hash size selects the hash
+    ix->hash_auto = false;
   }
   if (warps_per_cta) ix->wpc = warps_per_cta;
   const int rc = size_visited_bitmaps(ix);
@@ -998,6 +1071,25 @@ fgraft_status fgraft_tune_prune(int32_t tensor_cores) {
 fgraft_status fgraft_tune_scaffold_cap(int32_t cap) {
   if (cap < 0) return (fgraft_status)fail(FGRAFT_EINVAL, "cap must be >= 0");
   g_scaffold_cap = cap;
+  return FGRAFT_OK;
+}
+
+fgraft_status fgraft_tune_schedule(int32_t coherent) {
+  if (coherent < 0 || coherent > 2) return (fgraft_status)fail(FGRAFT_EINVAL, "coherent must be 0, 1 or 2");
+  g_coherent = coherent;
+  return FGRAFT_OK;
+}
+
+fgraft_status fgraft_index_schedule(const fgraft_index* ix, int32_t* pre, int32_t* qorder,
+                                    int32_t* coherent, fgraft_stream stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!ix) return (fgraft_status)fail(FGRAFT_EINVAL, "index is NULL");
+  if (coherent) *coherent = ix->qorder ? 1 : 0;
+  const int64_t n = ix->L.n;
+  if (pre && ix->pre)
+    FGS(cudaMemcpyAsync(pre, ix->pre, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  if (qorder && ix->qorder)
+    FGS(cudaMemcpyAsync(qorder, ix->qorder, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
   return FGRAFT_OK;
 }
 

@@ -130,6 +130,16 @@ extern int g_prune_tc;
 // The same for the SAT's closest-child assignment.
 extern int g_sat_tc;
 
+// Coherent harvest schedule (Section 5.5): pre[v] = the place of v in a
+// preorder of the tree given by parent (-1 at its root; siblings in no fixed
+// order), qorder = for blocks b = 0..nb-1 one after another, the query
+// indices i of the points b + i * nb of block b in preorder.  Sets *ok =
+// false and writes neither output when nb > 64, parent is not a forest, or
+// it is deeper than max_depth (one launch per depth).
+int coherent_schedule(int64_t n, const int32_t* parent, int nb, int max_depth, int32_t* pre,
+                      int32_t* qorder, cudaStream_t s, bool* ok);
+extern int g_coherent;
+
 // Dense-block top-k with the BF16 or FP8 tensor-core filter and canonical
 // rerank; stats (host, optional): rerank fraction, Gram ms, select ms, prep
 // ms, and with err64 the float64 error maxima over the reranked pairs.

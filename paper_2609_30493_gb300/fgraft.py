@@ -43,7 +43,8 @@ EXPORTS = ["fgraft_build_scaffold", "fgraft_harvest_block", "fgraft_harvest_all"
            "fgraft_index_sizes", "fgraft_index_counters", "fgraft_index_tune",
            "fgraft_index_profile", "fgraft_index_harvest_ms", "fgraft_kernel_launches",
            "fgraft_tune_sat", "fgraft_tune_prune", "fgraft_prune_lists_noalloc",
-           "fgraft_harvest_block_multi", "fgraft_tune_scaffold_cap",
+           "fgraft_harvest_block_multi", "fgraft_tune_scaffold_cap", "fgraft_tune_schedule",
+           "fgraft_index_schedule",
            "fgraft_index_destroy", "fgraft_last_error"]
 
 
@@ -209,6 +210,23 @@ def fgraft_tune_prune(tensor_cores: bool = True):
 
 def fgraft_tune_scaffold_cap(cap: int = 0):
     _check(load().fgraft_tune_scaffold_cap(C.c_int32(cap)))
+
+
+def fgraft_tune_schedule(coherent=2):
+    """0 / False: id order; 1 / True: tree-0 preorder; 2: preorder when X exceeds L2."""
+    _check(load().fgraft_tune_schedule(C.c_int32(int(coherent))))
+
+
+def fgraft_index_schedule(ix: Index):
+    """(pre, qorder) int32 CUDA tensors of the coherent harvest schedule, or None when
+    the index runs its searches in id order."""
+    n = ix.X.shape[0]
+    pre = torch.empty(n, dtype=torch.int32, device=ix.X.device)
+    qorder = torch.empty(n, dtype=torch.int32, device=ix.X.device)
+    coh = C.c_int32()
+    _check(load().fgraft_index_schedule(ix.handle, _ptr(pre), _ptr(qorder), C.byref(coh),
+                                        _stream(ix.X.device)))
+    return (pre, qorder) if coh.value else None
 
 
 def fgraft_tune_sat(big_node_min: int = 0, finish_len: int = 0):

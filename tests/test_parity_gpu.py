@@ -313,3 +313,121 @@ def test_scaffold_cap_parity(fg, kind, cap):
         fg.fgraft_tune_scaffold_cap(0)
     assert int(np.diff(_np(st["s_off"])).max()) <= cap
     _compare(ctr, st, fin, ref)
+
+
+def _check_preorder(parent, pre):
+    # pre is a preorder of the tree: a permutation in which every subtree
+    # occupies one contiguous range that starts at its root
+    n = parent.size
+    assert np.array_equal(np.sort(pre), np.arange(n))
+    kids = [[] for _ in range(n)]
+    roots = []
+    for v, u in enumerate(parent.tolist()):
+        (roots if u < 0 else kids[u]).append(v)
+    order, k = list(roots), 0
+    while k < len(order):
+        order.extend(kids[order[k]])
+        k += 1
+    assert len(order) == n
+    size = np.ones(n, dtype=np.int64)
+    for v in reversed(order):
+        if parent[v] >= 0:
+            size[parent[v]] += size[v]
+    u = parent[parent >= 0]
+    v = np.flatnonzero(parent >= 0)
+    assert (pre[u] < pre[v]).all()
+    assert (pre[v] + size[v] <= pre[u] + size[u]).all()
+
+
+@pytest.mark.parametrize("B", [1, 8, 64])
+def test_coherent_schedule_is_tree0_preorder(fg, B):
+    # the harvest claims each block's searches in a preorder of tree 0
+    ps = synth.vmf_like(20000, 100, 32, seed=21)
+    X = _dev(ps.X)
+    try:
+        fg.fgraft_tune_schedule(1)
+        ix = fg.fgraft_build_scaffold(X, 100, fg.Params(T=4, R=16, ef_h=32, B=B, alpha=1.2,
+                                                        metric=fg.ANGULAR_F32))
+    finally:
+        fg.fgraft_tune_schedule(2)
+    sched = fg.fgraft_index_schedule(ix)
+    assert sched is not None
+    pre, qorder = _np(sched[0]), _np(sched[1])
+    n = ps.X.shape[0]
+    parent0 = _np(fg.fgraft_index_copy(ix)["parents"]).reshape(-1)[:n]
+    _check_preorder(parent0, pre)
+    start = 0
+    for b in range(B):
+        pts = np.arange(b, n, B)
+        want = (pts[np.argsort(pre[pts], kind="stable")] - b) // B
+        assert np.array_equal(qorder[start:start + pts.size], want), b
+        start += pts.size
+    assert start == n
+
+
+def test_coherent_schedule_same_graph(fg):
+    # the schedule moves work, never results: id order and tree-0 preorder
+    # give the same rows, counters and final graph
+    ps = synth.vmf_like(20000, 100, 32, seed=22)
+    X = _dev(ps.X)
+    out = []
+    try:
+        for coherent in (False, True):
+            fg.fgraft_tune_schedule(coherent)
+            p = fg.Params(T=8, R=32, ef_h=64, B=8, alpha=1.2, metric=fg.ANGULAR_F32)
+            ix = fg.fgraft_build_scaffold(X, 100, p)
+            assert (fg.fgraft_index_schedule(ix) is not None) == coherent
+            ctr = fg.fgraft_harvest_all(ix, use_graph=True, counters=True)
+            st = fg.fgraft_index_copy(ix)
+            out.append((ctr, st["rows"], st["counts"], *fg.fgraft_prune(ix)))
+    finally:
+        fg.fgraft_tune_schedule(2)
+    a, b = out
+    assert a[0] == b[0]
+    for x, y in zip(a[1:], b[1:]):
+        assert torch.equal(x, y)
+
+
+def test_many_blocks_fall_back_to_id_order(fg):
+    # more than 64 blocks: searches in id order, same parity with the oracle
+    ps = synth.gaussian_mixture(1500, 16, 4, seed=23)
+    try:
+        fg.fgraft_tune_schedule(1)
+        ix, ctr, st, fin, D, ref = _build_both(fg, ps, T=4, R=16, ef=32, B=100)
+    finally:
+        fg.fgraft_tune_schedule(2)
+    assert fg.fgraft_index_schedule(ix) is None
+    _compare(ctr, st, fin, ref)
+    with pytest.raises(fg.FgraftError, match="EINVAL"):
+        fg.fgraft_tune_schedule(3)
+
+
+def test_schedule_auto_by_size(fg):
+    # the default picks the preorder only for vectors larger than the L2 cache
+    ps = synth.gaussian_mixture(3000, 16, 4, seed=24)
+    ix = fg.fgraft_build_scaffold(_dev(ps.X), 16, fg.Params(T=4, R=16, ef_h=32, B=4,
+                                                            alpha=1.2, metric=fg.L2_F32))
+    assert fg.fgraft_index_schedule(ix) is None
+
+
+def test_auto_visited_layout_same_graph(fg):
+    # at n = 200,000 the automatic layout takes a hash smaller than 2^12
+    # slots (more searches in flight, more of them continuing in the global
+    # bitmap); the rows and counters equal those of the explicit 2^12 hash
+    ps = synth.vmf_like(200_000, 100, 64, seed=25)
+    X = _dev(ps.X)
+    out = []
+    for hl2 in (0, 12):
+        p = fg.Params(T=8, R=32, ef_h=64, B=4, alpha=1.2, metric=fg.ANGULAR_F32)
+        ix = fg.fgraft_build_scaffold(X, 100, p)
+        if hl2:
+            fg.fgraft_index_tune(ix, hash_log2=hl2)
+        ctr = fg.fgraft_harvest_all(ix, use_graph=True, counters=True)
+        st = fg.fgraft_index_copy(ix)
+        out.append((ctr, st["rows"], st["counts"], *fg.fgraft_prune(ix)))
+        del ix
+    a, b = out
+    for k in ("harvest_evals", "prune_evals", "expansions", "final_prune_evals"):
+        assert a[0][k] == b[0][k], k
+    for x, y in zip(a[1:], b[1:]):
+        assert torch.equal(x, y)
