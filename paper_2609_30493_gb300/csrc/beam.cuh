@@ -436,7 +436,7 @@ struct Beam {
 };
 
 template <int METRIC, int G, int K, int S>
-__global__ void __launch_bounds__(128, METRIC == L2_U8 ? 1 : 4) beam_kernel(const BeamArgs a) {
+__global__ void __launch_bounds__(128, 4) beam_kernel(const BeamArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   Beam<METRIC, G, K, S>::run(a, smem);
 }
