@@ -201,16 +201,18 @@ struct Beam {
       int len0 = a.T, len1 = 0, len2 = 0;
       for (;;) {
         const int total = len0 + len1 + len2;
+        // the ids of the next chunk of 32 are loaded before this chunk is
+        // processed, so their latency overlaps its visited inserts and merge
+        auto load_id = [&](int i) -> int32_t {
+          if (i < len0) return sp0[i];
+          if (i < len0 + len1) return sp1[i - len0];
+          if (i < total) return sp2[i - len0 - len1];
+          return -1;
+        };
+        int32_t v_next = load_id(lane);
         for (int base = 0; base < total; base += 32) {
-          const int i = base + lane;
-          int32_t v = -1;
-          if (i < len0) {
-            v = sp0[i];
-          } else if (i < len0 + len1) {
-            v = sp1[i - len0];
-          } else if (i < total) {
-            v = sp2[i - len0 - len1];
-          }
+          const int32_t v = v_next;
+          if (base + 32 < total) v_next = load_id(base + 32 + lane);
           bool isnew = false;
           if (v >= 0) {
             if (bm) {
