@@ -450,20 +450,20 @@ def run_ours(args):
         "clocks": clk,
     }
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(ps, spec)
+        out["cpu_baseline"] = cpu_baselines(ps, spec)
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def cpu_baseline(ps, spec, sample_n=CPU_SAMPLE_N, seed=7):
+def cpu_baseline(ps, spec, sample_n=CPU_SAMPLE_N, seed=7, nthreads=None):
     """The oracle, as it stands, on a random subset of the workload's points."""
     import oracle
     rng = np.random.default_rng(seed)
     sel = np.sort(rng.choice(ps.n, size=min(sample_n, ps.n), replace=False))
     Xs = np.ascontiguousarray(ps.X[sel])
     D = oracle.Data(Xs, spec["d"], 1)
-    cores = os.cpu_count() or 1
+    cores = nthreads or os.cpu_count() or 1
     t0 = time.perf_counter()
     oracle.build_graph(D, spec["T"], spec["R"], spec["ef_h"], spec["B"], spec["alpha"],
                        spec["seed"], nthreads=cores)
@@ -472,6 +472,15 @@ def cpu_baseline(ps, spec, sample_n=CPU_SAMPLE_N, seed=7):
             "sample": f"oracle FGraft build (SAT forest, scaffold, {spec['B']} blocks, final graph) "
                       f"of a seeded {len(sel)}-point subset of the workload, same T/R/ef_h/B/alpha",
             "seconds": round(dt, 2)}
+
+
+def cpu_baselines(ps, spec):
+    """The oracle on all host cores (the reported baseline) and on one core (a
+    smaller subset, so that the bench stays within minutes)."""
+    out = cpu_baseline(ps, spec)
+    one = cpu_baseline(ps, spec, sample_n=CPU_SAMPLE_N // 4, seed=8, nthreads=1)
+    out["single_thread"] = {k: one[k] for k in ("value", "unit", "cores", "sample", "seconds")}
+    return out
 
 
 def run_reference(args):
