@@ -29,8 +29,10 @@ def _worker(rank, world, port, out):
 
 def test_job_rate_two_ranks():
     port = _free_port()
-    out = mp.Manager().dict()
-    mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
+    with mp.Manager() as mgr:
+        shared = mgr.dict()
+        mp.spawn(_worker, args=(2, port, shared), nprocs=2, join=True)
+        out = dict(shared)
     for r in range(2):
         ms, value = out[r]
         assert ms == pytest.approx(250.0 / 5)
