@@ -8,6 +8,8 @@ CPU-baseline leg of ``bench.py`` may import this package; the CUDA library
 never calls it, and this package imports nothing from the CUDA path.
 
 Parity status of each function (what pins it, see ``tests/test_oracle_*``):
+  splitmix64 / roots  pinned: SplitMix64's published reference outputs for
+                      state 0; roots distinct and keyed.
   dist / dist_f64     pinned: exact on integer-valued inputs, within the
                       gamma_d rounding bound of the float64 value otherwise,
                       uint8 exact, symmetric.
@@ -25,8 +27,14 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*``):
   fgraft              pinned: B = 0 and B = 1 give the frozen harvest, the
                       graph is identical at 1 and N threads, S_b grows
                       monotonically, rows hold at most R ids and never p.
-  final               pinned: rows contain the tree-0 spine, are sorted, the
-                      over-degree rows obey the prune invariants.
+  final               pinned: a hand-worked fixture (an over-degree row whose
+                      prune removes a candidate the tree-0 spine adds back,
+                      rows of exactly R, the work count); every row contains
+                      the spine and is sorted; a row with at most R
+                      candidates is C(u) with the spine; an over-degree row
+                      minus its spine-only vertices equals a plain-Python
+                      prune of C(u) and obeys the prune invariants; the work
+                      counter equals its definition.
   search              pinned: equals brute force when ef >= n.
   bruteforce          pinned: equals a float64 numpy sort up to rounding ties.
   dense_block         pinned: equals the brute-force sort of the same block.

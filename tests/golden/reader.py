@@ -23,6 +23,8 @@ def load(name):
                 edges.append((int(rest[0]), int(rest[1])))
             elif key == "case":
                 cases.append(dict(kv.split("=") for kv in rest))
+            elif key == "arow":
+                out.setdefault("arows", {})[int(rest[0])] = [int(v) for v in rest[1:]]
             elif key in ("query", "cand"):
                 out[key] = [float(v) for v in rest]
             elif key == "alpha":

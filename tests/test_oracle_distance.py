@@ -138,3 +138,14 @@ def test_splitmix64_is_a_bijective_mixer():
     outs = {oracle.splitmix64(z) for z in range(4096)}
     assert len(outs) == 4096
     assert oracle.splitmix64(0) != 0
+
+
+def test_splitmix64_reference_outputs():
+    # The reference sequence of SplitMix64 (Steele, Lea and Flood, OOPSLA
+    # 2014) seeded with 0: its first two outputs are 0xE220A8397B1DCDAF and
+    # 0x6E789E6AA1B965F4.  The generator advances its state by the
+    # golden-ratio increment before mixing, so the second output is the first
+    # output of the generator started at that increment.  A wrong constant,
+    # shift or multiplier changes both.
+    assert oracle.splitmix64(0) == 0xE220A8397B1DCDAF
+    assert oracle.splitmix64(0x9E3779B97F4A7C15) == 0x6E789E6AA1B965F4

@@ -8,8 +8,14 @@ reproduces Graft); the graph is identical at 1 and N threads
 prune of a beam over S_b rebuilt here from the rows of earlier blocks only
 (a row of the same or a later block leaking into S_b fails this); rows hold
 at most R distinct ids and never the point itself.
-Final graph: contains the tree-0 spine; sorted by (delta, id); a row that
-needed no prune is exactly C(u).
+Final graph: a hand-worked fixture (an over-degree row whose prune removes a
+candidate that the tree-0 spine adds back, rows of exactly R candidates, the
+work count); on the tiny workload every row contains the tree-0 spine and is
+sorted by (delta, id), a row that needed no prune is exactly C(u) with the
+spine, and an over-degree row minus its spine-only vertices equals a prune
+of C(u) restated here in plain Python, which passes the prune invariants;
+the work counter equals |C(u) U spine(u)| summed plus those prunes' removal
+passes.
 Search: equals brute force at full width.  Brute force: agrees with a float64
 numpy sort wherever the float64 gap exceeds the rounding bound.
 Dense block: the float32 top-k equals the float64 top-k up to rank swaps
@@ -19,7 +25,9 @@ import numpy as np
 import pytest
 
 import oracle
+from golden import reader
 from paper_2609_30493_gb300 import synth
+from test_oracle_beam_prune import _check_prune
 
 
 @pytest.fixture(scope="module")
@@ -70,11 +78,55 @@ def test_blocks_see_only_earlier_rows(tiny):
         assert p not in row and len(set(row.tolist())) == len(row)
 
 
+def _prune_py(D, p, cand, alpha, R):
+    """Section 3's occlusion prune in plain Python (independent of the C
+    oracle's prune): candidates minus p, deduplicated, sorted by
+    (delta(p, c), id); keep the first alive c*, remove each alive c after it
+    with fl(alpha^2 * delta(c*, c)) <= delta(p, c); stop at R kept.  Returns
+    (kept ids, candidates examined in the removal passes)."""
+    a2 = np.float32(np.float32(alpha) * np.float32(alpha))
+    C = sorted({int(c) for c in cand if int(c) != p}, key=lambda c: (oracle.dist(D, p, c), c))
+    dp = [np.float32(oracle.dist(D, p, c)) for c in C]
+    alive = [True] * len(C)
+    kept, ev = [], 0
+    for i, c in enumerate(C):
+        if not alive[i]:
+            continue
+        kept.append(c)
+        alive[i] = False
+        if len(kept) == R:
+            break
+        for j in range(i + 1, len(C)):
+            if alive[j]:
+                ev += 1
+                if np.float32(a2 * np.float32(oracle.dist(D, c, C[j]))) <= dp[j]:
+                    alive[j] = False
+    return kept, ev
+
+
+@pytest.mark.parametrize("R", [2, 3])
+def test_final_golden(R):
+    g = reader.load("final_spine.txt")
+    D = oracle.Data(g["X"], g["d"], g["metric"])
+    n = len(g["X"])
+    A = np.full((n, R), -1, np.int32)
+    cnt = np.zeros(n, np.int32)
+    for p, row in g["arows"].items():
+        A[p, :len(row)] = row
+        cnt[p] = len(row)
+    parent0 = np.array([g["parents"][i] for i in range(n)], np.int32)
+    case = next(c for c in g["cases"] if int(c["R"]) == R)
+    off, ids, ev = oracle.final(D, A, cnt, R, g["alpha"], parent0)
+    for u in range(n):
+        assert ids[off[u]:off[u + 1]].tolist() == [int(v) for v in case[f"row{u}"].split(",")]
+    assert ev == int(case["evals"])
+
+
 def test_final_graph(tiny):
     ps, D, rts, parents, s_off, s_ids = tiny
-    R = 16
-    A, cnt, ctr, per = oracle.fgraft(D, rts, s_off, s_ids, R, 32, 4, 1.2)
-    off, ids, ev = oracle.final(D, A, cnt, R, 1.2, parents[0])
+    R, alpha = 16, 1.2
+    A, cnt, ctr, per = oracle.fgraft(D, rts, s_off, s_ids, R, 32, 4, alpha)
+    off, ids, ev = oracle.final(D, A, cnt, R, alpha, parents[0])
     n = 2000
     cand = [set() for _ in range(n)]
     for p in range(n):
@@ -86,16 +138,24 @@ def test_final_graph(tiny):
         if parents[0, x] >= 0:
             spine[x].add(int(parents[0, x]))
             spine[int(parents[0, x])].add(x)
+    work, over = 0, 0
     for u in range(n):
         row = ids[off[u]:off[u + 1]].tolist()
         assert len(set(row)) == len(row)
         assert spine[u] <= set(row)
         keys = [(oracle.dist(D, u, v), v) for v in row]
         assert keys == sorted(keys)
+        work += len(cand[u] | spine[u])
         if len(cand[u]) <= R:
             assert set(row) == cand[u] | spine[u]
         else:
-            assert len(set(row) - spine[u]) <= R
+            over += 1
+            kept, pev = _prune_py(D, u, sorted(cand[u]), alpha, R)
+            work += pev
+            assert set(row) - (spine[u] - set(kept)) == set(kept)
+            _check_prune(D, u, sorted(cand[u]), alpha, R, kept)
+    assert over > 50  # the over-degree branch is exercised
+    assert ev == work
 
 
 def test_search_full_width_equals_bruteforce(tiny):
