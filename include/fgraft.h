@@ -53,7 +53,12 @@ typedef enum {
   FGRAFT_ENOMEM = 2,    /* a device allocation failed */
   FGRAFT_ECUDA = 3,     /* a CUDA runtime call failed (message has the CUDA error) */
   FGRAFT_EOVERFLOW = 4, /* an output capacity was too small, or a search outgrew its scratch */
-  FGRAFT_ETIMEOUT = 5   /* reserved: a bounded device wait gave up */
+  FGRAFT_ETIMEOUT = 5   /* a tensor-core kernel's bounded wait for its MMA
+                           products gave up (see fgraft_tune_mma_wait); the
+                           kernel drained its products in flight, freed its
+                           tensor memory and returned, so the CUDA context
+                           stays usable; the outputs of that call (and of an
+                           index's blocks harvested since) are unspecified */
 } fgraft_status;
 
 typedef enum { FGRAFT_L2_F32 = 0, FGRAFT_ANGULAR_F32 = 1, FGRAFT_L2_U8 = 2 } fgraft_metric;
@@ -161,28 +166,32 @@ fgraft_status fgraft_prune(fgraft_index* ix, fgraft_stream stream, fgraft_counte
  * cand_off[i+1]); the owner itself and repeated ids are dropped, the rest is
  * sorted by (delta(owner, c), id) and pruned with alpha to at most R kept
  * ids, written to out_ids[i*R ..] (-1 padded) with the count in out_cnt[i].
- * X as in fgraft_build_scaffold.  Lists longer than 4096 candidates return
- * EINVAL. */
+ * X as in fgraft_build_scaffold.  Lists of any length are accepted; the
+ * scratch is allocated stream-ordered for the longest one. */
 fgraft_status fgraft_prune_lists(const void* X, int64_t n, int32_t d, int64_t ld, int32_t metric,
                                  const int32_t* owner, const int64_t* cand_off,
                                  const int32_t* cand_ids, int64_t nlists, float alpha, int32_t R,
                                  int32_t* out_ids, int32_t* out_cnt, fgraft_stream stream);
 
-/* The list prune above, for callers that cannot allocate device memory when
- * they need it: code running while a stream is captured into a CUDA graph,
- * serving loops that must never wait on or fail in the allocator, and hosts
- * whose device memory is already owned by their own pool.  The paper has no
- * counterpart: this is a property of the library, not of the method.
+/* The list prune above, for callers that cannot allocate device memory at
+ * the moment they prune: a serving loop whose latency budget has no room for
+ * an allocator call (or for its failure under memory pressure), and a host
+ * application that has already handed all device memory to its own pool
+ * allocator.  The paper has no counterpart: this is a property of the
+ * library, not of the method.
  * Same arguments and results as fgraft_prune_lists, with fixed limits:
  * nlists <= 65536 (EINVAL otherwise, before any work) and at most 4096
- * candidates per list (EINVAL after the call; rows of such lists are then
- * unspecified).  The scratch is one file-scope device array of about 2.4 MiB
- * that every device loading the library keeps until the process exits.  The
- * first call on a device looks up that array's address (make it before any
- * stream capture); every call clears what must start at zero, and calls
- * whose work overlaps on the GPU race on the shared array.  The call
- * synchronises `stream` before returning (to report over-long lists).
- * It calls no cudaMalloc, cudaFree or allocating library routine. */
+ * candidates per list, counted before the owner and repeats are dropped
+ * (EINVAL after the call; the rows of such lists are then unspecified, the
+ * other rows are correct).  The scratch is one file-scope device array of
+ * about 2.4 MiB that every device loading the library keeps until the
+ * process exits.  The first call on a device looks up that array's device
+ * address once (cudaGetSymbolAddress).  Every call shares the array and it
+ * keeps the last call's contents: each call clears what must start at zero,
+ * and calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it.  The call synchronises `stream` before returning, to
+ * report over-long lists.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine. */
 fgraft_status fgraft_prune_lists_noalloc(const void* X, int64_t n, int32_t d, int64_t ld,
                                          int32_t metric, const int32_t* owner,
                                          const int64_t* cand_off, const int32_t* cand_ids,
@@ -279,6 +288,20 @@ fgraft_status fgraft_tune_prune(int32_t tensor_cores);
  * entry roots are unchanged.  0 (the default) turns it off.  The distances
  * the cap evaluates are not in any counter.  FGRAFT_EINVAL for cap < 0. */
 fgraft_status fgraft_tune_scaffold_cap(int32_t cap);
+
+/* Failure handling (tuning and tests; results do not depend on it unless a
+ * wait gives up).  Every kernel that waits on the tensor cores (the TF32
+ * prune of Section 3, the SAT's closest-child choice of Section 1, the dense
+ * blocks of Section 5.3) polls its MMA-completion barrier at most `polls`
+ * times before it gives up, sets an error flag, waits for its products in
+ * flight with the full bound (2^22 polls), frees its tensor memory and
+ * returns; the call that reads the flag returns FGRAFT_ETIMEOUT
+ * (fgraft_build_scaffold, fgraft_harvest_block with counters, fgraft_prune,
+ * fgraft_index_counters, fgraft_dense_block_dist).  polls = 0 gives up at
+ * the first wait, which tests that path without a fault; -1 restores the
+ * default of 2^22 polls.  Applies to later launches in this process.
+ * FGRAFT_EINVAL for polls < -1. */
+fgraft_status fgraft_tune_mma_wait(int32_t polls);
 
 /* SAT launch configuration for later fgraft_build_scaffold calls in this
  * process (tuning; results do not depend on it): tree nodes holding at least

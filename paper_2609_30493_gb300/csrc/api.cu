@@ -43,6 +43,18 @@ cudaError_t raise_smem_limit(const void* fn, int bytes) {
   return e;
 }
 
+int device_sms() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
+    return 1;
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
 int cuda_fail(cudaError_t e, const char* what) {
   set_error(FGRAFT_ECUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
                               cudaGetErrorString(e) + ")");
@@ -102,6 +114,7 @@ static void keyed_roots(uint64_t seed, int T, int64_t n, std::vector<int32_t>& r
 using namespace fg;
 
 // Nodes of at least this many points are built by the multi-CTA SAT path.
+int fg::g_mma_wait_polls = 1 << 22;
 static int32_t g_sat_big_min = 16384;
 static int32_t g_sat_finish_len = 512;
 static int32_t g_scaffold_cap = 0;  // 0: no degree cap
@@ -395,7 +408,7 @@ int check_err_flag(fgraft_index* ix, cudaStream_t s) {
   FG_CUDA(cudaMemcpyAsync(f, ix->work + 3, sizeof(f), cudaMemcpyDeviceToHost, s));
   FG_CUDA(cudaStreamSynchronize(s));
   if (f[0]) return fail(FGRAFT_EOVERFLOW, "a search outgrew its global-memory scratch");
-  if (f[1]) return fail(FGRAFT_ECUDA, "a tensor-core prune timed out waiting for its products");
+  if (f[1]) return fail(FGRAFT_ETIMEOUT, "a tensor-core prune timed out waiting for its products");
   return 0;
 }
 
@@ -1065,6 +1078,12 @@ fgraft_status fgraft_tune_prune(int32_t tensor_cores) {
     return (fgraft_status)fail(FGRAFT_EINVAL, "tensor_cores must be 0 or 1");
   g_prune_tc = tensor_cores;
   g_sat_tc = tensor_cores;
+  return FGRAFT_OK;
+}
+
+fgraft_status fgraft_tune_mma_wait(int32_t polls) {
+  if (polls < -1) return (fgraft_status)fail(FGRAFT_EINVAL, "polls must be >= -1");
+  g_mma_wait_polls = polls == -1 ? (1 << 22) : polls;
   return FGRAFT_OK;
 }
 

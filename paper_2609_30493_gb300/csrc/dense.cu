@@ -108,7 +108,7 @@ int dense_block(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs
   }
   DenseArgs a{L.X, L.ld_bytes, L.d, L.nchunks, block_ids, nb, bs, k, out_ids, out_dist};
   const int64_t rows = nb * bs;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, 152 * 16));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, (int64_t)device_sms() * 16));
   kern<<<grid, 256, 0, s>>>(a);
   note_launch();
   FG_CUDA(cudaGetLastError());

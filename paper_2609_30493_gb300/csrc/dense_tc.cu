@@ -63,6 +63,7 @@ struct TcArgs {
   uint32_t* err;  // [0] timeout flag, [8] and [9] error maxima (float bits)
   unsigned long long* pairs;  // valid ordered pairs over all blocks
   int32_t errstat;  // measure the filter's error against float64 on the reranked pairs
+  int32_t wait_polls;  // first bounded wait for a slice's products
 };
 
 __global__ void __launch_bounds__(256) dense_prep_kernel(const TcArgs a) {
@@ -199,11 +200,14 @@ __global__ void __launch_bounds__(TC_THREADS) dense_gram_kernel(const TcArgs a) 
     // wait (bounded) for the slice's products before its buffers are reused;
     // every thread takes the same decision
     bool done = false;
-    for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(bar, sl & 1);
+    for (int it = 0; it < a.wait_polls && !done; ++it) done = mbar_try_wait(bar, sl & 1);
     done = __syncthreads_and(done);
     if (!done) {
       ok = false;
       if (tid == 0) atomicOr(a.err, 1u);
+      // let the slice's products land before the tensor memory is released
+      for (int it = 0; it < kDrainPolls; ++it)
+        if (mbar_try_wait(bar, sl & 1)) break;
       break;
     }
     tc_fence_after();
@@ -393,6 +397,7 @@ int dense_block_tc(const VecLayout& L, const int32_t* block_ids, int64_t nb, int
   a.d = L.d;
   a.fp8 = fp8 ? 1 : 0;
   a.errstat = stats && err64 ? 1 : 0;
+  a.wait_polls = g_mma_wait_polls;
   const int slice = a.fp8 ? TC_KB : TC_KB / 2;  // elements per slice
   a.dpad = (L.d + slice - 1) / slice * slice;
   a.rowb = a.fp8 ? a.dpad : 2 * a.dpad;
@@ -457,7 +462,7 @@ int dense_block_tc(const VecLayout& L, const int32_t* block_ids, int64_t nb, int
     }
     const int64_t rows = nb * bs;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((rows + SEL_WARPS - 1) / SEL_WARPS,
-                                                                 152 * 16));
+                                                                 (int64_t)device_sms() * 16));
     sel<<<grid, SEL_WARPS * 32, ssm, s>>>(a, k, out_ids, out_dist, reranked);
     note_launch();
     if (stats) cudaEventRecord(ev[3], s);

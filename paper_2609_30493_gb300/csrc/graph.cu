@@ -95,7 +95,7 @@ __global__ void scan_apply_kernel(const uint32_t* in, int64_t* out, int64_t n,
 
 int scan_u32(const uint32_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStream_t s) {
   const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 152 * 8));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)device_sms() * 8));
   scan_tiles_kernel<<<grid, SCAN_THREADS, 0, s>>>(in, n, tmp);
   note_launch();
   scan_prefix_kernel<<<1, SCAN_THREADS, 0, s>>>(tmp, ntiles);
@@ -108,7 +108,7 @@ int scan_u32(const uint32_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStre
 
 static int grid1d(int64_t tot, int threads = 256) {
   int64_t g = (tot + threads - 1) / threads;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)device_sms() * 32));
 }
 
 // ---------------------------------------------------------------------------
@@ -878,9 +878,9 @@ int final_graph(const VecLayout& L, int R, float alpha2, const int32_t* A, const
   FG_TRY(cudaMemcpyAsync(&tc_err, def_count + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   FG_TRY(cudaStreamSynchronize(s));
   if (tc_err) {
-    set_error(3, "a tensor-core prune timed out waiting for its products");
+    set_error(5, "a tensor-core prune timed out waiting for its products");
     cleanup();
-    return 3;
+    return 5;
   }
   if (*f_ids) {
     cudaFree(*f_ids);
@@ -917,11 +917,10 @@ int prune_lists(const VecLayout& L, const int32_t* owner, const int64_t* l_off,
 // ---------------------------------------------------------------------------
 // List prune that allocates nothing.
 //
-// Some callers cannot call cudaMalloc at the moment they need a prune: code
-// that runs while a stream is being captured into a CUDA graph (allocation
-// calls are not allowed there), serving loops that must never enter the
-// allocator because an allocation can stall or fail under memory pressure,
-// and hosts that have already handed all device memory to their own pool.
+// Some callers cannot call cudaMalloc at the moment they need a prune:
+// serving loops that must never enter the allocator because an allocation
+// can stall or fail under memory pressure, and hosts that have already handed
+// all device memory to their own pool allocator.
 // For them the scratch of the list prune lives in one file-scope device
 // array, reserved when the library is loaded on a device and kept until the
 // process exits.  Its size fixes the limits: at most NA_MAX_LISTS lists per

@@ -46,6 +46,7 @@ struct HPruneArgs {
   float tc_e1;
   float tc_e0;
   uint32_t* err;
+  int32_t wait_polls;  // first bounded wait for the Gram matrix
 };
 
 constexpr int HP_WARPS = 4;
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(TCP_M) harvest_prune_tc_kernel(const HPruneArg
     }
     // wait (bounded) for the Gram matrix; every thread takes the same decision
     bool done = false;
-    for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(bar, phase);
+    for (int it = 0; it < a.wait_polls && !done; ++it) done = mbar_try_wait(bar, phase);
     done = __syncthreads_and(done);  // also publishes col
     if (!done) {
       ok = false;
@@ -438,7 +439,7 @@ __global__ void __launch_bounds__(TCP_M) harvest_prune_tc_kernel(const HPruneArg
   }
   if (!ok) {
     // let the products in flight land before the tensor memory is released
-    for (int it = 0; it < (1 << 22); ++it)
+    for (int it = 0; it < kDrainPolls; ++it)
       if (mbar_try_wait(bar, phase)) break;
   }
   tc_fence_before();
@@ -489,7 +490,8 @@ int harvest_prune(const VecLayout& L, const uint64_t* Eg, const int32_t* Eg_cnt,
   }
   HPruneArgs a{L.X, L.ld_bytes, L.d, L.nchunks, Eg, Eg_cnt, ecap,
                harvest_prune_smem(ecap, L.nchunks), nq, q_first, q_step, R, alpha2,
-               A_out, cnt_out, prune_ctr, rows, Eg_off, nq_dev, K_out, 0.0f, 0.0f, err};
+               A_out, cnt_out, prune_ctr, rows, Eg_off, nq_dev, K_out, 0.0f, 0.0f, err,
+               g_mma_wait_polls};
   int threads = HP_WARPS * 32;
   int max_per_sm = 1 << 20;
   HPruneFn tck = hprune_tc_kernel_for(L.metric, L.G, L.K);

@@ -129,6 +129,15 @@ int harvest_prune(const VecLayout& L, const uint64_t* Eg, const int32_t* Eg_cnt,
 extern int g_prune_tc;
 // The same for the SAT's closest-child assignment.
 extern int g_sat_tc;
+// Polls of the first bounded wait of a tensor-core CTA for its MMA products
+// (default 2^22).  When it gives up, the CTA sets its error flag, waits for
+// the products in flight with the full bound kDrainPolls, frees its tensor
+// memory and returns; the host reports FGRAFT_ETIMEOUT.
+extern int g_mma_wait_polls;
+// Streaming multiprocessors of the current device (cached per device; 1 if
+// the query fails).  Grid caps of the grid-stride kernels are multiples of it.
+int device_sms();
+constexpr int kDrainPolls = 1 << 22;
 
 // Coherent harvest schedule (Section 5.5): pre[v] = the place of v in a
 // preorder of the tree given by parent (-1 at its root; siblings in no fixed

@@ -32,7 +32,7 @@ constexpr int kMaxBlocks = 64;
 constexpr int kMaxRounds = 32;
 
 int grid_of(int64_t m) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>((m + kThreads - 1) / kThreads, 152 * 32));
+  return (int)std::max<int64_t>(1, std::min<int64_t>((m + kThreads - 1) / kThreads, (int64_t)device_sms() * 32));
 }
 
 __global__ void jump_init_kernel(int64_t n, const int32_t* parent, int32_t* anc, int32_t* dep) {

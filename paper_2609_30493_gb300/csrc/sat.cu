@@ -48,6 +48,7 @@ struct SatSegArgs {
   int32_t* node_of;
   int32_t* parent;
   unsigned long long* ctr;
+  int32_t wait_polls;  // first bounded wait of the tensor-core assignment
 };
 
 // Minimum of one key per thread over the CTA; rk[parity] is the scratch, and
@@ -551,7 +552,7 @@ __global__ void __launch_bounds__(AT_M)
     }
     if (tid < kn) nrb[tid] = tc_norm2(Bs, tid, NQ, nch);
     bool done = false;
-    for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(bar, phase);
+    for (int it = 0; it < a.wait_polls && !done; ++it) done = mbar_try_wait(bar, phase);
     done = __syncthreads_and(done);  // also publishes nrb
     if (!done) {
       ok = false;
@@ -598,7 +599,7 @@ __global__ void __launch_bounds__(AT_M)
   }
   if (ok && i < na) a.node_of[tbase + pt] = self ? -1 : key_id(best);
   if (!ok) {
-    for (int it = 0; it < (1 << 22); ++it)
+    for (int it = 0; it < kDrainPolls; ++it)
       if (mbar_try_wait(bar, phase)) break;
   }
   tc_fence_before();
@@ -858,7 +859,7 @@ __global__ void sat_scatter_kernel(int64_t n, int64_t tot, const int32_t* node_o
 
 static int grid_for(int64_t tot) {
   int64_t g = (tot + 255) / 256;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)device_sms() * 32));
 }
 
 int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* parents,
@@ -896,6 +897,7 @@ int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* paren
   a.ctr = ctr_sat;
   a.seg_off = 0;
   a.seg_k = nullptr;
+  a.wait_polls = g_mma_wait_polls;
   SatSegArgs at = a;
   a.seg_k = S.seg_k;
   const size_t smem = sat_smem_plan(a, SAT_SMEM);
@@ -962,8 +964,8 @@ int sat_forest(const VecLayout& L, int T, const int32_t* roots_d, int32_t* paren
       return 3;
     }
     if (cnts[4]) {
-      set_error(3, "SAT: a tensor-core assignment timed out waiting for its products");
-      return 3;
+      set_error(5, "SAT: a tensor-core assignment timed out waiting for its products");
+      return 5;
     }
     const uint32_t ntiny = cnts[0], nbig = cnts[1], nsmall = cnts[3];
     if (ntiny == 0 && nsmall == 0 && nbig == 0) return 0;

@@ -44,7 +44,7 @@ EXPORTS = ["fgraft_build_scaffold", "fgraft_harvest_block", "fgraft_harvest_all"
            "fgraft_index_profile", "fgraft_index_harvest_ms", "fgraft_kernel_launches",
            "fgraft_tune_sat", "fgraft_tune_prune", "fgraft_prune_lists_noalloc",
            "fgraft_harvest_block_multi", "fgraft_tune_scaffold_cap", "fgraft_tune_schedule",
-           "fgraft_index_schedule",
+           "fgraft_index_schedule", "fgraft_tune_mma_wait",
            "fgraft_index_destroy", "fgraft_last_error"]
 
 
@@ -208,6 +208,12 @@ def fgraft_tune_prune(tensor_cores: bool = True):
     _check(load().fgraft_tune_prune(C.c_int32(1 if tensor_cores else 0)))
 
 
+def fgraft_tune_mma_wait(polls: int = -1):
+    """Polls of a tensor-core kernel's first wait for its MMA products before it
+    gives up (0: at once, which tests the FGRAFT_ETIMEOUT path; -1: default)."""
+    _check(load().fgraft_tune_mma_wait(C.c_int32(polls)))
+
+
 def fgraft_tune_scaffold_cap(cap: int = 0):
     _check(load().fgraft_tune_scaffold_cap(C.c_int32(cap)))
 
@@ -285,12 +291,19 @@ def fgraft_prune_lists_noalloc(X: torch.Tensor, d: int, metric: int, owner: torc
                                cand_off: torch.Tensor, cand_ids: torch.Tensor, alpha: float, R: int,
                                out: torch.Tensor = None, cnt: torch.Tensor = None):
     """fgraft_prune_lists without any device allocation inside the library; the
-    output tensors may be passed in (preallocated by the caller)."""
+    output tensors may be passed in (preallocated by the caller).  The kernel
+    writes nlists * R ids and nlists counts through plain pointers, so passed
+    tensors must be contiguous int32 on X's device with exactly those shapes."""
     nl = owner.shape[0]
     if out is None:
         out = torch.empty((nl, R), dtype=torch.int32, device=X.device)
     if cnt is None:
         cnt = torch.empty(nl, dtype=torch.int32, device=X.device)
+    for name, t, shape in (("out", out, (nl, R)), ("cnt", cnt, (nl,))):
+        if (tuple(t.shape) != shape or t.dtype != torch.int32 or not t.is_contiguous()
+                or t.device != X.device):
+            raise ValueError(f"{name} must be a contiguous int32 tensor of shape {shape} "
+                             f"on {X.device}")
     _check(load().fgraft_prune_lists_noalloc(_ptr(X), C.c_int64(X.shape[0]), C.c_int32(d),
                                              C.c_int64(X.shape[1]), C.c_int32(metric),
                                              _ptr(owner), _ptr(cand_off), _ptr(cand_ids),
