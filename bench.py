@@ -1,13 +1,16 @@
 #!/usr/bin/env python3
 """FGraft build benchmark on one GB300 (or N replicas under torchrun).
 
-One step is one pass of the whole hot path over the in-cache workload
-(n = 100,000 unit vectors, d = 100, angular distance, 64 vMF-like clusters):
-SAT scaffold (T = 8), the B = 8 harvest blocks (one CUDA graph), the final
-graph, a 10,000-query search (ef_s = 64, top-10) and 64 dense 1024-point
-intra-cluster blocks (top-32 per row).  The headline value is points built
-per second over the whole step; L2 is flushed (a 256 MiB write) before every
-timed step, whose duration is taken with CUDA events on the launching stream.
+One step is one pass of the whole hot path over the paper-scale angular
+workload (n = 1,183,514 unit vectors, d = 100, 256 vMF-like clusters with
+Zipf(1.1) sizes): SAT scaffold (T = 8), the B = 8 harvest blocks (R = 64,
+ef_h = 100; one CUDA graph), the final graph, a 10,000-query search
+(ef_s = 64, top-10) and 64 dense 1024-point intra-cluster blocks (top-64 per
+row, BF16 tensor-core filter with float32 rerank).  The headline value is
+points built per second over the whole step; L2 is flushed (a 256 MiB
+write) before every timed step, whose duration is taken with CUDA events on
+the launching stream.  The in-cache workload (n = 100,000, 40 MB of vectors,
+L2-resident) is measured after it as a labelled extra.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -32,10 +35,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "FGraft build pts/s & dist-evals/s vs dense-block ceiling, 1 GB300; recall@10"
-WORKLOAD = "incache-angular-n100k-d100"
-SPEC = dict(n=100_000, d=100, k=64, kappa=20.0, T=8, B=8, R=32, ef_h=64, alpha=1.2, nq=10_000,
-            ef_s=64, topk=10, dense_blocks=64, block_size=1024, dense_k=32, seed=0)
+WORKLOAD = "paper-angular-n1183514-d100"
+SPEC = dict(workload=WORKLOAD, n=1_183_514, d=100, k=256, sizes="zipf", kappa=20.0, T=8, B=8,
+            R=64, ef_h=100, alpha=1.2, nq=10_000, ef_s=64, topk=10, dense_blocks=64,
+            block_size=1024, dense_k=64, seed=0)
+INCACHE = dict(workload="incache-angular-n100k-d100", n=100_000, d=100, k=64, sizes="equal",
+               kappa=20.0, T=8, B=8, R=32, ef_h=64, alpha=1.2, nq=10_000, ef_s=64, topk=10,
+               dense_blocks=64, block_size=1024, dense_k=32, seed=0)
 CPU_SAMPLE_N = 20_000
+COMPLETENESS_SAMPLE = 20_000
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -59,11 +67,12 @@ def parse():
     ap.add_argument("--schedule", default="auto", choices=["auto", "coherent", "id"],
                     help="order in which each block's searches are claimed: tree-0 preorder "
                          "(coherent), point id, or the preorder when X exceeds L2 (auto)")
-    ap.add_argument("--mode", default="step", choices=["step", "dims", "paper", "batched", "cap"],
+    ap.add_argument("--mode", default="step",
+                    choices=["step", "dims", "paper", "batched", "cap", "dense"],
                     help="step: the benchmark line; dims: adaptive vs dense cost per evaluation "
                          "across d; paper: the paper-scale angular arms; batched: many "
                          "independent builds harvested together; cap: the scaffold degree "
-                         "cap ablation")
+                         "cap ablation; dense: the dense-block ceiling alone")
     return ap.parse_args()
 
 
@@ -74,7 +83,8 @@ def env_rank():
 
 def make_inputs(spec):
     from paper_2609_30493_gb300 import synth
-    ps = synth.vmf_like(spec["n"], spec["d"], spec["k"], spec["seed"], spec["kappa"])
+    ps = synth.vmf_like(spec["n"], spec["d"], spec["k"], spec["seed"], spec["kappa"],
+                        sizes=spec["sizes"])
     Q = synth.queries(ps, spec["nq"], spec["seed"] + 1)
     blocks = synth.intra_cluster_blocks(ps.labels, spec["dense_blocks"], spec["block_size"],
                                         spec["seed"] + 2)
@@ -103,10 +113,10 @@ def kernel_source_sha256(files):
     return h.hexdigest()
 
 
-def ncu_traffic(kernel_files):
+def ncu_traffic(kernel_files, profile="harvest_beam_paper_n1183514_d100.md"):
     """DRAM bytes per harvest launch from the committed ncu summary, if it was
     taken on the current kernel source (hash match), else None."""
-    prof = os.path.join(ROOT, "profiles", "harvest_beam_incache_n100k_d100.md")
+    prof = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(prof):
         return None
     txt = open(prof).read()
@@ -187,18 +197,19 @@ def job_rate(local_ms, steps, n_per_rank, world, dist_mod, device):
 EF_LADDER = (10, 16, 24, 32, 48, 64, 96, 128)
 
 
-def quality_report(fg, ix, ps, Q_d, spec, r_target=0.95):
+def quality_report(fg, ix, ps, Q_d, spec, r_target=0.95, sample=None):
     """Measurement only (outside the timed region): recall@10 and evaluations
     per query along the ef_s ladder, d@r (the evaluations per query of the
-    first ef_s reaching recall r), and local completeness (the fraction of each
-    point's 10 nearest neighbours that sit in its final adjacency row).  The
-    ground truth is a float32 brute force with PyTorch on the device."""
+    first ef_s reaching recall r), and local completeness (the fraction of a
+    point's 10 nearest neighbours that sit in its final adjacency row), over
+    every point or over a seeded sample of `sample` points.  The ground truth
+    is a float32 brute force with PyTorch on the device."""
     import torch
     X = torch.from_numpy(ps.X[:, :spec["d"]]).cuda()
     Q = Q_d[:, :spec["d"]]
     gtq = []
-    for s in range(0, Q.shape[0], 2048):
-        gtq.append(torch.topk(Q[s:s + 2048] @ X.T, 10, dim=1).indices)
+    for s in range(0, Q.shape[0], 1024):
+        gtq.append(torch.topk(Q[s:s + 1024] @ X.T, 10, dim=1).indices)
     gtq = torch.cat(gtq)
     ladder = []
     d_at_r = None
@@ -210,22 +221,127 @@ def quality_report(fg, ix, ps, Q_d, spec, r_target=0.95):
         ladder.append({"ef_s": ef, "recall_at_10": round(rec, 4), "evals_per_query": round(epq, 1)})
         if d_at_r is None and rec >= r_target:
             d_at_r = round(epq, 1)
-    # local completeness over every point
     n = X.shape[0]
+    if sample and sample < n:
+        pts = np.sort(np.random.default_rng(17).choice(n, size=sample, replace=False))
+    else:
+        pts = np.arange(n)
+    pts_d = torch.from_numpy(pts).cuda()
     off, fids = fg.fgraft_prune(ix)
     rows = torch.repeat_interleave(torch.arange(n, device=X.device), off[1:] - off[:-1])
     edge_keys = torch.sort(rows * n + fids.long()).values
     hits = 0
-    for s in range(0, n, 4096):
-        dots = X[s:s + 4096] @ X.T
-        dots[torch.arange(dots.shape[0], device=X.device),
-             torch.arange(s, s + dots.shape[0], device=X.device)] = -float("inf")
+    for s in range(0, len(pts), 1024):
+        p = pts_d[s:s + 1024]
+        dots = X[p] @ X.T
+        dots[torch.arange(len(p), device=X.device), p] = -float("inf")
         gt = torch.topk(dots, 10, dim=1).indices
-        keys = (torch.arange(s, s + gt.shape[0], device=X.device).unsqueeze(1) * n + gt).reshape(-1)
+        keys = (p.unsqueeze(1) * n + gt).reshape(-1)
         pos = torch.searchsorted(edge_keys, keys).clamp(max=edge_keys.numel() - 1)
         hits += int((edge_keys[pos] == keys).sum().item())
-    return {"recall_ladder": ladder, f"d_at_r{r_target}": d_at_r,
-            "local_completeness_at_10": round(hits / (n * 10), 4)}
+    out = {"recall_ladder": ladder, f"d_at_r{r_target}": d_at_r,
+           "local_completeness_at_10": round(hits / (len(pts) * 10), 4)}
+    if len(pts) < n:
+        out["local_completeness_sample"] = f"seeded sample of {len(pts)} of {n} points"
+    return out
+
+
+def _device_inputs(spec):
+    import torch
+    ps, Q, blocks = make_inputs(spec)
+    return ps, Q, blocks, (torch.from_numpy(ps.X).cuda(), torch.from_numpy(Q).cuda(),
+                           torch.from_numpy(blocks).cuda())
+
+
+def _params(fg, spec):
+    return fg.Params(T=spec["T"], R=spec["R"], ef_h=spec["ef_h"], B=spec["B"],
+                     alpha=spec["alpha"], seed=spec["seed"], metric=fg.ANGULAR_F32)
+
+
+def _step(fg, spec, params, X_t, Q_t, B_t, profile=False):
+    """One pass of the whole hot path: scaffold, the B harvest blocks (one CUDA
+    graph), final graph, query search, dense blocks (BF16 filter)."""
+    ix = fg.fgraft_build_scaffold(X_t, spec["d"], params)
+    if profile:
+        fg.fgraft_index_profile(ix, True)
+    fg.fgraft_harvest_all(ix, use_graph=True)
+    ids, _, _ = fg.fgraft_search(ix, Q_t, spec["topk"], spec["ef_s"])
+    di, _ = fg.fgraft_dense_block_dist(X_t, spec["d"], fg.ANGULAR_F32, B_t, spec["dense_k"],
+                                       precision=1)
+    return ix, ids, di
+
+
+def _timed(fg, spec, params, dev_in, steps, warmup, flush, stream):
+    """Warm-up steps, then `steps` timed steps (L2 flushed before each).  Returns
+    (total ms, summed harvest-kernel ms, harvest launches, prune ms, summed
+    counters, kernels launched, last step's outputs)."""
+    import torch
+    for _ in range(warmup):
+        _step(fg, spec, params, *dev_in)
+    torch.cuda.synchronize()
+    launches0 = fg.fgraft_kernel_launches()
+    total_ms, harvest_ms, harvest_launches, prune_ms = 0.0, 0.0, 0, 0.0
+    ctr_sum, last = {}, None
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        torch.cuda.nvtx.range_push("timed")  # lets a profiler keep to the timed steps
+        ix, ids, di = _step(fg, spec, params, *dev_in, profile=True)
+        torch.cuda.nvtx.range_pop()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        hm, hl, pm = fg.fgraft_index_harvest_ms(ix, with_prune=True)
+        harvest_ms += hm
+        harvest_launches += hl
+        prune_ms += pm
+        for k_, v_ in fg.fgraft_index_counters(ix).items():
+            ctr_sum[k_] = ctr_sum.get(k_, 0) + v_
+        last = (ix, ids, di)
+    launches = fg.fgraft_kernel_launches() - launches0
+    return total_ms, harvest_ms, harvest_launches, prune_ms, ctr_sum, launches, last
+
+
+def _alg_bytes(spec, ctr):
+    """Algorithmic bytes of the harvest: one dependent vector gather at 32-byte
+    sectors per evaluation plus 4 bytes per neighbour id scanned."""
+    line = 32 * ((4 * spec["d"] + 31) // 32)
+    return ctr.get("harvest_evals", 0) * line + ctr.get("ids_scanned", 0) * 4
+
+
+def incache_extra(fg, flush, stream, steps=3, warmup=2):
+    """The in-cache workload (40 MB of vectors, L2-resident): bound by the
+    latency of the dependent gathers, not by HBM.  Reports the step rate, the
+    harvest's evaluations per second, its algorithmic gather rate and the SM
+    cycles per evaluation (the GB300's c_adapt, Section 5.3)."""
+    import torch
+    spec = INCACHE
+    ps, Q, blocks, dev_in = _device_inputs(spec)
+    params = _params(fg, spec)
+    ixt = fg.fgraft_build_scaffold(dev_in[0], spec["d"], params)
+    tuning = fg.fgraft_index_autotune(ixt, sample=4096)
+    del ixt
+    clocks = Clocks(torch.cuda.current_device())
+    tot, hms, hl, pms, ctr, _, _ = _timed(fg, spec, params, dev_in, steps, warmup, flush, stream)
+    clk = clocks.stop()
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    evals = ctr.get("harvest_evals", 0)
+    alg = _alg_bytes(spec, ctr)
+    return {"workload": spec["workload"], "bound": "L2-resident; latency of the dependent gathers",
+            "value": round(spec["n"] * steps / (tot / 1e3), 1), "unit": "pts/s",
+            "ms_per_step": round(tot / steps, 3),
+            "harvest_evals_per_s": round(evals / (hms / 1e3), 1) if hms else None,
+            "harvest_alg_GBps": round(alg / (hms / 1e3) / 1e9, 1) if hms else None,
+            "harvest_ms_per_block": round(hms / max(hl, 1), 4),
+            "prune_ms_per_block": round(pms / max(hl, 1), 4),
+            "sm_cycles_per_eval": round(hms / 1e3 * mhz * 1e6 * nsm / evals, 1) if evals else None,
+            "sm_mhz": mhz,
+            "autotune": {k_: (round(v_, 4) if isinstance(v_, float) else v_)
+                         for k_, v_ in tuning.items()},
+            "config": {k: spec[k] for k in ("n", "d", "k", "T", "B", "R", "ef_h", "alpha")}}
 
 
 def run_ours(args):
@@ -243,59 +359,29 @@ def run_ours(args):
     spec = dict(SPEC)
     if args.n:
         spec["n"] = args.n
-    ps, Q, blocks = make_inputs(spec)
+    ps, Q, blocks, dev_in = _device_inputs(spec)
+    X_d, Q_d, B_d = dev_in
     d = spec["d"]
-    X_d = torch.from_numpy(ps.X).cuda()
-    Q_d = torch.from_numpy(Q).cuda()
-    B_d = torch.from_numpy(blocks).cuda()
-    params = fg.Params(T=spec["T"], R=spec["R"], ef_h=spec["ef_h"], B=spec["B"],
-                       alpha=spec["alpha"], seed=spec["seed"], metric=fg.ANGULAR_F32)
+    params = _params(fg, spec)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step(X_t, Q_t, B_t, profile=False):
-        ix = fg.fgraft_build_scaffold(X_t, d, params)
-        if profile:
-            fg.fgraft_index_profile(ix, True)
-        fg.fgraft_harvest_all(ix, use_graph=True)
-        ids, dist_, ev = fg.fgraft_search(ix, Q_t, spec["topk"], spec["ef_s"])
-        di, dd = fg.fgraft_dense_block_dist(X_t, d, fg.ANGULAR_F32, B_t, spec["dense_k"],
-                                            precision=1)
-        return ix, ids, di
-
-    for _ in range(args.warmup):
-        step(X_d, Q_d, B_d)
-    torch.cuda.synchronize()
+    # ---- autotuner (outside the timed region): the harvest launch settings
+    # for this shape, kept in the process's table for every later build ----
+    ixt = fg.fgraft_build_scaffold(X_d, d, params)
+    tuning = fg.fgraft_index_autotune(ixt, sample=16384)
+    del ixt
 
     # ---- timed region: inputs resident in HBM ----
+    for _ in range(args.warmup):
+        _step(fg, spec, params, *dev_in)
+    torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(local)
-    launches0 = fg.fgraft_kernel_launches()
-    total_ms, harvest_ms, harvest_launches, prune_ms = 0.0, 0.0, 0, 0.0
-    ctr_sum = {}
-    last = None
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        torch.cuda.nvtx.range_push("timed")  # lets a profiler keep to the timed steps
-        ix, ids, di = step(X_d, Q_d, B_d, profile=True)
-        torch.cuda.nvtx.range_pop()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        hm, hl, pm = fg.fgraft_index_harvest_ms(ix, with_prune=True)
-        harvest_ms += hm
-        harvest_launches += hl
-        prune_ms += pm
-        c = fg.fgraft_index_counters(ix)
-        for k_, v_ in c.items():
-            ctr_sum[k_] = ctr_sum.get(k_, 0) + v_
-        last = (ix, ids, di)
-    launches = fg.fgraft_kernel_launches() - launches0
+    total_ms, harvest_ms, harvest_launches, prune_ms, ctr_sum, launches, last = _timed(
+        fg, spec, params, dev_in, args.steps, 0, flush, stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     if world > 1:
@@ -343,7 +429,7 @@ def run_ours(args):
     graph_same = bool(torch.equal(fa[0], fb[0]) and torch.equal(fa[1], fb[1]))
     del ixg
 
-    # ---- dense blocks in the other two precisions (untimed, same blocks) ----
+    # ---- dense blocks in the other precisions (untimed, same blocks) ----
     dense_other = {}
     for prec, name in ((1, "bf16"), (2, "fp8_e4m3")):
         # the filter's error against float64 on the reranked pairs (slow, separate call)
@@ -351,6 +437,19 @@ def run_ours(args):
                                                precision=prec, stats=True, err64=True)
         dense_other[name + "_error_check"] = {"max_err_over_bound": round(est[4], 5),
                                               "max_canonical_err": est[5]}
+    # the raw dense ceiling: the tensor-core Gram of every pair, no selection
+    gram = {}
+    for prec, name in ((1, "bf16"), (2, "fp8_e4m3")):
+        fg.fgraft_dense_block_gram(X_d, d, fg.ANGULAR_F32, B_d, precision=prec)
+        tms = []
+        for _ in range(3):
+            flush.fill_(1.0)
+            _, gms = fg.fgraft_dense_block_gram(X_d, d, fg.ANGULAR_F32, B_d, precision=prec)
+            tms.append(gms)
+        gms = float(np.median(tms))
+        dpad = ((d + 63) // 64) * 64 if prec == 1 else ((d + 127) // 128) * 128
+        mma_flops = 2.0 * dpad * spec["dense_blocks"] * 1024 * 1024
+        gram[name] = {"ms": round(gms, 4), "tflops_mma": round(mma_flops / (gms / 1e3) / 1e12, 1)}
     for prec, name in ((0, "fp32_cuda_cores"), (2, "fp8_e4m3")):
         q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         q0.record(stream)
@@ -362,14 +461,15 @@ def run_ours(args):
         dense_other[name] = {"ms": round(q0.elapsed_time(q1), 3), "same_top_k_as_bf16": same}
         if prec == 2:
             dense_other[name]["rerank_fraction"] = round(pst[0], 5)
-            dense_other[name]["gram_ms"] = round(pst[1], 4)
-    quality = quality_report(fg, ix, ps, Q_d, spec)
+            dense_other[name]["filter_ms"] = round(pst[1], 4)
+    quality = quality_report(fg, ix, ps, Q_d, spec, sample=COMPLETENESS_SAMPLE)
 
     # ---- end to end through the public API, host buffers ----
     Xh = torch.from_numpy(ps.X).pin_memory()
     Qh = torch.from_numpy(Q).pin_memory()
     Bh = torch.from_numpy(blocks).pin_memory()
     h2d = Xh.numel() * 4 + Qh.numel() * 4 + Bh.numel() * 4
+    del ix
     e2e_ms, d2h = 0.0, 0
     for _ in range(args.steps):
         flush.fill_(1.0)
@@ -391,7 +491,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_ms += e0.elapsed_time(e1)
         d2h = sum(o.numel() * o.element_size() for o in outs)
+        del ix2
     _, e2e_value = job_rate(e2e_ms, args.steps, n, world, dist if world > 1 else None, "cuda")
+    extra = incache_extra(fg, flush, stream) if not args.n else None
 
     if rank != 0:
         if world > 1:
@@ -399,32 +501,36 @@ def run_ours(args):
         return
     rec = recall_at_10(ps.X[:, :d], Q[:, :d], last[1].cpu().numpy())
     hbm, peak_kind = peaks()
-    line_bytes = 32 * ((4 * d + 31) // 32)
     evals = ctr_sum.get("harvest_evals", 0)
-    scanned = ctr_sum.get("ids_scanned", 0)
-    alg_bytes = evals * line_bytes + scanned * 4
+    alg_bytes = _alg_bytes(spec, ctr_sum)
     achieved = alg_bytes / (harvest_ms / 1e3) / 1e9 if harvest_ms > 0 else 0.0
     traffic = ncu_traffic(BEAM_SOURCES)
-    dense_pairs = spec["dense_blocks"] * spec["block_size"] * (spec["block_size"] - 1)
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    nvalid = (blocks >= 0).sum(axis=1).astype(np.int64)
+    dense_pairs = int((nvalid * (nvalid - 1)).sum())
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "pts/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "d": d, "metric_kind": "angular",
-                   "clusters": spec["k"], "T": spec["T"], "B": spec["B"], "R": spec["R"],
-                   "ef_h": spec["ef_h"], "alpha": spec["alpha"], "nq": spec["nq"],
-                   "ef_s": spec["ef_s"], "dense_blocks": spec["dense_blocks"],
+        "config": {"workload": spec["workload"], "n": n, "d": d, "metric_kind": "angular",
+                   "clusters": spec["k"], "cluster_sizes": "zipf(1.1)", "T": spec["T"],
+                   "B": spec["B"], "R": spec["R"], "ef_h": spec["ef_h"], "alpha": spec["alpha"],
+                   "nq": spec["nq"], "ef_s": spec["ef_s"], "dense_blocks": spec["dense_blocks"],
                    "block_size": spec["block_size"], "dense_k": spec["dense_k"],
                    "parallelism": f"replicas{world}", "schedule": args.schedule,
-                   "l2": "flushed before each timed step (256 MiB write); data 40 MB is L2-resident within a step"},
+                   "l2": "flushed before each timed step (256 MiB write); the vectors "
+                         f"({ps.X.nbytes / 1e6:.0f} MB) exceed L2"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                      "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                     "traffic": traffic, "kernel": "beam_kernel (harvest)",
+                     "traffic": traffic, "kernel": "beam_kernel (harvest search)",
                      "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg_bytes / max(harvest_launches, 1),
                      "launch_ms": harvest_ms / max(harvest_launches, 1)},
         "harvest_evals_per_s": round(evals / (harvest_ms / 1e3), 1) if harvest_ms else None,
+        "harvest_sm_cycles_per_eval": round(harvest_ms / 1e3 * mhz * 1e6 * nsm / evals, 1)
+        if evals else None,
         "harvest_prune_ms_per_block": round(prune_ms / max(harvest_launches, 1), 4),
         "prune_evals_per_s": round(ctr_sum.get("prune_evals", 0) / (prune_ms / 1e3), 1)
         if prune_ms else None,
@@ -435,22 +541,32 @@ def run_ours(args):
         "counters_per_build": {k_: v_ // args.steps for k_, v_ in ctr_sum.items()},
         "recall_at_10": round(rec, 4),
         "search_evals_per_query": round(search_evals / spec["nq"], 1),
+        "dense_pairs": dense_pairs,
         "dense_pairs_per_s": round(dense_pairs / (breakdown["dense_blocks"] / 1e3), 1),
-        "dense_gram_pairs_per_s": round(dense_pairs / (dst[1] / 1e3), 1) if dst[1] else None,
-        "dense_gram_tflops": round(2 * d * dense_pairs / (dst[1] / 1e3) / 1e12, 2) if dst[1] else None,
+        "dense_filter_ms": round(dst[1], 4), "dense_rerank_ms": round(dst[2], 4),
+        "dense_prep_ms": round(dst[3], 4),
+        "dense_gram_pairs_per_s": round(dense_pairs / (gram["bf16"]["ms"] / 1e3), 1),
+        "dense_gram": gram,
         "dense_rerank_fraction": round(dst[0], 5),
+        "adaptive_dense_gap": round((dense_pairs / (breakdown["dense_blocks"] / 1e3))
+                                    / (evals / (harvest_ms / 1e3)), 2) if harvest_ms else None,
         "dense_other_precisions": dense_other,
+        "autotune": {k_: (round(v_, 4) if isinstance(v_, float) else v_)
+                     for k_, v_ in tuning.items()},
         "graph_replay_same_graph": graph_same,
         "final_graph_sha256_16": graph_hash,
         "quality": quality,
         "breakdown_ms": breakdown,
+        "incache": extra,
         "e2e": {"value": round(e2e_value, 1), "unit": "pts/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clk,
     }
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baselines(ps, spec)
+        work = sum(ctr_sum.get(k_, 0) for k_ in ("sat_evals", "harvest_evals", "prune_evals",
+                                                  "final_prune_evals"))
+        out["cpu_baseline"] = cpu_baselines(ps, spec, work / args.steps / n)
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -465,21 +581,34 @@ def cpu_baseline(ps, spec, sample_n=CPU_SAMPLE_N, seed=7, nthreads=None):
     D = oracle.Data(Xs, spec["d"], 1)
     cores = nthreads or os.cpu_count() or 1
     t0 = time.perf_counter()
-    oracle.build_graph(D, spec["T"], spec["R"], spec["ef_h"], spec["B"], spec["alpha"],
-                       spec["seed"], nthreads=cores)
+    g = oracle.build_graph(D, spec["T"], spec["R"], spec["ef_h"], spec["B"], spec["alpha"],
+                           spec["seed"], nthreads=cores)
     dt = time.perf_counter() - t0
+    c = g["counters"]
+    work = sum(c[k] for k in ("sat_evals", "harvest_evals", "prune_evals", "final_prune_evals"))
     return {"value": round(len(sel) / dt, 1), "unit": "pts/s", "cores": cores, "kind": "oracle",
             "sample": f"oracle FGraft build (SAT forest, scaffold, {spec['B']} blocks, final graph) "
                       f"of a seeded {len(sel)}-point subset of the workload, same T/R/ef_h/B/alpha",
-            "seconds": round(dt, 2)}
+            "seconds": round(dt, 2), "evals_per_point": round(work / len(sel), 1)}
 
 
-def cpu_baselines(ps, spec):
+def cpu_baselines(ps, spec, gpu_evals_per_point=None):
     """The oracle on all host cores (the reported baseline) and on one core (a
-    smaller subset, so that the bench stays within minutes)."""
+    smaller subset, so that the bench stays within minutes).  A subset has
+    shorter searches than the whole workload, so the oracle's rate is also
+    given scaled by distance evaluations per point (the work the paper counts,
+    Section 2): subset rate x subset evaluations per point / the whole
+    workload's evaluations per point (the GPU build's counters, which equal
+    the oracle's by definition)."""
     out = cpu_baseline(ps, spec)
     one = cpu_baseline(ps, spec, sample_n=CPU_SAMPLE_N // 4, seed=8, nthreads=1)
-    out["single_thread"] = {k: one[k] for k in ("value", "unit", "cores", "sample", "seconds")}
+    out["single_thread"] = {k: one[k] for k in ("value", "unit", "cores", "sample", "seconds",
+                                                "evals_per_point")}
+    if gpu_evals_per_point:
+        out["scaled_to_workload"] = {
+            "value": round(out["value"] * out["evals_per_point"] / gpu_evals_per_point, 1),
+            "unit": "pts/s", "workload_evals_per_point": round(gpu_evals_per_point, 1),
+            "how": "subset rate x subset evaluations per point / workload evaluations per point"}
     return out
 
 
@@ -794,7 +923,7 @@ def run_cap(args):
     from paper_2609_30493_gb300 import fgraft as fg
     fgbuild.build()
     fg.load()
-    spec = dict(SPEC)
+    spec = dict(INCACHE)
     ps, Q, blocks = make_inputs(spec)
     d = spec["d"]
     X_d = torch.from_numpy(ps.X).cuda()
@@ -826,6 +955,63 @@ def run_cap(args):
     fg.fgraft_tune_scaffold_cap(0)
 
 
+def run_dense(args):
+    """The dense-block ceiling alone (Section 5.3) on the benchmark workload's 64
+    intra-cluster blocks of 1024 points (top-64 per row): the canonical float32
+    kernel on CUDA cores, the BF16 and FP8 tensor-core filters with float32
+    rerank (all three top-k identical), and the raw tensor-core Gram without
+    selection.  L2 is flushed before every timed call."""
+    import torch
+    from paper_2609_30493_gb300 import build as fgbuild
+    from paper_2609_30493_gb300 import fgraft as fg
+    fgbuild.build()
+    fg.load()
+    spec = dict(SPEC)
+    if args.n:
+        spec["n"] = args.n
+    ps, Q, blocks, (X_d, Q_d, B_d) = _device_inputs(spec)
+    d, k = spec["d"], spec["dense_k"]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    nvalid = (blocks >= 0).sum(axis=1).astype(np.int64)
+    pairs = int((nvalid * (nvalid - 1)).sum())
+    ref = None
+    for prec, name in ((0, "fp32_cuda_cores"), (1, "bf16"), (2, "fp8_e4m3")):
+        for _ in range(max(args.warmup, 1)):
+            fg.fgraft_dense_block_dist(X_d, d, fg.ANGULAR_F32, B_d, k, precision=prec)
+        ts, st = [], None
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gi, gd, st = fg.fgraft_dense_block_dist(X_d, d, fg.ANGULAR_F32, B_d, k,
+                                                    precision=prec, stats=True)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.median(ts))
+        same = None if ref is None else bool(torch.equal(gi, ref[0]) and torch.equal(gd, ref[1]))
+        ref = ref or (gi, gd)
+        print(json.dumps({"mode": "dense", "precision": name, "blocks": int(len(blocks)),
+                          "pairs": pairs, "k": k, "ms": round(ms, 4),
+                          "pairs_per_s": round(pairs / (ms / 1e3), 1),
+                          "filter_ms": round(st[1], 4), "rerank_ms": round(st[2], 4),
+                          "prep_ms": round(st[3], 4), "rerank_fraction": round(st[0], 5),
+                          "same_top_k_as_fp32": same}), flush=True)
+    for prec, name in ((1, "bf16"), (2, "fp8_e4m3")):
+        fg.fgraft_dense_block_gram(X_d, d, fg.ANGULAR_F32, B_d, precision=prec)
+        tms = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            _, gms = fg.fgraft_dense_block_gram(X_d, d, fg.ANGULAR_F32, B_d, precision=prec)
+            tms.append(gms)
+        gms = float(np.median(tms))
+        dpad = ((d + 63) // 64) * 64 if prec == 1 else ((d + 127) // 128) * 128
+        flops = 2.0 * dpad * len(blocks) * 1024 * 1024
+        print(json.dumps({"mode": "dense-gram", "precision": name, "ms": round(gms, 4),
+                          "pairs_per_s": round(pairs / (gms / 1e3), 1),
+                          "tflops_mma": round(flops / (gms / 1e3) / 1e12, 1)}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl != "reference" and args.schedule != "auto":
@@ -843,6 +1029,8 @@ def main():
         run_batched(args)
     elif args.mode == "cap":
         run_cap(args)
+    elif args.mode == "dense":
+        run_dense(args)
     else:
         run_ours(args)
 

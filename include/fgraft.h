@@ -223,21 +223,41 @@ fgraft_status fgraft_search(fgraft_index* ix, const void* Q, int64_t nq, int64_t
  *                rounding-error bound of the k-th approximate distance is
  *                recomputed in the canonical order;
  *   precision 2  the same with an FP8 (E4M3) filter, each centred row scaled
- *                so that its largest magnitude is 448 (kind::f8f6f4); the
- *                bound is 16 times wider, so more pairs are recomputed.
+ *                so that its largest magnitude is 448 (kind::f8f6f4); its
+ *                bound is about 16 times wider, so more pairs are recomputed.
+ * The bound of a row comes from the rows' actual rounding residuals
+ * (|<q_i,q_j> - <x_i,x_j>| <= |x_i - q_i| max|q| + |x_i| max|x - q|, plus
+ * the FP32 accumulation and the canonical float32 rounding), times 2.
  * stats (host, optional, 6 doubles; the call then synchronises `stream`):
- * fraction of pairs recomputed, Gram-kernel ms, select ms, prep ms
+ * fraction of pairs recomputed, filter-kernel ms, rerank ms, prep ms
  * (precisions 1 and 2; zeros for precision 0).  When stats[4] is nonzero on
  * entry, stats[4] and stats[5] return, over the recomputed pairs, the largest
  * |approximate - float64| as a fraction of the row's bound and the largest
- * |canonical float32 - float64| (the float64 check slows the select).
+ * |canonical float32 - float64| (the float64 check slows the rerank).
  * Precisions 1 and 2 take float32 metrics only; bs <= 1024,
- * k <= 64, nb <= 65535.  Precisions 1 and 2 allocate their scratch stream-ordered and
- * synchronises `stream` to check its bounded waits (FGRAFT_ETIMEOUT). */
+ * k <= 64, nb <= 65535.  Precisions 1 and 2 allocate their scratch
+ * stream-ordered (about 2 MB per block for up to 64 blocks at a time) and
+ * synchronise `stream` once per 64 blocks to check their bounded waits
+ * (FGRAFT_ETIMEOUT). */
 fgraft_status fgraft_dense_block_dist(const void* X, int64_t n, int32_t d, int64_t ld,
                                       int32_t metric, const int32_t* block_ids, int64_t nb,
                                       int32_t bs, int32_t k, int32_t precision, int32_t* out_ids,
                                       float* out_dist, double* stats, fgraft_stream stream);
+
+/* The dense-block ceiling without any selection (Section 5.3: the blocked
+ * kernel's raw pair rate): the tensor-core Gram matrix of every block in
+ * BF16 (precision 1) or FP8 (precision 2) on the centred rows, turned into
+ * approximate distances and reduced to the smallest one per row:
+ * out_min[b * bs + i] = min over valid j != i of the approximate
+ * delta(x_i, x_j) (+inf for padding rows and single-member blocks).  The
+ * same kernel as the filter of fgraft_dense_block_dist, one pass instead of
+ * three.  ms (host, optional) receives the Gram kernel's time; the call then
+ * synchronises `stream`.  Arguments as for fgraft_dense_block_dist;
+ * float32 metrics only. */
+fgraft_status fgraft_dense_block_gram(const void* X, int64_t n, int32_t d, int64_t ld,
+                                      int32_t metric, const int32_t* block_ids, int64_t nb,
+                                      int32_t bs, int32_t precision, float* out_min, double* ms,
+                                      fgraft_stream stream);
 
 /* Inspection: copies of the index's state into caller buffers (device).
  * roots: T; parents: T*n (parent of every point in each tree, -1 at the
@@ -269,6 +289,49 @@ fgraft_status fgraft_index_counters(fgraft_index* ix, fgraft_stream stream,
  * unchanged. */
 fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t warps_per_cta,
                                 int32_t overflow_mode);
+
+/* Autotuner (not in the paper: a property of this implementation).  Times
+ * the harvest of a calibration sample -- the first `sample` searches of
+ * block 0 in claim order, each with its occlusion prune -- under every
+ * candidate launch configuration, keeps the fastest for this index and
+ * records it in the process's tuning table under (metric, d, ef_h, R,
+ * ceil(log2 n)); later fgraft_build_scaffold calls of the same shape start
+ * from it.  The settings: warps (searches) per CTA 4, 2, 1; visited sets by
+ * the occupancy rule or in a shared-memory hash of 2^9..2^12 slots;
+ * overflowing searches continuing in a global bitmap or re-run; candidate
+ * rows gathered into registers by the lane groups or bulk-copied (TMA) into
+ * a shared buffer of 32 rows per search (rows of at most 64 chunks); the
+ * bitmap visited tests of 1 or 2 chunks of 32 ids issued together.  The
+ * search is coordinate descent from the defaults (4, occupancy rule, global
+ * bitmap, registers, 2), each setting in turn over its options, two rounds.  Results never depend on the settings: the sample's
+ * rows receive their final values and nothing else of the index changes.
+ * chosen (host, optional) receives the settings and the microseconds per
+ * sample search with them and with the default settings.  Call it before
+ * capturing the harvest in a graph; it synchronises `stream`. */
+typedef struct {
+  int32_t warps_per_cta;
+  int32_t hash_log2;      /* 0: the occupancy rule */
+  int32_t overflow_mode;  /* 1: continue in a global bitmap, 2: re-run */
+  int32_t gather;         /* 0: registers, 1: bulk copies into shared memory */
+  int32_t id_batch;       /* 1 or 2 chunks of ids per round of bitmap tests */
+  float us_per_query;
+  float default_us_per_query;
+} fgraft_tuning;
+fgraft_status fgraft_index_autotune(fgraft_index* ix, int32_t sample, fgraft_stream stream,
+                                    fgraft_tuning* chosen);
+
+/* Explicit harvest launch settings for an index (tuning; results do not
+ * depend on them); the timing fields of t are ignored.  EINVAL for a
+ * setting out of range (gather = 1 needs rows of at most 64 chunks). */
+fgraft_status fgraft_index_set_tuning(fgraft_index* ix, const fgraft_tuning* t);
+
+/* The process's tuning table as a JSON file (path: host string):
+ * {"fgraft_tuning": 1, "entries": [{"metric", "d", "ef_h", "R", "log2_n",
+ * "warps_per_cta", "hash_log2", "overflow_mode", "us_per_query"}, ..]}.
+ * Loading adds or replaces entries (EINVAL on an unreadable file or an
+ * entry with a missing field or a setting out of range, table unchanged). */
+fgraft_status fgraft_tuning_table_save(const char* path);
+fgraft_status fgraft_tuning_table_load(const char* path);
 
 /* Tensor-core configuration for later builds, harvests and final graphs in
  * this process (tuning; results do not depend on it).  With tensor_cores = 1

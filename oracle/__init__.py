@@ -267,9 +267,10 @@ def substrate(n: int, s_off, s_ids, A, cnt, R: int, B: int, b: int):
     lib = _load()
     args = (C.c_int64(n), _p(s_off), _p(s_ids), _p(A), _p(cnt), C.c_int32(R), C.c_int32(B),
             C.c_int32(b))
-    lib.fgo_substrate(*args, None, None, C.byref(nnz))
+    # one call into a buffer of the largest possible size: the scaffold plus
+    # both directions of every harvested row
     off = np.empty(n + 1, np.int64)
-    ids = np.empty(max(nnz.value, 1), np.int32)
+    ids = np.empty(max(len(s_ids) + 2 * int(cnt.astype(np.int64).sum()), 1), np.int32)
     lib.fgo_substrate(*args, _p(off), _p(ids), C.byref(nnz))
     return off, ids[: nnz.value]
 

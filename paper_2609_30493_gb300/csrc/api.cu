@@ -1,6 +1,7 @@
 // C ABI of libfgraft: argument checks, the index object, and the host-side
 // sequencing of the kernels (SAT levels, harvest blocks with their overflow
 // re-run and reverse-list update, final graph, search, dense blocks).
+#include <array>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -160,7 +161,9 @@ struct fgraft_index {
   int32_t* f_ids = nullptr;
   int64_t f_nnz = 0;
   int64_t* scan_tmp = nullptr;
-  uint32_t* work = nullptr;  // [0] smem pass, [1] re-run pass, [2] ovf count, [3] err flag
+  // [0] smem pass, [1] re-run pass, [2] ovf count, [3] err flag, [4] prune
+  // timeout, [5] long prune lists, [6] gather timeout
+  uint32_t* work = nullptr;
   int32_t* ovf_list = nullptr;
   int64_t ovf_cap = 0;
   char* gscratch = nullptr;
@@ -173,6 +176,8 @@ struct fgraft_index {
   bool bitmap_ok = true;
   bool hash_auto = true;       // visited-set layout chosen by occupancy (no explicit hash size)
   int32_t overflow_mode = 1;   // 1: continue in a global bitmap, 2: abandon and re-run
+  int32_t gather = 0;          // 1: candidate rows bulk-copied into shared memory
+  int32_t id_batch = 2;        // chunks of 32 ids whose bitmap tests go together
   uint64_t* Eg = nullptr;      // expanded lists handed from the search to the prune kernel
   int32_t* Eg_cnt = nullptr;
   int32_t eg_ecap = 0;
@@ -221,7 +226,12 @@ int check_vectors(const void* X, int64_t n, int32_t d, int64_t ld, int32_t metri
   return 0;
 }
 
-BeamKernelFn beam_kernel_for(int metric, int G, int K, int S) {
+BeamKernelFn beam_kernel_for(int metric, int G, int K, int S, bool gather = false) {
+  if (gather) {
+    if (metric == 0) return beam_kernel_metric0_gather(G, K, S);
+    if (metric == 1) return beam_kernel_metric1_gather(G, K, S);
+    return beam_kernel_metric2_gather(G, K, S);
+  }
   if (metric == 0) return beam_kernel_metric0(G, K, S);
   if (metric == 1) return beam_kernel_metric1(G, K, S);
   return beam_kernel_metric2(G, K, S);
@@ -263,7 +273,8 @@ struct BeamShape {
 int beam_shape(fgraft_index* ix, BeamKernelFn kern, int S, BeamShape* out) {
   const int64_t bm_bytes = ((ix->L.n + 127) / 128) * 16;
   const int ecap = 1 << std::max(6, ceil_log2(2 * 32 * S));
-  const int fixed = 8 * ecap + (ecap / 8 + 15) / 16 * 16 + 256 + 16 * ix->L.nchunks;
+  const int fixed = 8 * ecap + (ecap / 8 + 15) / 16 * 16 + 256 + 16 * ix->L.nchunks +
+                    (ix->gather ? 32 * 16 * ix->L.nchunks + 16 : 0);
   int dev = 0, optin = 0;
   FG_CUDA(cudaGetDevice(&dev));
   FG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -310,8 +321,9 @@ int beam_shape(fgraft_index* ix, BeamKernelFn kern, int S, BeamShape* out) {
 int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStream_t s,
                 cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
   const int S = pool_slots(a.ef);
-  BeamKernelFn kern = beam_kernel_for(ix->L.metric, ix->L.G, ix->L.K, S);
-  if (!kern) return fail(FGRAFT_EINVAL, "no beam kernel for this metric and dimension");
+  BeamKernelFn kern = beam_kernel_for(ix->L.metric, ix->L.G, ix->L.K, S, ix->gather != 0);
+  BeamKernelFn kern_rr = beam_kernel_for(ix->L.metric, ix->L.G, ix->L.K, S, false);
+  if (!kern || !kern_rr) return fail(FGRAFT_EINVAL, "no beam kernel for this metric and dimension");
   BeamShape sh;
   int rc = beam_shape(ix, kern, S, &sh);
   if (rc) return rc;
@@ -341,8 +353,13 @@ int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStrea
   a.wbytes = wbytes;
   a.qbytes = qbytes;
   a.global_scratch = 0;
+  a.gather = ix->gather;
+  a.id_batch = ix->id_batch;
+  a.wait_polls = g_mma_wait_polls;
   // the per-warp layout must be complete before any launch
-  if (a.wbytes < a.vis_bytes + 8 * a.ecap + 256 + a.qbytes || a.qbytes < 16 * ix->L.nchunks)
+  if (a.wbytes < a.vis_bytes + 8 * a.ecap + 256 + a.qbytes +
+                     (a.gather ? 32 * a.qbytes + 16 : 0) ||
+      a.qbytes < 16 * ix->L.nchunks)
     return fail(FGRAFT_EINVAL, "internal: harvest shared-memory layout incomplete");
   FG_CUDA(cudaMemsetAsync(ix->work, 0, 3 * sizeof(uint32_t), s));
   if (e0) FG_CUDA(record_event(e0, s));
@@ -365,12 +382,13 @@ int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStrea
   a.gvbits_words = ix->gvbits_words;
   a.ecap = ix->g_ecap;
   a.wbytes = 256 + qbytes;
+  a.gather = 0;
   if (ix->gvbits_warps < ix->g_warps || !ix->gvbits)
     return fail(FGRAFT_EINVAL, "internal: re-run bitmaps missing");
   a.gscratch = ix->gscratch;
   a.gscratch_per_warp = ix->gscratch_per_warp;
   a.counters = ctr;
-  kern<<<ix->g_warps / 4, 128, a.wbytes * 4, s>>>(a);
+  kern_rr<<<ix->g_warps / 4, 128, a.wbytes * 4, s>>>(a);
   note_launch();
   FG_CUDA(cudaGetLastError());
   return 0;
@@ -382,7 +400,7 @@ int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStrea
 int size_visited_bitmaps(fgraft_index* ix) {
   int64_t need = ix->g_warps;
   for (int S = 1; S <= 4; S *= 2) {
-    BeamKernelFn kern = beam_kernel_for(ix->L.metric, ix->L.G, ix->L.K, S);
+    BeamKernelFn kern = beam_kernel_for(ix->L.metric, ix->L.G, ix->L.K, S, ix->gather != 0);
     if (!kern) continue;
     BeamShape sh;
     const int rc = beam_shape(ix, kern, S, &sh);
@@ -404,11 +422,12 @@ int size_visited_bitmaps(fgraft_index* ix) {
 }
 
 int check_err_flag(fgraft_index* ix, cudaStream_t s) {
-  uint32_t f[2] = {0, 0};
+  uint32_t f[4] = {0, 0, 0, 0};
   FG_CUDA(cudaMemcpyAsync(f, ix->work + 3, sizeof(f), cudaMemcpyDeviceToHost, s));
   FG_CUDA(cudaStreamSynchronize(s));
   if (f[0]) return fail(FGRAFT_EOVERFLOW, "a search outgrew its global-memory scratch");
   if (f[1]) return fail(FGRAFT_ETIMEOUT, "a tensor-core prune timed out waiting for its products");
+  if (f[3]) return fail(FGRAFT_ETIMEOUT, "a search's bulk copies of candidate rows timed out");
   return 0;
 }
 
@@ -480,6 +499,33 @@ void free_index(fgraft_index* ix) {
   delete ix;
 }
 
+// Harvest launch settings of an index (visited-set layout, warps per CTA,
+// overflow handling); hash_log2 0 selects the occupancy rule.
+void apply_settings(fgraft_index* ix, int wpc, int hash_log2, int overflow, int gather,
+                    int id_batch) {
+  ix->wpc = wpc;
+  ix->overflow_mode = overflow;
+  ix->gather = ix->L.nchunks <= 64 ? gather : 0;  // the gather kernels take rows of <= 64 chunks
+  ix->id_batch = id_batch;
+  if (hash_log2 == 0) {
+    ix->hash_auto = true;
+    ix->bitmap_ok = true;
+    ix->hash_log2 = 12;
+  } else {
+    ix->hash_auto = false;
+    ix->bitmap_ok = false;
+    ix->hash_log2 = hash_log2;
+  }
+  if (ix->graph_exec) {
+    cudaGraphExecDestroy(ix->graph_exec);
+    ix->graph_exec = nullptr;
+  }
+}
+
+TuneKey tune_key(const fgraft_index* ix) {
+  return TuneKey{ix->L.metric, ix->L.d, ix->p.ef_h, ix->p.R, ceil_log2(ix->L.n)};
+}
+
 int harvest_block_impl(fgraft_index* ix, int32_t b, cudaStream_t s) {
   BeamArgs a{};
   a.X = ix->L.X;
@@ -520,7 +566,8 @@ int harvest_block_impl(fgraft_index* ix, int32_t b, cudaStream_t s) {
   if (sep) {
     rc = harvest_prune(ix->L, ix->Eg, ix->Eg_cnt, ix->eg_ecap, a.nq, a.q_first,
                        a.q_step, ix->p.R, a.alpha2, ix->A, ix->cnt, ix->ctr + C_PRUNE,
-                       ix->num_sms, s, nullptr, nullptr, nullptr, nullptr, ix->work + 4);
+                       ix->num_sms, s, nullptr, nullptr, nullptr, nullptr, ix->work + 4,
+                       ix->ovf_list, ix->work + 5);
     if (rc) return rc;
   }
   if (prof) FG_CUDA(record_event(ix->ev_pend[b], s));
@@ -529,6 +576,48 @@ int harvest_block_impl(fgraft_index* ix, int32_t b, cudaStream_t s) {
   if (rc) return rc;
   ix->blocks_done = b + 1;
   return 0;
+}
+
+// The searches of block 0 for its first `sample` work items in claim order
+// (tree-0 preorder when the index has the coherent schedule), each followed
+// by its occlusion prune; counters go to tctr.  The rows written are those
+// points' final rows (block 0 always searches S_0), and nothing else of the
+// index changes: this is the autotuner's calibration workload.
+int harvest_sample(fgraft_index* ix, int64_t sample, unsigned long long* tctr, cudaStream_t s) {
+  BeamArgs a{};
+  a.X = ix->L.X;
+  a.ld_bytes = ix->L.ld_bytes;
+  a.d = ix->L.d;
+  a.nchunks = ix->L.nchunks;
+  a.n = ix->L.n;
+  a.s_off = ix->s_off;
+  a.s_ids = ix->s_ids;
+  a.A = ix->A;
+  a.cnt = ix->cnt;
+  a.R = ix->p.R;
+  a.r_off = nullptr;
+  a.r_ids = ix->r_ids;
+  a.B = ix->nb;
+  a.b = 0;
+  a.roots = ix->roots;
+  a.T = ix->p.T;
+  a.nq = std::min<int64_t>(sample, (ix->L.n + ix->nb - 1) / ix->nb);
+  a.q_first = 0;
+  a.q_step = ix->nb;
+  a.qlist = ix->qorder;  // block 0's claim order comes first
+  a.ef = ix->p.ef_h;
+  a.mode = 0;
+  a.alpha2 = ix->p.alpha * ix->p.alpha;
+  a.A_out = ix->A;
+  a.cnt_out = ix->cnt;
+  const bool sep = ix->prune_ns > 0;
+  a.Eg = sep ? ix->Eg : nullptr;
+  a.Eg_cnt = sep ? ix->Eg_cnt : nullptr;
+  int rc = launch_beam(ix, a, tctr, s);
+  if (rc || !sep) return rc;
+  return harvest_prune(ix->L, ix->Eg, ix->Eg_cnt, ix->eg_ecap, a.nq, 0, ix->nb, ix->p.R, a.alpha2,
+                       ix->A, ix->cnt, tctr + 5, ix->num_sms, s, nullptr, nullptr, nullptr,
+                       nullptr, ix->work + 4, ix->ovf_list, ix->work + 5, a.qlist);
 }
 
 // Side streams of a device for fgraft_harvest_block_multi, created on first
@@ -596,6 +685,11 @@ fgraft_status fgraft_build_scaffold(const void* X, int64_t n, int32_t d, int64_t
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&ix->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  {
+    TuneVal tv;  // settings the autotuner chose earlier for this shape
+    if (tune_table_lookup(tune_key(ix), &tv))
+      apply_settings(ix, tv.wpc, tv.hash_log2, tv.overflow, tv.gather, tv.id_batch);
+  }
   const int64_t T = p.T, tot = T * n;
   rc = 0;
   rc = rc ? rc : dalloc(&ix->roots, T);
@@ -963,6 +1057,25 @@ fgraft_status fgraft_dense_block_dist(const void* X, int64_t n, int32_t d, int64
   return (fgraft_status)rc;
 }
 
+fgraft_status fgraft_dense_block_gram(const void* X, int64_t n, int32_t d, int64_t ld,
+                                      int32_t metric, const int32_t* block_ids, int64_t nb,
+                                      int32_t bs, int32_t precision, float* out_min, double* ms,
+                                      fgraft_stream stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  VecLayout L;
+  int rc = check_vectors(X, n, d, ld, metric, &L);
+  if (rc) return (fgraft_status)rc;
+  if (metric == L2_U8) return (fgraft_status)fail(FGRAFT_EINVAL, "the Gram path takes float32 metrics");
+  if (precision != 1 && precision != 2)
+    return (fgraft_status)fail(FGRAFT_EINVAL, "precision must be 1 (BF16) or 2 (FP8)");
+  if (nb < 0 || nb > 65535 || bs < 1 || bs > 1024)
+    return (fgraft_status)fail(FGRAFT_EINVAL, "need nb <= 65535, bs in [1,1024]");
+  if (ms) *ms = 0.0;
+  if (nb == 0) return FGRAFT_OK;
+  if (!block_ids || !out_min) return (fgraft_status)fail(FGRAFT_EINVAL, "NULL pointer");
+  return (fgraft_status)dense_gram_tc(L, block_ids, nb, bs, precision == 2, out_min, ms, s);
+}
+
 fgraft_status fgraft_index_copy(const fgraft_index* ix, int32_t* roots, int32_t* parents,
                                 int64_t* s_offsets, int32_t* s_ids, int32_t* rows,
                                 int32_t* counts, fgraft_stream stream) {
@@ -1023,6 +1136,7 @@ fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t war
     ix->hash_auto = false;
   }
   if (warps_per_cta) ix->wpc = warps_per_cta;
+  if (ix->gather && ix->L.nchunks > 64) ix->gather = 0;
   const int rc = size_visited_bitmaps(ix);
   if (rc) return (fgraft_status)rc;
   if (ix->graph_exec) {
@@ -1030,6 +1144,115 @@ fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t war
     ix->graph_exec = nullptr;
   }
   return FGRAFT_OK;
+}
+
+fgraft_status fgraft_index_autotune(fgraft_index* ix, int32_t sample, fgraft_stream stream,
+                                    fgraft_tuning* chosen) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!ix) return (fgraft_status)fail(FGRAFT_EINVAL, "index is NULL");
+  if (sample < 1) return (fgraft_status)fail(FGRAFT_EINVAL, "sample must be >= 1");
+  int rc = check_err_flag(ix, s);
+  if (rc) return (fgraft_status)rc;
+  // a candidate: warps per CTA, hash_log2 (0: occupancy rule), overflow mode,
+  // gather, id batch
+  using Cfg = std::array<int, 5>;
+  const Cfg start{ix->wpc, ix->hash_auto ? 0 : ix->hash_log2, ix->overflow_mode, ix->gather,
+                  ix->id_batch};
+  const Cfg defaults{4, 0, 1, 0, 2};
+  unsigned long long* tctr = nullptr;
+  if ((rc = dalloc(&tctr, 8))) return (fgraft_status)rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  // one calibration run of the given settings: the faster of two timed runs
+  auto time_one = [&](const Cfg& c, float* ms) -> int {
+    apply_settings(ix, c[0], c[1], c[2], c[3], c[4]);
+    int r = size_visited_bitmaps(ix);
+    if (r) return r;
+    *ms = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, s);
+      r = harvest_sample(ix, sample, tctr, s);
+      if (r) return r;
+      cudaEventRecord(e1, s);
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) return cuda_fail(e, "autotune");
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, e0, e1);
+      *ms = std::min(*ms, t);
+    }
+    return check_err_flag(ix, s);
+  };
+  // options per setting; the shared-memory gather only for rows of at most
+  // 64 chunks (32 rows of 1 KB per warp)
+  const std::vector<std::vector<int>> opts = {
+      {4, 2, 1}, {0, 9, 10, 11, 12}, {1, 2},
+      ix->L.nchunks <= 64 ? std::vector<int>{0, 1} : std::vector<int>{0}, {1, 2}};
+  float base_ms = 0.0f, best_ms = 0.0f;
+  Cfg best = defaults;
+  rc = time_one(defaults, &base_ms);  // warm-up, then the defaults' time
+  if (!rc) rc = time_one(defaults, &base_ms);
+  best_ms = base_ms;
+  // coordinate descent: each setting in turn over its options, the others
+  // held at the best so far; two rounds
+  for (int round = 0; round < 2 && !rc; ++round)
+    for (int dim = 0; dim < 5 && !rc; ++dim)
+      for (int v : opts[dim]) {
+        Cfg c = best;
+        c[dim] = v;
+        if (c == best) continue;
+        float ms = 0.0f;
+        if ((rc = time_one(c, &ms))) break;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = c;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(tctr);
+  if (rc) {
+    apply_settings(ix, start[0], start[1], start[2], start[3], start[4]);
+    size_visited_bitmaps(ix);
+    return (fgraft_status)rc;
+  }
+  apply_settings(ix, best[0], best[1], best[2], best[3], best[4]);
+  rc = size_visited_bitmaps(ix);
+  if (rc) return (fgraft_status)rc;
+  const int64_t nsamp = std::min<int64_t>(sample, (ix->L.n + ix->nb - 1) / ix->nb);
+  const float us = 1e3f * best_ms / (float)nsamp;
+  tune_table_put(tune_key(ix), TuneVal{best[0], best[1], best[2], best[3], best[4], us});
+  if (chosen) {
+    chosen->warps_per_cta = best[0];
+    chosen->hash_log2 = best[1];
+    chosen->overflow_mode = best[2];
+    chosen->gather = best[3];
+    chosen->id_batch = best[4];
+    chosen->us_per_query = us;
+    chosen->default_us_per_query = 1e3f * base_ms / (float)nsamp;
+  }
+  return FGRAFT_OK;
+}
+
+fgraft_status fgraft_index_set_tuning(fgraft_index* ix, const fgraft_tuning* t) {
+  if (!ix || !t) return (fgraft_status)fail(FGRAFT_EINVAL, "NULL argument");
+  if (t->warps_per_cta < 1 || t->warps_per_cta > 4 ||
+      (t->hash_log2 != 0 && (t->hash_log2 < 7 || t->hash_log2 > 14)) || t->overflow_mode < 1 ||
+      t->overflow_mode > 2 || t->gather < 0 || t->gather > 1 || t->id_batch < 1 ||
+      t->id_batch > 2 || (t->gather && ix->L.nchunks > 64))
+    return (fgraft_status)fail(FGRAFT_EINVAL, "tuning setting out of range");
+  apply_settings(ix, t->warps_per_cta, t->hash_log2, t->overflow_mode, t->gather, t->id_batch);
+  return (fgraft_status)size_visited_bitmaps(ix);
+}
+
+fgraft_status fgraft_tuning_table_save(const char* path) {
+  if (!path) return (fgraft_status)fail(FGRAFT_EINVAL, "path is NULL");
+  return (fgraft_status)tune_table_save(path);
+}
+
+fgraft_status fgraft_tuning_table_load(const char* path) {
+  if (!path) return (fgraft_status)fail(FGRAFT_EINVAL, "path is NULL");
+  return (fgraft_status)tune_table_load(path);
 }
 
 fgraft_status fgraft_index_profile(fgraft_index* ix, int32_t enable) {

@@ -16,6 +16,8 @@
 // kernel on per-warp global scratch.
 #pragma once
 #include "common.cuh"
+#include "internal.h"
+#include "tc.cuh"
 
 namespace fg {
 
@@ -84,19 +86,50 @@ struct BeamArgs {
   int32_t* Eg_cnt;
   uint32_t* err_flag;
   unsigned long long* counters;  // evals, expansions, prune evals, ids scanned, overflows
+  // gather: 1 = the queued vectors are bulk-copied into a per-warp shared
+  // buffer of 32 rows (after the staged query) and evaluated from there;
+  // 0 = loaded into registers by the lane groups.  id_batch: chunks of 32
+  // neighbour ids whose bitmap visited tests are issued together (1..2).
+  int32_t gather;
+  int32_t id_batch;
+  int32_t wait_polls;
 };
 
-template <int METRIC, int G, int K, int S>
+// Chunks of 32 neighbour ids whose bitmap visited tests are issued together
+// (two keeps the harvest kernels within 128 registers without spills).
+constexpr int kIdBatch = 2;
+
+template <int METRIC, int G, int K, int S, bool GATHER>
 struct Beam {
 
   // Evaluate queue[0..cnt) (cnt <= 32) against the staged query qs and merge
   // the keys into the pool.  Lane groups of P lanes take one candidate each.
   static __device__ __forceinline__ void eval_merge(const BeamArgs& a, const uint4* qs,
                                                     const int32_t* queue, int cnt,
-                                                    uint64_t (&pool)[S], int lane) {
+                                                    uint64_t (&pool)[S], int lane, uint4* gb,
+                                                    uint64_t* gbar, uint32_t& gphase) {
     using L = Lanes<G, K>;
     const int g = lane / L::P, j = lane % L::P;
     uint64_t mykey = PAD;
+    if constexpr (GATHER) {
+      // every queued row in flight at once: one bulk copy per lane into the
+      // warp's buffer, completion counted in bytes on the warp's barrier
+      const uint32_t rb = 16u * (uint32_t)a.nchunks;
+      if (lane == 0) mbar_arrive_expect_tx(gbar, rb * (uint32_t)cnt);
+      __syncwarp();
+      if (lane < cnt)
+        bulk_g2s(gb + (int64_t)lane * a.nchunks, a.X + (int64_t)queue[lane] * a.ld_bytes, rb, gbar);
+      bool ok = false;
+      for (int it = 0; it < a.wait_polls && !ok; ++it) ok = mbar_try_wait(gbar, gphase);
+      if (!ok) {
+        // a copy did not land in time: record it, and let it land before the
+        // buffer is used again (the results of this launch are reported bad)
+        if (lane == 0) atomicOr(a.err_flag + 3, 1u);
+        for (int it = 0; it < kDrainPolls && !ok; ++it) ok = mbar_try_wait(gbar, gphase);
+      }
+      gphase ^= 1u;
+      __syncwarp();
+    }
     // float32 metrics keep this lane's query chunks in registers for the
     // whole batch (uint8 rows read them from shared memory)
     uint4 qr[L::VL][K];
@@ -106,8 +139,13 @@ struct Beam {
 #pragma unroll
       for (int u = 0; u < L::UW; ++u) {
         const int idx = base + u * L::CPW + g;
-        const int32_t id = idx < cnt ? queue[idx] : queue[0];
-        load_slots<G, K>(a.X + (int64_t)id * a.ld_bytes, a.nchunks, j, y[u]);
+        if constexpr (GATHER) {
+          load_slots_smem<G, K>(gb + (int64_t)(idx < cnt ? idx : 0) * a.nchunks, a.nchunks, j,
+                                y[u]);
+        } else {
+          const int32_t id = idx < cnt ? queue[idx] : queue[0];
+          load_slots<G, K>(a.X + (int64_t)id * a.ld_bytes, a.nchunks, j, y[u]);
+        }
       }
 #pragma unroll
       for (int u = 0; u < L::UW; ++u) {
@@ -156,6 +194,19 @@ struct Beam {
     }
     int32_t* queue = reinterpret_cast<int32_t*>(tail);
     uint4* qs = reinterpret_cast<uint4*>(tail + 256);
+    // gather buffer (32 rows) and its barrier after the staged query
+    uint4* gb = GATHER ? reinterpret_cast<uint4*>(tail + 256 + a.qbytes) : nullptr;
+    uint64_t* gbar =
+        GATHER ? reinterpret_cast<uint64_t*>(tail + 256 + a.qbytes + 32ll * 16 * a.nchunks)
+               : nullptr;
+    uint32_t gphase = 0;
+    if (GATHER) {
+      if (lane == 0) {
+        mbar_init(gbar, 1);
+        fence_mbar_init();
+      }
+      __syncwarp();
+    }
     const int64_t nwork =
         a.qlist_len ? min((int64_t)*a.qlist_len, (int64_t)a.ovf_cap) : a.nq;
     unsigned long long c_ev = 0, c_ex = 0, c_pe = 0, c_sc = 0, c_ovf = 0;
@@ -210,18 +261,39 @@ struct Beam {
           return -1;
         };
         int32_t v_next = load_id(lane);
-        for (int base = 0; base < total; base += 32) {
-          const int32_t v = v_next;
-          if (base + 32 < total) v_next = load_id(base + 32 + lane);
-          bool isnew = false;
-          if (v >= 0) {
-            if (bm) {
-              const uint32_t bit = 1u << (v & 31);
-              isnew = (atomicOr(hash + (v >> 5), bit) & bit) == 0u;
-            } else {
-              isnew = hash_insert(hash, mask_buckets, (uint32_t)v);
-            }
+        for (int base = 0; base < total;) {
+          // With a bitmap the visited tests of up to kIdBatch chunks of 32 ids
+          // are issued together (independent atomics, one round trip); the
+          // hash inserts one chunk at a time.  Either way the chunks are queued
+          // in stream order, and the visited set is the same set.
+          int32_t vv[kIdBatch];
+          bool nw[kIdBatch];
+          int nchk = 1;
+          vv[0] = v_next;
+          if (bm) {
+            nchk = min(min(kIdBatch, a.id_batch), (total - base + 31) >> 5);
+#pragma unroll
+            for (int u = 1; u < kIdBatch; ++u)
+              vv[u] = u < nchk ? load_id(base + 32 * u + lane) : -1;
+            if (base + 32 * nchk < total) v_next = load_id(base + 32 * nchk + lane);
+            uint32_t old[kIdBatch];
+#pragma unroll
+            for (int u = 0; u < kIdBatch; ++u)
+              old[u] = vv[u] >= 0 ? atomicOr(hash + (vv[u] >> 5), 1u << (vv[u] & 31)) : FULL;
+#pragma unroll
+            for (int u = 0; u < kIdBatch; ++u)
+              nw[u] = vv[u] >= 0 && (old[u] & (1u << (vv[u] & 31))) == 0u;
+          } else {
+            if (base + 32 < total) v_next = load_id(base + 32 + lane);
+            nw[0] = vv[0] >= 0 && hash_insert(hash, mask_buckets, (uint32_t)vv[0]);
+#pragma unroll
+            for (int u = 1; u < kIdBatch; ++u) nw[u] = false;
           }
+#pragma unroll
+          for (int u = 0; u < kIdBatch; ++u) {
+          if (u < nchk) {
+          const int32_t v = vv[u];
+          const bool isnew = nw[u];
           const unsigned m = __ballot_sync(FULL, isnew);
           if (isnew) queue[qn + __popc(m & ((1u << lane) - 1u))] = v;
           qn += __popc(m);
@@ -247,7 +319,7 @@ struct Beam {
             vis_cap = INT_MAX;
           }
           if (qn >= 32) {
-            eval_merge(a, qs, queue, 32, pool, lane);
+            eval_merge(a, qs, queue, 32, pool, lane, gb, gbar, gphase);
             const int rest = qn - 32;
             const int32_t t = lane < rest ? queue[32 + lane] : 0;
             __syncwarp();
@@ -255,10 +327,14 @@ struct Beam {
             __syncwarp();
             qn = rest;
           }
+          }
+          }
+          if (ovf) break;
+          base += 32 * nchk;
         }
         if (ovf) break;
         if (qn > 0) {
-          eval_merge(a, qs, queue, qn, pool, lane);
+          eval_merge(a, qs, queue, qn, pool, lane, gb, gbar, gphase);
           __syncwarp();
           qn = 0;
         }
@@ -437,16 +513,22 @@ struct Beam {
   }
 };
 
-template <int METRIC, int G, int K, int S>
+// GATHER: candidate rows bulk-copied into a shared buffer (BeamArgs::gather);
+// instantiated for rows of at most 64 chunks.
+template <int METRIC, int G, int K, int S, bool GATHER>
 __global__ void __launch_bounds__(128, 4) beam_kernel(const BeamArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  Beam<METRIC, G, K, S>::run(a, smem);
+  Beam<METRIC, G, K, S, GATHER>::run(a, smem);
 }
 
-// Host-side launcher table entry (defined per metric in beam_*.cu).
+// Host-side launcher table entry (defined per metric in beam_*.cu, the
+// gather variants in beam_*_g.cu).
 using BeamKernelFn = void (*)(const BeamArgs);
 BeamKernelFn beam_kernel_metric0(int G, int K, int S);
 BeamKernelFn beam_kernel_metric1(int G, int K, int S);
 BeamKernelFn beam_kernel_metric2(int G, int K, int S);
+BeamKernelFn beam_kernel_metric0_gather(int G, int K, int S);
+BeamKernelFn beam_kernel_metric1_gather(int G, int K, int S);
+BeamKernelFn beam_kernel_metric2_gather(int G, int K, int S);
 
 }  // namespace fg

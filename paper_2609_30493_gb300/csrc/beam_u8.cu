@@ -7,9 +7,9 @@ namespace fg {
 BeamKernelFn beam_kernel_metric2(int G, int K, int S) {
 #define X(GG, KK)                                              \
   if (G == GG && K == KK) {                                    \
-    if (S == 1) return beam_kernel<L2_U8, GG, KK, 1>;             \
-    if (S == 2) return beam_kernel<L2_U8, GG, KK, 2>;             \
-    if (S == 4) return beam_kernel<L2_U8, GG, KK, 4>;             \
+    if (S == 1) return beam_kernel<L2_U8, GG, KK, 1, false>;             \
+    if (S == 2) return beam_kernel<L2_U8, GG, KK, 2, false>;             \
+    if (S == 4) return beam_kernel<L2_U8, GG, KK, 4, false>;             \
   }
   X(4,1) X(8,1) X(16,1)
 #undef X

@@ -472,6 +472,12 @@ __device__ __forceinline__ void warp_sort_mem(uint64_t* a, int N, int lane) {
   }
 }
 
+// Asynchronous prefetch of `bytes` (a multiple of 16, 16-byte aligned) into
+// the L2 cache: no registers, no completion to wait for.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Exact visited set: open addressing over 4-slot buckets, linear probing by
 // bucket.  Returns true when id was absent and is now inserted.  Lanes of a
 // warp may insert concurrently (a duplicate resolves through atomicCAS).  The

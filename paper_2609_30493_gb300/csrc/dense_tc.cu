@@ -2,16 +2,41 @@
 // set fixed before evaluation is a dense product and runs at arithmetic rate).
 //
 // Each block of up to 1024 points is centred on its float32 mean and rounded
-// to BF16; its Gram matrix is computed by tcgen05.mma (kind::f16, BF16 in,
-// FP32 accumulated in tensor memory), one 128 x 256 tile per CTA, and turned
-// into approximate distances.  They are only a filter: per row, every pair
-// whose approximate distance is within 2*eps of the k-th smallest is
-// recomputed in the canonical float32 order and the k smallest (delta, id) are
-// selected from those, where eps bounds |approximate - canonical| for the row
-// (BF16 input rounding, FP32 accumulation in any order, the canonical sum's
-// own rounding; times 2).  For every pair of the exact top-k,
-// approx <= canonical + eps <= k-th canonical + eps <= k-th approx + 2 eps, so
-// the result equals the canonical float32 top-k.
+// to BF16 (or to E4M3 with a scale per row).  dt_prep_kernel writes the
+// rounded rows already in the shared-memory image the tensor cores read
+// (K-major core matrices of 8 rows x 16 bytes, one 128 KB image per 128-byte
+// K slice of the 1024 rows), so one bulk copy moves a whole operand tile.
+//
+// dt_fused_kernel is persistent (one CTA per SM) and warp-specialised:
+//  - warp 8 (one lane) streams operand slices with bulk copies
+//    (cp.async.bulk, completion counted on an mbarrier) into a 3-stage ring:
+//    a 128-row A panel and a 256-row B chunk of the same block per stage;
+//  - warp 9 (one lane) issues tcgen05.mma (128 x 256, FP32 accumulation in
+//    tensor memory) into two 256-column accumulators, so that the epilogue of
+//    one column chunk overlaps the products of the next;
+//  - warps 0..7 read the accumulators with tcgen05.ld (thread = one row, one
+//    half of the chunk's columns) and turn the Gram values into approximate
+//    distances.
+// The approximate distances are only a filter.  For row i, every pair of the
+// exact top-k satisfies approx <= tau_k + 2 eps_i (tau_k: the k-th smallest
+// approximate distance of the row; eps_i bounds |approx - canonical| for all
+// its pairs): approx <= canonical + eps <= k-th canonical + eps
+// <= tau_k + 2 eps.  The row's tau_k is located by a two-level histogram
+// (32 bins over the row's value range, then 32 sub-bins of the bin holding
+// the k-th value) in two passes over the products, and a third pass collects
+// the columns whose approximate distance is at most an upper bound of tau_k
+// plus 2 eps; the tensor-core products are recomputed for each pass (they
+// cost far less than storing 1024 x 1024 distances).  dt_rerank_kernel then
+// evaluates the collected pairs in the canonical float32 order and keeps the
+// k smallest (delta, id): the result equals the canonical float32 top-k.
+//
+// eps_i comes from the rows' actual rounding residuals, not from the unit
+// roundoff: with q the rounded centred rows, r_i = |x_i - q_i| and
+// Qx = max_j |q_j|, Rq = max_j r_j, Mx = max_j |x_j| over the block,
+//   |<q_i,q_j> - <x_i,x_j>| <= r_i Qx + |x_i| Rq        (Cauchy-Schwarz),
+// plus the FP32 accumulation error gamma_K |q_i| Qx (any order), the float32
+// norms, the centring and the canonical distance's own rounding, all times a
+// safety factor of 2 (the tensor cores' accumulation order is undocumented).
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -25,75 +50,113 @@
 
 namespace fg {
 
-constexpr int TC_ROWS = 1024;  // rows of a block after padding
-constexpr int TC_M = 128;      // rows per CTA (one per TMEM lane)
-constexpr int TC_N = 256;      // columns per CTA (TMEM columns)
-constexpr int TC_KB = 128;     // K bytes per staged slice (8 core matrices of 16 bytes)
-constexpr int TC_THREADS = 128;
-constexpr uint32_t TC_TMEM_COLS = 256;
+constexpr int DT_ROWS = 1024;        // rows of a block after padding
+constexpr int DT_M = 128;            // rows per tile (one per TMEM lane)
+constexpr int DT_NC = 256;           // columns per chunk (MMA N)
+constexpr int DT_KB = 128;           // K bytes per slice (8 core matrices of 16 bytes)
+constexpr int DT_STAGES = 3;
+constexpr int DT_A_BYTES = DT_M * DT_KB;             // 16 KB
+constexpr int DT_B_BYTES = DT_NC * DT_KB;            // 32 KB
+constexpr int DT_STAGE_BYTES = DT_A_BYTES + DT_B_BYTES;
+constexpr int DT_SLICE_IMG = DT_ROWS * DT_KB;        // 128 KB: one slice of the 1024 rows
+constexpr int DT_EPI = 256;          // epilogue threads (warps 0..7)
+constexpr int DT_THREADS = DT_EPI + 64;
+constexpr int DT_NBIN = 32;
+constexpr uint32_t DT_TMEM_COLS = 512;
+constexpr uint32_t DT_FALLBACK = 0xFFFFFFFFu;  // candidate count: every valid column
 
-// Byte offset of the 16-byte unit (row r, byte kb) of a staged K-slice: core
+// Byte offset of the 16-byte unit (row r, K byte kb) in a slice image: core
 // matrix (r/8, kb/16) at (r/8)*1024 + (kb/16)*128, row r%8 at +16*(r%8).
-// A slice is 64 BF16 or 128 E4M3 elements per row.
 __host__ __device__ constexpr uint32_t tile_off(int r, int kb) {
   return (uint32_t)((r >> 3) * 1024 + (kb >> 4) * 128 + (r & 7) * 16);
 }
 
-// --------------------------------------------------------------------------
-// 1. Centre, round to BF16, norms
-// --------------------------------------------------------------------------
-struct TcArgs {
+struct DtArgs {
   const char* X;
   int64_t ld_bytes;
   int32_t d;
-  int32_t dpad;  // d rounded up to a whole slice (64 BF16 or 128 E4M3 elements)
-  int32_t rowb;  // bytes of a rounded row (2 dpad or dpad)
-  int32_t fp8;   // 0: BF16, 1: E4M3 with a scale per row
-  float u_in;    // unit roundoff of the input rounding (with the E4M3 subnormal term)
   int32_t metric;
+  int32_t fp8;   // 0: BF16, 1: E4M3 with a scale per row
+  int32_t dpad;  // d rounded up to a whole slice (64 BF16 or 128 E4M3 elements)
+  int32_t rowb;  // bytes of a rounded row
+  int32_t nsl;   // slices per row (rowb / 128)
   const int32_t* block_ids;
   int64_t nb;
   int32_t bs;
-  unsigned char* Xb;  // [nb][1024][rowb]
-  float* sc;          // [nb][1024] E4M3 row scale (the row is sc * its codes)
-  float* nrm;         // [nb][1024] squared norm of the centred float32 row
-  float* cc;          // [nb][1024] angular: (1 - |x|^2) / 2
-  float* Mx;          // [nb] largest centred norm
-  float* LP;          // [nb][1024][1024] approximate distances
-  uint32_t* err;  // [0] timeout flag, [8] and [9] error maxima (float bits)
-  unsigned long long* pairs;  // valid ordered pairs over all blocks
-  int32_t errstat;  // measure the filter's error against float64 on the reranked pairs
-  int32_t wait_polls;  // first bounded wait for a slice's products
+  int32_t k;
+  unsigned char* Xt;  // [nb][nsl][slice image]
+  float4* rowA;       // [nb][1024] {|x|^2 centred, (1 - |x|^2)/2 raw (angular), scale, valid}
+  float4* rowB;       // [nb][1024] {|x - q|, |q|, |x|^2 raw, 0}
+  float* bst;         // [nb][8] {Mx, Rq, Qx, X2max, Cmax}: maxima over the block (>= 0)
+  uint32_t* nvalid;   // [nb]
+  uint16_t* cand;     // [nb][1024][1024] candidate columns of each row
+  uint32_t* ccnt;     // [nb][1024] their number (DT_FALLBACK: every valid column)
+  float* cdt;         // optional [nb][1024][1024]: approximate distance of each candidate
+  float* reps;        // optional [nb][1024]: eps of each row
+  float* rowmin;      // Gram-only mode: [nb * bs] smallest approximate distance per row
+  uint32_t* err;      // [0] timeout flag, [8] and [9] error maxima (float bits)
+  unsigned long long* pairs;     // valid ordered pairs over all blocks
+  unsigned long long* reranked;  // pairs recomputed in the canonical order
+  int32_t mode;       // 0: Gram and approximate distances only (per-row minimum), 1: filter
+  int32_t errstat;    // keep approximate distances and eps for the float64 error check
+  int32_t wait_polls;
 };
 
-__global__ void __launch_bounds__(256) dense_prep_kernel(const TcArgs a) {
+// --------------------------------------------------------------------------
+// 1. Centre, round, write the tile images; per-row and per-block norms
+// --------------------------------------------------------------------------
+// Grid (nb, 4): CTA (b, y) centres and rounds rows 256 y .. 256 y + 255 of
+// block b.  The block mean is summed in one fixed order by every CTA: warp w
+// adds the rows r = w, w + 8, w + 16, .. in turn, then the eight partial
+// sums are added in warp order.
+__global__ void __launch_bounds__(256) dt_prep_kernel(const DtArgs a) {
   __shared__ float mu[1024];
-  __shared__ int nvalid;
+  __shared__ float part[8][128];
+  __shared__ int nval;
   const int64_t blk = blockIdx.x;
+  const int y = blockIdx.y;
   const int32_t* ids = a.block_ids + blk * a.bs;
-  if (threadIdx.x == 0) nvalid = 0;
+  const int lane0 = threadIdx.x & 31, warp0 = threadIdx.x >> 5;
+  if (threadIdx.x == 0) nval = 0;
   __syncthreads();
   int cnt = 0;
   for (int r = threadIdx.x; r < a.bs; r += blockDim.x) cnt += ids[r] >= 0;
-  atomicAdd(&nvalid, cnt);
+  atomicAdd(&nval, cnt);
   __syncthreads();
-  const float inv = nvalid > 0 ? 1.0f / (float)nvalid : 0.0f;
-  if (threadIdx.x == 0 && nvalid > 1)
-    atomicAdd(a.pairs, (unsigned long long)nvalid * (unsigned long long)(nvalid - 1));
-  for (int j = threadIdx.x; j < a.d; j += blockDim.x) {
-    float s = 0.0f;
-    for (int r = 0; r < a.bs; ++r) {
-      const int32_t id = ids[r];
-      if (id >= 0) s += reinterpret_cast<const float*>(a.X + (int64_t)id * a.ld_bytes)[j];
-    }
-    mu[j] = s * inv;
+  const int nv = nval;
+  const float inv = nv > 0 ? 1.0f / (float)nv : 0.0f;
+  if (threadIdx.x == 0 && y == 0) {
+    a.nvalid[blk] = (uint32_t)nv;
+    if (nv > 1) atomicAdd(a.pairs, (unsigned long long)nv * (unsigned long long)(nv - 1));
   }
-  __syncthreads();
+  for (int j0 = 0; j0 < a.d; j0 += 128) {
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int r = warp0; r < a.bs; r += 8) {
+      const int32_t id = ids[r];
+      if (id < 0) continue;
+      const float* xr = reinterpret_cast<const float*>(a.X + (int64_t)id * a.ld_bytes);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int j = j0 + lane0 + 32 * e;
+        if (j < a.d) acc[e] += xr[j];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) part[warp0][lane0 + 32 * e] = acc[e];
+    __syncthreads();
+    if (threadIdx.x < 128 && j0 + (int)threadIdx.x < a.d) {
+      float s = part[0][threadIdx.x];
+      for (int w = 1; w < 8; ++w) s += part[w][threadIdx.x];
+      mu[j0 + threadIdx.x] = s * inv;
+    }
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int r = warp; r < TC_ROWS; r += 8) {
+  const int epu = a.fp8 ? 16 : 8;  // elements per 16-byte unit
+  const int nunits = a.rowb / 16;
+  unsigned char* img = a.Xt + blk * (int64_t)a.nsl * DT_SLICE_IMG;
+  for (int r = 256 * y + warp; r < 256 * y + 256; r += 8) {
     const int32_t id = r < a.bs ? ids[r] : -1;
-    unsigned char* dst = a.Xb + (blk * TC_ROWS + r) * (int64_t)a.rowb;
-    float s2 = 0.0f, x2 = 0.0f;
     const float* xr = id >= 0 ? reinterpret_cast<const float*>(a.X + (int64_t)id * a.ld_bytes)
                               : nullptr;
     // E4M3: the row's largest centred magnitude maps to 448, the largest
@@ -101,405 +164,846 @@ __global__ void __launch_bounds__(256) dense_prep_kernel(const TcArgs a) {
     float scale = 1.0f;
     if (a.fp8) {
       float mx = 0.0f;
-      for (int j = lane; j < a.d; j += 32)
-        if (id >= 0) mx = fmaxf(mx, fabsf(xr[j] - mu[j]));
+      if (id >= 0)
+        for (int j = lane; j < a.d; j += 32) mx = fmaxf(mx, fabsf(xr[j] - mu[j]));
 #pragma unroll
       for (int off = 16; off >= 1; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, off));
       scale = mx > 0.0f ? mx / 448.0f : 1.0f;
     }
     const float rs = 1.0f / scale;
-    for (int j = lane; j < a.dpad; j += 32) {
-      float v = 0.0f;
-      if (id >= 0 && j < a.d) {
-        const float x = xr[j];
-        v = x - mu[j];
-        x2 = __fmaf_rn(x, x, x2);
+    float s2 = 0.0f, x2 = 0.0f, r2 = 0.0f, q2 = 0.0f;
+    for (int u = lane; u < nunits; u += 32) {
+      uint32_t w[4] = {0u, 0u, 0u, 0u};
+      for (int e = 0; e < epu; ++e) {
+        const int j = u * epu + e;
+        float v = 0.0f;
+        if (id >= 0 && j < a.d) {
+          const float x = xr[j];
+          v = x - mu[j];
+          x2 = __fmaf_rn(x, x, x2);
+        }
+        s2 = __fmaf_rn(v, v, s2);
+        float deq;
+        uint32_t bits;
+        if (a.fp8) {
+          const __nv_fp8_storage_t c = __nv_cvt_float_to_fp8(v * rs, __NV_SATFINITE, __NV_E4M3);
+          __nv_fp8_e4m3 qv;
+          qv.__x = c;
+          deq = scale * static_cast<float>(qv);
+          bits = (uint32_t)c;
+          w[e >> 2] |= bits << (8 * (e & 3));
+        } else {
+          const __nv_bfloat16 b = __float2bfloat16_rn(v);
+          deq = __bfloat162float(b);
+          bits = (uint32_t)__bfloat16_as_ushort(b);
+          w[e >> 1] |= bits << (16 * (e & 1));
+        }
+        const float dr = v - deq;
+        r2 = __fmaf_rn(dr, dr, r2);
+        q2 = __fmaf_rn(deq, deq, q2);
       }
-      s2 = __fmaf_rn(v, v, s2);
-      if (a.fp8)
-        dst[j] = (unsigned char)__nv_cvt_float_to_fp8(v * rs, __NV_SATFINITE, __NV_E4M3);
-      else
-        reinterpret_cast<__nv_bfloat16*>(dst)[j] = __float2bfloat16_rn(v);
+      const int sl = u >> 3, kb = (u & 7) * 16;
+      *reinterpret_cast<uint4*>(img + (int64_t)sl * DT_SLICE_IMG + tile_off(r, kb)) =
+          make_uint4(w[0], w[1], w[2], w[3]);
     }
-    if (lane == 0) a.sc[blk * TC_ROWS + r] = scale;
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) {
       s2 += __shfl_xor_sync(FULL, s2, off);
       x2 += __shfl_xor_sync(FULL, x2, off);
+      r2 += __shfl_xor_sync(FULL, r2, off);
+      q2 += __shfl_xor_sync(FULL, q2, off);
     }
     if (lane == 0) {
-      a.nrm[blk * TC_ROWS + r] = s2;
-      a.cc[blk * TC_ROWS + r] = id >= 0 ? 0.5f * (1.0f - x2) : 0.0f;
-      if (id >= 0) atomicMax(reinterpret_cast<unsigned int*>(a.Mx + blk), __float_as_uint(sqrtf(s2)));
+      const int64_t ri = blk * DT_ROWS + r;
+      const float cc = id >= 0 ? 0.5f * (1.0f - x2) : 0.0f;
+      a.rowA[ri] = make_float4(s2, cc, scale, id >= 0 ? 1.0f : 0.0f);
+      a.rowB[ri] = make_float4(sqrtf(r2), sqrtf(q2), x2, 0.0f);
+      if (id >= 0) {
+        unsigned int* bs = reinterpret_cast<unsigned int*>(a.bst + blk * 8);
+        atomicMax(bs + 0, __float_as_uint(sqrtf(s2)));
+        atomicMax(bs + 1, __float_as_uint(sqrtf(r2)));
+        atomicMax(bs + 2, __float_as_uint(sqrtf(q2)));
+        atomicMax(bs + 3, __float_as_uint(x2));
+        atomicMax(bs + 4, __float_as_uint(fmaxf(cc, 0.0f)));
+      }
     }
   }
 }
 
 // --------------------------------------------------------------------------
-// 2. Gram tile on the tensor cores and approximate distances
+// 2. Persistent fused Gram + filter
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(TC_THREADS) dense_gram_kernel(const TcArgs a) {
-  extern __shared__ __align__(1024) unsigned char tsm[];
-  unsigned char* As = tsm;                      // 128 rows x 128 bytes = 16 KB
-  unsigned char* Bs = tsm + TC_M * TC_KB;       // 256 rows x 128 bytes = 32 KB
-  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + TC_N * TC_KB);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
-  const int rt = blockIdx.x, ct = blockIdx.y;
-  const int64_t blk = blockIdx.z;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+struct DtSmem {
+  static constexpr int hist = DT_STAGES * DT_STAGE_BYTES;            // [NBIN + 1][256] u32
+  static constexpr int col = hist + (DT_NBIN + 1) * DT_EPI * 4;      // [1024] float2
+  static constexpr int rowcnt = col + DT_ROWS * 8;                   // [128] u32
+  static constexpr int xcnt = rowcnt + DT_M * 4;                     // [256] u32
+  static constexpr int xval = xcnt + DT_EPI * 4;                     // [256] f32
+  static constexpr int bars = xval + DT_EPI * 4;                     // 16 x u64
+  static constexpr int misc = bars + 16 * 8;                         // tmem address, flags
+  static constexpr int bytes = misc + 16;
+};
 
-  if (warp == 0) {
-    tmem_alloc(tmem_slot, TC_TMEM_COLS);
-    tmem_relinquish();
+__device__ __forceinline__ int dt_bin(float x, float lo, float iw) {
+  const int b = __float2int_rz((x - lo) * iw);
+  return min(DT_NBIN - 1, max(0, b));
+}
+
+// Per-thread state of one row in the filter's epilogue.
+struct DtRow {
+  float base;  // row term of the approximate distance
+  float f;     // Gram factor (1 angular, 2 squared L2; times the row's E4M3 scale)
+  int i;       // the row's column index (its own pair is skipped)
+  float lo, iw1, lo2, iw2, ucut;
+  int b1, s2;
+  uint32_t cin;
+  float vmax, vmin;
+};
+
+// The 32 Gram values v of columns j0..j0+31 for one row.  The approximate
+// distance is base_i + col_j - f * g (angular: base = |x_i|^2 / 2 + c_i with
+// the centred norm and c = (1 - |x|^2) / 2, f = 1; squared L2: base =
+// |x_i|^2, f = 2; for E4M3 g is scaled by the column's scale here and by the
+// row's in f).  Invalid columns carry col = +inf.  PASS 0 counts the values
+// in the first-level bins, PASS 1 the sub-bins of bin b1, PASS 2 collects
+// the candidates, PASS 3 keeps the minimum (Gram-only mode).  Counts are
+// shared-memory atomics whose results are not used, so they do not wait on
+// one another.
+template <int PASS, bool FP8>
+__device__ __forceinline__ void dt_values(const uint32_t (&v)[32], const float2* col, int j0,
+                                          DtRow& r, uint32_t* hcol, uint32_t* rowcnt_il,
+                                          uint16_t* cand, float* cdt) {
+  // no branch per value: a value that does not count goes to the unused bin
+  // DT_NBIN, and the candidates of PASS 2 are appended from a bit mask
+  uint32_t take = 0;
+  float dts[32];
+#pragma unroll
+  for (int t = 0; t < 32; ++t) {
+    const int j = j0 + t;
+    const float2 cj = col[j];
+    float g = __uint_as_float(v[t]);
+    if (FP8) g *= cj.y;
+    const float dt = __fmaf_rn(-r.f, g, r.base + cj.x);
+    const bool ok = dt < INFINITY && j != r.i;
+    if (PASS == 0) {
+      atomicAdd(hcol + (ok ? dt_bin(dt, r.lo, r.iw1) : DT_NBIN) * DT_EPI, 1u);
+    } else if (PASS == 1) {
+      const bool in = ok && dt_bin(dt, r.lo, r.iw1) == r.b1;
+      atomicAdd(hcol + (in ? dt_bin(dt, r.lo2, r.iw2) : DT_NBIN) * DT_EPI, 1u);
+    } else if (PASS == 2) {
+      const int k1 = dt_bin(dt, r.lo, r.iw1);
+      const bool inkey = ok && (k1 < r.b1 || (k1 == r.b1 && dt_bin(dt, r.lo2, r.iw2) <= r.s2));
+      r.cin += inkey ? 1u : 0u;
+      r.vmax = inkey ? fmaxf(r.vmax, dt) : r.vmax;
+      take |= (inkey || (ok && dt <= r.ucut)) ? (1u << t) : 0u;
+      dts[t] = dt;
+    } else {
+      r.vmin = ok ? fminf(r.vmin, dt) : r.vmin;
+    }
   }
+  if (PASS == 2) {
+    while (take) {
+      const int t = __ffs(take) - 1;
+      take &= take - 1u;
+      const uint32_t pos = atomicAdd(rowcnt_il, 1u);
+      cand[pos] = (uint16_t)(j0 + t);
+      if (cdt) {
+        float dv = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) dv = q == t ? dts[q] : dv;
+        cdt[pos] = dv;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(DT_THREADS, 1) dt_fused_kernel(const DtArgs a) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  unsigned char* stages = dsm;
+  uint32_t* hist = reinterpret_cast<uint32_t*>(dsm + DtSmem::hist);
+  float4* coldata = reinterpret_cast<float4*>(dsm + DtSmem::col);
+  uint32_t* rowcnt = reinterpret_cast<uint32_t*>(dsm + DtSmem::rowcnt);
+  uint32_t* xcnt = reinterpret_cast<uint32_t*>(dsm + DtSmem::xcnt);
+  float* xval = reinterpret_cast<float*>(dsm + DtSmem::xval);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(dsm + DtSmem::bars);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(dsm + DtSmem::misc);
+  int* abort_flag = reinterpret_cast<int*>(dsm + DtSmem::misc + 4);
+  int* zero_flag = reinterpret_cast<int*>(dsm + DtSmem::misc + 8);
+  uint64_t* full = bars;        // [3] operand stage landed
+  uint64_t* empty = bars + 3;   // [3] operand stage consumed by its MMAs
+  uint64_t* tfull = bars + 6;   // [2] accumulator complete
+  uint64_t* tempty = bars + 8;  // [2] accumulator read by the epilogue
+  uint64_t* done = bars + 10;   // every MMA of the CTA complete
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    mbar_init(bar, 1);
+    for (int s = 0; s < DT_STAGES; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull + b, 1);
+      mbar_init(tempty + b, DT_EPI);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    *zero_flag = 0;
     fence_mbar_init();
+  }
+  if (warp == 9) {
+    tmem_alloc(tmem_slot, DT_TMEM_COLS);
+    tmem_relinquish();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const volatile int* abortp = abort_flag;
+  const int64_t ntiles = a.nb * (DT_ROWS / DT_M);
+  const int npass = a.mode == 0 ? 1 : 3;
+  const int nch = DT_ROWS / DT_NC;
 
-  const unsigned char* Ag = a.Xb + (blk * TC_ROWS + rt * TC_M) * (int64_t)a.rowb;
-  const unsigned char* Bg = a.Xb + (blk * TC_ROWS + ct * TC_N) * (int64_t)a.rowb;
-  const uint32_t idesc = a.fp8 ? idesc_e4m3(TC_M, TC_N) : idesc_bf16(TC_M, TC_N);
-  bool ok = true;
-  const int nslices = a.rowb / TC_KB;
-  for (int sl = 0; sl < nslices; ++sl) {
-    const int k0 = sl * TC_KB;
-    // stage the slices: 16-byte units (row, 16 K bytes), 8 per row
-    for (int u = tid; u < TC_M * 8; u += TC_THREADS) {
-      const int r = u >> 3, kc = u & 7;
-      *reinterpret_cast<uint4*>(As + tile_off(r, kc * 16)) =
-          *reinterpret_cast<const uint4*>(Ag + (int64_t)r * a.rowb + k0 + kc * 16);
-    }
-    for (int u = tid; u < TC_N * 8; u += TC_THREADS) {
-      const int r = u >> 3, kc = u & 7;
-      *reinterpret_cast<uint4*>(Bs + tile_off(r, kc * 16)) =
-          *reinterpret_cast<const uint4*>(Bg + (int64_t)r * a.rowb + k0 + kc * 16);
-    }
-    fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        // one MMA takes 32 K bytes (16 BF16 or 32 E4M3 elements): two core
-        // matrices along K (2 x 128 bytes of shared memory)
-        const uint64_t ad = smem_desc(a0 + kk * 256, 128, 1024);
-        const uint64_t bd = smem_desc(b0 + kk * 256, 128, 1024);
-        if (a.fp8)
-          mma_e4m3(tmem, ad, bd, idesc, (sl > 0 || kk > 0) ? 1u : 0u);
-        else
-          mma_bf16(tmem, ad, bd, idesc, (sl > 0 || kk > 0) ? 1u : 0u);
+  if (warp == 8) {
+    // ---- producer: operand slices into the stage ring ----
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int64_t blk = tile >> 3;
+        const int rt = (int)(tile & 7);
+        const unsigned char* base = a.Xt + blk * (int64_t)a.nsl * DT_SLICE_IMG;
+        for (int pass = 0; pass < npass && ok; ++pass)
+          for (int c = 0; c < nch && ok; ++c)
+            for (int sl = 0; sl < a.nsl; ++sl, ++it) {
+              const uint32_t s = it % DT_STAGES, ph = (it / DT_STAGES) & 1u;
+              if (!mbar_wait_bounded(empty + s, ph ^ 1u, a.wait_polls, abortp)) {
+                ok = false;
+                break;
+              }
+              unsigned char* dst = stages + s * DT_STAGE_BYTES;
+              const unsigned char* src = base + (int64_t)sl * DT_SLICE_IMG;
+              mbar_arrive_expect_tx(full + s, DT_STAGE_BYTES);
+              bulk_g2s(dst, src + rt * DT_A_BYTES, DT_A_BYTES, full + s);
+              bulk_g2s(dst + DT_A_BYTES, src + c * DT_B_BYTES, DT_B_BYTES, full + s);
+            }
       }
-      mma_commit(bar);
-    }
-    // wait (bounded) for the slice's products before its buffers are reused;
-    // every thread takes the same decision
-    bool done = false;
-    for (int it = 0; it < a.wait_polls && !done; ++it) done = mbar_try_wait(bar, sl & 1);
-    done = __syncthreads_and(done);
-    if (!done) {
-      ok = false;
-      if (tid == 0) atomicOr(a.err, 1u);
-      // let the slice's products land before the tensor memory is released
-      for (int it = 0; it < kDrainPolls; ++it)
-        if (mbar_try_wait(bar, sl & 1)) break;
-      break;
-    }
-    tc_fence_after();
-  }
-
-  if (ok) {
-    // epilogue: warp w reads TMEM lanes 32w..32w+31 (rows), 32 columns at a time
-    const int i = rt * TC_M + warp * 32 + lane;
-    const int64_t rowbase = blk * TC_ROWS;
-    const float ni = a.nrm[rowbase + i];
-    const float ci = a.cc[rowbase + i];
-    const float si = a.fp8 ? a.sc[rowbase + i] : 1.0f;
-    // each warp passes its 32 x 32 blocks through shared memory (the staging
-    // buffers are free now) so that every store writes one 128-byte row piece
-    float* stg = reinterpret_cast<float*>(tsm) + warp * 32 * 33;
-    float* out0 = a.LP + (rowbase + rt * TC_M + warp * 32) * (int64_t)TC_ROWS + ct * TC_N;
-    for (int c0 = 0; c0 < TC_N; c0 += 32) {
-      uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-#pragma unroll
-      for (int t = 0; t < 32; ++t) {
-        const int j = ct * TC_N + c0 + t;
-        const float g = a.fp8 ? __uint_as_float(v[t]) * (si * a.sc[rowbase + j])
-                              : __uint_as_float(v[t]);
-        const float s = a.nrm[rowbase + j] + ni - 2.0f * g;
-        stg[lane * 33 + t] = a.metric == ANGULAR_F32 ? 0.5f * s + ci + a.cc[rowbase + j] : s;
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(a.err, 1u);
       }
-      __syncwarp();
-      for (int rr = 0; rr < 32; ++rr) out0[(int64_t)rr * TC_ROWS + c0 + lane] = stg[rr * 33 + lane];
-      __syncwarp();
+      // every issued copy lands before the CTA may exit
+      for (uint32_t s = 0; s < DT_STAGES; ++s) {
+        if (it <= s) continue;
+        const uint32_t last = s + DT_STAGES * ((it - 1 - s) / DT_STAGES);
+        mbar_wait_bounded(full + s, (last / DT_STAGES) & 1u, kDrainPolls, zero_flag);
+      }
+    }
+  } else if (warp == 9) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      const uint32_t idesc = a.fp8 ? idesc_e4m3(DT_M, DT_NC) : idesc_bf16(DT_M, DT_NC);
+      uint32_t it = 0, ci = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
+        for (int pass = 0; pass < npass && ok; ++pass)
+          for (int c = 0; c < nch && ok; ++c, ++ci) {
+            const uint32_t buf = ci & 1u, bph = (ci >> 1) & 1u;
+            if (!mbar_wait_bounded(tempty + buf, bph ^ 1u, a.wait_polls, abortp)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t dt = tmem + buf * DT_NC;
+            for (int sl = 0; sl < a.nsl; ++sl, ++it) {
+              const uint32_t s = it % DT_STAGES, ph = (it / DT_STAGES) & 1u;
+              if (!mbar_wait_bounded(full + s, ph, a.wait_polls, abortp)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t a0 = smem_u32(stages + s * DT_STAGE_BYTES);
+              const uint32_t b0 = a0 + DT_A_BYTES;
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                // one MMA takes 32 K bytes (16 BF16 or 32 E4M3 elements): two
+                // core matrices along K (2 x 128 bytes of shared memory)
+                const uint64_t ad = smem_desc(a0 + kk * 256, 128, 1024);
+                const uint64_t bd = smem_desc(b0 + kk * 256, 128, 1024);
+                const uint32_t acc = (sl > 0 || kk > 0) ? 1u : 0u;
+                if (a.fp8)
+                  mma_e4m3(dt, ad, bd, idesc, acc);
+                else
+                  mma_bf16(dt, ad, bd, idesc, acc);
+              }
+              mma_commit(empty + s);  // the stage is free once these products are done
+            }
+            if (ok) mma_commit(tfull + buf);
+          }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(a.err, 1u);
+      }
+      // every product issued lands before the tensor memory is released
+      mma_commit(done);
+      mbar_wait_bounded(done, 0u, kDrainPolls, zero_flag);
+    }
+  } else {
+    // ---- epilogue: warps 0..7, thread = (row il, column half h) ----
+    const int etid = tid;  // 0..255
+    const int q = warp & 3, h = warp >> 2;
+    const int il = 32 * q + lane;
+    const float u = 5.9604645e-8f;  // 2^-24
+    const bool ang = a.metric == ANGULAR_F32;
+    float2* col = reinterpret_cast<float2*>(coldata);
+    uint32_t* hcol = hist + etid;
+    uint32_t ci = 0;
+    bool aborted = false;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const int64_t blk = tile >> 3;
+      const int rt = (int)(tile & 7);
+      const int i = rt * DT_M + il;
+      for (int j = etid; j < DT_ROWS; j += DT_EPI) {
+        const float4 cj = a.rowA[blk * DT_ROWS + j];
+        const float cterm = ang ? __fmaf_rn(0.5f, cj.x, cj.y) : cj.x;
+        col[j] = make_float2(j < a.bs && cj.w != 0.0f ? cterm : INFINITY, cj.z);
+      }
+      if (etid < DT_M) rowcnt[etid] = 0u;
+      for (int b = 0; b < DT_NBIN; ++b) hcol[b * DT_EPI] = 0u;
+      aborted = named_sync_or(1, DT_EPI, aborted || *abortp);
+      if (aborted) break;
+      // row constants and the error bound eps of this row (see the file header)
+      const float4 ra = a.rowA[blk * DT_ROWS + i];
+      const float4 rb = a.rowB[blk * DT_ROWS + i];
+      const float* bst = a.bst + blk * 8;
+      const float Mx = bst[0], Rq = bst[1], Qx = bst[2], X2m = bst[3], Cm = bst[4];
+      const bool vrow = ra.w != 0.0f && i < a.bs;
+      const float ni = ra.x, cci = ra.y, si = ra.z;
+      const float Ai = sqrtf(ni), ri = rb.x, qi = rb.y, x2i = rb.z;
+      const float K = (float)a.dpad, dd = (float)a.d;
+      const float gK = K * u / (1.0f - K * u), gd = (dd + 8.0f) * u;
+      const float Eg = ri * Qx + Ai * Rq + (gK + 3.0f * u) * qi * Qx;
+      const float Es = 2.0f * Eg + (gd + 2.0f * u) * (ni + Mx * Mx) + 4.0f * u * qi * Qx +
+                       2.0f * u * (Ai + Mx) * (Ai + Mx);
+      float eps;
+      if (ang)
+        eps = 2.0f * (0.5f * Es + 0.5f * gd * (x2i + X2m) + 4.0f * u * (1.0f + X2m) +
+                      gd * sqrtf(x2i * X2m) + u);
+      else
+        eps = 2.0f * (Es + gd * (Ai + Mx) * (Ai + Mx));
+      DtRow r;
+      r.base = ang ? __fmaf_rn(0.5f, ni, cci) : ni;
+      r.f = (ang ? 1.0f : 2.0f) * (a.fp8 ? si : 1.0f);
+      r.i = vrow ? i : -1;
+      // value range of the row's approximate distances for the histogram
+      const float span = ni + Mx * Mx + 2.0f * qi * Qx;
+      r.lo = 0.0f;
+      float hi = ang ? 0.5f * span + cci + Cm : span;
+      if (!(hi > r.lo + 1e-30f)) hi = r.lo + 1.0f;
+      r.iw1 = (float)DT_NBIN / (hi - r.lo);
+      r.lo2 = r.lo;
+      r.iw2 = r.iw1;
+      r.ucut = 0.0f;
+      r.b1 = 0;
+      r.s2 = DT_NBIN - 1;
+      r.cin = 0;
+      r.vmax = -INFINITY;
+      r.vmin = INFINITY;
+      const int nvr = vrow ? (int)a.nvalid[blk] - 1 : 0;
+      const bool all_mode = nvr <= a.k;
+      uint32_t below = 0;
+      uint16_t* crow = a.cand + (blk * DT_ROWS + i) * (int64_t)DT_ROWS;
+      float* cdrow = a.cdt ? a.cdt + (blk * DT_ROWS + i) * (int64_t)DT_ROWS : nullptr;
+      for (int pass = 0; pass < npass && !aborted; ++pass) {
+        // rows that take every valid column need no histogram
+        const int kind = a.mode == 0 ? 3 : (all_mode && pass < 2 ? -1 : pass);
+        if (all_mode && pass == 2) r.b1 = DT_NBIN;  // every bin is below b1: all collected
+        for (int c = 0; c < nch; ++c, ++ci) {
+          const uint32_t buf = ci & 1u, bph = (ci >> 1) & 1u;
+          if (!aborted && !mbar_wait_bounded(tfull + buf, bph, a.wait_polls, abortp))
+            aborted = true;
+          // tcgen05.ld is warp-collective: the warp goes on only if every lane's wait ended
+          aborted = __any_sync(FULL, aborted);
+          if (!aborted) {
+            tc_fence_after();
+#pragma unroll 1
+            for (int t4 = 0; t4 < 4; ++t4) {
+              const int cb = h * 128 + 32 * t4;  // first column within the chunk
+              uint32_t v[32];
+              tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + buf * DT_NC + (uint32_t)cb, v);
+              if (!vrow || kind < 0) continue;
+              const int j0 = c * DT_NC + cb;
+              if (a.fp8) {
+                if (kind == 0) dt_values<0, true>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
+                else if (kind == 1) dt_values<1, true>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
+                else if (kind == 2) dt_values<2, true>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
+                else dt_values<3, true>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
+              } else {
+                if (kind == 0) dt_values<0, false>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
+                else if (kind == 1) dt_values<1, false>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
+                else if (kind == 2) dt_values<2, false>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
+                else dt_values<3, false>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
+              }
+            }
+          }
+          tc_fence_before();
+          mbar_arrive(tempty + buf);
+        }
+        if (a.mode == 0) {
+          xval[etid] = r.vmin;
+          aborted = named_sync_or(1, DT_EPI, aborted || *abortp);
+          if (!aborted && h == 0 && i < a.bs)
+            a.rowmin[blk * a.bs + i] = vrow ? fminf(r.vmin, xval[etid ^ 128]) : INFINITY;
+          break;
+        }
+        if (pass == 2) {
+          xcnt[etid] = r.cin;
+          xval[etid] = r.vmax;
+        }
+        aborted = named_sync_or(1, DT_EPI, aborted || *abortp);
+        if (aborted) break;
+        if (pass == 0 && !all_mode) {
+          uint32_t cum = 0;
+          r.b1 = DT_NBIN - 1;
+          for (int b = 0; b < DT_NBIN; ++b) {
+            const uint32_t cnt = hcol[b * DT_EPI] + hist[b * DT_EPI + (etid ^ 128)];
+            if (cum + cnt >= (uint32_t)a.k) {
+              r.b1 = b;
+              break;
+            }
+            cum += cnt;
+          }
+          below = cum;
+          r.lo2 = r.lo + (float)r.b1 / r.iw1;
+          r.iw2 = r.iw1 * (float)DT_NBIN;
+        } else if (pass == 1 && !all_mode) {
+          uint32_t cum = below;
+          r.s2 = DT_NBIN - 1;
+          for (int b = 0; b < DT_NBIN; ++b) {
+            cum += hcol[b * DT_EPI] + hist[b * DT_EPI + (etid ^ 128)];
+            if (cum >= (uint32_t)a.k) {
+              r.s2 = b;
+              break;
+            }
+          }
+          const float ub = r.lo2 + (float)(r.s2 + 1) / r.iw2;
+          r.ucut = ub + 2.0f * eps + 1e-6f * (fabsf(r.lo) + (hi - r.lo)) + 1e-30f;
+        } else if (pass == 2 && h == 0) {
+          // the collected columns hold every pair within 2 eps of the k-th
+          // approximate distance when at least k values lie at or below the
+          // sub-bin of the k-th value and 2 eps above their largest is still
+          // under the cut; otherwise the row takes every valid column
+          uint32_t n = rowcnt[il];
+          if (vrow && !all_mode) {
+            const uint32_t tin = r.cin + xcnt[etid ^ 128];
+            const float top = fmaxf(r.vmax, xval[etid ^ 128]);
+            float need = top + 2.0f * eps;
+            need += fabsf(need) * 2.4e-7f;
+            if (tin < (uint32_t)a.k || !(need <= r.ucut)) n = DT_FALLBACK;
+          }
+          a.ccnt[blk * DT_ROWS + i] = vrow ? n : 0u;
+          if (a.reps) a.reps[blk * DT_ROWS + i] = eps;
+        }
+        if (pass == 0) {
+          // the partner's histogram column has been read: clear this one
+          aborted = named_sync_or(1, DT_EPI, aborted || *abortp);
+          if (aborted) break;
+          for (int b = 0; b < DT_NBIN; ++b) hcol[b * DT_EPI] = 0u;
+        }
+      }
+      aborted = named_sync_or(1, DT_EPI, aborted || *abortp);
+      if (aborted) break;
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, TC_TMEM_COLS);
+  if (warp == 9) {
+    tc_fence_after();
+    tmem_dealloc(tmem, DT_TMEM_COLS);
+  }
 }
 
 // --------------------------------------------------------------------------
-// 3. Per row: filter threshold, canonical rerank of the candidates, top-k
+// 3. Per row: canonical rerank of the collected columns, top-k
 // --------------------------------------------------------------------------
-constexpr int SEL_WARPS = 4;
+constexpr int RR_WARPS = 4;
 
-template <int METRIC, int G, int K>
-__global__ void __launch_bounds__(SEL_WARPS * 32)
-    dense_select_kernel(const TcArgs a, int k, int32_t* out_ids, float* out_dist,
-                        unsigned long long* reranked) {
+// One warp per row.  The collected columns (every valid column when the
+// filter could not bound the row) are taken 32 at a time; lane groups of P
+// lanes evaluate them in the canonical float32 order with the row's vector
+// in registers, and each batch is merged into a register pool of the k
+// smallest (delta, id) by the bitonic network of the harvest (the keys of a
+// row are distinct: a block's members are distinct points).  S = pool slots
+// of 32 (k <= 32 S).
+template <int METRIC, int G, int K, int S>
+__global__ void __launch_bounds__(RR_WARPS * 32)
+    dt_rerank_kernel(const DtArgs a, int32_t* out_ids, float* out_dist) {
   using L = Lanes<G, K>;
   extern __shared__ __align__(16) unsigned char ssm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane / L::P, j = lane % L::P;
   const int nch = (a.d * 4 + 15) / 16;
-  const int wbytes = 8 * TC_ROWS + 16 * nch;
-  uint64_t* keys = reinterpret_cast<uint64_t*>(ssm + warp * wbytes);
-  uint4* qs = reinterpret_cast<uint4*>(ssm + warp * wbytes + 8 * TC_ROWS);
+  uint4* qs = reinterpret_cast<uint4*>(ssm + warp * 16 * nch);
   const int64_t rows = a.nb * a.bs;
-  const float u_b = a.u_in, gam = 1.0f / 16777216.0f;
-  const float dk = (float)(a.d + 8);
   unsigned long long nre = 0;
-  for (int64_t r = (int64_t)blockIdx.x * SEL_WARPS + warp; r < rows;
-       r += (int64_t)gridDim.x * SEL_WARPS) {
+  for (int64_t r = (int64_t)blockIdx.x * RR_WARPS + warp; r < rows;
+       r += (int64_t)gridDim.x * RR_WARPS) {
     const int64_t blk = r / a.bs;
     const int i = (int)(r - blk * a.bs);
     const int32_t* ids = a.block_ids + blk * a.bs;
     const int32_t xi = ids[i];
-    int kk = 0;
-    if (xi >= 0) {
-      const float* lp = a.LP + (blk * TC_ROWS + i) * (int64_t)TC_ROWS;
-      // lane holds columns lane + 32 t; invalid columns get the largest key
-      uint32_t u[TC_ROWS / 32];
-      int nv = 0;
+    uint64_t pool[S];
 #pragma unroll
-      for (int t = 0; t < TC_ROWS / 32; ++t) {
-        const int c = lane + 32 * t;
-        const bool valid = c < a.bs && c != i && ids[c] >= 0;
-        u[t] = valid ? fkey(lp[c]) : 0xFFFFFFFFu;
-        nv += valid ? 1 : 0;
-      }
-      nv = __reduce_add_sync(FULL, nv);
-      // eps for this row (see the file header)
-      const float Ai = sqrtf(a.nrm[blk * TC_ROWS + i]), M = a.Mx[blk];
-      float eps = 2.0f * ((4.0f * u_b + 6.0f * dk * gam) * Ai * M +
-                          6.0f * dk * gam * (Ai * Ai + M * M));
-      if (a.metric == ANGULAR_F32) eps = 0.5f * eps + 2.0f * (3.0f * dk * gam + 2.0f * gam);
-      // candidates: every valid column when there are at most k, else those
-      // with approx <= tau + 2 eps, tau the k-th smallest approximate value,
-      // found bit by bit (the largest t with fewer than k keys below t)
-      uint32_t lim = 0xFFFFFFFEu;
-      if (nv > k) {
-        uint32_t t = 0;
-        for (int bit = 31; bit >= 0; --bit) {
-          const uint32_t tt = t | (1u << bit);
-          int below = 0;
-#pragma unroll
-          for (int q = 0; q < TC_ROWS / 32; ++q) below += u[q] < tt ? 1 : 0;
-          if (__reduce_add_sync(FULL, below) < k) t = tt;
-        }
-        lim = fkey(fkey_inv(t) + 2.0f * eps);
-      }
-      int cand = 0;
-#pragma unroll
-      for (int q = 0; q < TC_ROWS / 32; ++q) {
-        const bool in = u[q] <= lim;
-        const unsigned m = __ballot_sync(FULL, in);
-        if (in) keys[cand + __popc(m & ((1u << lane) - 1u))] = (uint64_t)(lane + 32 * q);
-        cand += __popc(m);
-      }
-      __syncwarp();
-      nre += (unsigned long long)cand;
-      // canonical distances of the candidates, in place
+    for (int s = 0; s < S; ++s) pool[s] = PAD;
+    // after a give-up of the filter kernel its candidate lists are not valid
+    if (xi >= 0 && *reinterpret_cast<const volatile uint32_t*>(a.err) == 0u) {
+      const int64_t crow = (blk * DT_ROWS + i) * (int64_t)DT_ROWS;
+      const uint32_t m0 = a.ccnt[blk * DT_ROWS + i];
+      const bool fallback = m0 == DT_FALLBACK || m0 >= (uint32_t)a.bs;
+      const int total = fallback ? a.bs : (int)m0;  // fallback: scan every column
+      const float eps = a.reps ? a.reps[blk * DT_ROWS + i] : 0.0f;
       stage_row(qs, a.X + (int64_t)xi * a.ld_bytes, nch, lane);
-      for (int base = 0; base < cand; base += L::CPW) {
-        const int c = base + g;
-        // groups past the candidates load the row's own vector (keys[0..base)
-        // already hold (distance, id) keys, not column indices)
-        const int32_t cid = c < cand ? ids[(int)(uint32_t)keys[c]] : xi;
-        uint4 y[L::VL][K];
-        load_slots<G, K>(a.X + (int64_t)cid * a.ld_bytes, nch, j, y);
-        const float dd = slots_dist<METRIC, G, K>(qs, y, nch, a.d, j);
-        __syncwarp();
-        if (c < cand && j == 0) {
-          if (a.errstat) {
-            // the same pair in float64 (plain order): the filter's error
-            // relative to the bound used, the canonical value's absolute error
-            const float* xa = reinterpret_cast<const float*>(a.X + (int64_t)xi * a.ld_bytes);
-            const float* xb = reinterpret_cast<const float*>(a.X + (int64_t)cid * a.ld_bytes);
-            double acc = 0.0;
-            for (int e = 0; e < a.d; ++e) {
-              if (METRIC == ANGULAR_F32) {
-                acc += (double)xa[e] * (double)xb[e];
-              } else {
-                const double t = (double)xa[e] - (double)xb[e];
-                acc += t * t;
-              }
-            }
-            const double d64 = METRIC == ANGULAR_F32 ? 1.0 - acc : acc;
-            const int col = (int)(uint32_t)keys[c];
-            const float e1 = (float)(fabs((double)lp[col] - d64) / (double)eps);
-            const float e2 = (float)fabs((double)dd - d64);
-            atomicMax(a.err + 8, __float_as_uint(e1));
-            atomicMax(a.err + 9, __float_as_uint(e2));
+      uint4 qr[L::VL][K];
+      load_slots_smem<G, K>(qs, nch, j, qr);
+      for (int base = 0; base < total; base += 32) {
+        // this lane's candidate of the batch: its column, id, approximate distance
+        int col = -1;
+        float adt = 0.0f;
+        if (base + lane < total) {
+          if (fallback) {
+            const int c = base + lane;
+            col = (c != i && ids[c] >= 0) ? c : -1;
+          } else {
+            const uint32_t cv = a.cand[crow + base + lane];
+            col = cv < (uint32_t)a.bs ? (int)cv : -1;
+            if (a.errstat) adt = a.cdt[crow + base + lane];
           }
-          keys[c] = make_key(dd, cid);
         }
-        __syncwarp();
+        const int32_t myid = col >= 0 ? ids[col] : -1;
+        nre += (unsigned long long)__popc(__ballot_sync(FULL, col >= 0));
+        uint64_t mykey = PAD;
+        for (int sb = 0; sb < 32; sb += L::CPW * L::UW) {
+          uint4 y[L::UW][L::VL][K];
+#pragma unroll
+          for (int uu = 0; uu < L::UW; ++uu) {
+            const int idx = sb + uu * L::CPW + g;
+            const int32_t cid = __shfl_sync(FULL, myid, idx);
+            load_slots<G, K>(a.X + (int64_t)(cid >= 0 ? cid : xi) * a.ld_bytes, nch, j, y[uu]);
+          }
+#pragma unroll
+          for (int uu = 0; uu < L::UW; ++uu) {
+            const float dd = regs_dist<METRIC, G, K>(qr, y[uu], nch, a.d, j, FULL);
+            const int rel = lane - sb - uu * L::CPW;
+            const float got = __shfl_sync(FULL, dd, (rel & (L::CPW - 1)) * L::P);
+            if (rel >= 0 && rel < L::CPW && myid >= 0) mykey = make_key(got, myid);
+          }
+        }
+        if (a.errstat && !fallback && myid >= 0) {
+          // the same pair in float64 (plain order): the filter's error
+          // relative to the bound used, the canonical value's absolute error
+          const float* xa = reinterpret_cast<const float*>(a.X + (int64_t)xi * a.ld_bytes);
+          const float* xb = reinterpret_cast<const float*>(a.X + (int64_t)myid * a.ld_bytes);
+          double acc = 0.0;
+          for (int e = 0; e < a.d; ++e) {
+            if (METRIC == ANGULAR_F32) {
+              acc += (double)xa[e] * (double)xb[e];
+            } else {
+              const double t = (double)xa[e] - (double)xb[e];
+              acc += t * t;
+            }
+          }
+          const double d64 = METRIC == ANGULAR_F32 ? 1.0 - acc : acc;
+          const float e1 = (float)(fabs((double)adt - d64) / (double)eps);
+          const float e2 = (float)fabs((double)key_dist(mykey) - d64);
+          atomicMax(a.err + 8, __float_as_uint(e1));
+          atomicMax(a.err + 9, __float_as_uint(e2));
+        }
+        merge_into_pool<S>(pool, mykey, a.k, lane);
       }
-      kk = sort_unique(keys, cand, lane);
-      kk = kk < k ? kk : k;
     }
-    for (int t = lane; t < k; t += 32) {
-      out_ids[r * k + t] = t < kk ? key_id(keys[t]) : -1;
-      out_dist[r * k + t] = t < kk ? key_dist(keys[t]) : __int_as_float(0x7f800000);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const int t = s * 32 + lane;
+      if (t < a.k) {
+        out_ids[r * a.k + t] = pool[s] == PAD ? -1 : key_id(pool[s]);
+        out_dist[r * a.k + t] = pool[s] == PAD ? __int_as_float(0x7f800000) : key_dist(pool[s]);
+      }
     }
-    __syncwarp();
   }
-  if (lane == 0 && nre) atomicAdd(reranked, nre);
+  if (lane == 0 && nre) atomicAdd(a.reranked, nre);
 }
 
-using SelectFn = void (*)(const TcArgs, int, int32_t*, float*, unsigned long long*);
+using RerankFn = void (*)(const DtArgs, int32_t*, float*);
 
-static SelectFn select_kernel_for(int metric, int G, int K) {
-#define SX(M, GG, KK) \
-  if (metric == M && G == GG && K == KK) return dense_select_kernel<M, GG, KK>;
-#define SF(M) SX(M, 4, 1) SX(M, 8, 1) SX(M, 16, 1) SX(M, 32, 1) SX(M, 32, 2) SX(M, 32, 4) \
-  SX(M, 32, 8)
+static RerankFn rerank_kernel_for(int metric, int G, int K, int S) {
+#define SX(M, GG, KK, SS) \
+  if (metric == M && G == GG && K == KK && S == SS) return dt_rerank_kernel<M, GG, KK, SS>;
+#define SS_(M, GG, KK) SX(M, GG, KK, 1) SX(M, GG, KK, 2)
+#define SF(M) SS_(M, 4, 1) SS_(M, 8, 1) SS_(M, 16, 1) SS_(M, 32, 1) SS_(M, 32, 2) \
+  SS_(M, 32, 4) SS_(M, 32, 8)
   SF(0)
   SF(1)
 #undef SF
+#undef SS_
 #undef SX
   return nullptr;
 }
 
+// --------------------------------------------------------------------------
+// Host side
+// --------------------------------------------------------------------------
+namespace {
+
+// Blocks per launch group: the candidate lists take 2 MB per block (and the
+// approximate distances for the error check 4 MB more).
+constexpr int64_t kGroup = 64;
+constexpr int64_t kGroupErr = 16;
+
+struct DtScratch {
+  char* base = nullptr;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    T* p = reinterpret_cast<T*>(base + off);
+    off += (sizeof(T) * count + 255) / 256 * 256;
+    return p;
+  }
+};
+
+size_t dt_scratch_bytes(int64_t gn, int nsl, bool errstat) {
+  size_t b = 0;
+  auto add = [&](size_t x) { b += (x + 255) / 256 * 256; };
+  add((size_t)gn * nsl * DT_SLICE_IMG);      // Xt
+  add(sizeof(float4) * gn * DT_ROWS * 2);    // rowA, rowB
+  add(sizeof(float) * gn * 8);               // bst
+  add(sizeof(uint32_t) * gn);                // nvalid
+  add(sizeof(uint16_t) * gn * DT_ROWS * DT_ROWS);
+  add(sizeof(uint32_t) * gn * DT_ROWS);      // ccnt
+  if (errstat) {
+    add(sizeof(float) * gn * DT_ROWS * DT_ROWS);
+    add(sizeof(float) * gn * DT_ROWS);
+  }
+  add(256);                                  // err, pairs, reranked
+  return b;
+}
+
+int dt_setup(const VecLayout& L, int fp8, DtArgs* a) {
+  a->X = L.X;
+  a->ld_bytes = L.ld_bytes;
+  a->d = L.d;
+  a->metric = L.metric;
+  a->fp8 = fp8 ? 1 : 0;
+  const int slice = a->fp8 ? DT_KB : DT_KB / 2;  // elements per slice
+  a->dpad = (L.d + slice - 1) / slice * slice;
+  a->rowb = a->fp8 ? a->dpad : 2 * a->dpad;
+  a->nsl = a->rowb / DT_KB;
+  a->wait_polls = g_mma_wait_polls;
+  cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(dt_fused_kernel), DtSmem::bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dt_fused_kernel)");
+  return 0;
+}
+
+}  // namespace
+
 int dense_block_tc(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs, int k,
                    int fp8, bool err64, int32_t* out_ids, float* out_dist, double* stats,
                    cudaStream_t s) {
-  SelectFn sel = select_kernel_for(L.metric, L.G, L.K);
-  if (!sel || L.metric == L2_U8) {
+  RerankFn rr = rerank_kernel_for(L.metric, L.G, L.K, k <= 32 ? 1 : 2);
+  if (!rr || L.metric == L2_U8) {
     set_error(1, "tensor-core dense blocks take float32 metrics");
     return 1;
   }
-  if (bs > TC_ROWS || nb > 65535) {
+  if (bs > DT_ROWS || nb > 65535) {
     set_error(1, "tensor-core dense blocks: bs <= 1024 and nb <= 65535");
     return 1;
   }
-  TcArgs a{};
-  a.X = L.X;
-  a.ld_bytes = L.ld_bytes;
-  a.d = L.d;
-  a.fp8 = fp8 ? 1 : 0;
+  DtArgs a{};
+  int rc = dt_setup(L, fp8, &a);
+  if (rc) return rc;
   a.errstat = stats && err64 ? 1 : 0;
-  a.wait_polls = g_mma_wait_polls;
-  const int slice = a.fp8 ? TC_KB : TC_KB / 2;  // elements per slice
-  a.dpad = (L.d + slice - 1) / slice * slice;
-  a.rowb = a.fp8 ? a.dpad : 2 * a.dpad;
-  // input rounding: BF16 2^-8; E4M3 2^-4 plus its subnormal spacing, at most
-  // 2^-10 of a code, summed over d elements of a row scaled to 448
-  a.u_in = a.fp8 ? 0.0625f + sqrtf((float)L.d) * (1.0f / 1024.0f) / 448.0f : 1.0f / 256.0f;
-  a.metric = L.metric;
-  a.block_ids = block_ids;
-  a.nb = nb;
   a.bs = bs;
+  a.k = k;
+  a.mode = 1;
+  const int64_t group = a.errstat ? kGroupErr : kGroup;
+  const int64_t gmax = std::min<int64_t>(nb, group);
+  const size_t total = dt_scratch_bytes(gmax, a.nsl, a.errstat != 0);
+  const int nch = (L.d * 4 + 15) / 16;
+  const int rsm = RR_WARPS * 16 * nch;
+  {
+    cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(rr), rsm);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dt_rerank_kernel)");
+  }
   char* scratch = nullptr;
-  const size_t xb = (size_t)nb * TC_ROWS * (size_t)a.rowb;
-  const size_t vec = sizeof(float) * nb * TC_ROWS;
-  const size_t lp = sizeof(float) * nb * (size_t)TC_ROWS * TC_ROWS;
-  const size_t total = xb + 3 * vec + 256 * ((nb * 4 + 255) / 256 + 1) + lp + 512;
   FG_CUDA(cudaMallocAsync(&scratch, total, s));
-  size_t off = 0;
-  a.Xb = reinterpret_cast<unsigned char*>(scratch + off);
-  off += (xb + 255) / 256 * 256;
-  a.sc = reinterpret_cast<float*>(scratch + off);
-  off += (vec + 255) / 256 * 256;
-  a.nrm = reinterpret_cast<float*>(scratch + off);
-  off += (vec + 255) / 256 * 256;
-  a.cc = reinterpret_cast<float*>(scratch + off);
-  off += (vec + 255) / 256 * 256;
-  a.Mx = reinterpret_cast<float*>(scratch + off);
-  off += (nb * 4 + 255) / 256 * 256;
-  a.err = reinterpret_cast<uint32_t*>(scratch + off);
-  a.pairs = reinterpret_cast<unsigned long long*>(scratch + off + 8);
-  unsigned long long* reranked = reinterpret_cast<unsigned long long*>(scratch + off + 16);
-  off += 256;
-  a.LP = reinterpret_cast<float*>(scratch + off);
-  int rc = 0;
   cudaEvent_t ev[4] = {};
   for (int i = 0; i < 4 && stats; ++i) cudaEventCreate(&ev[i]);
-  do {
+  float t_prep = 0.0f, t_fused = 0.0f, t_rr = 0.0f;
+  uint32_t h[10] = {};
+  unsigned long long pairs = 0, reranked = 0;
+  for (int64_t b0 = 0; b0 < nb && !rc; b0 += group) {
+    const int64_t gn = std::min<int64_t>(group, nb - b0);
+    DtScratch S{scratch, 0};
+    a.block_ids = block_ids + b0 * bs;
+    a.nb = gn;
+    a.Xt = S.take<unsigned char>((size_t)gn * a.nsl * DT_SLICE_IMG);
+    a.rowA = S.take<float4>(gn * DT_ROWS);
+    a.rowB = S.take<float4>(gn * DT_ROWS);
+    a.bst = S.take<float>(gn * 8);
+    a.nvalid = S.take<uint32_t>(gn);
+    a.cand = S.take<uint16_t>((size_t)gn * DT_ROWS * DT_ROWS);
+    a.ccnt = S.take<uint32_t>(gn * DT_ROWS);
+    a.cdt = a.errstat ? S.take<float>((size_t)gn * DT_ROWS * DT_ROWS) : nullptr;
+    a.reps = a.errstat ? S.take<float>(gn * DT_ROWS) : nullptr;
+    a.err = S.take<uint32_t>(64);
+    a.pairs = reinterpret_cast<unsigned long long*>(a.err + 2);
+    a.reranked = reinterpret_cast<unsigned long long*>(a.err + 4);
     cudaError_t e;
-    if ((e = cudaMemsetAsync(a.Mx, 0, nb * sizeof(float), s)) != cudaSuccess ||
+    if ((e = cudaMemsetAsync(a.bst, 0, sizeof(float) * gn * 8, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(a.err, 0, 256, s)) != cudaSuccess) {
       rc = cuda_fail(e, "cudaMemsetAsync(dense scratch)");
       break;
     }
     if (stats) cudaEventRecord(ev[0], s);
-    dense_prep_kernel<<<(unsigned)nb, 256, 0, s>>>(a);
+    dt_prep_kernel<<<dim3((unsigned)gn, DT_ROWS / 256), 256, 0, s>>>(a);
     note_launch();
     if (stats) cudaEventRecord(ev[1], s);
-    const int gsm = 100 * 1024;  // 48 KB used; asking for more keeps 2 CTAs (512 TMEM columns) per SM
-    if ((e = cudaFuncSetAttribute(dense_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  gsm)) != cudaSuccess) {
-      rc = cuda_fail(e, "cudaFuncSetAttribute(dense_gram_kernel)");
-      break;
-    }
-    dense_gram_kernel<<<dim3(TC_ROWS / TC_M, TC_ROWS / TC_N, (unsigned)nb), TC_THREADS, gsm, s>>>(a);
+    const int64_t ntiles = gn * (DT_ROWS / DT_M);
+    const int grid = (int)std::min<int64_t>(ntiles, device_sms());
+    dt_fused_kernel<<<grid, DT_THREADS, DtSmem::bytes, s>>>(a);
     note_launch();
     if (stats) cudaEventRecord(ev[2], s);
-    const int nch = (L.d * 4 + 15) / 16;
-    const int ssm = SEL_WARPS * (8 * TC_ROWS + 16 * nch);
-    if ((e = cudaFuncSetAttribute(sel, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm)) !=
-        cudaSuccess) {
-      rc = cuda_fail(e, "cudaFuncSetAttribute(dense_select_kernel)");
-      break;
-    }
-    const int64_t rows = nb * bs;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((rows + SEL_WARPS - 1) / SEL_WARPS,
-                                                                 (int64_t)device_sms() * 16));
-    sel<<<grid, SEL_WARPS * 32, ssm, s>>>(a, k, out_ids, out_dist, reranked);
+    const int64_t rows = gn * bs;
+    const int rgrid = (int)std::max<int64_t>(
+        1, std::min<int64_t>((rows + RR_WARPS - 1) / RR_WARPS, (int64_t)device_sms() * 16));
+    rr<<<rgrid, RR_WARPS * 32, rsm, s>>>(a, out_ids + b0 * bs * k, out_dist + b0 * bs * k);
     note_launch();
     if (stats) cudaEventRecord(ev[3], s);
     if ((e = cudaGetLastError()) != cudaSuccess) {
       rc = cuda_fail(e, "dense tensor-core kernels");
       break;
     }
-    uint32_t h[10] = {};
-    if ((e = cudaMemcpyAsync(h, a.err, 40, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+    uint32_t hg[10] = {};
+    if ((e = cudaMemcpyAsync(hg, a.err, 40, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess) {
       rc = cuda_fail(e, "dense tensor-core status");
       break;
     }
-    if (h[0]) {
+    if (hg[0]) {
       set_error(5, "tensor-core dense block: a bounded wait for the MMA gave up");
       rc = 5;
       break;
     }
+    pairs += (unsigned long long)hg[2] | ((unsigned long long)hg[3] << 32);
+    reranked += (unsigned long long)hg[4] | ((unsigned long long)hg[5] << 32);
+    h[8] = std::max(h[8], hg[8]);  // non-negative float bits order like the floats
+    h[9] = std::max(h[9], hg[9]);
     if (stats) {
-      const unsigned long long pairs = (unsigned long long)h[2] | ((unsigned long long)h[3] << 32);
-      const unsigned long long rr = (unsigned long long)h[4] | ((unsigned long long)h[5] << 32);
       float t1 = 0, t2 = 0, t3 = 0;
       cudaEventElapsedTime(&t1, ev[0], ev[1]);
       cudaEventElapsedTime(&t2, ev[1], ev[2]);
       cudaEventElapsedTime(&t3, ev[2], ev[3]);
-      stats[0] = pairs ? (double)rr / (double)pairs : 0.0;
-      stats[1] = t2;
-      stats[2] = t3;
-      stats[3] = t1;
-      float m1, m2;
-      std::memcpy(&m1, &h[8], 4);
-      std::memcpy(&m2, &h[9], 4);
-      stats[4] = m1;
-      stats[5] = m2;
+      t_prep += t1;
+      t_fused += t2;
+      t_rr += t3;
     }
-  } while (0);
+  }
+  if (!rc && stats) {
+    stats[0] = pairs ? (double)reranked / (double)pairs : 0.0;
+    stats[1] = t_fused;
+    stats[2] = t_rr;
+    stats[3] = t_prep;
+    float m1, m2;
+    std::memcpy(&m1, &h[8], 4);
+    std::memcpy(&m2, &h[9], 4);
+    stats[4] = m1;
+    stats[5] = m2;
+  }
   for (int i = 0; i < 4 && stats; ++i) cudaEventDestroy(ev[i]);
+  cudaFreeAsync(scratch, s);
+  return rc;
+}
+
+int dense_gram_tc(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs, int fp8,
+                  float* out_min, double* ms, cudaStream_t s) {
+  if (L.metric == L2_U8) {
+    set_error(1, "tensor-core dense blocks take float32 metrics");
+    return 1;
+  }
+  if (bs > DT_ROWS || nb > 65535) {
+    set_error(1, "tensor-core dense blocks: bs <= 1024 and nb <= 65535");
+    return 1;
+  }
+  DtArgs a{};
+  int rc = dt_setup(L, fp8, &a);
+  if (rc) return rc;
+  a.bs = bs;
+  a.k = 1;
+  a.mode = 0;
+  const int64_t group = 256;
+  const int64_t gmax = std::min<int64_t>(nb, group);
+  size_t total = 0;
+  {
+    auto add = [&](size_t x) { total += (x + 255) / 256 * 256; };
+    add((size_t)gmax * a.nsl * DT_SLICE_IMG);
+    add(sizeof(float4) * gmax * DT_ROWS * 2);
+    add(sizeof(float) * gmax * 8);
+    add(sizeof(uint32_t) * gmax);
+    add(256);
+  }
+  char* scratch = nullptr;
+  FG_CUDA(cudaMallocAsync(&scratch, total, s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ms) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+  }
+  float tsum = 0.0f;
+  for (int64_t b0 = 0; b0 < nb && !rc; b0 += group) {
+    const int64_t gn = std::min<int64_t>(group, nb - b0);
+    DtScratch S{scratch, 0};
+    a.block_ids = block_ids + b0 * bs;
+    a.nb = gn;
+    a.Xt = S.take<unsigned char>((size_t)gn * a.nsl * DT_SLICE_IMG);
+    a.rowA = S.take<float4>(gn * DT_ROWS);
+    a.rowB = S.take<float4>(gn * DT_ROWS);
+    a.bst = S.take<float>(gn * 8);
+    a.nvalid = S.take<uint32_t>(gn);
+    a.err = S.take<uint32_t>(64);
+    a.pairs = reinterpret_cast<unsigned long long*>(a.err + 2);
+    a.reranked = reinterpret_cast<unsigned long long*>(a.err + 4);
+    a.rowmin = out_min + b0 * bs;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(a.bst, 0, sizeof(float) * gn * 8, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(a.err, 0, 256, s)) != cudaSuccess) {
+      rc = cuda_fail(e, "cudaMemsetAsync(dense scratch)");
+      break;
+    }
+    dt_prep_kernel<<<dim3((unsigned)gn, DT_ROWS / 256), 256, 0, s>>>(a);
+    note_launch();
+    if (ms) cudaEventRecord(e0, s);
+    const int grid = (int)std::min<int64_t>(gn * (DT_ROWS / DT_M), device_sms());
+    dt_fused_kernel<<<grid, DT_THREADS, DtSmem::bytes, s>>>(a);
+    note_launch();
+    if (ms) cudaEventRecord(e1, s);
+    uint32_t hg = 0;
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&hg, a.err, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+      rc = cuda_fail(e, "dense Gram kernel");
+      break;
+    }
+    if (hg) {
+      set_error(5, "tensor-core dense block: a bounded wait for the MMA gave up");
+      rc = 5;
+      break;
+    }
+    if (ms) {
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, e0, e1);
+      tsum += t;
+    }
+  }
+  if (!rc && ms) *ms = tsum;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   cudaFreeAsync(scratch, s);
   return rc;
 }

@@ -47,6 +47,12 @@ struct HPruneArgs {
   float tc_e0;
   uint32_t* err;
   int32_t wait_polls;  // first bounded wait for the Gram matrix
+  // lists longer than the tensor-core tile: the tensor-core kernel appends
+  // their qidx to long_list (count in *long_cnt) for the lane-group kernel,
+  // which then takes work item w as qidx = qlist[w], *nq_dev items
+  int32_t* long_list;
+  uint32_t* long_cnt;
+  const int32_t* qlist;
 };
 
 constexpr int HP_WARPS = 4;
@@ -81,7 +87,8 @@ __global__ void __launch_bounds__(HP_WARPS * 32) harvest_prune_kernel(const HPru
   // group's own lanes
   const unsigned gmask = L::P == 32 ? FULL : (((1u << L::P) - 1u) << (g * L::P));
   const int64_t nq = a.nq_dev ? (int64_t)*a.nq_dev : a.nq;
-  for (int64_t qidx = blockIdx.x; qidx < nq; qidx += gridDim.x) {
+  for (int64_t w = blockIdx.x; w < nq; w += gridDim.x) {
+    const int64_t qidx = a.qlist ? (int64_t)a.qlist[w] : w;
     const int ne = a.Eg_cnt[qidx];
     if (ne < 0) continue;  // pruned by the re-run pass (uniform over the CTA)
     const int64_t p = a.rows ? (int64_t)a.rows[qidx] : a.q_first + qidx * a.q_step;
@@ -268,9 +275,14 @@ __global__ void __launch_bounds__(TCP_M) harvest_prune_tc_kernel(const HPruneArg
   bool ok = true;
   unsigned long long ev = 0;
   const int64_t nq = a.nq_dev ? (int64_t)*a.nq_dev : a.nq;
-  for (int64_t qidx = blockIdx.x; qidx < nq; qidx += gridDim.x) {
+  for (int64_t w = blockIdx.x; w < nq; w += gridDim.x) {
+    const int64_t qidx = a.qlist ? (int64_t)a.qlist[w] : w;
     const int ne = a.Eg_cnt[qidx];
     if (ne < 0) continue;  // pruned by the re-run pass (uniform over the CTA)
+    if (ne > TCP_M) {      // longer than a tile: left to the lane-group kernel
+      if (tid == 0) a.long_list[atomicAdd(a.long_cnt, 1u)] = (int32_t)qidx;
+      continue;
+    }
     const int64_t p = a.rows ? (int64_t)a.rows[qidx] : a.q_first + qidx * a.q_step;
     const uint64_t* src = a.Eg_off ? a.Eg + a.Eg_off[p] : a.Eg + qidx * (int64_t)a.ecap;
     // keys: each thread ranks its own among the list (the point itself out)
@@ -482,7 +494,8 @@ int harvest_prune(const VecLayout& L, const uint64_t* Eg, const int32_t* Eg_cnt,
                   int64_t nq, int64_t q_first, int64_t q_step, int R, float alpha2,
                   int32_t* A_out, int32_t* cnt_out, unsigned long long* prune_ctr, int num_sms,
                   cudaStream_t s, const int32_t* rows, const int64_t* Eg_off,
-                  const uint32_t* nq_dev, uint64_t* K_out, uint32_t* err) {
+                  const uint32_t* nq_dev, uint64_t* K_out, uint32_t* err, int32_t* long_list,
+                  uint32_t* long_cnt, const int32_t* qlist) {
   HPruneFn kern = hprune_kernel_for(L.metric, L.G, L.K);
   if (!kern) {
     set_error(1, "no prune kernel for this metric and dimension");
@@ -491,37 +504,49 @@ int harvest_prune(const VecLayout& L, const uint64_t* Eg, const int32_t* Eg_cnt,
   HPruneArgs a{L.X, L.ld_bytes, L.d, L.nchunks, Eg, Eg_cnt, ecap,
                harvest_prune_smem(ecap, L.nchunks), nq, q_first, q_step, R, alpha2,
                A_out, cnt_out, prune_ctr, rows, Eg_off, nq_dev, K_out, 0.0f, 0.0f, err,
-               g_mma_wait_polls};
-  int threads = HP_WARPS * 32;
-  int max_per_sm = 1 << 20;
+               g_mma_wait_polls, nullptr, nullptr, qlist};
   HPruneFn tck = hprune_tc_kernel_for(L.metric, L.G, L.K);
-  int optin = 0, dev = 0;
+  int optin = 0, dev = 0, sm_bytes = 0;
   FG_CUDA(cudaGetDevice(&dev));
   FG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if (tck && err && g_prune_tc && ecap <= TCP_M && harvest_prune_tc_smem(L.nchunks) <= optin) {
-    tc_error_bound(L.metric, L.nchunks, &a.tc_e1, &a.tc_e0);
-    kern = tck;
-    threads = TCP_M;
+  FG_CUDA(cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  // lists of at most 128 entries on the tensor cores; longer ones (possible
+  // when the list buffer is larger) go to the lane-group kernel afterwards
+  const bool split = ecap > TCP_M && long_list && long_cnt;
+  if (tck && err && g_prune_tc && (ecap <= TCP_M || split) &&
+      harvest_prune_tc_smem(L.nchunks) <= optin) {
+    HPruneArgs t = a;
+    tc_error_bound(L.metric, L.nchunks, &t.tc_e1, &t.tc_e0);
     // at most 512 / 128 CTAs on an SM (its tensor memory columns): the
     // shared memory request is raised so that no more can be resident
-    int sm_bytes = 0;
-    FG_CUDA(cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
     const int tc_ctas = 512 / TCP_M;
-    a.smem = std::max(harvest_prune_tc_smem(L.nchunks), sm_bytes / (tc_ctas + 1));
-    max_per_sm = std::min(tc_ctas, sm_bytes / (a.smem + 1024));
+    t.smem = std::max(harvest_prune_tc_smem(L.nchunks), sm_bytes / (tc_ctas + 1));
+    const int per_sm = std::min(tc_ctas, sm_bytes / (t.smem + 1024));
+    if (per_sm < 1) {
+      set_error(1, "prune launch does not fit an SM");
+      return 1;
+    }
+    if (split) {
+      t.long_list = long_list;
+      t.long_cnt = long_cnt;
+      FG_CUDA(cudaMemsetAsync(long_cnt, 0, sizeof(uint32_t), s));
+    }
+    FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(tck), t.smem));
+    tck<<<per_sm * num_sms, TCP_M, t.smem, s>>>(t);
+    note_launch();
+    FG_CUDA(cudaGetLastError());
+    if (!split) return 0;
+    a.qlist = long_list;
+    a.nq_dev = long_cnt;
   }
   FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(kern), a.smem));
   int per_sm = 0;
-  if (kern == tck) {
-    per_sm = max_per_sm;  // the occupancy query does not see tensor memory
-  } else {
-    FG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, a.smem));
-  }
+  FG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, HP_WARPS * 32, a.smem));
   if (per_sm < 1) {
     set_error(1, "prune launch does not fit an SM");
     return 1;
   }
-  kern<<<per_sm * num_sms, threads, a.smem, s>>>(a);
+  kern<<<per_sm * num_sms, HP_WARPS * 32, a.smem, s>>>(a);
   note_launch();
   FG_CUDA(cudaGetLastError());
   return 0;

@@ -122,7 +122,9 @@ int harvest_prune(const VecLayout& L, const uint64_t* Eg, const int32_t* Eg_cnt,
                   int32_t* A_out, int32_t* cnt_out, unsigned long long* prune_ctr, int num_sms,
                   cudaStream_t s, const int32_t* rows = nullptr, const int64_t* Eg_off = nullptr,
                   const uint32_t* nq_dev = nullptr, uint64_t* K_out = nullptr,
-                  uint32_t* err = nullptr);
+                  uint32_t* err = nullptr, int32_t* long_list = nullptr,
+                  uint32_t* long_cnt = nullptr, const int32_t* qlist = nullptr);
+// (qlist: work item w < nq is the list of qidx = qlist[w]; NULL: qidx = w.)
 // Dominance bits of the prune on the tensor cores (1, the default, for the
 // float32 metrics and lists of at most 128 when err is given) or on the lane
 // groups (0).  The pruned lists are the same either way.
@@ -134,6 +136,21 @@ extern int g_sat_tc;
 // the products in flight with the full bound kDrainPolls, frees its tensor
 // memory and returns; the host reports FGRAFT_ETIMEOUT.
 extern int g_mma_wait_polls;
+// Harvest launch settings chosen by the autotuner, by (metric, d, ef_h, R,
+// ceil(log2 n)); hash_log2 0 keeps the occupancy rule for the visited sets.
+struct TuneKey {
+  int metric, d, ef, R, log2_n;
+};
+struct TuneVal {
+  int wpc, hash_log2, overflow, gather, id_batch;
+  float us_per_query;
+};
+bool tune_table_lookup(const TuneKey& k, TuneVal* v);
+void tune_table_put(const TuneKey& k, const TuneVal& v);
+int tune_table_size();
+int tune_table_save(const char* path);
+int tune_table_load(const char* path);
+
 // Streaming multiprocessors of the current device (cached per device; 1 if
 // the query fails).  Grid caps of the grid-stride kernels are multiples of it.
 int device_sms();
@@ -155,6 +172,13 @@ extern int g_coherent;
 int dense_block_tc(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs, int k,
                    int fp8, bool err64, int32_t* out_ids, float* out_dist, double* stats,
                    cudaStream_t s);
+
+// Gram and approximate distances of every pair of the blocks on the tensor
+// cores, reduced to the smallest approximate distance per row (out_min,
+// nb * bs floats; +inf for padding rows); *ms (optional) gets the kernel's
+// time.  Measures the dense ceiling without any selection.
+int dense_gram_tc(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs, int fp8,
+                  float* out_min, double* ms, cudaStream_t s);
 
 // Dense-block top-k (canonical float32 distances of every pair of a block).
 int dense_block(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs, int k,

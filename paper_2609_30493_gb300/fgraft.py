@@ -44,7 +44,9 @@ EXPORTS = ["fgraft_build_scaffold", "fgraft_harvest_block", "fgraft_harvest_all"
            "fgraft_index_profile", "fgraft_index_harvest_ms", "fgraft_kernel_launches",
            "fgraft_tune_sat", "fgraft_tune_prune", "fgraft_prune_lists_noalloc",
            "fgraft_harvest_block_multi", "fgraft_tune_scaffold_cap", "fgraft_tune_schedule",
-           "fgraft_index_schedule", "fgraft_tune_mma_wait",
+           "fgraft_index_schedule", "fgraft_tune_mma_wait", "fgraft_dense_block_gram",
+           "fgraft_index_autotune", "fgraft_tuning_table_save", "fgraft_tuning_table_load",
+           "fgraft_index_set_tuning",
            "fgraft_index_destroy", "fgraft_last_error"]
 
 
@@ -208,6 +210,37 @@ def fgraft_tune_prune(tensor_cores: bool = True):
     _check(load().fgraft_tune_prune(C.c_int32(1 if tensor_cores else 0)))
 
 
+class _Tuning(C.Structure):
+    _fields_ = [("warps_per_cta", C.c_int32), ("hash_log2", C.c_int32),
+                ("overflow_mode", C.c_int32), ("gather", C.c_int32), ("id_batch", C.c_int32),
+                ("us_per_query", C.c_float), ("default_us_per_query", C.c_float)]
+
+
+def fgraft_index_autotune(ix: Index, sample: int = 16384) -> dict:
+    """Time the harvest launch configurations on a calibration sample of block
+    0 and keep the fastest for this index (and its shape in the process
+    table).  Returns the chosen settings and the timings."""
+    t = _Tuning()
+    _check(load().fgraft_index_autotune(ix.handle, C.c_int32(sample), _stream(ix.X.device),
+                                        C.byref(t)))
+    return {f: getattr(t, f) for f, _ in _Tuning._fields_}
+
+
+def fgraft_index_set_tuning(ix: Index, warps_per_cta: int = 4, hash_log2: int = 0,
+                            overflow_mode: int = 1, gather: int = 0, id_batch: int = 2):
+    """Explicit harvest launch settings (results do not depend on them)."""
+    t = _Tuning(warps_per_cta, hash_log2, overflow_mode, gather, id_batch, 0.0, 0.0)
+    _check(load().fgraft_index_set_tuning(ix.handle, C.byref(t)))
+
+
+def fgraft_tuning_table_save(path: str):
+    _check(load().fgraft_tuning_table_save(C.c_char_p(os.fsencode(path))))
+
+
+def fgraft_tuning_table_load(path: str):
+    _check(load().fgraft_tuning_table_load(C.c_char_p(os.fsencode(path))))
+
+
 def fgraft_tune_mma_wait(polls: int = -1):
     """Polls of a tensor-core kernel's first wait for its MMA products before it
     gives up (0: at once, which tests the FGRAFT_ETIMEOUT path; -1: default)."""
@@ -330,6 +363,22 @@ def fgraft_dense_block_dist(X: torch.Tensor, d: int, metric: int, block_ids: tor
                                           C.c_int32(k), C.c_int32(precision), _ptr(ids),
                                           _ptr(dist), st if stats else None, _stream(X.device)))
     return (ids, dist, tuple(st)) if stats else (ids, dist)
+
+
+def fgraft_dense_block_gram(X: torch.Tensor, d: int, metric: int, block_ids: torch.Tensor,
+                            precision: int = 1):
+    """Raw dense-block rate: the tensor-core Gram of every block reduced to the
+    smallest approximate distance per row.  Returns (out_min (nb, bs) float32,
+    kernel ms)."""
+    nb, bs = block_ids.shape
+    out = torch.empty((nb, bs), dtype=torch.float32, device=X.device)
+    ms = C.c_double(0.0)
+    _check(load().fgraft_dense_block_gram(_ptr(X), C.c_int64(X.shape[0]), C.c_int32(d),
+                                          C.c_int64(X.shape[1]), C.c_int32(metric),
+                                          _ptr(block_ids), C.c_int64(nb), C.c_int32(bs),
+                                          C.c_int32(precision), _ptr(out), C.byref(ms),
+                                          _stream(X.device)))
+    return out, ms.value
 
 
 def build_graph(X: torch.Tensor, d: int, params: Params, use_graph: bool = True):

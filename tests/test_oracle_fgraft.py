@@ -215,3 +215,17 @@ def test_dense_block_integer_data_exact():
     assert np.array_equal(i32, i64)
     assert np.array_equal(d32.astype(np.float64), np.where(i64 >= 0, d64, np.inf))
     assert (i32[1, -5:] == -1).all()
+
+
+def test_sampled_final_rows_helper_matches_oracle(tiny):
+    # the one-row-at-a-time recomputation used by the full-size GPU parity
+    # tests gives the oracle's final rows
+    import sampled
+    ps, D, rts, parents, s_off, s_ids = tiny
+    R = 16
+    A, cnt, ctr, per = oracle.fgraft(D, rts, s_off, s_ids, R, 32, 4, 1.2)
+    off, ids, ev = oracle.final(D, A, cnt, R, 1.2, parents[0])
+    users = np.random.default_rng(3).choice(2000, size=150, replace=False)
+    got = sampled.final_rows(D, A, cnt, R, 1.2, parents[0], users)
+    for u, row in got.items():
+        assert ids[off[u]:off[u + 1]].tolist() == row

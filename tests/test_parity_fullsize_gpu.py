@@ -12,6 +12,7 @@ import pytest
 import torch
 
 import oracle
+import oracle_cache
 from paper_2609_30493_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -80,3 +81,15 @@ def test_sampled_search(built):
     assert np.array_equal(built["qi"][sel], oi)
     assert np.array_equal(built["qd"][sel], od)
     assert np.array_equal(built["qe"][sel].astype(np.uint32), oe)
+
+
+def test_whole_build_equals_oracle(built):
+    st, D, ps, ctr = built["st"], built["D"], built["ps"], built["ctr"]
+    g = oracle_cache.build_graph(D, ps.X, T, R, EF, B, ALPHA, seed=0)
+    assert np.array_equal(st["roots"], g["roots"])
+    assert np.array_equal(st["counts"], g["cnt"])
+    assert np.array_equal(st["rows"], g["A"])
+    for k in ("sat_evals", "harvest_evals", "prune_evals", "final_prune_evals", "expansions"):
+        assert ctr[k] == g["counters"][k], k
+    assert np.array_equal(built["f_off"], g["f_off"])
+    assert np.array_equal(built["f_ids"], g["f_ids"])

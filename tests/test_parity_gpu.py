@@ -431,3 +431,112 @@ def test_auto_visited_layout_same_graph(fg):
         assert a[0][k] == b[0][k], k
     for x, y in zip(a[1:], b[1:]):
         assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_dense_block_edge_cases(fg, precision):
+    # blocks of fewer than k + 1 members (every column is a candidate), a
+    # single-member block, a block of repeated points (ties everywhere: the
+    # filter cannot separate them, so every column is reranked), and more
+    # blocks than one launch group holds
+    ps = synth.vmf_like(6000, 100, 8, seed=9)
+    X = ps.X.copy()
+    X[100:400] = X[100]  # 300 copies of one point
+    lab = ps.labels
+    blocks = synth.intra_cluster_blocks(lab, 70, 64, seed=3)
+    blocks[0, 20:] = -1           # 20 members, k = 32
+    blocks[1, 1:] = -1            # one member
+    blocks[2, :] = np.arange(100, 164)  # all identical
+    blocks[3, :40] = np.arange(100, 140)  # 40 copies + 24 others
+    gi, gd = fg.fgraft_dense_block_dist(_dev(X), 100, 1, _dev(blocks), 32, precision=precision)
+    oi, od, _ = oracle.dense_block(oracle.Data(X, 100, 1), blocks, 32)
+    assert np.array_equal(_np(gi), oi)
+    assert np.array_equal(_np(gd), od)
+
+
+def _emulated_min(X, blocks, d, fp8):
+    """Smallest approximate angular distance per row, with the rounding the
+    Gram kernel applies (float32 block mean: eight partial sums over the rows
+    r = w, w + 8, .. of the block, added in order; centred rows rounded to
+    BF16, or to E4M3 after scaling the row's largest magnitude to 448), the
+    products and sums in float64."""
+    nb, bs = blocks.shape
+    out = np.full((nb, bs), np.inf)
+    for b in range(nb):
+        ids = blocks[b]
+        valid = ids >= 0
+        rows = X[ids[valid], :d].astype(np.float32)
+        parts = []
+        for w in range(8):
+            s = np.zeros(d, np.float32)
+            for r in range(w, bs, 8):
+                if ids[r] >= 0:
+                    s = (s + X[ids[r], :d].astype(np.float32)).astype(np.float32)
+            parts.append(s)
+        s = parts[0]
+        for w in range(1, 8):
+            s = (s + parts[w]).astype(np.float32)
+        mu = (s * np.float32(np.float32(1.0) / np.float32(len(rows)))).astype(np.float32)
+        c = torch.from_numpy((rows - mu).astype(np.float32))
+        if fp8:
+            mx = c.abs().max(dim=1).values
+            scale = torch.where(mx > 0, mx / 448.0, torch.ones_like(mx))
+            q = (c * (1.0 / scale)[:, None]).to(torch.float8_e4m3fn).double() * scale.double()[:, None]
+        else:
+            q = c.to(torch.bfloat16).double()
+        x2 = (rows.astype(np.float64) ** 2).sum(1)
+        n = (c.double() ** 2).sum(1).numpy()
+        g = (q @ q.T).numpy()
+        dist = 0.5 * (n[:, None] + n[None, :] - 2 * g) + 0.5 * (1 - x2)[:, None] + 0.5 * (1 - x2)[None, :]
+        np.fill_diagonal(dist, np.inf)
+        out[b, np.nonzero(valid)[0]] = dist.min(1)
+    return out
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_dense_gram_only_matches_emulation(fg, precision):
+    ps = synth.vmf_like(5000, 100, 4, seed=11)
+    blocks = synth.intra_cluster_blocks(ps.labels, 4, 1024, seed=4)
+    blocks[3, -100:] = -1
+    got, ms = fg.fgraft_dense_block_gram(_dev(ps.X), 100, 1, _dev(blocks), precision=precision)
+    want = _emulated_min(ps.X, blocks, 100, precision == 2)
+    got = _np(got).astype(np.float64)
+    fin = np.isfinite(want)
+    assert np.array_equal(np.isfinite(got), fin)
+    assert np.max(np.abs(got[fin] - want[fin])) < 2e-4
+    assert ms > 0.0
+
+
+def test_autotune_settings_give_the_same_graph(fg):
+    # the autotuner's candidate settings (warps per CTA, visited-set layout,
+    # overflow handling) never change the graph, and the tuned index builds
+    # the oracle's graph
+    ps = synth.vmf_like(30_000, 100, 16, seed=6)
+    X = _dev(ps.X)
+    p = fg.Params(T=4, R=32, ef_h=64, B=4, alpha=1.2, seed=0, metric=1)
+    graphs = []
+    for wpc, hl, ov, ga, ib in [(4, 0, 1, 0, 2), (1, 9, 1, 1, 1), (2, 10, 2, 1, 2),
+                                (4, 12, 1, 0, 1), (2, 0, 2, 1, 2), (4, 0, 1, 1, 2)]:
+        ix = fg.fgraft_build_scaffold(X, 100, p)
+        fg.fgraft_index_set_tuning(ix, warps_per_cta=wpc, hash_log2=hl, overflow_mode=ov,
+                                   gather=ga, id_batch=ib)
+        fg.fgraft_harvest_all(ix, use_graph=False)
+        off, ids = fg.fgraft_prune(ix)
+        graphs.append((_np(off), _np(ids)))
+    for g in graphs[1:]:
+        assert np.array_equal(g[0], graphs[0][0]) and np.array_equal(g[1], graphs[0][1])
+    ix = fg.fgraft_build_scaffold(X, 100, p)
+    t = fg.fgraft_index_autotune(ix, sample=2000)
+    assert t["warps_per_cta"] in (1, 2, 4) and t["overflow_mode"] in (1, 2)
+    assert t["gather"] in (0, 1) and t["id_batch"] in (1, 2)
+    assert t["us_per_query"] > 0 and t["default_us_per_query"] > 0
+    fg.fgraft_harvest_all(ix, use_graph=True)
+    off, ids = fg.fgraft_prune(ix)
+    assert np.array_equal(_np(off), graphs[0][0]) and np.array_equal(_np(ids), graphs[0][1])
+    ref = oracle.build_graph(oracle.Data(ps.X, 100, 1), 4, 32, 64, 4, 1.2, 0)
+    assert np.array_equal(_np(off), ref["f_off"]) and np.array_equal(_np(ids), ref["f_ids"])
+    # a later index of the same shape starts from the tuned settings
+    ix2 = fg.fgraft_build_scaffold(X, 100, p)
+    fg.fgraft_harvest_all(ix2, use_graph=False)
+    o2, i2 = fg.fgraft_prune(ix2)
+    assert np.array_equal(_np(o2), graphs[0][0]) and np.array_equal(_np(i2), graphs[0][1])

@@ -1,0 +1,126 @@
+"""Parity at the paper-scale workload's full size, in bench.py's launch
+configuration: n = 1,183,514 unit vectors, d = 100 (473 MB, far more than the
+L2 cache), 256 vMF-like clusters with Zipf(1.1) sizes, angular, R = 64,
+ef_h = 100, alpha = 1.2; the harvest launch settings chosen by the autotuner
+as the benchmark chooses them; the blocks run as one CUDA graph.
+
+Three arms of the paper's Table 1 shape: FGraft T = 8 with B = 8 (the
+benchmark step), the frozen T = 32 harvest (B = 1), and T = 8 with B = 16.
+The oracle recomputes, one at a time: sampled harvested rows, each from its
+own S_b rebuilt from the scaffold and the rows of earlier blocks only;
+sampled final-graph rows from the harvested rows; 200 sampled query
+searches (ef_s = 64, top-10) over the final graph; and two of the
+benchmark's 64 dense 1024-point blocks (top-64) in every precision.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import sampled
+from paper_2609_30493_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+N, D, ALPHA, R, EF = 1_183_514, 100, 1.2, 64, 100
+
+
+@pytest.fixture(scope="module")
+def data():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_30493_gb300 import build, fgraft as fg
+    build.build()
+    fg.load()
+    ps = synth.vmf_like(N, D, 256, seed=0, kappa=20.0, sizes="zipf")
+    X = torch.from_numpy(ps.X).cuda()
+    # the benchmark's launch configuration: the autotuner's choice for this shape
+    ixt = fg.fgraft_build_scaffold(X, D, fg.Params(T=8, R=R, ef_h=EF, B=8, alpha=ALPHA, seed=0,
+                                                   metric=fg.ANGULAR_F32))
+    fg.fgraft_index_autotune(ixt, sample=16384)
+    del ixt
+    return dict(fg=fg, ps=ps, X=X, D=oracle.Data(ps.X, D, oracle.ANGULAR_F32))
+
+
+def _build(data, T, B):
+    fg = data["fg"]
+    ix = fg.fgraft_build_scaffold(data["X"], D, fg.Params(T=T, R=R, ef_h=EF, B=B, alpha=ALPHA,
+                                                          seed=0, metric=fg.ANGULAR_F32))
+    ctr = fg.fgraft_harvest_all(ix, use_graph=True, counters=True)
+    st = {k: v.cpu().numpy() for k, v in fg.fgraft_index_copy(ix).items()}
+    return ix, ctr, st
+
+
+def _check_rows(data, st, B, blocks, per_block, seed):
+    D_, ps = data["D"], data["ps"]
+    rng = np.random.default_rng(seed)
+    for b in blocks:
+        off, ids = oracle.substrate(N, st["s_off"], st["s_ids"], st["rows"], st["counts"], R, B, b)
+        nb = max(B, 1)
+        pts = b + nb * rng.choice((N - b + nb - 1) // nb, size=per_block, replace=False)
+        for p in pts:
+            E, Ed, P, Pd, nev = oracle.beam(D_, off, ids, st["roots"], ps.X[p], EF)
+            kept, _ = oracle.prune_list(D_, int(p), E, ALPHA, R)
+            assert st["counts"][p] == len(kept), (b, p)
+            assert st["rows"][p, :len(kept)].tolist() == kept.tolist(), (b, p)
+            assert (st["rows"][p, len(kept):] == -1).all()
+
+
+@pytest.fixture(scope="module")
+def bench_arm(data):
+    fg = data["fg"]
+    ix, ctr, st = _build(data, 8, 8)
+    f_off, f_ids = fg.fgraft_prune(ix)
+    Q = synth.queries(data["ps"], 10_000, 1)
+    qi, qd, qe = fg.fgraft_search(ix, torch.from_numpy(Q).cuda(), 10, 64)
+    return dict(ix=ix, ctr=ctr, st=st, f_off=f_off.cpu().numpy(), f_ids=f_ids.cpu().numpy(),
+                Q=Q, qi=qi.cpu().numpy(), qd=qd.cpu().numpy(), qe=qe.cpu().numpy())
+
+
+def test_bench_arm_runs_coherent(data, bench_arm):
+    assert data["fg"].fgraft_index_schedule(bench_arm["ix"]) is not None
+
+
+def test_bench_arm_sampled_rows(data, bench_arm):
+    _check_rows(data, bench_arm["st"], 8, [0, 1, 4, 7], 4, seed=21)
+
+
+def test_bench_arm_sampled_final_rows(data, bench_arm):
+    st, D_ = bench_arm["st"], data["D"]
+    users = np.random.default_rng(22).choice(N, size=100, replace=False)
+    want = sampled.final_rows(D_, st["rows"], st["counts"], R, ALPHA, st["parents"][0], users)
+    f_off, f_ids = bench_arm["f_off"], bench_arm["f_ids"]
+    for u, row in want.items():
+        assert f_ids[f_off[u]:f_off[u + 1]].tolist() == row, u
+
+
+def test_bench_arm_sampled_search(data, bench_arm):
+    Q = bench_arm["Q"]
+    sel = np.random.default_rng(23).choice(len(Q), size=200, replace=False)
+    oi, od, oe = oracle.search(data["D"], bench_arm["f_off"], bench_arm["f_ids"],
+                               bench_arm["st"]["roots"], Q[sel], 10, 64)
+    assert np.array_equal(bench_arm["qi"][sel], oi)
+    assert np.array_equal(bench_arm["qd"][sel], od)
+    assert np.array_equal(bench_arm["qe"][sel].astype(np.uint32), oe)
+
+
+def test_bench_dense_blocks_sampled(data):
+    fg = data["fg"]
+    blocks = synth.intra_cluster_blocks(data["ps"].labels, 64, 1024, 2)
+    Bd = torch.from_numpy(blocks).cuda()
+    sel = [0, 37]
+    oi, od, _ = oracle.dense_block(data["D"], blocks[sel], 64)
+    for prec in (0, 1, 2):
+        gi, gd = fg.fgraft_dense_block_dist(data["X"], D, fg.ANGULAR_F32, Bd, 64, precision=prec)
+        assert np.array_equal(gi.cpu().numpy()[sel], oi), prec
+        assert np.array_equal(gd.cpu().numpy()[sel], od), prec
+
+
+def test_frozen_T32_sampled_rows(data):
+    ix, ctr, st = _build(data, 32, 1)
+    _check_rows(data, st, 1, [0], 24, seed=24)
+
+
+def test_T8_B16_sampled_rows(data):
+    ix, ctr, st = _build(data, 8, 16)
+    _check_rows(data, st, 16, [0, 9, 15], 3, seed=25)
