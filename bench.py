@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune-table", default=None,
+                    help="autotuner table (JSON): loaded when the file exists, otherwise "
+                         "written after tuning (a profiled run then reuses the settings of "
+                         "the plain run instead of tuning under the profiler)")
     ap.add_argument("--n", type=int, default=None, help="override n (smaller runs)")
     ap.add_argument("--batch", type=int, default=64, help="builds of --mode batched")
     ap.add_argument("--arms", default="32x1,8x1,8x2,8x4,8x8,8x16",
@@ -311,7 +315,23 @@ def _alg_bytes(spec, ctr):
     return ctr.get("harvest_evals", 0) * line + ctr.get("ids_scanned", 0) * 4
 
 
-def incache_extra(fg, flush, stream, steps=3, warmup=2):
+def tune(fg, X_d, spec, params, sample, table=None):
+    """The autotuner's harvest settings for this shape (kept in the process's
+    table for every later build).  With a table file that exists, its
+    settings are loaded instead; a table file that does not exist yet is
+    written after tuning."""
+    if table and os.path.exists(table):
+        fg.fgraft_tuning_table_load(table)
+        return {"loaded_from": os.path.basename(table)}
+    ixt = fg.fgraft_build_scaffold(X_d, spec["d"], params)
+    t = fg.fgraft_index_autotune(ixt, sample=sample)
+    del ixt
+    if table:
+        fg.fgraft_tuning_table_save(table)
+    return t
+
+
+def incache_extra(fg, flush, stream, steps=3, warmup=2, tune_table=None):
     """The in-cache workload (40 MB of vectors, L2-resident): bound by the
     latency of the dependent gathers, not by HBM.  Reports the step rate, the
     harvest's evaluations per second, its algorithmic gather rate and the SM
@@ -320,9 +340,7 @@ def incache_extra(fg, flush, stream, steps=3, warmup=2):
     spec = INCACHE
     ps, Q, blocks, dev_in = _device_inputs(spec)
     params = _params(fg, spec)
-    ixt = fg.fgraft_build_scaffold(dev_in[0], spec["d"], params)
-    tuning = fg.fgraft_index_autotune(ixt, sample=4096)
-    del ixt
+    tuning = tune(fg, dev_in[0], spec, params, 4096, tune_table)
     clocks = Clocks(torch.cuda.current_device())
     tot, hms, hl, pms, ctr, _, _ = _timed(fg, spec, params, dev_in, steps, warmup, flush, stream)
     clk = clocks.stop()
@@ -368,9 +386,7 @@ def run_ours(args):
 
     # ---- autotuner (outside the timed region): the harvest launch settings
     # for this shape, kept in the process's table for every later build ----
-    ixt = fg.fgraft_build_scaffold(X_d, d, params)
-    tuning = fg.fgraft_index_autotune(ixt, sample=16384)
-    del ixt
+    tuning = tune(fg, X_d, spec, params, 32768, args.tune_table)
 
     # ---- timed region: inputs resident in HBM ----
     for _ in range(args.warmup):
@@ -493,7 +509,9 @@ def run_ours(args):
         d2h = sum(o.numel() * o.element_size() for o in outs)
         del ix2
     _, e2e_value = job_rate(e2e_ms, args.steps, n, world, dist if world > 1 else None, "cuda")
-    extra = incache_extra(fg, flush, stream) if not args.n else None
+    extra = incache_extra(fg, flush, stream,
+                          tune_table=args.tune_table + ".incache" if args.tune_table else None) \
+        if not args.n else None
 
     if rank != 0:
         if world > 1:

@@ -303,7 +303,8 @@ fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t war
  * a shared buffer of 32 rows per search (rows of at most 64 chunks); the
  * bitmap visited tests of 1 or 2 chunks of 32 ids issued together.  The
  * search is coordinate descent from the defaults (4, occupancy rule, global
- * bitmap, registers, 2), each setting in turn over its options, two rounds.  Results never depend on the settings: the sample's
+ * bitmap, registers, 2), each setting in turn over its options, two rounds;
+ * each candidate is timed as the fastest of three runs of the sample.  Results never depend on the settings: the sample's
  * rows receive their final values and nothing else of the index changes.
  * chosen (host, optional) receives the settings and the microseconds per
  * sample search with them and with the default settings.  Call it before

@@ -1164,13 +1164,13 @@ fgraft_status fgraft_index_autotune(fgraft_index* ix, int32_t sample, fgraft_str
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  // one calibration run of the given settings: the faster of two timed runs
+  // one calibration run of the given settings: the fastest of three timed runs
   auto time_one = [&](const Cfg& c, float* ms) -> int {
     apply_settings(ix, c[0], c[1], c[2], c[3], c[4]);
     int r = size_visited_bitmaps(ix);
     if (r) return r;
     *ms = 1e30f;
-    for (int rep = 0; rep < 2; ++rep) {
+    for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(e0, s);
       r = harvest_sample(ix, sample, tctr, s);
       if (r) return r;

@@ -429,6 +429,7 @@ struct FinalArgs {
   int32_t* def_rows;
   int32_t* def_m;
   uint32_t* def_count;
+  int32_t* def_long;
   int32_t def_cap;
   const uint64_t* def_kept;
   const int32_t* def_kcnt;
@@ -459,7 +460,7 @@ __device__ void final_spine_out(const FinalArgs& a, int32_t u, const uint4* us, 
 
 constexpr int FIN_WARPS = 4;
 constexpr int FIN_CAP = 1024;
-constexpr int FIN_DEF_CAP = 128;  // longest final row list the CTA prune takes
+constexpr int FIN_DEF_CAP = 256;  // longest final row list the CTA prune takes
 
 // Shared memory per warp: key buffer and bit words (unless the row works in
 // global scratch), then two staged vectors (the row's owner, the kept c*).
@@ -724,7 +725,7 @@ static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, int nu
     rc = harvest_prune(L, a.def_keys, a.def_m, a.def_cap, 0, 0, 0, a.R, a.alpha2, nullptr,
                        const_cast<int32_t*>(a.def_kcnt), a.ctr, num_sms, s, a.def_rows,
                        a.def_koff, a.def_count, const_cast<uint64_t*>(a.def_kept),
-                       a.def_count + 1);
+                       a.def_count + 1, a.def_long, a.def_count + 2);
     if (!rc) {
       FinalArgs b = a;
       b.mode = 2;
@@ -767,6 +768,7 @@ int final_graph(const VecLayout& L, int R, float alpha2, const int32_t* A, const
   uint64_t *def_keys = nullptr, *def_kept = nullptr;
   int32_t *def_rows = nullptr, *def_m = nullptr, *def_kcnt = nullptr;
   uint32_t* def_count = nullptr;
+  int32_t* def_long = nullptr;
   int rc = 0;
   auto cleanup = [&]() {
     cudaFreeAsync(c0cnt, s);
@@ -783,6 +785,7 @@ int final_graph(const VecLayout& L, int R, float alpha2, const int32_t* A, const
     cudaFreeAsync(def_m, s);
     cudaFreeAsync(def_kcnt, s);
     cudaFreeAsync(def_count, s);
+    cudaFreeAsync(def_long, s);
   };
 #define FG_TRY(call)                                \
   do {                                              \
@@ -840,14 +843,17 @@ int final_graph(const VecLayout& L, int R, float alpha2, const int32_t* A, const
   FG_TRY(cudaMallocAsync(&def_rows, sizeof(int32_t) * std::max<int64_t>(n, 1), s));
   FG_TRY(cudaMallocAsync(&def_m, sizeof(int32_t) * std::max<int64_t>(n, 1), s));
   FG_TRY(cudaMallocAsync(&def_kcnt, sizeof(int32_t) * std::max<int64_t>(n, 1), s));
-  FG_TRY(cudaMallocAsync(&def_count, 2 * sizeof(uint32_t), s));  // count, timeout flag
-  FG_TRY(cudaMemsetAsync(def_count, 0, 2 * sizeof(uint32_t), s));
+  // count, timeout flag, rows longer than the 128-candidate tile
+  FG_TRY(cudaMallocAsync(&def_count, 4 * sizeof(uint32_t), s));
+  FG_TRY(cudaMemsetAsync(def_count, 0, 4 * sizeof(uint32_t), s));
+  FG_TRY(cudaMallocAsync(&def_long, sizeof(int32_t) * std::max<int64_t>(n, 1), s));
   FinalArgs a{};
   a.def_keys = def_cap ? def_keys : nullptr;
   a.def_koff = def_koff;
   a.def_rows = def_rows;
   a.def_m = def_m;
   a.def_count = def_count;
+  a.def_long = def_long;
   a.def_cap = def_cap;
   a.def_kept = def_kept;
   a.def_kcnt = def_kcnt;

@@ -540,3 +540,30 @@ def test_autotune_settings_give_the_same_graph(fg):
     fg.fgraft_harvest_all(ix2, use_graph=False)
     o2, i2 = fg.fgraft_prune(ix2)
     assert np.array_equal(_np(o2), graphs[0][0]) and np.array_equal(_np(i2), graphs[0][1])
+
+
+def test_wide_lists_use_both_prune_tiles(fg):
+    # ef_h = 100 gives list buffers of 256 entries and R = 64 final rows of
+    # more than 128 candidates: the harvest and the final graph take the
+    # 128- and 256-candidate tensor-core tiles; the whole graph and every
+    # counter equal the oracle's
+    ps = synth.vmf_like(12_000, 100, 8, seed=14)
+    A, cnt, off, ids, ctr, _ = _build_both_simple(fg, ps, T=4, R=64, ef=100, B=2)
+    ref = oracle.build_graph(oracle.Data(ps.X, 100, 1), 4, 64, 100, 2, 1.2, 0)
+    assert np.array_equal(A, ref["A"]) and np.array_equal(cnt, ref["cnt"])
+    assert np.array_equal(off, ref["f_off"]) and np.array_equal(ids, ref["f_ids"])
+    for k in ("harvest_evals", "prune_evals", "final_prune_evals", "expansions", "sat_evals"):
+        assert ctr[k] == ref["counters"][k], k
+    # the final graph did prune rows past one 128-candidate tile
+    indeg = np.bincount(ref["A"][ref["A"] >= 0], minlength=12_000)
+    assert ((ref["cnt"] + indeg) > 128).sum() > 100
+
+
+def _build_both_simple(fg, ps, T, R, ef, B):
+    X = _dev(ps.X)
+    ix = fg.fgraft_build_scaffold(X, ps.d, fg.Params(T=T, R=R, ef_h=ef, B=B, alpha=1.2, seed=0,
+                                                     metric=ps.metric))
+    ctr = fg.fgraft_harvest_all(ix, use_graph=True, counters=True)
+    off, ids = fg.fgraft_prune(ix)
+    st = fg.fgraft_index_copy(ix)
+    return _np(st["rows"]), _np(st["counts"]), _np(off), _np(ids), ctr, ix
