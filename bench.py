@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-dims", action="store_true", help="skip the dimension sweep extra")
     ap.add_argument("--tune-table", default=None,
                     help="autotuner table (JSON): loaded when the file exists, otherwise "
                          "written after tuning (a profiled run then reuses the settings of "
@@ -362,6 +363,118 @@ def incache_extra(fg, flush, stream, steps=3, warmup=2, tune_table=None):
             "config": {k: spec[k] for k in ("n", "d", "k", "T", "B", "R", "ef_h", "alpha")}}
 
 
+def paper_arms(fg, X_d, Q_d, ps, Q, spec, arms=((32, 1), (8, 1), (8, 2), (8, 4), (8, 8), (8, 16))):
+    """The paper's Table 1 shape on the benchmark workload (untimed extra): the
+    frozen T = 32 harvest and FGraft T = 8 at B = 1..16, R = 64, ef_h = 100;
+    build time (scaffold, harvest, final graph), harvest evaluations per
+    second and recall@10 at ef_s = 64 and 128 (float32 brute force)."""
+    import torch
+    d = spec["d"]
+    gt = []
+    for s0 in range(0, Q_d.shape[0], 1024):
+        gt.append(torch.topk(Q_d[s0:s0 + 1024, :d] @ X_d[:, :d].T, 10, dim=1).indices)
+    gt = torch.cat(gt)
+    out = []
+    for T, B in arms:
+        p = fg.Params(T=T, R=spec["R"], ef_h=spec["ef_h"], B=B, alpha=spec["alpha"],
+                      seed=spec["seed"], metric=fg.ANGULAR_F32)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        ix = fg.fgraft_build_scaffold(X_d, d, p)
+        fg.fgraft_index_profile(ix, True)
+        fg.fgraft_harvest_all(ix, use_graph=True)
+        e1.record()
+        torch.cuda.synchronize()
+        hms, _ = fg.fgraft_index_harvest_ms(ix)
+        c = fg.fgraft_index_counters(ix)
+        rec = {}
+        for ef in (64, 128):
+            ids, _, ev = fg.fgraft_search(ix, Q_d, 10, ef)
+            hit = (ids.long().unsqueeze(2) == gt.unsqueeze(1)).any(dim=2).sum().item()
+            rec[f"recall_at_10_ef{ef}"] = round(hit / (Q_d.shape[0] * 10), 4)
+            rec[f"evals_per_query_ef{ef}"] = round(float(ev.double().mean().item()), 1)
+        ms = e0.elapsed_time(e1)
+        out.append({"T": T, "B": B, "build_ms": round(ms, 1),
+                    "pts_per_s": round(spec["n"] / (ms / 1e3), 1),
+                    "harvest_evals": c["harvest_evals"],
+                    "harvest_evals_per_s": round(c["harvest_evals"] / (hms / 1e3), 1), **rec})
+        del ix
+    return out
+
+
+def dims_sweep(fg, dims=(32, 64, 128, 256, 512, 960), n=1_000_000):
+    """Adaptive vs blocked cost per evaluation across d (Section 5.4, Table 5),
+    untimed extra: Gaussian mixtures of 128 clusters (centres N(0, 25 I), unit
+    noise, generated on the device), L2, T = 8, B = 8, R = 32, ef_h = 64; the
+    harvest's evaluations per second and SM cycles per evaluation against the
+    dense blocks' pairs per second (64 intra-cluster blocks of 1024, BF16
+    filter with float32 rerank, and the raw Gram), and the fitted exponents."""
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    rows = []
+    for d in dims:
+        g = torch.Generator(device="cuda")
+        g.manual_seed(d)
+        lab = torch.randint(0, 128, (n,), generator=g, device="cuda")
+        cent = 5.0 * torch.randn(128, d, generator=g, device="cuda")
+        ld = (d + 3) // 4 * 4
+        X = torch.zeros(n, ld, device="cuda")
+        X[:, :d] = cent[lab] + torch.randn(n, d, generator=g, device="cuda")
+        del cent
+        p = fg.Params(T=8, R=32, ef_h=64, B=8, alpha=1.2, seed=0, metric=fg.L2_F32)
+        ix = fg.fgraft_build_scaffold(X, d, p)
+        fg.fgraft_index_profile(ix, True)
+        fg.fgraft_harvest_all(ix, use_graph=False)
+        hms, _ = fg.fgraft_index_harvest_ms(ix)
+        c = fg.fgraft_index_counters(ix)
+        del ix
+        labn = lab.cpu().numpy()
+        blocks = []
+        rng = np.random.default_rng(d)
+        for cl in rng.permutation(128):
+            members = np.nonzero(labn == cl)[0]
+            if len(members) >= 1024:
+                blocks.append(np.sort(rng.choice(members, 1024, replace=False)))
+            if len(blocks) == 64:
+                break
+        Bd = torch.from_numpy(np.stack(blocks).astype(np.int32)).cuda()
+        pairs = len(blocks) * 1024 * 1023
+        fg.fgraft_dense_block_dist(X, d, fg.L2_F32, Bd, 32, precision=1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fg.fgraft_dense_block_dist(X, d, fg.L2_F32, Bd, 32, precision=1)
+        e1.record()
+        torch.cuda.synchronize()
+        dense = pairs / (e0.elapsed_time(e1) / 1e3)
+        _, gms = fg.fgraft_dense_block_gram(X, d, fg.L2_F32, Bd, precision=1)
+        gram = pairs / (gms / 1e3)
+        rate = c["harvest_evals"] / (hms / 1e3)
+        mhz = _sm_clock_mhz() or 2070.0
+        rows.append({"d": d, "harvest_evals_per_s": round(rate, 1),
+                     "sm_cycles_per_eval": round(hms / 1e3 * mhz * 1e6 * nsm / c["harvest_evals"], 1),
+                     "harvest_alg_GBps": round(rate * 32 * ((4 * d + 31) // 32) / 1e9, 1),
+                     "dense_pairs_per_s": round(dense, 1), "gram_pairs_per_s": round(gram, 1),
+                     "gap_W": round(dense / rate, 2), "gap_W_gram": round(gram / rate, 2)})
+        del X, Bd
+        torch.cuda.empty_cache()
+    ld = np.log([r["d"] for r in rows])
+    fit = {"adaptive_cost_exponent": round(float(np.polyfit(ld, np.log([1 / r["harvest_evals_per_s"] for r in rows]), 1)[0]), 3),
+           "dense_cost_exponent": round(float(np.polyfit(ld, np.log([1 / r["dense_pairs_per_s"] for r in rows]), 1)[0]), 3),
+           "gram_cost_exponent": round(float(np.polyfit(ld, np.log([1 / r["gram_pairs_per_s"] for r in rows]), 1)[0]), 3)}
+    fit["gap_exponent"] = round(fit["adaptive_cost_exponent"] - fit["dense_cost_exponent"], 3)
+    return {"n": n, "rows": rows, "fit": fit,
+            "data": "Gaussian mixture generated on the device (torch generator per d)"}
+
+
+def _extra(fn, *a, **kw):
+    """An untimed extra measurement; a failure is recorded, not raised."""
+    try:
+        return fn(*a, **kw)
+    except Exception as e:  # noqa: BLE001 - reported in the JSON line
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -509,6 +622,8 @@ def run_ours(args):
         d2h = sum(o.numel() * o.element_size() for o in outs)
         del ix2
     _, e2e_value = job_rate(e2e_ms, args.steps, n, world, dist if world > 1 else None, "cuda")
+    arms = _extra(paper_arms, fg, X_d, Q_d, ps, Q, spec) if not args.n else None
+    dims = _extra(dims_sweep, fg) if not args.n and not args.no_dims else None
     extra = incache_extra(fg, flush, stream,
                           tune_table=args.tune_table + ".incache" if args.tune_table else None) \
         if not args.n else None
@@ -576,6 +691,8 @@ def run_ours(args):
         "quality": quality,
         "breakdown_ms": breakdown,
         "incache": extra,
+        "paper_arms": arms,
+        "dims_sweep": dims,
         "e2e": {"value": round(e2e_value, 1), "unit": "pts/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),

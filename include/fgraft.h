@@ -135,10 +135,18 @@ fgraft_status fgraft_harvest_block(fgraft_index* ix, int32_t b, fgraft_stream st
 /* Block b of several independent indices at once (many builds of the same
  * schedule, for example one per data shard or tenant): every index must be
  * at block b (0..B-1 in order, as for fgraft_harvest_block) and appear once.
- * The harvests are issued on internal side streams that wait for `stream`,
- * so the kernels of different indices overlap on the GPU, and `stream`
- * waits for all of them on return (nothing is synchronised on the host).
- * Each index's rows equal those of its own fgraft_harvest_block call.  The
+ * The indices are grouped by kernel shape (metric, lane groups of the
+ * dimension, pool slots of ef_h, 16-byte chunks per row); each group of up
+ * to 64 indices takes ONE persistent search launch whose work items are the
+ * (index, search) pairs of all of them, claimed from one counter, each with
+ * its index's descriptor.  The per-warp layout of that launch is common to
+ * the group (a shared-memory hash sized by occupancy, 4 warps per CTA,
+ * register gathers; visited sets outgrowing the hash go on in global bitmaps
+ * sized for the largest index, kept on the device for the process).  Then,
+ * per index, the re-run pass, the prune and the reverse lists run on
+ * `stream` as for fgraft_harvest_block.  Each index's rows equal those of
+ * its own fgraft_harvest_block call.  Nothing is synchronised on the host;
+ * not for use during stream capture (the bitmaps may be reallocated).  The
  * paper has no counterpart; it runs one build at a time. */
 fgraft_status fgraft_harvest_block_multi(fgraft_index* const* ixs, int32_t nix, int32_t b,
                                          fgraft_stream stream);

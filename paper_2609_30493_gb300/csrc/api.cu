@@ -316,14 +316,15 @@ int beam_shape(fgraft_index* ix, BeamKernelFn kern, int S, BeamShape* out) {
   return 0;
 }
 
+int launch_rerun(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStream_t s);
+
 // Launch the beam over `nq` work items (shared-memory pass), then the
 // overflow list on global scratch.  `a` carries everything but the scratch.
 int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStream_t s,
                 cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
   const int S = pool_slots(a.ef);
   BeamKernelFn kern = beam_kernel_for(ix->L.metric, ix->L.G, ix->L.K, S, ix->gather != 0);
-  BeamKernelFn kern_rr = beam_kernel_for(ix->L.metric, ix->L.G, ix->L.K, S, false);
-  if (!kern || !kern_rr) return fail(FGRAFT_EINVAL, "no beam kernel for this metric and dimension");
+  if (!kern) return fail(FGRAFT_EINVAL, "no beam kernel for this metric and dimension");
   BeamShape sh;
   int rc = beam_shape(ix, kern, S, &sh);
   if (rc) return rc;
@@ -367,7 +368,17 @@ int launch_beam(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStrea
   note_launch();
   FG_CUDA(cudaGetLastError());
   if (e1) FG_CUDA(record_event(e1, s));
-  // re-run of the overflowed items with per-warp global scratch (pruned in place)
+  return launch_rerun(ix, a, ctr, s);
+}
+
+// Re-run of the work items a harvest or search launch of index ix abandoned
+// (listed in ix->ovf_list, count ix->work[2]) with per-warp global scratch,
+// pruned in place.  `a` is that launch's descriptor.
+int launch_rerun(fgraft_index* ix, BeamArgs a, unsigned long long* ctr, cudaStream_t s) {
+  const int S = pool_slots(a.ef);
+  BeamKernelFn kern_rr = beam_kernel_for(ix->L.metric, ix->L.G, ix->L.K, S, false);
+  if (!kern_rr) return fail(FGRAFT_EINVAL, "no beam kernel for this metric and dimension");
+  const int qbytes = 16 * ix->L.nchunks;
   a.global_scratch = 1;
   a.Eg = nullptr;
   a.Eg_cnt = nullptr;
@@ -526,7 +537,9 @@ TuneKey tune_key(const fgraft_index* ix) {
   return TuneKey{ix->L.metric, ix->L.d, ix->p.ef_h, ix->p.R, ceil_log2(ix->L.n)};
 }
 
-int harvest_block_impl(fgraft_index* ix, int32_t b, cudaStream_t s) {
+// The harvest search arguments of block b of index ix (everything but the
+// launch layout, which launch_beam or a many-builds launch fills in).
+BeamArgs harvest_args(fgraft_index* ix, int32_t b) {
   BeamArgs a{};
   a.X = ix->L.X;
   a.ld_bytes = ix->L.ld_bytes;
@@ -559,23 +572,35 @@ int harvest_block_impl(fgraft_index* ix, int32_t b, cudaStream_t s) {
   const bool sep = ix->prune_ns > 0;
   a.Eg = sep ? ix->Eg : nullptr;
   a.Eg_cnt = sep ? ix->Eg_cnt : nullptr;
+  return a;
+}
+
+// After block b's searches: the occlusion prune (when it runs in its own
+// kernels) and the reverse lists that make S_{b+1}.
+int harvest_after(fgraft_index* ix, int32_t b, const BeamArgs& a, cudaStream_t s) {
+  const bool prof = ix->profile && (int)ix->ev_beg.size() > b;
+  if (ix->prune_ns > 0) {
+    const int rc = harvest_prune(ix->L, ix->Eg, ix->Eg_cnt, ix->eg_ecap, a.nq, a.q_first,
+                                 a.q_step, ix->p.R, a.alpha2, ix->A, ix->cnt, ix->ctr + C_PRUNE,
+                                 ix->num_sms, s, nullptr, nullptr, nullptr, nullptr, ix->work + 4,
+                                 ix->ovf_list, ix->work + 5);
+    if (rc) return rc;
+  }
+  if (prof) FG_CUDA(record_event(ix->ev_pend[b], s));
+  const int rc = reverse_rows(ix->L.n, ix->p.R, ix->nb, b, ix->A, ix->cnt, ix->rcnt, ix->rcur,
+                              ix->r_off, ix->r_ids, ix->scan_tmp, s);
+  if (rc) return rc;
+  ix->blocks_done = b + 1;
+  return 0;
+}
+
+int harvest_block_impl(fgraft_index* ix, int32_t b, cudaStream_t s) {
+  BeamArgs a = harvest_args(ix, b);
   const bool prof = ix->profile && (int)ix->ev_beg.size() > b;
   int rc = launch_beam(ix, a, ix->ctr + C_HARVEST, s, prof ? ix->ev_beg[b] : nullptr,
                        prof ? ix->ev_end[b] : nullptr);
   if (rc) return rc;
-  if (sep) {
-    rc = harvest_prune(ix->L, ix->Eg, ix->Eg_cnt, ix->eg_ecap, a.nq, a.q_first,
-                       a.q_step, ix->p.R, a.alpha2, ix->A, ix->cnt, ix->ctr + C_PRUNE,
-                       ix->num_sms, s, nullptr, nullptr, nullptr, nullptr, ix->work + 4,
-                       ix->ovf_list, ix->work + 5);
-    if (rc) return rc;
-  }
-  if (prof) FG_CUDA(record_event(ix->ev_pend[b], s));
-  rc = reverse_rows(ix->L.n, ix->p.R, ix->nb, b, ix->A, ix->cnt, ix->rcnt, ix->rcur, ix->r_off,
-                    ix->r_ids, ix->scan_tmp, s);
-  if (rc) return rc;
-  ix->blocks_done = b + 1;
-  return 0;
+  return harvest_after(ix, b, a, s);
 }
 
 // The searches of block 0 for its first `sample` work items in claim order
@@ -584,35 +609,9 @@ int harvest_block_impl(fgraft_index* ix, int32_t b, cudaStream_t s) {
 // points' final rows (block 0 always searches S_0), and nothing else of the
 // index changes: this is the autotuner's calibration workload.
 int harvest_sample(fgraft_index* ix, int64_t sample, unsigned long long* tctr, cudaStream_t s) {
-  BeamArgs a{};
-  a.X = ix->L.X;
-  a.ld_bytes = ix->L.ld_bytes;
-  a.d = ix->L.d;
-  a.nchunks = ix->L.nchunks;
-  a.n = ix->L.n;
-  a.s_off = ix->s_off;
-  a.s_ids = ix->s_ids;
-  a.A = ix->A;
-  a.cnt = ix->cnt;
-  a.R = ix->p.R;
-  a.r_off = nullptr;
-  a.r_ids = ix->r_ids;
-  a.B = ix->nb;
-  a.b = 0;
-  a.roots = ix->roots;
-  a.T = ix->p.T;
-  a.nq = std::min<int64_t>(sample, (ix->L.n + ix->nb - 1) / ix->nb);
-  a.q_first = 0;
-  a.q_step = ix->nb;
-  a.qlist = ix->qorder;  // block 0's claim order comes first
-  a.ef = ix->p.ef_h;
-  a.mode = 0;
-  a.alpha2 = ix->p.alpha * ix->p.alpha;
-  a.A_out = ix->A;
-  a.cnt_out = ix->cnt;
+  BeamArgs a = harvest_args(ix, 0);  // block 0's claim order comes first in qorder
+  a.nq = std::min<int64_t>(sample, a.nq);
   const bool sep = ix->prune_ns > 0;
-  a.Eg = sep ? ix->Eg : nullptr;
-  a.Eg_cnt = sep ? ix->Eg_cnt : nullptr;
   int rc = launch_beam(ix, a, tctr, s);
   if (rc || !sep) return rc;
   return harvest_prune(ix->L, ix->Eg, ix->Eg_cnt, ix->eg_ecap, a.nq, 0, ix->nb, ix->p.R, a.alpha2,
@@ -620,36 +619,138 @@ int harvest_sample(fgraft_index* ix, int64_t sample, unsigned long long* tctr, c
                        nullptr, ix->work + 4, ix->ovf_list, ix->work + 5, a.qlist);
 }
 
-// Side streams of a device for fgraft_harvest_block_multi, created on first
-// use and kept for the process.
-struct MultiStreams {
-  static constexpr int kStreams = 8;
-  cudaStream_t st[kStreams];
-  cudaEvent_t fork;
-  cudaEvent_t join[kStreams];
+// Scratch of the many-builds launches on a device: the launch's claim
+// counter and the per-warp global bitmaps of visited sets that outgrow the
+// shared-memory hash, sized for the largest index of the launch; created on
+// first use, grown when needed, kept for the process.  Not for use during
+// stream capture.
+struct MultiScratch {
+  uint32_t* work = nullptr;
+  uint32_t* gvbits = nullptr;
+  int64_t gv_words = 0;  // allocated words
   std::mutex mu;
 };
 
-int multi_streams(MultiStreams** out) {
+int multi_scratch(MultiScratch** out) {
   static std::mutex mu;
-  static MultiStreams* per_dev[64] = {};
+  static MultiScratch* per_dev[64] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (dev < 0 || dev >= 64) return fail(FGRAFT_EINVAL, "device index out of range");
   std::lock_guard<std::mutex> lock(mu);
   if (!per_dev[dev]) {
-    MultiStreams* m = new MultiStreams();
-    e = cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming);
-    for (int k = 0; k < MultiStreams::kStreams && e == cudaSuccess; ++k) {
-      e = cudaStreamCreateWithFlags(&m->st[k], cudaStreamNonBlocking);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->join[k], cudaEventDisableTiming);
+    MultiScratch* m = new MultiScratch();
+    if ((e = cudaMalloc(&m->work, 16)) != cudaSuccess) {
+      delete m;
+      return cuda_fail(e, "cudaMalloc(multi-build counter)");
     }
-    if (e != cudaSuccess) return cuda_fail(e, "side streams");
     per_dev[dev] = m;
   }
   *out = per_dev[dev];
   return 0;
+}
+
+// Block b of the indices g[0..cnt) -- same metric, lane groups, pool slots
+// and row chunks -- in one search launch: every index's work items are one
+// range of a single claim counter, each with its own descriptor.  The
+// per-warp layout is common: a shared-memory hash sized by occupancy (the
+// n-bit shared bitmap depends on n), warps per CTA 4, register gathers;
+// searches whose visited set outgrows the hash go on in global bitmaps sized
+// for the largest n.  Then, per index, the re-run pass, the prune and the
+// reverse lists, as fgraft_harvest_block does.
+int harvest_multi_launch(fgraft_index* const* g, int cnt, int32_t b, cudaStream_t s) {
+  fgraft_index* ix0 = g[0];
+  const int S = pool_slots(ix0->p.ef_h);
+  BeamMultiFn kern = ix0->L.metric == 0 ? beam_multi_metric0(ix0->L.G, ix0->L.K, S)
+                     : ix0->L.metric == 1 ? beam_multi_metric1(ix0->L.G, ix0->L.K, S)
+                                          : beam_multi_metric2(ix0->L.G, ix0->L.K, S);
+  if (!kern) return fail(FGRAFT_EINVAL, "no beam kernel for this metric and dimension");
+  const int wpc = 4;
+  const int ecap = 1 << std::max(6, ceil_log2(2 * 32 * S));
+  const int qbytes = 16 * ix0->L.nchunks;
+  const int fixed = 8 * ecap + (ecap / 8 + 15) / 16 * 16 + 256 + qbytes;
+  int dev = 0, optin = 0;
+  FG_CUDA(cudaGetDevice(&dev));
+  FG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  // the largest hash of 2^7..2^12 slots that keeps the CTAs per SM of 2^7
+  int nslots = 0, per_sm = 0, base_per_sm = -1;
+  for (int k = 7; k <= 12; ++k) {
+    const int wb = 4 * (1 << k) + fixed;
+    if (wb * wpc > optin) break;
+    FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(kern), wb * wpc));
+    int ps = 0;
+    FG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, kern, wpc * 32, wb * wpc));
+    if (base_per_sm < 0) base_per_sm = ps;
+    if (ps >= base_per_sm && ps > 0) {
+      nslots = 1 << k;
+      per_sm = ps;
+    }
+  }
+  if (per_sm < 1) return fail(FGRAFT_EINVAL, "many-builds launch does not fit an SM");
+  const int wbytes = 4 * nslots + fixed;
+  MultiScratch* ms = nullptr;
+  int rc = multi_scratch(&ms);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lock(ms->mu);
+  int64_t words = 0;
+  for (int k = 0; k < cnt; ++k) words = std::max<int64_t>(words, (g[k]->L.n + 127) / 128 * 4);
+  const int64_t grid_warps = (int64_t)per_sm * ix0->num_sms * wpc;
+  if (words * grid_warps > ms->gv_words) {
+    if (ms->gvbits) cudaFree(ms->gvbits);
+    ms->gvbits = nullptr;
+    ms->gv_words = 0;
+    cudaError_t e = cudaMalloc(&ms->gvbits, sizeof(uint32_t) * words * grid_warps);
+    if (e != cudaSuccess) {
+      set_error(FGRAFT_ENOMEM, std::string("cudaMalloc(visited bitmaps): ") + cudaGetErrorString(e));
+      return FGRAFT_ENOMEM;
+    }
+    ms->gv_words = words * grid_warps;
+  }
+  BeamMulti P{};
+  P.nidx = cnt;
+  P.work = ms->work;
+  P.start[0] = 0;
+  for (int k = 0; k < cnt; ++k) {
+    fgraft_index* ix = g[k];
+    BeamArgs a = harvest_args(ix, b);
+    a.counters = ix->ctr + C_HARVEST;
+    a.work = nullptr;  // the launch's counter
+    a.ovf_list = ix->ovf_list;
+    a.ovf_count = ix->work + 2;
+    a.ovf_cap = (uint32_t)ix->ovf_cap;
+    a.err_flag = ix->work + 3;
+    a.hash_log2 = ceil_log2(nslots);
+    a.bitmap = 0;
+    a.vis_bytes = 4 * nslots;
+    a.vis_cap = (int32_t)(0.8 * nslots) - 32;
+    a.ecap = ecap;
+    a.gvbits = ix->overflow_mode == 1 ? ms->gvbits : nullptr;
+    a.gvbits_words = words;
+    a.wbytes = wbytes;
+    a.qbytes = qbytes;
+    a.global_scratch = 0;
+    a.gather = 0;
+    a.id_batch = ix->id_batch;
+    a.wait_polls = g_mma_wait_polls;
+    P.d[k] = a;
+    P.start[k + 1] = P.start[k] + a.nq;
+    FG_CUDA(cudaMemsetAsync(ix->work, 0, 3 * sizeof(uint32_t), s));
+  }
+  FG_CUDA(cudaMemsetAsync(ms->work, 0, sizeof(uint32_t), s));
+  for (int k = 0; k < cnt; ++k)  // profiled indices time the shared launch
+    if (g[k]->profile && (int)g[k]->ev_beg.size() > b) FG_CUDA(record_event(g[k]->ev_beg[b], s));
+  kern<<<per_sm * ix0->num_sms, wpc * 32, wbytes * wpc, s>>>(P);
+  note_launch();
+  FG_CUDA(cudaGetLastError());
+  for (int k = 0; k < cnt; ++k)
+    if (g[k]->profile && (int)g[k]->ev_end.size() > b) FG_CUDA(record_event(g[k]->ev_end[b], s));
+  for (int k = 0; k < cnt && !rc; ++k) {
+    fgraft_index* ix = g[k];
+    rc = launch_rerun(ix, P.d[k], ix->ctr + C_HARVEST, s);
+    if (!rc) rc = harvest_after(ix, b, P.d[k], s);
+  }
+  return rc;
 }
 
 }  // namespace
@@ -895,19 +996,21 @@ fgraft_status fgraft_harvest_block_multi(fgraft_index* const* ixs, int32_t nix, 
       if (ixs[j] == ix) return (fgraft_status)fail(FGRAFT_EINVAL, "an index is listed twice");
   }
   if (nix == 0) return FGRAFT_OK;
-  // fan out over the device's side streams (they wait for `stream`), join back
-  MultiStreams* ms = nullptr;
-  int rc = multi_streams(&ms);
-  if (rc) return (fgraft_status)rc;
-  std::lock_guard<std::mutex> lock(ms->mu);
-  FGS(cudaEventRecord(ms->fork, s));
-  const int ns = std::min<int>(nix, MultiStreams::kStreams);
-  for (int k = 0; k < ns; ++k) FGS(cudaStreamWaitEvent(ms->st[k], ms->fork, 0));
-  for (int32_t i = 0; i < nix && !rc; ++i) rc = harvest_block_impl(ixs[i], b, ms->st[i % ns]);
-  for (int k = 0; k < ns; ++k) {
-    cudaError_t e = cudaEventRecord(ms->join[k], ms->st[k]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ms->join[k], 0);
-    if (e != cudaSuccess && !rc) rc = cuda_fail(e, "multi-index join");
+  // one search launch per group of indices sharing a kernel shape (metric,
+  // lane groups, pool slots, row chunks), at most kMaxMulti per launch
+  std::map<std::array<int, 5>, std::vector<fgraft_index*>> groups;
+  for (int32_t i = 0; i < nix; ++i) {
+    fgraft_index* ix = ixs[i];
+    groups[{ix->L.metric, ix->L.G, ix->L.K, pool_slots(ix->p.ef_h), ix->L.nchunks}].push_back(ix);
+  }
+  int rc = 0;
+  for (auto& kv : groups) {
+    const std::vector<fgraft_index*>& g = kv.second;
+    for (size_t i0 = 0; i0 < g.size() && !rc; i0 += kMaxMulti) {
+      const size_t cnt = std::min<size_t>(kMaxMulti, g.size() - i0);
+      rc = harvest_multi_launch(g.data() + i0, (int)cnt, b, s);
+    }
+    if (rc) break;
   }
   return (fgraft_status)rc;
 }

@@ -95,6 +95,51 @@ struct BeamArgs {
   int32_t wait_polls;
 };
 
+// Up to kMaxMulti independent builds in one launch (many indices harvested
+// together): work item w belongs to build k with start[k] <= w < start[k+1]
+// and is that build's work item w - start[k].  The descriptors travel in the
+// kernel parameters (__grid_constant__, read in place); every field that
+// shapes the per-warp shared layout is the same in all of them.
+constexpr int kMaxMulti = 64;
+struct BeamMulti {
+  int32_t nidx;
+  uint32_t* work;
+  int64_t start[kMaxMulti + 1];
+  BeamArgs d[kMaxMulti];
+};
+
+// Where a beam launch takes its work items from: one build (BeamArgs) or
+// several (BeamMulti).
+struct BeamSrcOne {
+  static constexpr bool kMulti = false;
+  const BeamArgs& a;
+  __device__ const BeamArgs& first() const { return a; }
+  __device__ uint32_t* work() const { return a.work; }
+  __device__ int64_t total() const {
+    return a.qlist_len ? min((int64_t)*a.qlist_len, (int64_t)a.ovf_cap) : a.nq;
+  }
+  __device__ int find(uint32_t) const { return 0; }
+  __device__ const BeamArgs& desc(int) const { return a; }
+  __device__ int64_t local(int, uint32_t w) const { return (int64_t)w; }
+};
+struct BeamSrcMany {
+  static constexpr bool kMulti = true;
+  const BeamMulti& P;
+  __device__ const BeamArgs& first() const { return P.d[0]; }
+  __device__ uint32_t* work() const { return P.work; }
+  __device__ int64_t total() const { return P.start[P.nidx]; }
+  __device__ int find(uint32_t w) const {
+    int lo = 0, hi = P.nidx - 1;  // the last k with start[k] <= w
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (P.start[mid] <= (int64_t)w) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  }
+  __device__ const BeamArgs& desc(int k) const { return P.d[k]; }
+  __device__ int64_t local(int k, uint32_t w) const { return (int64_t)w - P.start[k]; }
+};
+
 // Chunks of 32 neighbour ids whose bitmap visited tests are issued together
 // (two keeps the harvest kernels within 128 registers without spills).
 constexpr int kIdBatch = 2;
@@ -162,14 +207,16 @@ struct Beam {
     merge_into_pool<S>(pool, mykey, a.ef, lane);
   }
 
-  static __device__ void run(const BeamArgs& a, unsigned char* smem) {
+  template <class Src>
+  static __device__ void run(const Src& src, unsigned char* smem) {
     using L = Lanes<G, K>;
+    const BeamArgs& a0 = src.first();  // the per-warp layout (the same in every descriptor)
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int g = lane / L::P, j = lane % L::P;
     const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
-    unsigned char* wsm = smem + (int64_t)wib * a.wbytes;
-    const uint32_t nslots = 1u << a.hash_log2;
+    unsigned char* wsm = smem + (int64_t)wib * a0.wbytes;
+    const uint32_t nslots = 1u << a0.hash_log2;
     const uint32_t mask_buckets = nslots / 4 - 1;
     // Shared-memory pass: [visited | expanded list | alive bits | queue | staged vector]
     // per warp.  Re-run pass (global_scratch): the visited set is this warp's
@@ -179,25 +226,25 @@ struct Beam {
     uint64_t* E;
     uint32_t* alive;
     unsigned char* tail;
-    if (a.global_scratch) {
-      vis0 = a.gvbits + gwarp * a.gvbits_words;
-      E = reinterpret_cast<uint64_t*>(a.gscratch + gwarp * a.gscratch_per_warp);
-      alive = reinterpret_cast<uint32_t*>(E + a.ecap);
+    if (a0.global_scratch) {
+      vis0 = a0.gvbits + gwarp * a0.gvbits_words;
+      E = reinterpret_cast<uint64_t*>(a0.gscratch + gwarp * a0.gscratch_per_warp);
+      alive = reinterpret_cast<uint32_t*>(E + a0.ecap);
       tail = wsm;
     } else {
       vis0 = reinterpret_cast<uint32_t*>(wsm);
-      E = reinterpret_cast<uint64_t*>(wsm + a.vis_bytes);
-      alive = reinterpret_cast<uint32_t*>(wsm + a.vis_bytes + 8ll * a.ecap);
+      E = reinterpret_cast<uint64_t*>(wsm + a0.vis_bytes);
+      alive = reinterpret_cast<uint32_t*>(wsm + a0.vis_bytes + 8ll * a0.ecap);
       // the alive bits take ecap/8 bytes, rounded up so that the staged vector
       // after the queue keeps its 16-byte alignment
-      tail = wsm + a.vis_bytes + 8ll * a.ecap + ((a.ecap / 8 + 15) & ~15);
+      tail = wsm + a0.vis_bytes + 8ll * a0.ecap + ((a0.ecap / 8 + 15) & ~15);
     }
     int32_t* queue = reinterpret_cast<int32_t*>(tail);
     uint4* qs = reinterpret_cast<uint4*>(tail + 256);
     // gather buffer (32 rows) and its barrier after the staged query
-    uint4* gb = GATHER ? reinterpret_cast<uint4*>(tail + 256 + a.qbytes) : nullptr;
+    uint4* gb = GATHER ? reinterpret_cast<uint4*>(tail + 256 + a0.qbytes) : nullptr;
     uint64_t* gbar =
-        GATHER ? reinterpret_cast<uint64_t*>(tail + 256 + a.qbytes + 32ll * 16 * a.nchunks)
+        GATHER ? reinterpret_cast<uint64_t*>(tail + 256 + a0.qbytes + 32ll * 16 * a0.nchunks)
                : nullptr;
     uint32_t gphase = 0;
     if (GATHER) {
@@ -207,16 +254,33 @@ struct Beam {
       }
       __syncwarp();
     }
-    const int64_t nwork =
-        a.qlist_len ? min((int64_t)*a.qlist_len, (int64_t)a.ovf_cap) : a.nq;
+    const int64_t nwork = src.total();
     unsigned long long c_ev = 0, c_ex = 0, c_pe = 0, c_sc = 0, c_ovf = 0;
+    int kcur = 0;  // the build whose counters accumulate in c_*
+    auto flush = [&](const BeamArgs& ab) {
+      if (lane == 0) {
+        atomicAdd(ab.counters + 0, c_ev);
+        atomicAdd(ab.counters + 1, c_ex);
+        atomicAdd(ab.counters + 2, c_pe);
+        atomicAdd(ab.counters + 3, c_sc);
+        atomicAdd(ab.counters + 4, c_ovf);
+      }
+      c_ev = c_ex = c_pe = c_sc = c_ovf = 0;
+    };
 
     for (;;) {
-      uint32_t w = 0;
-      if (lane == 0) w = atomicAdd(a.work, 1u);
-      w = __shfl_sync(FULL, w, 0);
-      if ((int64_t)w >= nwork) break;
-      const int64_t qidx = a.qlist ? (int64_t)a.qlist[w] : (int64_t)w;
+      uint32_t w0 = 0;
+      if (lane == 0) w0 = atomicAdd(src.work(), 1u);
+      w0 = __shfl_sync(FULL, w0, 0);
+      if ((int64_t)w0 >= nwork) break;
+      const int kb = src.find(w0);
+      if (Src::kMulti && kb != kcur) {
+        flush(src.desc(kcur));
+        kcur = kb;
+      }
+      const BeamArgs& a = src.desc(kb);
+      const int64_t w = src.local(kb, w0);
+      const int64_t qidx = a.qlist ? (int64_t)a.qlist[w] : w;
       int64_t p = -1;
       const char* qrow;
       if (a.mode == 0) {
@@ -503,13 +567,7 @@ struct Beam {
       c_pe += q_pe;
       __syncwarp();
     }
-    if (lane == 0) {
-      atomicAdd(a.counters + 0, c_ev);
-      atomicAdd(a.counters + 1, c_ex);
-      atomicAdd(a.counters + 2, c_pe);
-      atomicAdd(a.counters + 3, c_sc);
-      atomicAdd(a.counters + 4, c_ovf);
-    }
+    flush(src.desc(kcur));
   }
 };
 
@@ -518,17 +576,28 @@ struct Beam {
 template <int METRIC, int G, int K, int S, bool GATHER>
 __global__ void __launch_bounds__(128, 4) beam_kernel(const BeamArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  Beam<METRIC, G, K, S, GATHER>::run(a, smem);
+  Beam<METRIC, G, K, S, GATHER>::run(BeamSrcOne{a}, smem);
+}
+
+// The same search over the work items of several builds in one launch.
+template <int METRIC, int G, int K, int S, bool GATHER>
+__global__ void __launch_bounds__(128, 4) beam_multi_kernel(const __grid_constant__ BeamMulti P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Beam<METRIC, G, K, S, GATHER>::run(BeamSrcMany{P}, smem);
 }
 
 // Host-side launcher table entry (defined per metric in beam_*.cu, the
 // gather variants in beam_*_g.cu).
 using BeamKernelFn = void (*)(const BeamArgs);
+using BeamMultiFn = void (*)(const BeamMulti);
 BeamKernelFn beam_kernel_metric0(int G, int K, int S);
 BeamKernelFn beam_kernel_metric1(int G, int K, int S);
 BeamKernelFn beam_kernel_metric2(int G, int K, int S);
 BeamKernelFn beam_kernel_metric0_gather(int G, int K, int S);
 BeamKernelFn beam_kernel_metric1_gather(int G, int K, int S);
 BeamKernelFn beam_kernel_metric2_gather(int G, int K, int S);
+BeamMultiFn beam_multi_metric0(int G, int K, int S);
+BeamMultiFn beam_multi_metric1(int G, int K, int S);
+BeamMultiFn beam_multi_metric2(int G, int K, int S);
 
 }  // namespace fg

@@ -297,6 +297,39 @@ def test_harvest_block_multi_equals_single(fg):
         fg.fgraft_harvest_block_multi(multi, 0)  # already past block 0
 
 
+def test_many_builds_share_one_launch(fg):
+    # five angular builds of different sizes share one search launch per
+    # block, two uint8 builds another; rows, counters and final graphs equal
+    # their separate builds, and one of them equals the oracle
+    sets = [(synth.vmf_like(n, 100, 6, seed=30 + i), 100, fg.ANGULAR_F32)
+            for i, n in enumerate((1500, 4000, 700, 2500, 3000))]
+    sets += [(synth.uint8_mixture(n, 20, 4, seed=40 + i), 20, fg.L2_U8)
+             for i, n in enumerate((1200, 2600))]
+    p = dict(T=4, R=24, ef_h=64, B=3, alpha=1.2)
+    multi, single = [], []
+    for ps, d, metric in sets:
+        X = _dev(ps.X)
+        multi.append(fg.fgraft_build_scaffold(X, d, fg.Params(metric=metric, **p)))
+        single.append(fg.fgraft_build_scaffold(X, d, fg.Params(metric=metric, **p)))
+    for b in range(3):
+        fg.fgraft_harvest_block_multi(multi, b)
+    for ix in single:
+        for b in range(3):
+            fg.fgraft_harvest_block(ix, b)
+    for im, is_ in zip(multi, single):
+        cm, cs = fg.fgraft_index_copy(im), fg.fgraft_index_copy(is_)
+        assert torch.equal(cm["rows"], cs["rows"]) and torch.equal(cm["counts"], cs["counts"])
+        om, os_ = fg.fgraft_prune(im), fg.fgraft_prune(is_)
+        assert torch.equal(om[0], os_[0]) and torch.equal(om[1], os_[1])
+        ctm, cts = fg.fgraft_index_counters(im), fg.fgraft_index_counters(is_)
+        for k in ("harvest_evals", "prune_evals", "expansions", "final_prune_evals"):
+            assert ctm[k] == cts[k], k
+    ps, d, metric = sets[1]
+    ref = oracle.build_graph(oracle.Data(ps.X, d, metric), 4, 24, 64, 3, 1.2, 0)
+    om = fg.fgraft_prune(multi[1])
+    assert np.array_equal(_np(om[0]), ref["f_off"]) and np.array_equal(_np(om[1]), ref["f_ids"])
+
+
 @pytest.mark.parametrize("kind,cap", [("gauss", 3), ("vmf", 6), ("u8", 5)])
 def test_scaffold_cap_parity(fg, kind, cap):
     # Section 6's ablation: scaffold rows capped at their cap nearest entries
