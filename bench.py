@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dims", action="store_true", help="skip the dimension sweep extra")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip every extra after the headline (paper arms, dimension sweep, "
+                         "in-cache run): for profiling the step alone")
     ap.add_argument("--tune-table", default=None,
                     help="autotuner table (JSON): loaded when the file exists, otherwise "
                          "written after tuning (a profiled run then reuses the settings of "
@@ -622,11 +625,12 @@ def run_ours(args):
         d2h = sum(o.numel() * o.element_size() for o in outs)
         del ix2
     _, e2e_value = job_rate(e2e_ms, args.steps, n, world, dist if world > 1 else None, "cuda")
-    arms = _extra(paper_arms, fg, X_d, Q_d, ps, Q, spec) if not args.n else None
-    dims = _extra(dims_sweep, fg) if not args.n and not args.no_dims else None
+    extras = not args.n and not args.no_extras
+    arms = _extra(paper_arms, fg, X_d, Q_d, ps, Q, spec) if extras else None
+    dims = _extra(dims_sweep, fg) if extras and not args.no_dims else None
     extra = incache_extra(fg, flush, stream,
                           tune_table=args.tune_table + ".incache" if args.tune_table else None) \
-        if not args.n else None
+        if extras else None
 
     if rank != 0:
         if world > 1:
@@ -989,20 +993,39 @@ def run_batched(args):
         return fg.Params(T=8, R=32, ef_h=64, B=8, alpha=1.2, seed=0,
                          metric=fg.L2_U8 if d == 128 else fg.ANGULAR_F32)
 
-    def batched():
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record()
+        return e
+
+    def batched(phases=None):
+        e0 = ev()
         ixs = [fg.fgraft_build_scaffold(data[i], int(ds[i]), params(int(ds[i])))
                for i in range(nbuild)]
+        e1 = ev()
         for b in range(8):
             fg.fgraft_harvest_block_multi(ixs, b)
+        e2 = ev()
         for ix in ixs:
             fg.fgraft_prune(ix)
+        e3 = ev()
+        if phases is not None:
+            phases.append((e0, e1, e2, e3))
         return ixs
 
-    def one_by_one():
+    def one_by_one(phases):
+        # the same calls build after build: scaffold, blocks, final graph
         out = []
         for i in range(nbuild):
+            e0 = ev()
             ix = fg.fgraft_build_scaffold(data[i], int(ds[i]), params(int(ds[i])))
-            fg.fgraft_harvest_all(ix, use_graph=False)
+            e1 = ev()
+            for b in range(8):
+                fg.fgraft_harvest_block(ix, b)
+            e2 = ev()
+            fg.fgraft_prune(ix)
+            e3 = ev()
+            phases.append((int(ds[i]), e0, e1, e2, e3))
             out.append(ix)
         return out
 
@@ -1014,16 +1037,18 @@ def run_batched(args):
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     times = []
+    bph = []
     for _ in range(args.steps):
         t0.record()
-        ixs = batched()
+        ixs = batched(bph)
         t1.record()
         torch.cuda.synchronize()
         times.append(t0.elapsed_time(t1))
         del ixs
     clk = clocks.stop()
+    sph = []
     t0.record()
-    seq = one_by_one()
+    seq = one_by_one(sph)
     t1.record()
     torch.cuda.synchronize()
     seq_ms = t0.elapsed_time(t1)
@@ -1032,6 +1057,20 @@ def run_batched(args):
     for a_, b_ in zip(ixs, seq):
         oa, ob = fg.fgraft_prune(a_), fg.fgraft_prune(b_)
         same &= bool(torch.equal(oa[0], ob[0]) and torch.equal(oa[1], ob[1]))
+    # where the time goes: phase sums of both ways, and the one-by-one
+    # harvest by dimension
+    nst = max(len(bph), 1)
+    b_ms = {k: round(sum(p[i].elapsed_time(p[i + 1]) for p in bph) / nst, 3)
+            for i, k in enumerate(("scaffold", "harvest", "final"))}
+    s_ms = {k: round(sum(p[i + 1].elapsed_time(p[i + 2]) for p in sph), 3)
+            for i, k in enumerate(("scaffold", "harvest", "final"))}
+    by_d = {}
+    for p in sph:
+        t = by_d.setdefault(str(p[0]), {"builds": 0, "n": 0, "harvest_ms": 0.0})
+        t["builds"] += 1
+        t["harvest_ms"] = round(t["harvest_ms"] + p[2].elapsed_time(p[3]), 3)
+    for i in range(nbuild):
+        by_d[str(int(ds[i]))]["n"] += int(ns[i])
     ms = float(np.mean(times))
     total_n = int(ns.sum())
     print(json.dumps({
@@ -1045,6 +1084,8 @@ def run_batched(args):
                    "T": 8, "B": 8, "R": 32, "ef_h": 64},
         "one_by_one_ms": round(seq_ms, 3),
         "batched_vs_one_by_one": round(seq_ms / ms, 3),
+        "phases_ms": {"batched": b_ms, "one_by_one": s_ms},
+        "one_by_one_harvest_by_d": by_d,
         "same_graphs_as_one_by_one": same,
         "clocks": clk}), flush=True)
 
@@ -1145,6 +1186,26 @@ def run_dense(args):
         print(json.dumps({"mode": "dense-gram", "precision": name, "ms": round(gms, 4),
                           "pairs_per_s": round(pairs / (gms / 1e3), 1),
                           "tflops_mma": round(flops / (gms / 1e3) / 1e12, 1)}), flush=True)
+    # the same Gram over more blocks (the 64 blocks repeated): 64 blocks are
+    # 3.4 tiles of 128 rows per SM, too few to fill the MMA pipeline
+    for prec, name in ((1, "bf16"), (2, "fp8_e4m3")):
+        dpad = ((d + 63) // 64) * 64 if prec == 1 else ((d + 127) // 128) * 128
+        for reps in (4, 16, 64):
+            Bn = B_d.repeat(reps, 1).contiguous()
+            fg.fgraft_dense_block_gram(X_d, d, fg.ANGULAR_F32, Bn, precision=prec)
+            tms = []
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                _, gms = fg.fgraft_dense_block_gram(X_d, d, fg.ANGULAR_F32, Bn, precision=prec)
+                tms.append(gms)
+            gms = float(np.median(tms))
+            nbn = int(Bn.shape[0])
+            flops = 2.0 * dpad * nbn * 1024 * 1024
+            print(json.dumps({"mode": "dense-gram-scale", "precision": name, "blocks": nbn,
+                              "ms": round(gms, 4),
+                              "pairs_per_s": round(pairs * reps / (gms / 1e3), 1),
+                              "tflops_mma": round(flops / (gms / 1e3) / 1e12, 1)}), flush=True)
+            del Bn
 
 
 def main():

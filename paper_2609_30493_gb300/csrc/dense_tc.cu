@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(DT_THREADS, 1) dt_fused_kernel(const DtArgs a)
           for (int c = 0; c < nch && ok; ++c)
             for (int sl = 0; sl < a.nsl; ++sl, ++it) {
               const uint32_t s = it % DT_STAGES, ph = (it / DT_STAGES) & 1u;
-              if (!mbar_wait_bounded(empty + s, ph ^ 1u, a.wait_polls, abortp)) {
+              if (!mbar_wait_backoff(empty + s, ph ^ 1u, a.wait_polls, abortp, 64)) {
                 ok = false;
                 break;
               }
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(DT_THREADS, 1) dt_fused_kernel(const DtArgs a)
         for (int pass = 0; pass < npass && ok; ++pass)
           for (int c = 0; c < nch && ok; ++c, ++ci) {
             const uint32_t buf = ci & 1u, bph = (ci >> 1) & 1u;
-            if (!mbar_wait_bounded(tempty + buf, bph ^ 1u, a.wait_polls, abortp)) {
+            if (!mbar_wait_backoff(tempty + buf, bph ^ 1u, a.wait_polls, abortp, 64)) {
               ok = false;
               break;
             }
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(DT_THREADS, 1) dt_fused_kernel(const DtArgs a)
             const uint32_t dt = tmem + buf * DT_NC;
             for (int sl = 0; sl < a.nsl; ++sl, ++it) {
               const uint32_t s = it % DT_STAGES, ph = (it / DT_STAGES) & 1u;
-              if (!mbar_wait_bounded(full + s, ph, a.wait_polls, abortp)) {
+              if (!mbar_wait_backoff(full + s, ph, a.wait_polls, abortp, 32)) {
                 ok = false;
                 break;
               }

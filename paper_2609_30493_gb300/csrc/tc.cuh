@@ -113,6 +113,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+// The same for a thread that has nothing else to do meanwhile (a producer or
+// an MMA issuer): it sleeps about `ns` nanoseconds between polls, leaving
+// the issue slots to the warps that do the work.
+__device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity, int polls,
+                                                  const volatile int* abort, unsigned ns) {
+  for (int it = 0; it < polls; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    __nanosleep(ns);
+  }
+  return false;
+}
+
 // 32 consecutive FP32 columns of this thread's TMEM lane
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(

@@ -158,7 +158,8 @@ def fgraft_harvest_all(ix: Index, use_graph: bool = True, counters: bool = False
 
 
 def fgraft_harvest_block_multi(ixs, b: int):
-    """Block b of every index in ixs, their kernels overlapping on side streams."""
+    """Block b of every index in ixs: one persistent search launch per group of
+    indices that share a kernel shape, then the per-index prunes."""
     arr = (C.c_void_p * max(len(ixs), 1))(*[ix.handle for ix in ixs])
     dev = ixs[0].X.device if ixs else None
     _check(load().fgraft_harvest_block_multi(arr, C.c_int32(len(ixs)), C.c_int32(b),

@@ -100,3 +100,53 @@ def test_lockstep_density_measured(incache_subset, capsys):
     # every query shares the roots and the first expansions, so even random
     # groups overlap far above 1 / |group|
     assert min(dc + dr) > 4.0 / min(len(g) for g in coherent)
+
+
+def _preorder(parent0):
+    n = len(parent0)
+    ch = [[] for _ in range(n)]
+    root = -1
+    for x in range(n):
+        if parent0[x] >= 0:
+            ch[parent0[x]].append(x)
+        else:
+            root = x
+    order, stack = [], [root]
+    while stack:
+        u = stack.pop()
+        order.append(u)
+        stack.extend(reversed(ch[u]))
+    return np.array(order, np.int32)
+
+
+def test_preorder_windows_share_targets(incache_subset, capsys):
+    """Column-batched target loads (Section 5.5) save at most the share of a
+    window's gathers that another search of the same window also makes,
+    1 - |union| / (sum of sizes) = 1 - 1 / (W x density), and only if the
+    searches reached the shared targets at the same moment.  Windows of W
+    consecutive points of the tree-0 preorder (the order the harvest kernel
+    claims its searches in) against windows of random points: a report, with
+    the one property that the preorder's windows share more."""
+    ps, D, rts, parents, s_off, s_ids = incache_subset
+    pre = _preorder(parents[0])
+    assert sorted(pre.tolist()) == list(range(D.n))
+    run = pre[5000:5000 + 320]
+    rnd = np.random.default_rng(4).choice(D.n, size=len(run), replace=False).astype(np.int32)
+    vis_run = [oracle.visited(D, s_off, s_ids, rts, ps.X[p], 64) for p in run]
+    vis_rnd = [oracle.visited(D, s_off, s_ids, rts, ps.X[p], 64) for p in rnd]
+
+    def shared(vis, W):
+        out = []
+        for i in range(0, len(vis) - W + 1, W):
+            grp = vis[i:i + W]
+            dd = oracle.lockstep_density(grp)
+            out.append(1.0 - 1.0 / (W * dd))
+        return float(np.mean(out))
+
+    rows = [(W, shared(vis_run, W), shared(vis_rnd, W)) for W in (4, 8, 16)]
+    with capsys.disabled():
+        print("\nshared share of a window's gathers (W, tree-0 preorder, random): " +
+              ", ".join(f"({W}, {a:.3f}, {b:.3f})" for W, a, b in rows))
+    for W, a, b in rows:
+        assert 0.0 <= b <= 1.0 and 0.0 <= a <= 1.0
+    assert rows[-1][1] > rows[-1][2]
