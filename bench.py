@@ -43,7 +43,6 @@ INCACHE = dict(workload="incache-angular-n100k-d100", n=100_000, d=100, k=64, si
                kappa=20.0, T=8, B=8, R=32, ef_h=64, alpha=1.2, nq=10_000, ef_s=64, topk=10,
                dense_blocks=64, block_size=1024, dense_k=32, seed=0)
 CPU_SAMPLE_N = 20_000
-COMPLETENESS_SAMPLE = 20_000
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -76,11 +75,12 @@ def parse():
                     help="order in which each block's searches are claimed: tree-0 preorder "
                          "(coherent), point id, or the preorder when X exceeds L2 (auto)")
     ap.add_argument("--mode", default="step",
-                    choices=["step", "dims", "paper", "batched", "cap", "dense"],
+                    choices=["step", "dims", "paper", "batched", "cap", "dense", "lockstep"],
                     help="step: the benchmark line; dims: adaptive vs dense cost per evaluation "
                          "across d; paper: the paper-scale angular arms; batched: many "
                          "independent builds harvested together; cap: the scaffold degree "
-                         "cap ablation; dense: the dense-block ceiling alone")
+                         "cap ablation; dense: the dense-block ceiling alone; lockstep: the "
+                         "visited-set overlap of the GPU harvest (Section 5.5)")
     return ap.parse_args()
 
 
@@ -205,13 +205,13 @@ def job_rate(local_ms, steps, n_per_rank, world, dist_mod, device):
 EF_LADDER = (10, 16, 24, 32, 48, 64, 96, 128)
 
 
-def quality_report(fg, ix, ps, Q_d, spec, r_target=0.95, sample=None):
+def quality_report(fg, ix, ps, Q_d, spec, r_target=0.95):
     """Measurement only (outside the timed region): recall@10 and evaluations
     per query along the ef_s ladder, d@r (the evaluations per query of the
-    first ef_s reaching recall r), and local completeness (the fraction of a
-    point's 10 nearest neighbours that sit in its final adjacency row), over
-    every point or over a seeded sample of `sample` points.  The ground truth
-    is a float32 brute force with PyTorch on the device."""
+    first ef_s reaching recall r), with the queries' ground truth from a
+    float32 PyTorch product; and local completeness (the fraction of a
+    point's 10 nearest neighbours that sit in its final adjacency row) over
+    every point, the neighbours from fgraft_knn_exact."""
     import torch
     X = torch.from_numpy(ps.X[:, :spec["d"]]).cuda()
     Q = Q_d[:, :spec["d"]]
@@ -230,27 +230,41 @@ def quality_report(fg, ix, ps, Q_d, spec, r_target=0.95, sample=None):
         if d_at_r is None and rec >= r_target:
             d_at_r = round(epq, 1)
     n = X.shape[0]
-    if sample and sample < n:
-        pts = np.sort(np.random.default_rng(17).choice(n, size=sample, replace=False))
-    else:
-        pts = np.arange(n)
-    pts_d = torch.from_numpy(pts).cuda()
     off, fids = fg.fgraft_prune(ix)
     rows = torch.repeat_interleave(torch.arange(n, device=X.device), off[1:] - off[:-1])
     edge_keys = torch.sort(rows * n + fids.long()).values
-    hits = 0
-    for s in range(0, len(pts), 1024):
-        p = pts_d[s:s + 1024]
-        dots = X[p] @ X.T
-        dots[torch.arange(len(p), device=X.device), p] = -float("inf")
-        gt = torch.topk(dots, 10, dim=1).indices
-        keys = (p.unsqueeze(1) * n + gt).reshape(-1)
-        pos = torch.searchsorted(edge_keys, keys).clamp(max=edge_keys.numel() - 1)
-        hits += int((edge_keys[pos] == keys).sum().item())
+    # the exact 10-NN of every point with the library's own kernel (BF16
+    # tensor-core filter, canonical float32 rerank)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    kid, _, kst = fg.fgraft_knn_exact(ix.X, spec["d"], ps.metric, 10, stats=True)
+    e1.record()
+    torch.cuda.synchronize()
+    keys = (torch.arange(n, device=X.device).unsqueeze(1) * n + kid.long()).reshape(-1)
+    pos = torch.searchsorted(edge_keys, keys).clamp(max=edge_keys.numel() - 1)
+    hits = int(((edge_keys[pos] == keys) & (kid.reshape(-1) >= 0)).sum().item())
+    # cross-check of a sample against a float32 PyTorch product (equal up to
+    # rounding ties of the two summation orders)
+    pts = torch.from_numpy(np.random.default_rng(17).choice(n, size=min(n, 1000),
+                                                             replace=False)).cuda()
+    agree = 0
+    for c0 in range(0, len(pts), 100):
+        pc = pts[c0:c0 + 100]
+        sc = X[pc] @ X.T if ps.metric == 1 else -(torch.cdist(X[pc], X) ** 2)
+        sc[torch.arange(len(pc), device=X.device), pc] = -float("inf")
+        tt = torch.topk(sc, 10, dim=1).indices
+        agree += int((torch.sort(tt, dim=1).values == torch.sort(kid[pc].long(), dim=1).values)
+                     .all(dim=1).sum().item())
+        del sc
+    same = agree / len(pts)
     out = {"recall_ladder": ladder, f"d_at_r{r_target}": d_at_r,
-           "local_completeness_at_10": round(hits / (len(pts) * 10), 4)}
-    if len(pts) < n:
-        out["local_completeness_sample"] = f"seeded sample of {len(pts)} of {n} points"
+           "local_completeness_at_10": round(hits / (n * 10), 4),
+           "exact_knn": {"points": n, "k": 10, "ms": round(e0.elapsed_time(e1), 2),
+                         "filter_ms": round(kst["filter_ms"], 2),
+                         "rerank_ms": round(kst["rerank_ms"], 2),
+                         "rerank_evals_per_point": round(kst["rerank_evals"] / n, 1),
+                         "full_scan_rows": int(kst["full_scan_rows"]),
+                         "sample_rows_equal_to_torch_fp32": round(same, 4)}}
     return out
 
 
@@ -470,6 +484,131 @@ def dims_sweep(fg, dims=(32, 64, 128, 256, 512, 960), n=1_000_000):
             "data": "Gaussian mixture generated on the device (torch generator per d)"}
 
 
+def _subtree_groups(par, max_size):
+    """Maximal subtrees of at most max_size points of the tree with parent
+    array par: (roots, labels, sizes), labels[v] = the root of v's maximal
+    subtree (-1 for points in no such subtree), sizes[v] = |subtree(v)|."""
+    par = np.asarray(par, np.int64)
+    depth = (par >= 0).astype(np.int64)
+    anc = par.copy()
+    while True:  # pointer jumping: depth[v] = edges from v to anc[v]
+        m = anc >= 0
+        if not m.any():
+            break
+        a = anc[m]
+        nd, na = depth.copy(), anc.copy()
+        nd[m] = depth[m] + depth[a]
+        na[m] = anc[a]
+        depth, anc = nd, na
+    size = np.ones(len(par), np.int64)
+    levels = [np.flatnonzero(depth == dd) for dd in range(int(depth.max()) + 1)]
+    for nodes in reversed(levels[1:]):
+        np.add.at(size, par[nodes], size[nodes])
+    top = (size <= max_size) & ((par < 0) | (size[np.maximum(par, 0)] > max_size))
+    lab = np.full(len(par), -1, np.int64)
+    for nodes in levels:
+        t = top[nodes]
+        lab[nodes[t]] = nodes[t]
+        rest = nodes[~t]
+        rest = rest[par[rest] >= 0]
+        lab[rest] = lab[par[rest]]
+    return np.flatnonzero(top), lab, size
+
+
+def lockstep_gpu(fg, X_d, spec, ngroups=64, min_size=64, max_size=512, run_len=2432,
+                 cap=32768, wblock=3):
+    """Section 5.5 on the GPU harvest at the benchmark size (untimed extra).
+    Lockstep density (Table 6): the visited sets V_i logged by the harvest
+    searches themselves (fgraft_harvest_visited, each point on its own
+    block's substrate S_b) for 64 coherent groups -- maximal tree-0 subtrees
+    of at most 512 points, drawn among those of at least 64 -- and 64 random
+    groups of the same sizes; density = sum |V_i| / (|group| |union V_i|),
+    and the share of evaluations that go to vertices at least 8 members of
+    the group evaluate.  Column-batched target loads: for windows of W
+    consecutive searches of block 3's claim order (W = 4 is one CTA; 2432
+    the searches in flight), the share of the window's evaluations that
+    another search of the window repeats, 1 - |union| / sum |V_i|."""
+    import torch
+    params = _params(fg, spec)
+    B = spec["B"]
+    ix = fg.fgraft_build_scaffold(X_d, spec["d"], params)
+    st = fg.fgraft_index_copy(ix)
+    n = int(X_d.shape[0])
+    tops, lab, size = _subtree_groups(st["parents"][0].cpu().numpy(), max_size)
+    rng = np.random.default_rng(11)
+    cand = tops[size[tops] >= min_size]
+    pick = rng.choice(cand, size=min(ngroups, len(cand)), replace=False)
+    order = np.argsort(lab, kind="stable")
+    sl = lab[order]
+    coherent = [order[np.searchsorted(sl, u):np.searchsorted(sl, u, side="right")] for u in pick]
+    randoms = [rng.choice(n, size=len(g), replace=False) for g in coherent]
+    sched = fg.fgraft_index_schedule(ix)
+    q, r = n // B, n % B
+    nb_w = q + (1 if wblock < r else 0)
+    if sched is not None:
+        start = wblock * q + min(wblock, r)
+        qo = sched[1].cpu().numpy()[start:start + nb_w].astype(np.int64)
+    else:
+        qo = np.arange(nb_w, dtype=np.int64)
+    off0 = nb_w // 2
+    run = wblock + B * qo[off0:off0 + run_len]
+    allp = np.unique(np.concatenate(coherent + randoms + [run]))
+    pos = np.full(n, -1, np.int64)
+    ids_all, cnt_all = [], []
+    base = 0
+    for b in range(B):
+        pb = allp[allp % B == b].astype(np.int32)
+        if len(pb):
+            ids, cnt = fg.fgraft_harvest_visited(ix, torch.from_numpy(pb).cuda(), cap)
+            ids_all.append(ids)
+            cnt_all.append(cnt)
+            pos[pb] = base + np.arange(len(pb))
+            base += len(pb)
+        fg.fgraft_harvest_block(ix, b)
+    ids_all = torch.cat(ids_all)
+    cnt_all = torch.cat(cnt_all)
+    truncated = int((cnt_all > cap).sum().item())
+    ar = torch.arange(cap, device=ids_all.device)
+
+    def sets(pts):
+        idx = torch.from_numpy(pos[np.asarray(pts)]).cuda()
+        c = cnt_all[idx].clamp(max=cap)
+        return ids_all[idx][ar[None, :] < c[:, None]], int(c.sum().item())
+
+    def group_stats(groups):
+        dens, share8, vs, us = [], [], [], []
+        for g in groups:
+            vals, tot = sets(g)
+            uni, counts = torch.unique(vals, return_counts=True)
+            dens.append(tot / (len(g) * uni.numel()))
+            share8.append(float(counts[counts >= 8].sum().item()) / tot)
+            vs.append(tot / len(g))
+            us.append(uni.numel())
+        return {"groups": len(groups), "median_size": int(np.median([len(g) for g in groups])),
+                "mean_V": round(float(np.mean(vs)), 1), "mean_union": round(float(np.mean(us)), 1),
+                "density_mean": round(float(np.mean(dens)), 4),
+                "density_median": round(float(np.median(dens)), 4),
+                "share_of_evals_to_targets_of_8_plus": round(float(np.mean(share8)), 4)}
+
+    windows = []
+    for W in (4, 16, 64, 256, run_len):
+        sh = []
+        for i in range(0, len(run) - W + 1, W):
+            vals, tot = sets(run[i:i + W])
+            sh.append(1.0 - torch.unique(vals).numel() / tot)
+        windows.append({"W": W, "shared_share": round(float(np.mean(sh)), 4), "windows": len(sh)})
+    vals, tot = sets(run)
+    in_flight_union = int(torch.unique(vals).numel())
+    row_bytes = 16 * ((spec["d"] * 4 + 15) // 16)
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    del ix
+    return {"coherent": group_stats(coherent), "random": group_stats(randoms),
+            "windows_claim_order_block3": windows,
+            "in_flight_union_vectors": in_flight_union,
+            "l2_holds_vectors": int(l2 // row_bytes), "truncated_logs": truncated,
+            "cap": cap, "data": "benchmark workload; V_i from the GPU harvest's own searches"}
+
+
 def _extra(fn, *a, **kw):
     """An untimed extra measurement; a failure is recorded, not raised."""
     try:
@@ -594,7 +733,7 @@ def run_ours(args):
         if prec == 2:
             dense_other[name]["rerank_fraction"] = round(pst[0], 5)
             dense_other[name]["filter_ms"] = round(pst[1], 4)
-    quality = quality_report(fg, ix, ps, Q_d, spec, sample=COMPLETENESS_SAMPLE)
+    quality = quality_report(fg, ix, ps, Q_d, spec)
 
     # ---- end to end through the public API, host buffers ----
     Xh = torch.from_numpy(ps.X).pin_memory()
@@ -628,6 +767,7 @@ def run_ours(args):
     extras = not args.n and not args.no_extras
     arms = _extra(paper_arms, fg, X_d, Q_d, ps, Q, spec) if extras else None
     dims = _extra(dims_sweep, fg) if extras and not args.no_dims else None
+    lockstep = _extra(lockstep_gpu, fg, X_d, spec) if extras else None
     extra = incache_extra(fg, flush, stream,
                           tune_table=args.tune_table + ".incache" if args.tune_table else None) \
         if extras else None
@@ -697,6 +837,7 @@ def run_ours(args):
         "incache": extra,
         "paper_arms": arms,
         "dims_sweep": dims,
+        "lockstep_gpu": lockstep,
         "e2e": {"value": round(e2e_value, 1), "unit": "pts/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
@@ -1131,6 +1272,20 @@ def run_cap(args):
     fg.fgraft_tune_scaffold_cap(0)
 
 
+def run_lockstep(args):
+    """The lockstep-density and column-batching measurement alone."""
+    from paper_2609_30493_gb300 import build as fgbuild
+    from paper_2609_30493_gb300 import fgraft as fg
+    fgbuild.build()
+    fg.load()
+    spec = dict(SPEC)
+    if args.n:
+        spec["n"] = args.n
+    _, _, _, (X_d, _, _) = _device_inputs(spec)
+    print(json.dumps({"mode": "lockstep", "n": spec["n"], **lockstep_gpu(fg, X_d, spec)}),
+          flush=True)
+
+
 def run_dense(args):
     """The dense-block ceiling alone (Section 5.3) on the benchmark workload's 64
     intra-cluster blocks of 1024 points (top-64 per row): the canonical float32
@@ -1227,6 +1382,8 @@ def main():
         run_cap(args)
     elif args.mode == "dense":
         run_dense(args)
+    elif args.mode == "lockstep":
+        run_lockstep(args)
     else:
         run_ours(args)
 

@@ -206,6 +206,46 @@ fgraft_status fgraft_prune_lists_noalloc(const void* X, int64_t n, int32_t d, in
                                          int64_t nlists, float alpha, int32_t R, int32_t* out_ids,
                                          int32_t* out_cnt, fgraft_stream stream);
 
+/* Exact k nearest neighbours of points (Section 2: local completeness, the
+ * fraction of a point's true 10-NN that sit in its adjacency row, needs them
+ * for every point).  For each point i = row0 .. row0 + nrows - 1, the k
+ * smallest (delta(x_i, x_j), j) over all j != i in [0, n), delta the
+ * canonical float32 distance: the brute force of Section 2 restricted to the
+ * points themselves.  out_ids / out_dist (device, nrows*k, row r = point
+ * row0 + r): ids ascending by (delta, id), -1 / +inf past n - 1 neighbours.
+ * Computed as a dense product on the tensor cores: all rows rounded to BF16,
+ * a Gram pass that finds each row's k-th smallest approximate distance, a
+ * second that collects every column within twice the row's rounding bound
+ * of it, then the canonical rerank of the collected columns (a row that
+ * collected more than 256 scans all n points), so the result equals the
+ * float32 brute force exactly.  float32 metrics, 1 <= k <= 32.  stats (host,
+ * optional, 4 doubles): canonical evaluations of the rerank, rows that
+ * scanned every point, filter and rerank kernel milliseconds.  Scratch
+ * (about 256 bytes per point plus 1 KB per query row, at most 64 MB of it)
+ * is allocated stream-ordered; the call synchronises `stream` once per
+ * 65,536 rows to check its bounded waits (FGRAFT_ETIMEOUT). */
+fgraft_status fgraft_knn_exact(const void* X, int64_t n, int32_t d, int64_t ld, int32_t metric,
+                               int64_t row0, int64_t nrows, int32_t k, int32_t* out_ids,
+                               float* out_dist, double* stats, fgraft_stream stream);
+
+/* Visited-set log (Section 5.5, Table 6: the sets V_i whose overlap decides
+ * whether co-scheduled searches could share their work).  Runs the harvest
+ * searches of the next block -- the substrate S_b with b = the blocks
+ * harvested so far (fgraft_index_sizes) -- for the np query points listed
+ * in points (device, int32 ids), and records for each the vertices it
+ * evaluates: out_ids[i*cap ..] (device, np*cap int32) receives, in the
+ * order of insertion into the visited set, the first min(|V_i|, cap) of them
+ * (the tree roots first), and out_cnt[i] (device, np int32) receives |V_i|,
+ * or -1 when points[i] is not in [0, n).  A point of block b gets exactly the
+ * set its own harvest search evaluates (the harvest's `harvest_evals` sums
+ * these sizes); other points are searched on S_b all the same.  Nothing of
+ * the index changes: no row, prune or counter of the build.  The call
+ * synchronises `stream` to check the searches' scratch (FGRAFT_EOVERFLOW as
+ * for the harvest).  np < 2^31, cap >= 1. */
+fgraft_status fgraft_harvest_visited(fgraft_index* ix, const int32_t* points, int64_t np,
+                                     int32_t cap, int32_t* out_ids, int32_t* out_cnt,
+                                     fgraft_stream stream);
+
 /* Query search (Section 2: beam search over the final graph, graded against
  * a brute-force key).  The same beam as the harvest, width ef_s, entering at
  * the T roots; out_ids/out_dist (nq*k) get the first k pool entries (-1 /

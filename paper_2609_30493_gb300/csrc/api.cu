@@ -137,7 +137,8 @@ enum CtrSlot {
   C_SAT = 5,
   C_FINAL = 6,
   C_SEARCH = 8,  // search-side slots 8..12 (same layout as 0..4)
-  C_COUNT = 16
+  C_VLOG = 16,   // visited-set logs, slots 16..20 (same layout)
+  C_COUNT = 24
 };
 
 struct fgraft_index {
@@ -1132,6 +1133,33 @@ fgraft_status fgraft_search(fgraft_index* ix, const void* Q, int64_t nq, int64_t
   return (fgraft_status)rc;
 }
 
+fgraft_status fgraft_harvest_visited(fgraft_index* ix, const int32_t* points, int64_t np,
+                                     int32_t cap, int32_t* out_ids, int32_t* out_cnt,
+                                     fgraft_stream stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!ix) return (fgraft_status)fail(FGRAFT_EINVAL, "index is NULL");
+  if (np < 0 || np > INT32_MAX) return (fgraft_status)fail(FGRAFT_EINVAL, "need 0 <= np < 2^31");
+  if (cap < 1) return (fgraft_status)fail(FGRAFT_EINVAL, "need cap >= 1");
+  if (np == 0) return FGRAFT_OK;
+  if (!points || !out_ids || !out_cnt) return (fgraft_status)fail(FGRAFT_EINVAL, "NULL pointer");
+  // the searches of the next block's harvest (substrate S_b, b = blocks
+  // harvested so far), for the listed points, logging instead of pruning
+  BeamArgs a = harvest_args(ix, ix->blocks_done);
+  a.qlist = nullptr;
+  a.nq = np;
+  a.qpoints = points;
+  a.Eg = nullptr;
+  a.Eg_cnt = nullptr;
+  a.A_out = nullptr;
+  a.cnt_out = nullptr;
+  a.vlog = out_ids;
+  a.vlog_cnt = out_cnt;
+  a.vlog_cap = cap;
+  int rc = launch_beam(ix, a, ix->ctr + C_VLOG, s);
+  if (rc) return (fgraft_status)rc;
+  return (fgraft_status)check_err_flag(ix, s);
+}
+
 fgraft_status fgraft_dense_block_dist(const void* X, int64_t n, int32_t d, int64_t ld,
                                       int32_t metric, const int32_t* block_ids, int64_t nb,
                                       int32_t bs, int32_t k, int32_t precision, int32_t* out_ids,
@@ -1158,6 +1186,24 @@ fgraft_status fgraft_dense_block_dist(const void* X, int64_t n, int32_t d, int64
   rc = dense_block(L, block_ids, nb, bs, k, out_ids, out_dist, s);
   if (!rc && stats) FGS(cudaStreamSynchronize(s));
   return (fgraft_status)rc;
+}
+
+fgraft_status fgraft_knn_exact(const void* X, int64_t n, int32_t d, int64_t ld, int32_t metric,
+                               int64_t row0, int64_t nrows, int32_t k, int32_t* out_ids,
+                               float* out_dist, double* stats, fgraft_stream stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  VecLayout L;
+  int rc = check_vectors(X, n, d, ld, metric, &L);
+  if (rc) return (fgraft_status)rc;
+  if (metric == L2_U8) return (fgraft_status)fail(FGRAFT_EINVAL, "exact k-NN takes float32 metrics");
+  if (k < 1 || k > 32) return (fgraft_status)fail(FGRAFT_EINVAL, "need 1 <= k <= 32");
+  if (row0 < 0 || nrows < 0 || row0 + nrows > n)
+    return (fgraft_status)fail(FGRAFT_EINVAL, "need 0 <= row0 and row0 + nrows <= n");
+  if (stats)
+    for (int i = 0; i < 4; ++i) stats[i] = 0.0;
+  if (nrows == 0) return FGRAFT_OK;
+  if (!out_ids || !out_dist) return (fgraft_status)fail(FGRAFT_EINVAL, "NULL pointer");
+  return (fgraft_status)knn_tc(L, row0, nrows, k, out_ids, out_dist, stats, s);
 }
 
 fgraft_status fgraft_dense_block_gram(const void* X, int64_t n, int32_t d, int64_t ld,

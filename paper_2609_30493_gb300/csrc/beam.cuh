@@ -93,6 +93,16 @@ struct BeamArgs {
   int32_t gather;
   int32_t id_batch;
   int32_t wait_polls;
+  // visited-set log (Section 5.5, a measurement): with vlog set, a harvest
+  // search (mode 0) only searches; the ids it inserts into its visited set,
+  // in insertion order, go to vlog[qidx * vlog_cap ..] (the first vlog_cap of
+  // them) and the set's size to vlog_cnt[qidx] (-1 for a query point outside
+  // [0, n)); no expanded list, prune or row is written.  qpoints: the query
+  // point of work item qidx is qpoints[qidx] (NULL: q_first + qidx * q_step).
+  const int32_t* qpoints;
+  int32_t* vlog;
+  int32_t* vlog_cnt;
+  int32_t vlog_cap;
 };
 
 // Up to kMaxMulti independent builds in one launch (many indices harvested
@@ -107,6 +117,7 @@ struct BeamMulti {
   int64_t start[kMaxMulti + 1];
   BeamArgs d[kMaxMulti];
 };
+static_assert(sizeof(BeamMulti) <= 32764, "kernel parameters are limited to 32,764 bytes");
 
 // Where a beam launch takes its work items from: one build (BeamArgs) or
 // several (BeamMulti).
@@ -284,7 +295,11 @@ struct Beam {
       int64_t p = -1;
       const char* qrow;
       if (a.mode == 0) {
-        p = a.q_first + qidx * a.q_step;
+        p = a.qpoints ? (int64_t)a.qpoints[qidx] : a.q_first + qidx * a.q_step;
+        if (p < 0 || p >= a.n) {  // only a logged query list can hold such an id
+          if (lane == 0 && a.vlog_cnt) a.vlog_cnt[qidx] = -1;
+          continue;
+        }
         qrow = a.X + p * a.ld_bytes;
       } else {
         qrow = a.Q + qidx * a.ldq_bytes;
@@ -360,6 +375,10 @@ struct Beam {
           const bool isnew = nw[u];
           const unsigned m = __ballot_sync(FULL, isnew);
           if (isnew) queue[qn + __popc(m & ((1u << lane) - 1u))] = v;
+          if (a.vlog != nullptr && isnew) {
+            const int pos = nvis + __popc(m & ((1u << lane) - 1u));
+            if (pos < a.vlog_cap) a.vlog[qidx * (int64_t)a.vlog_cap + pos] = v;
+          }
           qn += __popc(m);
           nvis += __popc(m);
           __syncwarp();
@@ -463,6 +482,10 @@ struct Beam {
       c_ex += (unsigned long long)ne;
       c_sc += q_sc;
 
+      if (a.vlog != nullptr) {
+        if (lane == 0) a.vlog_cnt[qidx] = nvis;
+        continue;
+      }
       if (a.mode == 1) {
 #pragma unroll
         for (int s = 0; s < S; ++s) {

@@ -433,6 +433,9 @@ struct FinalArgs {
   int32_t def_cap;
   const uint64_t* def_kept;
   const int32_t* def_kcnt;
+  // non-null: warps claim the entries of the work list one at a time from
+  // this counter (a persistent grid), instead of a fixed stride
+  uint32_t* claim;
 };
 
 // Final row of u from its kept keys (sorted, kk of them, owner's vector
@@ -491,7 +494,13 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
   uint4* cs = reinterpret_cast<uint4*>(wsm + a.qbytes);
   const int64_t total = a.rowlist_len ? (int64_t)*a.rowlist_len : a.nrows;
   unsigned long long ev = 0;
-  for (int64_t w = gw; w < total; w += (int64_t)gridDim.x * FIN_WARPS) {
+  auto next_item = [&](int64_t cur) -> int64_t {
+    if (!a.claim) return cur + (int64_t)gridDim.x * FIN_WARPS;
+    uint32_t v = 0;
+    if (lane == 0) v = atomicAdd(a.claim, 1u);
+    return (int64_t)__shfl_sync(FULL, v, 0);
+  };
+  for (int64_t w = a.claim ? next_item(0) : gw; w < total; w = next_item(w)) {
     const int64_t r = a.rowlist ? a.rowlist[w] : w;
     if (a.mode == 2) {
       const int32_t u2 = a.def_rows[r];
@@ -667,6 +676,22 @@ static int fin_smem(FinalKernelFn kern, int qbytes, int* sm_shared, int* sm_glob
   return 0;
 }
 
+// The final graph's rows in the order the candidate kernel claims them: the
+// rows it prunes itself (more raw candidates than the CTA prune takes, or
+// than R when nothing is deferred) first, then the rest, so that the long
+// in-warp prunes start early instead of trailing the launch.
+__global__ void final_order_kernel(int64_t n, int heavy, const int32_t* cnt, const int64_t* r_off,
+                                   int32_t* order, uint32_t* ctr2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t mraw = cnt[i] + (r_off[i + 1] - r_off[i]);
+    if (mraw > heavy)
+      order[atomicAdd(&ctr2[0], 1u)] = (int32_t)i;
+    else
+      order[n - 1 - atomicAdd(&ctr2[1], 1u)] = (int32_t)i;
+  }
+}
+
 static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, int num_sms,
                           cudaStream_t s) {
   FinalKernelFn kern = final_kernel_for(L.metric, L.G, L.K);
@@ -680,9 +705,10 @@ static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, int nu
   if (rc0) return rc0;
   int32_t* long_rows = nullptr;
   uint32_t* small = nullptr;
+  int32_t* order = nullptr;
   FG_CUDA(cudaMallocAsync(&long_rows, sizeof(int32_t) * std::max<int64_t>(nrows, 1), s));
-  FG_CUDA(cudaMallocAsync(&small, 2 * sizeof(uint32_t), s));
-  FG_CUDA(cudaMemsetAsync(small, 0, 2 * sizeof(uint32_t), s));
+  FG_CUDA(cudaMallocAsync(&small, 5 * sizeof(uint32_t), s));
+  FG_CUDA(cudaMemsetAsync(small, 0, 5 * sizeof(uint32_t), s));
   a.rowlist = nullptr;
   a.rowlist_len = nullptr;
   a.nrows = nrows;
@@ -690,7 +716,23 @@ static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, int nu
   a.nlong = small;
   a.gbuf = nullptr;
   a.gcap = 0;
-  kern<<<grid1d(nrows * 32, FIN_WARPS * 32), FIN_WARPS * 32, sm0, s>>>(a);
+  a.claim = nullptr;
+  int per_sm = 0;
+  if (a.mode == 0 && num_sms > 0)
+    FG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FIN_WARPS * 32, sm0));
+  if (per_sm > 0) {
+    // final graph: heavy rows first, claimed one by one by a persistent grid
+    FG_CUDA(cudaMallocAsync(&order, sizeof(int32_t) * std::max<int64_t>(nrows, 1), s));
+    final_order_kernel<<<grid1d(nrows, 256), 256, 0, s>>>(
+        nrows, a.def_keys ? a.def_cap : a.R, a.cnt, a.r_off, order, small + 2);
+    note_launch();
+    FinalArgs m = a;
+    m.rowlist = order;
+    m.claim = small + 4;
+    kern<<<per_sm * num_sms, FIN_WARPS * 32, sm0, s>>>(m);
+  } else {
+    kern<<<grid1d(nrows * 32, FIN_WARPS * 32), FIN_WARPS * 32, sm0, s>>>(a);
+  }
   note_launch();
   max_final_need_kernel<<<64, 256, 0, s>>>(nrows, long_rows, small, a.mode, a.R, a.cnt, a.r_off,
                                            a.parent0, a.c0_off, a.l_off, small + 1);
@@ -741,6 +783,7 @@ static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, int nu
   }
   cudaFreeAsync(long_rows, s);
   cudaFreeAsync(small, s);
+  cudaFreeAsync(order, s);
   return rc;
 }
 

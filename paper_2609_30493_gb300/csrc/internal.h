@@ -179,6 +179,10 @@ int dense_block_tc(const VecLayout& L, const int32_t* block_ids, int64_t nb, int
 // time.  Measures the dense ceiling without any selection.
 int dense_gram_tc(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs, int fp8,
                   float* out_min, double* ms, cudaStream_t s);
+// Exact k nearest neighbours of points row0 .. row0 + nrows - 1 among all
+// points (self excluded): BF16 tensor-core filter, canonical rerank.
+int knn_tc(const VecLayout& L, int64_t row0, int64_t nrows, int k, int32_t* out_ids,
+           float* out_dist, double* stats, cudaStream_t s);
 
 // Dense-block top-k (canonical float32 distances of every pair of a block).
 int dense_block(const VecLayout& L, const int32_t* block_ids, int64_t nb, int bs, int k,

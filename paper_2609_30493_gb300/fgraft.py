@@ -46,7 +46,7 @@ EXPORTS = ["fgraft_build_scaffold", "fgraft_harvest_block", "fgraft_harvest_all"
            "fgraft_harvest_block_multi", "fgraft_tune_scaffold_cap", "fgraft_tune_schedule",
            "fgraft_index_schedule", "fgraft_tune_mma_wait", "fgraft_dense_block_gram",
            "fgraft_index_autotune", "fgraft_tuning_table_save", "fgraft_tuning_table_load",
-           "fgraft_index_set_tuning",
+           "fgraft_index_set_tuning", "fgraft_harvest_visited", "fgraft_knn_exact",
            "fgraft_index_destroy", "fgraft_last_error"]
 
 
@@ -293,6 +293,43 @@ def fgraft_index_copy(ix: Index):
                                     _ptr(out["counts"]), _stream(dev)))
     out["s_ids"] = out["s_ids"][: s["scaffold_nnz"]]
     return out
+
+
+def fgraft_knn_exact(X: torch.Tensor, d: int, metric: int, k: int, row0: int = 0,
+                     nrows: int = None, stats: bool = False):
+    """Exact k nearest neighbours of points row0 .. row0 + nrows - 1 among all
+    rows of X (self excluded), by the canonical float32 distance with ties by
+    id.  Returns (ids (nrows, k) int32, dist (nrows, k) float32[, stats])."""
+    n = X.shape[0]
+    if nrows is None:
+        nrows = n - row0
+    ids = torch.empty((nrows, k), dtype=torch.int32, device=X.device)
+    dist = torch.empty((nrows, k), dtype=torch.float32, device=X.device)
+    st = (C.c_double * 4)()
+    _check(load().fgraft_knn_exact(_ptr(X), C.c_int64(n), C.c_int32(d), C.c_int64(X.shape[1]),
+                                   C.c_int32(metric), C.c_int64(row0), C.c_int64(nrows),
+                                   C.c_int32(k), _ptr(ids), _ptr(dist),
+                                   st if stats else None, _stream(X.device)))
+    if stats:
+        return ids, dist, {"rerank_evals": st[0], "full_scan_rows": st[1],
+                           "filter_ms": st[2], "rerank_ms": st[3]}
+    return ids, dist
+
+
+def fgraft_harvest_visited(ix: Index, points: torch.Tensor, cap: int):
+    """Visited sets of the next block's harvest searches for the given points:
+    returns (ids (np, cap) int32, cnt (np,) int32); row i holds the first
+    min(cnt[i], cap) vertices point i's search evaluates, cnt[i] = |V_i|
+    (-1 for an id outside [0, n))."""
+    assert points.is_cuda and points.dtype == torch.int32 and points.dim() == 1
+    points = points.contiguous()
+    np_ = points.shape[0]
+    ids = torch.empty((np_, cap), dtype=torch.int32, device=ix.X.device)
+    cnt = torch.empty(np_, dtype=torch.int32, device=ix.X.device)
+    _check(load().fgraft_harvest_visited(ix.handle, _ptr(points), C.c_int64(np_),
+                                         C.c_int32(cap), _ptr(ids), _ptr(cnt),
+                                         _stream(ix.X.device)))
+    return ids, cnt
 
 
 def fgraft_search(ix: Index, Q: torch.Tensor, k: int, ef_s: int):
