@@ -550,6 +550,11 @@ __global__ void __launch_bounds__(DT_THREADS, 1) dt_fused_kernel(const DtArgs a)
       aborted = named_sync_or(1, DT_EPI, aborted || *abortp);
       if (aborted) break;
     }
+    // a wait of the epilogue that gave up is an error too (and stops the others)
+    if (aborted && etid == 0) {
+      *abort_flag = 1;
+      atomicOr(a.err, 1u);
+    }
   }
   tc_fence_before();
   __syncthreads();

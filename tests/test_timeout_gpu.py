@@ -5,8 +5,9 @@ first wait for MMA products: it sets its error flag, waits for the products
 in flight with the full bound, frees its tensor memory and returns.  Each
 call that reads a flag must return FGRAFT_ETIMEOUT: the SAT's closest-child
 assignment (fgraft_build_scaffold), the harvest's occlusion prune
-(fgraft_harvest_block with counters), the final graph's prune (fgraft_prune)
-and the dense blocks (fgraft_dense_block_dist).  Nothing faults or hangs,
+(fgraft_harvest_block with counters), the final graph's prune (fgraft_prune),
+the dense blocks (fgraft_dense_block_dist and its Gram-only form) and the
+exact k-NN filter (fgraft_knn_exact).  Nothing faults or hangs,
 and with the default limit restored the same calls give results bit-equal to
 those computed before.
 """
@@ -50,6 +51,7 @@ def test_tensor_core_waits_give_up_and_recover(fg):
     c_ref = fg.fgraft_index_counters(ix_ref)
     dense_ref = [fg.fgraft_dense_block_dist(X, 100, fg.ANGULAR_F32, blocks, 16, precision=pr)
                  for pr in (1, 2)]
+    knn_ref = fg.fgraft_knn_exact(X, 100, fg.ANGULAR_F32, 10, 0, 3000)
     ix_h = fg.fgraft_build_scaffold(X, 100, p)          # for the harvest's prune
     ix_f = fg.fgraft_build_scaffold(X, 100, p)          # for the final graph's prune
     fg.fgraft_harvest_all(ix_f, use_graph=False)
@@ -62,6 +64,9 @@ def test_tensor_core_waits_give_up_and_recover(fg):
         _timeout(fg, lambda: fg.fgraft_build_scaffold(X, 100, p))
         _timeout(fg, lambda: fg.fgraft_harvest_block(ix_h, 0, counters=True))
         _timeout(fg, lambda: fg.fgraft_prune(ix_f))
+        _timeout(fg, lambda: fg.fgraft_knn_exact(X, 100, fg.ANGULAR_F32, 10, 0, 3000))
+        _timeout(fg, lambda: fg.fgraft_dense_block_gram(X, 100, fg.ANGULAR_F32, blocks,
+                                                        precision=1))
     finally:
         fg.fgraft_tune_mma_wait(-1)
     # the context is intact and the next normal calls are bit-exact
@@ -71,5 +76,7 @@ def test_tensor_core_waits_give_up_and_recover(fg):
     for pr, (ri, rd) in zip((1, 2), dense_ref):
         gi, gd = fg.fgraft_dense_block_dist(X, 100, fg.ANGULAR_F32, blocks, 16, precision=pr)
         assert torch.equal(gi, ri) and torch.equal(gd, rd)
+    ki, kd = fg.fgraft_knn_exact(X, 100, fg.ANGULAR_F32, 10, 0, 3000)
+    assert torch.equal(ki, knn_ref[0]) and torch.equal(kd, knn_ref[1])
     with pytest.raises(fg.FgraftError, match="EINVAL"):
         fg.fgraft_tune_mma_wait(-2)
