@@ -161,11 +161,12 @@ fgraft_status fgraft_harvest_all(fgraft_index* ix, int32_t use_graph, fgraft_str
  * parent/child edges of tree 0).  C(u) = A[u] U {p : u in A[p]}; when |C(u)| > R
  * the row is the occlusion prune of C(u) to R, otherwise C(u); then the
  * tree-0 parent and children of u are added and the row is sorted by
- * (delta(u,v), id).  The index keeps the result for fgraft_search.
- * out_offsets (n+1 int64) and out_ids (cap int32) are optional device
- * outputs (both NULL: keep internally only); when cap is too small the call
- * returns EOVERFLOW and writes the size needed to *needed (host, optional).
- * Requires every block to have been harvested. */
+ * (delta(u,v), id).  The index keeps the result for fgraft_search; it is
+ * computed once per index (by this call or by fgraft_harvest_all), and later
+ * calls only copy it out.  out_offsets (n+1 int64) and out_ids (cap int32)
+ * are optional device outputs (both NULL: keep internally only); when cap is
+ * too small the call returns EOVERFLOW and writes the size needed to
+ * *needed (host, optional).  Requires every block to have been harvested. */
 fgraft_status fgraft_prune(fgraft_index* ix, fgraft_stream stream, fgraft_counters* counters,
                            int64_t* out_offsets, int32_t* out_ids, int64_t cap, int64_t* needed);
 
@@ -339,8 +340,10 @@ fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t war
                                 int32_t overflow_mode);
 
 /* Autotuner (not in the paper: a property of this implementation).  Times
- * the harvest of a calibration sample -- the first `sample` searches of
- * block 0 in claim order, each with its occlusion prune -- under every
+ * the harvest of a calibration sample -- the first `sample` searches in
+ * claim order of the index's next block b (the blocks harvested so far, or
+ * block 0 when all are), each with its occlusion prune, on the substrate
+ * S_b -- under every
  * candidate launch configuration, keeps the fastest for this index and
  * records it in the process's tuning table under (metric, d, ef_h, R,
  * ceil(log2 n)); later fgraft_build_scaffold calls of the same shape start
@@ -352,8 +355,12 @@ fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t war
  * bitmap visited tests of 1 or 2 chunks of 32 ids issued together.  The
  * search is coordinate descent from the defaults (4, occupancy rule, global
  * bitmap, registers, 2), each setting in turn over its options, two rounds;
- * each candidate is timed as the fastest of three runs of the sample.  Results never depend on the settings: the sample's
- * rows receive their final values and nothing else of the index changes.
+ * each candidate is timed as the fastest of three runs of the sample.  The
+ * searches of later blocks scan longer neighbour lists (S_b grows with b),
+ * so a sample from a middle block represents the whole harvest better than
+ * block 0: harvest some blocks of a scratch index first.  Results never
+ * depend on the settings: the sample's rows receive their final values (its
+ * block's harvest writes the same) and nothing else of the index changes.
  * chosen (host, optional) receives the settings and the microseconds per
  * sample search with them and with the default settings.  Call it before
  * capturing the harvest in a graph; it synchronises `stream`. */

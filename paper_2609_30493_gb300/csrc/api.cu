@@ -161,6 +161,7 @@ struct fgraft_index {
   int64_t* f_off = nullptr;
   int32_t* f_ids = nullptr;
   int64_t f_nnz = 0;
+  bool final_done = false;  // the final graph is computed (it never changes after)
   int64_t* scan_tmp = nullptr;
   // [0] smem pass, [1] re-run pass, [2] ovf count, [3] err flag, [4] prune
   // timeout, [5] long prune lists, [6] gather timeout
@@ -604,18 +605,21 @@ int harvest_block_impl(fgraft_index* ix, int32_t b, cudaStream_t s) {
   return harvest_after(ix, b, a, s);
 }
 
-// The searches of block 0 for its first `sample` work items in claim order
-// (tree-0 preorder when the index has the coherent schedule), each followed
-// by its occlusion prune; counters go to tctr.  The rows written are those
-// points' final rows (block 0 always searches S_0), and nothing else of the
-// index changes: this is the autotuner's calibration workload.
+// The searches of the next block b (the blocks harvested so far; block 0
+// when all are) for its first `sample` work items in claim order (tree-0
+// preorder when the index has the coherent schedule), each followed by its
+// occlusion prune; counters go to tctr.  The rows written are those points'
+// final rows (block b searches S_b, which holds rows of blocks < b only, and
+// its own harvest writes the same rows again), and nothing else of the index
+// changes: this is the autotuner's calibration workload.
 int harvest_sample(fgraft_index* ix, int64_t sample, unsigned long long* tctr, cudaStream_t s) {
-  BeamArgs a = harvest_args(ix, 0);  // block 0's claim order comes first in qorder
+  const int32_t b = ix->blocks_done < ix->nb ? ix->blocks_done : 0;
+  BeamArgs a = harvest_args(ix, b);
   a.nq = std::min<int64_t>(sample, a.nq);
   const bool sep = ix->prune_ns > 0;
   int rc = launch_beam(ix, a, tctr, s);
   if (rc || !sep) return rc;
-  return harvest_prune(ix->L, ix->Eg, ix->Eg_cnt, ix->eg_ecap, a.nq, 0, ix->nb, ix->p.R, a.alpha2,
+  return harvest_prune(ix->L, ix->Eg, ix->Eg_cnt, ix->eg_ecap, a.nq, b, ix->nb, ix->p.R, a.alpha2,
                        ix->A, ix->cnt, tctr + 5, ix->num_sms, s, nullptr, nullptr, nullptr,
                        nullptr, ix->work + 4, ix->ovf_list, ix->work + 5, a.qlist);
 }
@@ -965,12 +969,15 @@ fgraft_status fgraft_prune(fgraft_index* ix, fgraft_stream stream, fgraft_counte
     return (fgraft_status)fail(FGRAFT_EINVAL, "out_offsets and out_ids go together");
   int rc = check_err_flag(ix, s);
   if (rc) return (fgraft_status)rc;
-  FGS(cudaMemsetAsync(ix->ctr + C_FINAL, 0, sizeof(unsigned long long), s));
-  keep_pool_reserved();
-  rc = final_graph(ix->L, ix->p.R, ix->p.alpha * ix->p.alpha, ix->A, ix->cnt, ix->r_off,
-                   ix->r_ids, ix->parents, ix->f_off, &ix->f_ids, &ix->f_nnz, ix->scan_tmp,
-                   ix->ctr + C_FINAL, ix->num_sms, s);
-  if (rc) return (fgraft_status)rc;
+  if (!ix->final_done) {
+    FGS(cudaMemsetAsync(ix->ctr + C_FINAL, 0, sizeof(unsigned long long), s));
+    keep_pool_reserved();
+    rc = final_graph(ix->L, ix->p.R, ix->p.alpha * ix->p.alpha, ix->A, ix->cnt, ix->r_off,
+                     ix->r_ids, ix->parents, ix->f_off, &ix->f_ids, &ix->f_nnz, ix->scan_tmp,
+                     ix->ctr + C_FINAL, ix->num_sms, s);
+    if (rc) return (fgraft_status)rc;
+    ix->final_done = true;
+  }
   if (needed) *needed = ix->f_nnz;
   if (out_offsets) {
     if (cap < ix->f_nnz) return (fgraft_status)fail(FGRAFT_EOVERFLOW, "out_ids capacity too small");

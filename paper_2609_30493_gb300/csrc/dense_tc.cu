@@ -215,7 +215,7 @@ struct DtRow {
 // |x_i|^2, f = 2; for E4M3 g is scaled by the column's scale here and by the
 // row's in f).  Invalid columns carry col = +inf.  PASS 0 counts the values
 // in the first-level bins, PASS 1 the sub-bins of bin b1, PASS 2 collects
-// the candidates, PASS 3 keeps the minimum (Gram-only mode).  Counts are
+// the candidates (the Gram-only mode's minimum is dt_gram_min).  Counts are
 // shared-memory atomics whose results are not used, so they do not wait on
 // one another.
 template <int PASS, bool FP8>
@@ -246,8 +246,6 @@ __device__ __forceinline__ void dt_values(const uint32_t (&v)[32], const float2*
       r.vmax = inkey ? fmaxf(r.vmax, dt) : r.vmax;
       take |= (inkey || (ok && dt <= r.ucut)) ? (1u << t) : 0u;
       dts[t] = dt;
-    } else {
-      r.vmin = ok ? fminf(r.vmin, dt) : r.vmin;
     }
   }
   if (PASS == 2) {
@@ -262,6 +260,38 @@ __device__ __forceinline__ void dt_values(const uint32_t (&v)[32], const float2*
         for (int q = 0; q < 32; ++q) dv = q == t ? dts[q] : dv;
         cdt[pos] = dv;
       }
+    }
+  }
+}
+
+// Gram-only mode: the smallest (column term - f g) of 32 columns, two
+// columns per shared-memory read and two instructions per value; the row
+// term is added once at the end.  Only the group that holds the row's own
+// column (the same group for every lane of a warp) takes the slow path.
+template <bool FP8>
+__device__ __forceinline__ void dt_gram_min(const uint32_t (&v)[32], const float2* col, int j0,
+                                            int i, float f, float& m) {
+  const float4* c4 = reinterpret_cast<const float4*>(col + j0);
+  if ((unsigned)(i - j0) >= 32u) {
+#pragma unroll
+    for (int t = 0; t < 32; t += 2) {
+      const float4 cc = c4[t >> 1];
+      float g0 = __uint_as_float(v[t]), g1 = __uint_as_float(v[t + 1]);
+      if (FP8) {
+        g0 *= cc.y;
+        g1 *= cc.w;
+      }
+      m = fminf(m, __fmaf_rn(-f, g0, cc.x));
+      m = fminf(m, __fmaf_rn(-f, g1, cc.z));
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      const float2 cj = col[j0 + t];
+      float g = __uint_as_float(v[t]);
+      if (FP8) g *= cj.y;
+      const float y = __fmaf_rn(-f, g, cj.x);
+      m = (j0 + t != i) ? fminf(m, y) : m;
     }
   }
 }
@@ -473,12 +503,12 @@ __global__ void __launch_bounds__(DT_THREADS, 1) dt_fused_kernel(const DtArgs a)
                 if (kind == 0) dt_values<0, true>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
                 else if (kind == 1) dt_values<1, true>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
                 else if (kind == 2) dt_values<2, true>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
-                else dt_values<3, true>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
+                else dt_gram_min<true>(v, col, j0, r.i, r.f, r.vmin);
               } else {
                 if (kind == 0) dt_values<0, false>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
                 else if (kind == 1) dt_values<1, false>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
                 else if (kind == 2) dt_values<2, false>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
-                else dt_values<3, false>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
+                else dt_gram_min<false>(v, col, j0, r.i, r.f, r.vmin);
               }
             }
           }
@@ -489,7 +519,7 @@ __global__ void __launch_bounds__(DT_THREADS, 1) dt_fused_kernel(const DtArgs a)
           xval[etid] = r.vmin;
           aborted = named_sync_or(1, DT_EPI, aborted || *abortp);
           if (!aborted && h == 0 && i < a.bs)
-            a.rowmin[blk * a.bs + i] = vrow ? fminf(r.vmin, xval[etid ^ 128]) : INFINITY;
+            a.rowmin[blk * a.bs + i] = vrow ? r.base + fminf(r.vmin, xval[etid ^ 128]) : INFINITY;
           break;
         }
         if (pass == 2) {

@@ -72,6 +72,10 @@ def test_tiny_gauss_parity(fg, B):
     ps = synth.gaussian_mixture(2000, 16, 8, seed=0)
     ix, ctr, st, fin, D, ref = _build_both(fg, ps, T=4, R=16, ef=32, B=B)
     _compare(ctr, st, fin, ref)
+    # the final graph is computed once per index; a later call copies it out
+    off2, ids2 = fg.fgraft_prune(ix)
+    assert torch.equal(off2, fin[0]) and torch.equal(ids2, fin[1])
+    assert fg.fgraft_index_counters(ix)["final_prune_evals"] == ref["counters"]["final_prune_evals"]
     Q = synth.queries(ps, 200, 1)
     for ef_s in (10, 32, 64):
         gi, gd, ge = fg.fgraft_search(ix, _dev(Q), 10, ef_s)
@@ -573,6 +577,19 @@ def test_autotune_settings_give_the_same_graph(fg):
     fg.fgraft_harvest_all(ix2, use_graph=False)
     o2, i2 = fg.fgraft_prune(ix2)
     assert np.array_equal(_np(o2), graphs[0][0]) and np.array_equal(_np(i2), graphs[0][1])
+    # calibrating on a later block (2 of 4 harvested) writes block 2's rows
+    # early, with the values its own harvest gives them: the graph is the same
+    ix3 = fg.fgraft_build_scaffold(X, 100, p)
+    for b in range(2):
+        fg.fgraft_harvest_block(ix3, b)
+    t3 = fg.fgraft_index_autotune(ix3, sample=2000)
+    assert t3["us_per_query"] > 0
+    for b in range(2, 4):
+        fg.fgraft_harvest_block(ix3, b)
+    o3, i3 = fg.fgraft_prune(ix3)
+    assert np.array_equal(_np(o3), ref["f_off"]) and np.array_equal(_np(i3), ref["f_ids"])
+    st3 = fg.fgraft_index_copy(ix3)
+    assert np.array_equal(_np(st3["rows"]), ref["A"]) and np.array_equal(_np(st3["counts"]), ref["cnt"])
 
 
 def test_wide_lists_use_both_prune_tiles(fg):

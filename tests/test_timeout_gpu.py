@@ -54,7 +54,8 @@ def test_tensor_core_waits_give_up_and_recover(fg):
     knn_ref = fg.fgraft_knn_exact(X, 100, fg.ANGULAR_F32, 10, 0, 3000)
     ix_h = fg.fgraft_build_scaffold(X, 100, p)          # for the harvest's prune
     ix_f = fg.fgraft_build_scaffold(X, 100, p)          # for the final graph's prune
-    fg.fgraft_harvest_all(ix_f, use_graph=False)
+    for b in range(2):
+        fg.fgraft_harvest_block(ix_f, b)
     torch.cuda.synchronize()
     try:
         fg.fgraft_tune_mma_wait(0)
