@@ -276,13 +276,10 @@ __device__ __forceinline__ void dt_gram_min(const uint32_t (&v)[32], const float
 #pragma unroll
     for (int t = 0; t < 32; t += 2) {
       const float4 cc = c4[t >> 1];
-      float g0 = __uint_as_float(v[t]), g1 = __uint_as_float(v[t + 1]);
-      if (FP8) {
-        g0 *= cc.y;
-        g1 *= cc.w;
-      }
-      m = fminf(m, __fmaf_rn(-f, g0, cc.x));
-      m = fminf(m, __fmaf_rn(-f, g1, cc.z));
+      float2 g = make_float2(__uint_as_float(v[t]), __uint_as_float(v[t + 1]));
+      if (FP8) g = __fmul2_rn(g, make_float2(cc.y, cc.w));
+      const float2 y = __ffma2_rn(make_float2(-f, -f), g, make_float2(cc.x, cc.z));
+      m = fminf(m, fminf(y.x, y.y));
     }
   } else {
 #pragma unroll
@@ -490,7 +487,30 @@ __global__ void __launch_bounds__(DT_THREADS, 1) dt_fused_kernel(const DtArgs a)
             aborted = true;
           // tcgen05.ld is warp-collective: the warp goes on only if every lane's wait ended
           aborted = __any_sync(FULL, aborted);
-          if (!aborted) {
+          if (!aborted && kind == 3) {
+            // Gram-only: two loads in flight per wait
+            tc_fence_after();
+#pragma unroll 1
+            for (int t4 = 0; t4 < 4; t4 += 2) {
+              const int cb = h * 128 + 32 * t4;
+              uint32_t v0[32], v1[32];
+              const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + buf * DT_NC + (uint32_t)cb;
+              tmem_ld32_async(ta, v0);
+              tmem_ld32_async(ta + 32, v1);
+              tmem_wait_ld();
+              tmem_ld_fence(v0);
+              tmem_ld_fence(v1);
+              if (!vrow) continue;
+              const int j0 = c * DT_NC + cb;
+              if (a.fp8) {
+                dt_gram_min<true>(v0, col, j0, r.i, r.f, r.vmin);
+                dt_gram_min<true>(v1, col, j0 + 32, r.i, r.f, r.vmin);
+              } else {
+                dt_gram_min<false>(v0, col, j0, r.i, r.f, r.vmin);
+                dt_gram_min<false>(v1, col, j0 + 32, r.i, r.f, r.vmin);
+              }
+            }
+          } else if (!aborted) {
             tc_fence_after();
 #pragma unroll 1
             for (int t4 = 0; t4 < 4; ++t4) {
@@ -502,13 +522,11 @@ __global__ void __launch_bounds__(DT_THREADS, 1) dt_fused_kernel(const DtArgs a)
               if (a.fp8) {
                 if (kind == 0) dt_values<0, true>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
                 else if (kind == 1) dt_values<1, true>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
-                else if (kind == 2) dt_values<2, true>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
-                else dt_gram_min<true>(v, col, j0, r.i, r.f, r.vmin);
+                else dt_values<2, true>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
               } else {
                 if (kind == 0) dt_values<0, false>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
                 else if (kind == 1) dt_values<1, false>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
-                else if (kind == 2) dt_values<2, false>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
-                else dt_gram_min<false>(v, col, j0, r.i, r.f, r.vmin);
+                else dt_values<2, false>(v, col, j0, r, hcol, rowcnt + il, crow, cdrow);
               }
             }
           }

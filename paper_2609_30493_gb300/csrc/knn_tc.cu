@@ -259,46 +259,68 @@ __global__ void __launch_bounds__(DT_THREADS, 1) kn_fused_kernel(const KnArgs a)
           if (!aborted) {
             tc_fence_after();
 #pragma unroll 1
-            for (int t4 = 0; t4 < 4; ++t4) {
-              const int cb = h * 128 + 32 * t4;
-              uint32_t v[32];
-              tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + buf * DT_NC + (uint32_t)cb, v);
+            for (int t4 = 0; t4 < 4; t4 += 2) {
+              // two loads in flight per wait
+              const int cb0 = h * 128 + 32 * t4;
+              uint32_t vv[2][32];
+              const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + buf * DT_NC + (uint32_t)cb0;
+              tmem_ld32_async(ta, vv[0]);
+              tmem_ld32_async(ta + 32, vv[1]);
+              tmem_wait_ld();
+              tmem_ld_fence(vv[0]);
+              tmem_ld_fence(vv[1]);
               if (!vrow) continue;
-              const int64_t j0 = c * DT_NC + cb;
-              float ct[32];
-              const float4* cp = reinterpret_cast<const float4*>(a.colterm + j0);
 #pragma unroll
-              for (int e = 0; e < 8; ++e) {
-                const float4 w = __ldg(cp + e);
-                ct[4 * e] = w.x;
-                ct[4 * e + 1] = w.y;
-                ct[4 * e + 2] = w.z;
-                ct[4 * e + 3] = w.w;
-              }
-              // no branch per value: the few that count are taken from a bit mask
-              float dts[32];
-              uint32_t take = 0;
-              const float lim = pass == 0 ? worst : cut;
+              for (int hh = 0; hh < 2; ++hh) {
+                const uint32_t (&v)[32] = vv[hh];
+                const int64_t j0 = c * DT_NC + cb0 + 32 * hh;
+                float ct[32];
+                const float4* cp = reinterpret_cast<const float4*>(a.colterm + j0);
 #pragma unroll
-              for (int t = 0; t < 32; ++t) {
-                dts[t] = __fmaf_rn(-f, __uint_as_float(v[t]), base + ct[t]);
-                // padding columns carry +inf and are never taken, even under an infinite cut
-                take |= (pass == 0 ? dts[t] < lim : (dts[t] <= lim && dts[t] < INFINITY))
-                            ? (1u << t) : 0u;
-              }
-              if (i >= j0 && i < j0 + 32) take &= ~(1u << (int)(i - j0));  // not the point itself
-              while (take) {
-                const int t = __ffs(take) - 1;
-                take &= take - 1u;
-                if (pass == 0) {
-                  float dv = 0.0f;
+                for (int e = 0; e < 8; ++e) {
+                  const float4 w = __ldg(cp + e);
+                  ct[4 * e] = w.x;
+                  ct[4 * e + 1] = w.y;
+                  ct[4 * e + 2] = w.z;
+                  ct[4 * e + 3] = w.w;
+                }
+                // two values per packed instruction (each lane rounds as the
+                // scalar fma(-f, g, base + ct) would), and only the minimum is
+                // compared: a group with nothing under the limit costs no more
+                float dts[32];
+                float mn = INFINITY;
+                const float lim = pass == 0 ? worst : cut;
 #pragma unroll
-                  for (int q2 = 0; q2 < 32; ++q2) dv = q2 == t ? dts[q2] : dv;
-                  kn_insert(tk, dv, a.k, worst);
-                } else {
-                  const uint32_t pos = atomicAdd(rowcnt + il, 1u);
-                  if (pos < (uint32_t)KN_CAP)
-                    a.cand[(i - a.row0) * KN_CAP + pos] = (int32_t)(j0 + t);
+                for (int t = 0; t < 32; t += 2) {
+                  const float2 bc = __fadd2_rn(make_float2(base, base), make_float2(ct[t], ct[t + 1]));
+                  const float2 d2 = __ffma2_rn(
+                      make_float2(-f, -f),
+                      make_float2(__uint_as_float(v[t]), __uint_as_float(v[t + 1])), bc);
+                  dts[t] = d2.x;
+                  dts[t + 1] = d2.y;
+                  mn = fminf(mn, fminf(d2.x, d2.y));
+                }
+                if (!(pass == 0 ? mn < lim : mn <= lim)) continue;
+                uint32_t take = 0;
+#pragma unroll
+                for (int t = 0; t < 32; ++t)
+                  // padding columns carry +inf and are never taken, even under an infinite cut
+                  take |= (pass == 0 ? dts[t] < lim : (dts[t] <= lim && dts[t] < INFINITY))
+                              ? (1u << t) : 0u;
+                if (i >= j0 && i < j0 + 32) take &= ~(1u << (int)(i - j0));  // not the point itself
+                while (take) {
+                  const int t = __ffs(take) - 1;
+                  take &= take - 1u;
+                  if (pass == 0) {
+                    float dv = 0.0f;
+#pragma unroll
+                    for (int q2 = 0; q2 < 32; ++q2) dv = q2 == t ? dts[q2] : dv;
+                    kn_insert(tk, dv, a.k, worst);
+                  } else {
+                    const uint32_t pos = atomicAdd(rowcnt + il, 1u);
+                    if (pos < (uint32_t)KN_CAP)
+                      a.cand[(i - a.row0) * KN_CAP + pos] = (int32_t)(j0 + t);
+                  }
                 }
               }
             }
