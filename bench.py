@@ -75,12 +75,14 @@ def parse():
                     help="order in which each block's searches are claimed: tree-0 preorder "
                          "(coherent), point id, or the preorder when X exceeds L2 (auto)")
     ap.add_argument("--mode", default="step",
-                    choices=["step", "dims", "paper", "batched", "cap", "dense", "lockstep"],
+                    choices=["step", "dims", "paper", "batched", "cap", "dense", "lockstep", "tc"],
                     help="step: the benchmark line; dims: adaptive vs dense cost per evaluation "
                          "across d; paper: the paper-scale angular arms; batched: many "
                          "independent builds harvested together; cap: the scaffold degree "
                          "cap ablation; dense: the dense-block ceiling alone; lockstep: the "
-                         "visited-set overlap of the GPU harvest (Section 5.5)")
+                         "visited-set overlap of the GPU harvest (Section 5.5); tc: the two "
+                         "tensor-core Gram kernels alone (Gram-only dense blocks, exact k-NN), "
+                         "for profiling")
     return ap.parse_args()
 
 
@@ -1291,6 +1293,30 @@ def run_cap(args):
     fg.fgraft_tune_scaffold_cap(0)
 
 
+def run_tc(args):
+    """The tensor-core Gram kernels alone, for profiling: the Gram-only dense
+    blocks on the benchmark's 64 blocks repeated 16 times (1,024 blocks),
+    twice, then the exact 10-NN of the first 16,384 points among all n."""
+    from paper_2609_30493_gb300 import build as fgbuild
+    from paper_2609_30493_gb300 import fgraft as fg
+    fgbuild.build()
+    fg.load()
+    spec = dict(SPEC)
+    if args.n:
+        spec["n"] = args.n
+    _, _, _, (X_d, _, B_d) = _device_inputs(spec)
+    Bn = B_d.repeat(16, 1).contiguous()
+    d = spec["d"]
+    out = {"mode": "tc", "n": spec["n"], "gram_ms": []}
+    for _ in range(2):
+        _, gms = fg.fgraft_dense_block_gram(X_d, d, fg.ANGULAR_F32, Bn, precision=1)
+        out["gram_ms"].append(round(gms, 4))
+    _, _, st = fg.fgraft_knn_exact(X_d, d, fg.ANGULAR_F32, 10, 0, min(16384, spec["n"]),
+                                   stats=True)
+    out["knn"] = st
+    print(json.dumps(out), flush=True)
+
+
 def run_lockstep(args):
     """The lockstep-density and column-batching measurement alone."""
     from paper_2609_30493_gb300 import build as fgbuild
@@ -1403,6 +1429,8 @@ def main():
         run_dense(args)
     elif args.mode == "lockstep":
         run_lockstep(args)
+    elif args.mode == "tc":
+        run_tc(args)
     else:
         run_ours(args)
 

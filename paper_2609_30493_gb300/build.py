@@ -20,6 +20,12 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-r
               "-Xptxas", "-v"]
 
 
+def _defines():
+    """Measurement builds: -D flags from FGRAFT_NVCC_DEFINES (space-separated),
+    e.g. -DFGRAFT_GATHER_NO_L1.  Empty for the normal build."""
+    return [f for f in os.environ.get("FGRAFT_NVCC_DEFINES", "").split() if f.startswith("-D")]
+
+
 def _nvcc() -> str:
     cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
     p = os.path.join(cuda, "bin", "nvcc")
@@ -42,7 +48,7 @@ def _stamp() -> str:
         with open(f, "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
-    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    h.update(" ".join(ARCH + NVCC_FLAGS + _defines()).encode())
     return h.hexdigest()
 
 
@@ -59,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-I", INCLUDE, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *_defines(), "-I", INCLUDE, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

@@ -198,6 +198,24 @@ __device__ __forceinline__ void stage_row(uint4* dst, const char* __restrict__ r
   __syncwarp();
 }
 
+// One 16-byte chunk of a candidate row.  Normally through the read-only
+// path, so that a row one search of an SM has just loaded is served from L1
+// to the others (the SM's resident searches share repeated targets).  A
+// measurement build with -DFGRAFT_GATHER_NO_L1 caches the rows in L2 only,
+// to measure what that sharing is worth.
+__device__ __forceinline__ uint4 load_row_chunk(const uint4* p) {
+#ifdef FGRAFT_GATHER_NO_L1
+  uint4 v;
+  // not volatile: the rows are read-only, the loads may be scheduled freely
+  asm("ld.global.cg.v4.u32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p));
+  return v;
+#else
+  return __ldg(p);
+#endif
+}
+
 // The chunks lane j of a group needs from row; indices past the row are
 // clamped to its last chunk (the values are masked out later), so every load
 // is issued without a branch.
@@ -210,7 +228,7 @@ __device__ __forceinline__ void load_slots(const char* __restrict__ row, int nch
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int c = min(32 * k + j + L::P * i, nchunks - 1);
-      y[i][k] = __ldg(reinterpret_cast<const uint4*>(row) + c);
+      y[i][k] = load_row_chunk(reinterpret_cast<const uint4*>(row) + c);
     }
   }
 }

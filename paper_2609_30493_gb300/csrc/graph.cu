@@ -436,6 +436,8 @@ struct FinalArgs {
   // non-null: warps claim the entries of the work list one at a time from
   // this counter (a persistent grid), instead of a fixed stride
   uint32_t* claim;
+  // keys per warp in shared memory when gbuf is null (0: FIN_CAP)
+  int32_t scap;
 };
 
 // Final row of u from its kept keys (sorted, kk of them, owner's vector
@@ -465,10 +467,12 @@ constexpr int FIN_WARPS = 4;
 constexpr int FIN_CAP = 1024;
 constexpr int FIN_DEF_CAP = 256;  // longest final row list the CTA prune takes
 
-// Shared memory per warp: key buffer and bit words (unless the row works in
-// global scratch), then two staged vectors (the row's owner, the kept c*).
-__host__ __device__ inline int fin_warp_bytes(bool global_keys, int qbytes) {
-  return (global_keys ? 0 : 8 * FIN_CAP + FIN_CAP / 4) + 2 * qbytes;
+// Shared memory per warp: key buffer and bit words of scap keys (unless the
+// row works in global scratch), then two staged vectors (the row's owner,
+// the kept c*).
+__host__ __device__ inline int fin_warp_bytes(bool global_keys, int qbytes, int scap = 0) {
+  const int c = scap > 0 ? scap : FIN_CAP;
+  return (global_keys ? 0 : 8 * c + c / 4) + 2 * qbytes;
 }
 
 template <int METRIC, int G, int K>
@@ -476,7 +480,7 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
   extern __shared__ __align__(16) unsigned char fsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * FIN_WARPS + warp;
-  unsigned char* wsm = fsm + (int64_t)warp * fin_warp_bytes(a.gbuf != nullptr, a.qbytes);
+  unsigned char* wsm = fsm + (int64_t)warp * fin_warp_bytes(a.gbuf != nullptr, a.qbytes, a.scap);
   uint64_t* keys;
   uint32_t* bits;
   int cap;
@@ -485,10 +489,10 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
     bits = reinterpret_cast<uint32_t*>(keys + a.gcap);
     cap = a.gcap;
   } else {
+    cap = a.scap > 0 ? a.scap : FIN_CAP;
     keys = reinterpret_cast<uint64_t*>(wsm);
-    bits = reinterpret_cast<uint32_t*>(wsm + 8 * FIN_CAP);
-    wsm += 8 * FIN_CAP + FIN_CAP / 4;
-    cap = FIN_CAP;
+    bits = reinterpret_cast<uint32_t*>(wsm + 8 * cap);
+    wsm += 8 * cap + cap / 4;
   }
   uint4* us = reinterpret_cast<uint4*>(wsm);
   uint4* cs = reinterpret_cast<uint4*>(wsm + a.qbytes);
@@ -742,8 +746,32 @@ static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, int nu
   FG_CUDA(cudaMemcpyAsync(h, small, sizeof(h), cudaMemcpyDeviceToHost, s));
   FG_CUDA(cudaStreamSynchronize(s));
   int rc = 0;
-  if (h[0] > 0) {
-    const int gcap = pow2_at_least(h[1]);
+  int optin = 0;
+  {
+    int dev = 0;
+    FG_CUDA(cudaGetDevice(&dev));
+    FG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  }
+  const int lcap = h[0] > 0 ? pow2_at_least(h[1]) : 0;
+  const int lsm = FIN_WARPS * fin_warp_bytes(false, a.qbytes, lcap);
+  if (h[0] > 0 && lsm <= optin) {
+    // long rows whose keys fit shared memory: sorted and pruned there, one
+    // warp per row, as many CTAs as rows need
+    cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(kern), std::max(lsm, sm0));
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "cudaFuncSetAttribute(final_rows_kernel)");
+    } else {
+      FinalArgs l = a;
+      l.rowlist = long_rows;
+      l.rowlist_len = small;
+      l.scap = lcap;
+      kern<<<(int)((h[0] + FIN_WARPS - 1) / FIN_WARPS), FIN_WARPS * 32, lsm, s>>>(l);
+      note_launch();
+      e = cudaGetLastError();
+      if (e != cudaSuccess) rc = cuda_fail(e, "final_rows_kernel(long)");
+    }
+  } else if (h[0] > 0) {
+    const int gcap = lcap;
     const int ctas = (int)std::min<uint32_t>((h[0] + FIN_WARPS - 1) / FIN_WARPS, 64);
     uint64_t* gbuf = nullptr;
     cudaError_t e = cudaMallocAsync(

@@ -178,7 +178,9 @@ def test_prune_lists_parity(fg):
     nl, R = 300, 16
     owners = rng.integers(0, 3000, size=nl).astype(np.int32)
     lens = rng.integers(0, 200, size=nl)
-    lens[:3] = [0, 1, 1500]
+    # 1500: a long list sorted and pruned in shared memory; 5000: one too
+    # long for it, in global scratch
+    lens[:4] = [0, 1, 1500, 5000]
     off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
     cand = rng.integers(0, 3000, size=int(off[-1])).astype(np.int32)
     cand[off[5]] = owners[5]  # the owner itself appears in a list

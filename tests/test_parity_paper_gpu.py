@@ -94,6 +94,23 @@ def test_bench_arm_sampled_final_rows(data, bench_arm):
         assert f_ids[f_off[u]:f_off[u + 1]].tolist() == row, u
 
 
+def test_bench_arm_longest_final_rows(data, bench_arm):
+    # the rows with the most raw candidates (hubs of the reverse lists: more
+    # than 1024, pruned by the long-row launch) and some just above the
+    # tensor-core tiles' 256
+    st, D_ = bench_arm["st"], data["D"]
+    rows, cnt = st["rows"], st["counts"]
+    valid = np.arange(rows.shape[1])[None, :] < cnt[:, None]
+    indeg = np.bincount(rows[valid], minlength=N)
+    order = np.argsort(-(indeg + cnt), kind="stable")
+    users = np.concatenate([order[:6], order[np.searchsorted(-(indeg + cnt)[order], -300):][:6]])
+    want = sampled.final_rows(D_, rows, cnt, R, ALPHA, st["parents"][0], users)
+    f_off, f_ids = bench_arm["f_off"], bench_arm["f_ids"]
+    assert (indeg + cnt)[order[0]] > 1024
+    for u, row in want.items():
+        assert f_ids[f_off[u]:f_off[u + 1]].tolist() == row, u
+
+
 def test_bench_arm_sampled_search(data, bench_arm):
     Q = bench_arm["Q"]
     sel = np.random.default_rng(23).choice(len(Q), size=200, replace=False)
