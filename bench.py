@@ -388,8 +388,9 @@ def incache_extra(fg, flush, stream, steps=3, warmup=2, tune_table=None):
 def paper_arms(fg, X_d, Q_d, ps, Q, spec, arms=((32, 1), (8, 1), (8, 2), (8, 4), (8, 8), (8, 16))):
     """The paper's Table 1 shape on the benchmark workload (untimed extra): the
     frozen T = 32 harvest and FGraft T = 8 at B = 1..16, R = 64, ef_h = 100;
-    build time (scaffold, harvest, final graph), harvest evaluations per
-    second and recall@10 at ef_s = 64 and 128 (float32 brute force)."""
+    build time (scaffold, harvest, final graph; each arm autotuned first),
+    harvest evaluations per second and recall@10 at ef_s = 64 and 128
+    (float32 brute force)."""
     import torch
     d = spec["d"]
     gt = []
@@ -400,6 +401,8 @@ def paper_arms(fg, X_d, Q_d, ps, Q, spec, arms=((32, 1), (8, 1), (8, 2), (8, 4),
     for T, B in arms:
         p = fg.Params(T=T, R=spec["R"], ef_h=spec["ef_h"], B=B, alpha=spec["alpha"],
                       seed=spec["seed"], metric=fg.ANGULAR_F32)
+        # each arm's own launch settings (the tuning table is keyed by T and B)
+        tune(fg, X_d, dict(spec, T=T, B=B), p, 32768)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()

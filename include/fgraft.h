@@ -346,8 +346,8 @@ fgraft_status fgraft_index_tune(fgraft_index* ix, int32_t hash_log2, int32_t war
  * S_b -- under every
  * candidate launch configuration, keeps the fastest for this index and
  * records it in the process's tuning table under (metric, d, ef_h, R,
- * ceil(log2 n)); later fgraft_build_scaffold calls of the same shape start
- * from it.  The settings: warps (searches) per CTA 4, 2, 1; visited sets by
+ * ceil(log2 n), T, B); later fgraft_build_scaffold calls of the same shape
+ * start from it.  The settings: warps (searches) per CTA 4, 2, 1; visited sets by
  * the occupancy rule or in a shared-memory hash of 2^9..2^12 slots;
  * overflowing searches continuing in a global bitmap or re-run; candidate
  * rows gathered into registers by the lane groups or bulk-copied (TMA) into
@@ -382,8 +382,9 @@ fgraft_status fgraft_index_autotune(fgraft_index* ix, int32_t sample, fgraft_str
 fgraft_status fgraft_index_set_tuning(fgraft_index* ix, const fgraft_tuning* t);
 
 /* The process's tuning table as a JSON file (path: host string):
- * {"fgraft_tuning": 1, "entries": [{"metric", "d", "ef_h", "R", "log2_n",
- * "warps_per_cta", "hash_log2", "overflow_mode", "us_per_query"}, ..]}.
+ * {"fgraft_tuning": 1, "entries": [{"metric", "d", "ef_h", "R", "log2_n", "T",
+ * "B", "warps_per_cta", "hash_log2", "overflow_mode", "gather", "id_batch",
+ * "us_per_query"}, ..]} ("gather" and "id_batch" optional: 0 and 2).
  * Loading adds or replaces entries (EINVAL on an unreadable file or an
  * entry with a missing field or a setting out of range, table unchanged). */
 fgraft_status fgraft_tuning_table_save(const char* path);

@@ -536,7 +536,7 @@ void apply_settings(fgraft_index* ix, int wpc, int hash_log2, int overflow, int 
 }
 
 TuneKey tune_key(const fgraft_index* ix) {
-  return TuneKey{ix->L.metric, ix->L.d, ix->p.ef_h, ix->p.R, ceil_log2(ix->L.n)};
+  return TuneKey{ix->L.metric, ix->L.d, ix->p.ef_h, ix->p.R, ceil_log2(ix->L.n), ix->p.T, ix->nb};
 }
 
 // The harvest search arguments of block b of index ix (everything but the

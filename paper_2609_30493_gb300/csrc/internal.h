@@ -139,7 +139,7 @@ extern int g_mma_wait_polls;
 // Harvest launch settings chosen by the autotuner, by (metric, d, ef_h, R,
 // ceil(log2 n)); hash_log2 0 keeps the occupancy rule for the visited sets.
 struct TuneKey {
-  int metric, d, ef, R, log2_n;
+  int metric, d, ef, R, log2_n, T, B;
 };
 struct TuneVal {
   int wpc, hash_log2, overflow, gather, id_batch;

@@ -1,9 +1,10 @@
 // Process-wide table of harvest launch settings chosen by the autotuner,
-// keyed by what decides the harvest kernel's shape and its visited sets: the
-// metric, the dimension, the beam width, the degree bound and ceil(log2 n).
+// keyed by what decides the harvest kernel's shape, its visited sets and the
+// length of its neighbour lists: the metric, the dimension, the beam width,
+// the degree bound, ceil(log2 n), the number of trees and of blocks.
 // Saved and loaded as JSON of one fixed form:
 //   {"fgraft_tuning": 1, "entries": [
-//     {"metric": 1, "d": 100, "ef_h": 100, "R": 64, "log2_n": 21,
+//     {"metric": 1, "d": 100, "ef_h": 100, "R": 64, "log2_n": 21, "T": 8, "B": 8,
 //      "warps_per_cta": 4, "hash_log2": 0, "overflow_mode": 1, "gather": 1,
 //      "id_batch": 2, "us_per_query": 0.95}, ...]}
 // ("gather" and "id_batch" may be absent: 0 and 2).
@@ -23,7 +24,7 @@ namespace fg {
 
 namespace {
 
-using Key = std::tuple<int, int, int, int, int>;
+using Key = std::tuple<int, int, int, int, int, int, int>;
 
 std::mutex& table_mu() {
   static std::mutex mu;
@@ -34,7 +35,7 @@ std::map<Key, TuneVal>& table() {
   return t;
 }
 
-Key key_of(const TuneKey& k) { return Key{k.metric, k.d, k.ef, k.R, k.log2_n}; }
+Key key_of(const TuneKey& k) { return Key{k.metric, k.d, k.ef, k.R, k.log2_n, k.T, k.B}; }
 
 // Value of "name": <number> inside [b, e), or false.
 bool field(const char* b, const char* e, const char* name, double* out) {
@@ -93,11 +94,11 @@ int tune_table_save(const char* path) {
     const TuneVal& v = kv.second;
     fprintf(f,
             "%s\n  {\"metric\": %d, \"d\": %d, \"ef_h\": %d, \"R\": %d, \"log2_n\": %d, "
-            "\"warps_per_cta\": %d, \"hash_log2\": %d, \"overflow_mode\": %d, "
-            "\"gather\": %d, \"id_batch\": %d, \"us_per_query\": %.6g}",
+            "\"T\": %d, \"B\": %d, \"warps_per_cta\": %d, \"hash_log2\": %d, "
+            "\"overflow_mode\": %d, \"gather\": %d, \"id_batch\": %d, \"us_per_query\": %.6g}",
             first ? "" : ",", std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
-            std::get<4>(k), v.wpc, v.hash_log2, v.overflow, v.gather, v.id_batch,
-            v.us_per_query);
+            std::get<4>(k), std::get<5>(k), std::get<6>(k), v.wpc, v.hash_log2, v.overflow,
+            v.gather, v.id_batch, v.us_per_query);
     first = false;
   }
   fprintf(f, "\n]}\n");
@@ -137,9 +138,10 @@ int tune_table_load(const char* path) {
       set_error(1, std::string(path) + ": unterminated entry");
       return 1;
     }
-    double m, d, ef, R, ln, w, h, o, us = 0.0;
+    double m, d, ef, R, ln, T, B, w, h, o, us = 0.0;
     if (!field(b, e, "metric", &m) || !field(b, e, "d", &d) || !field(b, e, "ef_h", &ef) ||
-        !field(b, e, "R", &R) || !field(b, e, "log2_n", &ln) ||
+        !field(b, e, "R", &R) || !field(b, e, "log2_n", &ln) || !field(b, e, "T", &T) ||
+        !field(b, e, "B", &B) ||
         !field(b, e, "warps_per_cta", &w) || !field(b, e, "hash_log2", &h) ||
         !field(b, e, "overflow_mode", &o)) {
       set_error(1, std::string(path) + ": entry without a required field");
@@ -155,7 +157,7 @@ int tune_table_load(const char* path) {
       return 1;
     }
     TuneVal v{(int)w, (int)h, (int)o, (int)ga, (int)ib, (float)us};
-    loaded[Key{(int)m, (int)d, (int)ef, (int)R, (int)ln}] = v;
+    loaded[Key{(int)m, (int)d, (int)ef, (int)R, (int)ln, (int)T, (int)B}] = v;
     p = e + 1;
   }
   std::lock_guard<std::mutex> lock(table_mu());

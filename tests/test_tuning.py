@@ -18,8 +18,8 @@ def lib():
 
 
 def _entry(**kw):
-    e = {"metric": 1, "d": 100, "ef_h": 100, "R": 64, "log2_n": 21, "warps_per_cta": 2,
-         "hash_log2": 11, "overflow_mode": 1, "us_per_query": 0.5}
+    e = {"metric": 1, "d": 100, "ef_h": 100, "R": 64, "log2_n": 21, "T": 8, "B": 8,
+         "warps_per_cta": 2, "hash_log2": 11, "overflow_mode": 1, "us_per_query": 0.5}
     e.update(kw)
     return e
 
@@ -27,14 +27,14 @@ def _entry(**kw):
 def test_table_round_trip(lib, tmp_path):
     src = tmp_path / "in.json"
     entries = [_entry(), _entry(d=960, ef_h=64, R=32, log2_n=19, warps_per_cta=4, hash_log2=0,
-                                overflow_mode=2, us_per_query=3.25)]
+                                overflow_mode=2, us_per_query=3.25), _entry(T=32, B=1)]
     src.write_text(json.dumps({"fgraft_tuning": 1, "entries": entries}))
     assert lib.fgraft_tuning_table_load(os.fsencode(str(src))) == 0
     out = tmp_path / "out.json"
     assert lib.fgraft_tuning_table_save(os.fsencode(str(out))) == 0
     got = json.loads(out.read_text())
     assert got["fgraft_tuning"] == 1
-    key = ("metric", "d", "ef_h", "R", "log2_n")
+    key = ("metric", "d", "ef_h", "R", "log2_n", "T", "B")
     have = {tuple(e[k] for k in key): e for e in got["entries"]}
     for e in entries:
         g = have[tuple(e[k] for k in key)]
@@ -47,6 +47,7 @@ def test_table_round_trip(lib, tmp_path):
     "not json at all",
     json.dumps({"entries": [_entry()]}),
     json.dumps({"fgraft_tuning": 1, "entries": [{k: v for k, v in _entry().items() if k != "R"}]}),
+    json.dumps({"fgraft_tuning": 1, "entries": [{k: v for k, v in _entry().items() if k != "B"}]}),
     json.dumps({"fgraft_tuning": 1, "entries": [_entry(warps_per_cta=5)]}),
     json.dumps({"fgraft_tuning": 1, "entries": [_entry(hash_log2=3)]}),
     json.dumps({"fgraft_tuning": 1, "entries": [_entry(overflow_mode=0)]}),
