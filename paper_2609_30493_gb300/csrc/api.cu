@@ -153,6 +153,8 @@ struct fgraft_index {
   int32_t* s_ids = nullptr;
   int64_t s_nnz = 0;
   int32_t* A = nullptr;
+  float* Ad = nullptr;    // delta(p, A[p][i]) beside each harvested id
+  float* r_d = nullptr;   // delta(u, r_ids[k]) beside each reverse id (final rebuild)
   int32_t* cnt = nullptr;
   int64_t* r_off = nullptr;
   int32_t* r_ids = nullptr;
@@ -503,7 +505,7 @@ void free_index(fgraft_index* ix) {
   for (cudaEvent_t e : ix->ev_beg) cudaEventDestroy(e);
   for (cudaEvent_t e : ix->ev_end) cudaEventDestroy(e);
   for (cudaEvent_t e : ix->ev_pend) cudaEventDestroy(e);
-  void* ptrs[] = {ix->roots, ix->parents, ix->s_off, ix->s_ids, ix->A,   ix->cnt,
+  void* ptrs[] = {ix->roots, ix->parents, ix->s_off, ix->s_ids, ix->A,   ix->cnt, ix->Ad, ix->r_d,
                   ix->r_off, ix->r_ids,   ix->rcnt,  ix->rcur,  ix->f_off, ix->f_ids,
                   ix->scan_tmp, ix->work, ix->ovf_list, ix->gscratch, ix->ctr, ix->gvbits,
                   ix->Eg, ix->Eg_cnt, ix->pre, ix->qorder};
@@ -571,6 +573,7 @@ BeamArgs harvest_args(fgraft_index* ix, int32_t b) {
   a.alpha2 = ix->p.alpha * ix->p.alpha;
   a.A_out = ix->A;
   a.cnt_out = ix->cnt;
+  a.Ad_out = ix->Ad;
   const bool sep = ix->prune_ns > 0;
   a.Eg = sep ? ix->Eg : nullptr;
   a.Eg_cnt = sep ? ix->Eg_cnt : nullptr;
@@ -585,12 +588,15 @@ int harvest_after(fgraft_index* ix, int32_t b, const BeamArgs& a, cudaStream_t s
     const int rc = harvest_prune(ix->L, ix->Eg, ix->Eg_cnt, ix->eg_ecap, a.nq, a.q_first,
                                  a.q_step, ix->p.R, a.alpha2, ix->A, ix->cnt, ix->ctr + C_PRUNE,
                                  ix->num_sms, s, nullptr, nullptr, nullptr, nullptr, ix->work + 4,
-                                 ix->ovf_list, ix->work + 5);
+                                 ix->ovf_list, ix->work + 5, nullptr, ix->Ad);
     if (rc) return rc;
   }
   if (prof) FG_CUDA(record_event(ix->ev_pend[b], s));
+  // the last rebuild also carries the distances the final graph reads
+  const bool last = b == ix->nb - 1;
   const int rc = reverse_rows(ix->L.n, ix->p.R, ix->nb, b, ix->A, ix->cnt, ix->rcnt, ix->rcur,
-                              ix->r_off, ix->r_ids, ix->scan_tmp, s);
+                              ix->r_off, ix->r_ids, ix->scan_tmp, s, last ? ix->Ad : nullptr,
+                              last ? ix->r_d : nullptr);
   if (rc) return rc;
   ix->blocks_done = b + 1;
   return 0;
@@ -621,7 +627,7 @@ int harvest_sample(fgraft_index* ix, int64_t sample, unsigned long long* tctr, c
   if (rc || !sep) return rc;
   return harvest_prune(ix->L, ix->Eg, ix->Eg_cnt, ix->eg_ecap, a.nq, b, ix->nb, ix->p.R, a.alpha2,
                        ix->A, ix->cnt, tctr + 5, ix->num_sms, s, nullptr, nullptr, nullptr,
-                       nullptr, ix->work + 4, ix->ovf_list, ix->work + 5, a.qlist);
+                       nullptr, ix->work + 4, ix->ovf_list, ix->work + 5, a.qlist, ix->Ad);
 }
 
 // Scratch of the many-builds launches on a device: the launch's claim
@@ -802,9 +808,11 @@ fgraft_status fgraft_build_scaffold(const void* X, int64_t n, int32_t d, int64_t
   rc = rc ? rc : dalloc(&ix->parents, tot);
   rc = rc ? rc : dalloc(&ix->s_off, n + 1);
   rc = rc ? rc : dalloc(&ix->A, n * p.R);
+  rc = rc ? rc : dalloc(&ix->Ad, n * p.R);
   rc = rc ? rc : dalloc(&ix->cnt, n);
   rc = rc ? rc : dalloc(&ix->r_off, n + 1);
   rc = rc ? rc : dalloc(&ix->r_ids, n * p.R);
+  rc = rc ? rc : dalloc(&ix->r_d, n * p.R);
   rc = rc ? rc : dalloc(&ix->rcnt, n);
   rc = rc ? rc : dalloc(&ix->rcur, n);
   rc = rc ? rc : dalloc(&ix->f_off, n + 1);
@@ -974,7 +982,7 @@ fgraft_status fgraft_prune(fgraft_index* ix, fgraft_stream stream, fgraft_counte
     keep_pool_reserved();
     rc = final_graph(ix->L, ix->p.R, ix->p.alpha * ix->p.alpha, ix->A, ix->cnt, ix->r_off,
                      ix->r_ids, ix->parents, ix->f_off, &ix->f_ids, &ix->f_nnz, ix->scan_tmp,
-                     ix->ctr + C_FINAL, ix->num_sms, s);
+                     ix->ctr + C_FINAL, ix->num_sms, s, ix->Ad, ix->r_d);
     if (rc) return (fgraft_status)rc;
     ix->final_done = true;
   }
@@ -1159,6 +1167,7 @@ fgraft_status fgraft_harvest_visited(fgraft_index* ix, const int32_t* points, in
   a.Eg_cnt = nullptr;
   a.A_out = nullptr;
   a.cnt_out = nullptr;
+  a.Ad_out = nullptr;
   a.vlog = out_ids;
   a.vlog_cnt = out_cnt;
   a.vlog_cap = cap;

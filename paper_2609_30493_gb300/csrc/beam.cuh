@@ -56,6 +56,7 @@ struct BeamArgs {
   float alpha2;
   int32_t* A_out;
   int32_t* cnt_out;
+  float* Ad_out;  // optional: delta(p, A_out[p][i]) beside each kept id
   int32_t k;
   int32_t* top_ids;
   float* top_d;
@@ -541,6 +542,7 @@ struct Beam {
         const int32_t cid = key_id(E[cur]);
         if (lane == 0) {
           row[kept] = cid;
+          if (a.Ad_out) a.Ad_out[p * a.R + kept] = key_dist(E[cur]);
           alive[cur / 32] &= ~(1u << (cur % 32));
         }
         ++kept;

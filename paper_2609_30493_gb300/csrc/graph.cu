@@ -357,28 +357,31 @@ __global__ void rev_count_kernel(int64_t n, int R, int nb, int b, const int32_t*
 
 __global__ void rev_fill_kernel(int64_t n, int R, int nb, int b, const int32_t* A,
                                 const int32_t* cnt, uint32_t* rcur, const int64_t* r_off,
-                                int32_t* r_ids) {
+                                int32_t* r_ids, const float* Ad, float* r_d) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * R;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = i / R;
     const int j = (int)(i - p * R);
     if ((int)(p % nb) <= b && j < cnt[p]) {
       const int32_t u = A[i];
-      r_ids[r_off[u] + atomicAdd(&rcur[u], 1u)] = (int32_t)p;
+      const int64_t k = r_off[u] + atomicAdd(&rcur[u], 1u);
+      r_ids[k] = (int32_t)p;
+      if (r_d) r_d[k] = Ad[i];
     }
   }
 }
 
 int reverse_rows(int64_t n, int R, int nb, int b, const int32_t* A, const int32_t* cnt,
                  uint32_t* rcnt, uint32_t* rcur, int64_t* r_off, int32_t* r_ids,
-                 int64_t* scan_tmp, cudaStream_t s) {
+                 int64_t* scan_tmp, cudaStream_t s, const float* Ad, float* r_d) {
   FG_CUDA(cudaMemsetAsync(rcnt, 0, sizeof(uint32_t) * n, s));
   FG_CUDA(cudaMemsetAsync(rcur, 0, sizeof(uint32_t) * n, s));
   rev_count_kernel<<<grid1d(n * R), 256, 0, s>>>(n, R, nb, b, A, cnt, rcnt);
   note_launch();
   int rc = scan_u32(rcnt, r_off, n, scan_tmp, s);
   if (rc) return rc;
-  rev_fill_kernel<<<grid1d(n * R), 256, 0, s>>>(n, R, nb, b, A, cnt, rcur, r_off, r_ids);
+  rev_fill_kernel<<<grid1d(n * R), 256, 0, s>>>(n, R, nb, b, A, cnt, rcur, r_off, r_ids,
+                                                Ad, Ad ? r_d : nullptr);
   note_launch();
   FG_CUDA(cudaGetLastError());
   return 0;
@@ -438,6 +441,10 @@ struct FinalArgs {
   uint32_t* claim;
   // keys per warp in shared memory when gbuf is null (0: FIN_CAP)
   int32_t scap;
+  // final graph (optional, both or neither): the distance beside each id of
+  // A and of the reverse lists; the candidate keys are then read, not evaluated
+  const float* Ad;
+  const float* r_d;
 };
 
 // Final row of u from its kept keys (sorted, kk of them, owner's vector
@@ -544,7 +551,11 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
     if (a.mode == 0) {
       // C(u) = A[u] u rev(u): neither list repeats an id or holds u, so only
       // the reverse ids that also sit in A[u] are dropped
-      for (int i = lane; i < len0; i += 32) keys[i] = (uint64_t)(uint32_t)seg0[i] << 1;
+      // (with the distances at hand the keys are complete already)
+      const float* dseg0 = a.Ad ? a.Ad + (int64_t)u * a.R : nullptr;
+      const float* dseg1 = a.Ad ? a.r_d + a.r_off[u] : nullptr;
+      for (int i = lane; i < len0; i += 32)
+        keys[i] = dseg0 ? make_key(dseg0[i], seg0[i]) : (uint64_t)(uint32_t)seg0[i] << 1;
       __syncwarp();
       m = len0;
       for (int base = 0; base < len1; base += 32) {
@@ -553,7 +564,9 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
         bool dup = v < 0;
         for (int x = 0; x < len0; ++x) dup |= key_id(keys[x]) == v;
         const unsigned keep = __ballot_sync(FULL, !dup);
-        if (!dup) keys[m + __popc(keep & ((1u << lane) - 1u))] = (uint64_t)(uint32_t)v << 1;
+        if (!dup)
+          keys[m + __popc(keep & ((1u << lane) - 1u))] =
+              dseg1 ? make_key(dseg1[i], v) : (uint64_t)(uint32_t)v << 1;
         m += __popc(keep);
       }
       __syncwarp();
@@ -568,8 +581,8 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
       if (m > 0 && __shfl_sync(FULL, keys[m - 1] == PAD ? 1 : 0, 0)) --m;  // dropped owner
     }
     stage_row(us, a.V.X + (int64_t)u * a.V.ld_bytes, a.V.nchunks, lane);
-    if (m > 0) eval_keys_inplace<METRIC, G, K>(a.V, us, keys, m, lane);
-    ev += (unsigned long long)m;
+    if (m > 0 && !(a.mode == 0 && a.Ad)) eval_keys_inplace<METRIC, G, K>(a.V, us, keys, m, lane);
+    ev += (unsigned long long)m;  // the evaluations C(u) takes, whether done here or earlier
     // rows the CTA prune takes stay unsorted (that kernel orders them)
     const bool defer =
         a.mode == 0 && a.def_keys && !a.gbuf && m > a.R && m <= a.def_cap;
@@ -829,7 +842,8 @@ __global__ void final_defcap_kernel(int64_t n, int R, int def_cap, const int32_t
 int final_graph(const VecLayout& L, int R, float alpha2, const int32_t* A, const int32_t* cnt,
                 const int64_t* r_off, const int32_t* r_ids, const int32_t* parent0,
                 int64_t* f_off, int32_t** f_ids, int64_t* f_nnz, int64_t* scan_tmp,
-                unsigned long long* ctr, int num_sms, cudaStream_t s) {
+                unsigned long long* ctr, int num_sms, cudaStream_t s, const float* Ad,
+                const float* r_d) {
   const int64_t n = L.n;
   uint32_t *c0cnt = nullptr, *capc = nullptr;
   int64_t *c0_off = nullptr, *cap_off = nullptr;
@@ -919,6 +933,8 @@ int final_graph(const VecLayout& L, int R, float alpha2, const int32_t* A, const
   FG_TRY(cudaMemsetAsync(def_count, 0, 4 * sizeof(uint32_t), s));
   FG_TRY(cudaMallocAsync(&def_long, sizeof(int32_t) * std::max<int64_t>(n, 1), s));
   FinalArgs a{};
+  a.Ad = Ad;
+  a.r_d = Ad ? r_d : nullptr;
   a.def_keys = def_cap ? def_keys : nullptr;
   a.def_koff = def_koff;
   a.def_rows = def_rows;

@@ -142,10 +142,12 @@ __global__ void __launch_bounds__(HP_WARPS * 32) harvest_prune_kernel(const HPru
         const uint32_t bw = __shfl_sync(FULL, al, w0);
         const int cur = w0 * 32 + __ffs(bw) - 1;
         if (lane == 0) {
-          if (krow)
+          if (krow) {
             krow[kept] = keys[cur];
-          else
+          } else {
             row[kept] = key_id(keys[cur]);
+            if (a.D_out) a.D_out[p * a.R + kept] = key_dist(keys[cur]);
+          }
         }
         ++kept;
         if (lane == w0) al &= ~(1u << (cur % 32));
@@ -191,7 +193,7 @@ int harvest_prune(const VecLayout& L, const uint64_t* Eg, const int32_t* Eg_cnt,
                   int32_t* A_out, int32_t* cnt_out, unsigned long long* prune_ctr, int num_sms,
                   cudaStream_t s, const int32_t* rows, const int64_t* Eg_off,
                   const uint32_t* nq_dev, uint64_t* K_out, uint32_t* err, int32_t* long_list,
-                  uint32_t* long_cnt, const int32_t* qlist) {
+                  uint32_t* long_cnt, const int32_t* qlist, float* D_out) {
   HPruneFn kern = hprune_kernel_for(L.metric, L.G, L.K);
   if (!kern) {
     set_error(1, "no prune kernel for this metric and dimension");
@@ -199,7 +201,7 @@ int harvest_prune(const VecLayout& L, const uint64_t* Eg, const int32_t* Eg_cnt,
   }
   HPruneArgs a{L.X, L.ld_bytes, L.d, L.nchunks, Eg, Eg_cnt, ecap,
                harvest_prune_smem(ecap, L.nchunks), nq, q_first, q_step, R, alpha2,
-               A_out, cnt_out, prune_ctr, rows, Eg_off, nq_dev, K_out, 0.0f, 0.0f, err,
+               A_out, cnt_out, D_out, prune_ctr, rows, Eg_off, nq_dev, K_out, 0.0f, 0.0f, err,
                g_mma_wait_polls, nullptr, nullptr, qlist};
   int optin = 0, dev = 0, sm_bytes = 0;
   FG_CUDA(cudaGetDevice(&dev));

@@ -253,10 +253,12 @@ __global__ void __launch_bounds__(NC) harvest_prune_tc_kernel(const HPruneArgs a
 #pragma unroll
         for (int w = 0; w < W; ++w)
           if (w == cur / 32) al[w] &= al[w] - 1u;  // the word without c*
-        if (krow)
+        if (krow) {
           krow[kept] = keys[cur];
-        else
+        } else {
           row[kept] = key_id(keys[cur]);
+          if (a.D_out) a.D_out[p * a.R + kept] = key_dist(keys[cur]);
+        }
         ++kept;
         if (kept == a.R) break;
         // the removal pass examines every alive candidate after c* (all alive

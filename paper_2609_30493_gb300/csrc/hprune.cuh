@@ -21,6 +21,7 @@ struct HPruneArgs {
   float alpha2;
   int32_t* A_out;
   int32_t* cnt_out;
+  float* D_out;  // optional: delta(p, A_out[p][i]) beside each kept id (harvest)
   unsigned long long* prune_ctr;
   // the final graph's rows (all null for the harvest): point of list qidx,
   // start of its keys in Eg by point, list count on the device, and kept

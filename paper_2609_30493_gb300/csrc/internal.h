@@ -87,17 +87,23 @@ int scaffold_csr(int64_t n, int T, const int32_t* parents, int64_t* s_off, int32
                  int64_t* nnz_out, uint32_t* deg, int64_t* tmp_off, int32_t* tmp_ids,
                  int64_t* scan_tmp, cudaStream_t s, const VecLayout* L, int cap);
 
-// Reverse lists of the rows of blocks 0..b: r_off (n+1), r_ids (<= n*R).
+// Reverse lists of the rows of blocks 0..b: r_off (n+1), r_ids (<= n*R);
+// with Ad and r_d given, r_d[k] = delta(u, r_ids[k]) beside each reverse id
+// (the distance its row holds: the canonical distance is symmetric).
 int reverse_rows(int64_t n, int R, int nb, int b, const int32_t* A, const int32_t* cnt,
                  uint32_t* rcnt, uint32_t* rcur, int64_t* r_off, int32_t* r_ids,
-                 int64_t* scan_tmp, cudaStream_t s);
+                 int64_t* scan_tmp, cudaStream_t s, const float* Ad = nullptr,
+                 float* r_d = nullptr);
 
 // Final graph (rows of all blocks symmetrised, re-pruned when over R, tree-0
-// spine added, sorted).  f_ids is (re)allocated here.
+// spine added, sorted).  f_ids is (re)allocated here.  Ad / r_d (optional):
+// the distances beside the rows' and the reverse lists' ids, so that the
+// candidate keys need no evaluation.
 int final_graph(const VecLayout& L, int R, float alpha2, const int32_t* A, const int32_t* cnt,
                 const int64_t* r_off, const int32_t* r_ids, const int32_t* parent0,
                 int64_t* f_off, int32_t** f_ids, int64_t* f_nnz, int64_t* scan_tmp,
-                unsigned long long* ctr, int num_sms, cudaStream_t s);
+                unsigned long long* ctr, int num_sms, cudaStream_t s,
+                const float* Ad = nullptr, const float* r_d = nullptr);
 
 // Batched occlusion prune of explicit candidate lists.
 int prune_lists(const VecLayout& L, const int32_t* owner, const int64_t* l_off,
@@ -123,7 +129,8 @@ int harvest_prune(const VecLayout& L, const uint64_t* Eg, const int32_t* Eg_cnt,
                   cudaStream_t s, const int32_t* rows = nullptr, const int64_t* Eg_off = nullptr,
                   const uint32_t* nq_dev = nullptr, uint64_t* K_out = nullptr,
                   uint32_t* err = nullptr, int32_t* long_list = nullptr,
-                  uint32_t* long_cnt = nullptr, const int32_t* qlist = nullptr);
+                  uint32_t* long_cnt = nullptr, const int32_t* qlist = nullptr,
+                  float* D_out = nullptr);
 // (qlist: work item w < nq is the list of qidx = qlist[w]; NULL: qidx = w.)
 // Dominance bits of the prune on the tensor cores (1, the default, for the
 // float32 metrics and lists of at most 128 when err is given) or on the lane
