@@ -445,6 +445,9 @@ struct FinalArgs {
   // A and of the reverse lists; the candidate keys are then read, not evaluated
   const float* Ad;
   const float* r_d;
+  // rows with more raw candidates than heavy_thr whose keys fit FH_CAP are
+  // left to final_heavy_kernel (0: none)
+  int32_t heavy_thr;
 };
 
 // Final row of u from its kept keys (sorted, kk of them, owner's vector
@@ -473,6 +476,24 @@ __device__ void final_spine_out(const FinalArgs& a, int32_t u, const uint4* us, 
 constexpr int FIN_WARPS = 4;
 constexpr int FIN_CAP = 1024;
 constexpr int FIN_DEF_CAP = 256;  // longest final row list the CTA prune takes
+
+// The CTA-wide kernel for final rows with many candidates (below).
+constexpr int FH_WARPS = 8;
+constexpr int FH_CAP = 4096;  // keys of one row (a power of two)
+
+__host__ __device__ inline int fh_smem_bytes(int qbytes) {
+  return 8 * FH_CAP + 2 * (FH_CAP / 8) + 2 * qbytes + 64;
+}
+
+// Whether the CTA-wide kernel takes a row: more raw candidates than the
+// threshold, and its keys, with the kept ones and the spine after the
+// prune, fit the shared buffer.
+__device__ __forceinline__ bool fh_takes(int mraw, int sdeg, int R, int thr) {
+  if (thr <= 0 || mraw <= thr) return false;
+  const int need = max(pow2_dev(mraw), pow2_dev(min(mraw, R) + sdeg));
+  return need <= FH_CAP;
+}
+
 
 // Shared memory per warp: key buffer and bit words of scap keys (unless the
 // row works in global scratch), then two staged vectors (the row's owner,
@@ -541,6 +562,7 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
       len1 = 0;
     }
     const int mraw = len0 + len1;
+    if (a.mode == 0 && fh_takes(mraw, sdeg, a.R, a.heavy_thr)) continue;  // the CTA-wide kernel's
     const int need = max(pow2_dev(mraw), pow2_dev(min(mraw, a.R) + sdeg));
     if (need > cap) {
       if (lane == 0) a.long_rows[atomicAdd(a.nlong, 1u)] = (int32_t)r;
@@ -633,6 +655,221 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
 
 using FinalKernelFn = void (*)(const FinalArgs);
 
+// ---------------------------------------------------------------------------
+// Final graph rows with many candidates: one CTA of 8 warps per row.  The
+// keys come from the stored distances (A[u] and the reverse list of u);
+// the CTA sorts them in shared memory (a repeated key -- a candidate both in
+// A[u] and in the reverse list -- stays out of the alive set), and each
+// removal pass of the prune is spread over the warps, a word of 32
+// candidates at a time: every candidate of a pass is tested against the same
+// c*, so the words are independent.  Then warp 0 adds the tree-0 spine and
+// writes the row, as the one-warp kernel does.
+// ---------------------------------------------------------------------------
+template <int METRIC, int G, int K>
+__global__ void __launch_bounds__(FH_WARPS * 32) final_heavy_kernel(const FinalArgs a,
+                                                                     const int32_t* hrows,
+                                                                     const uint32_t* hcount,
+                                                                     uint32_t* claim) {
+  using L = Lanes<G, K>;
+  extern __shared__ __align__(16) unsigned char hsm[];
+  uint64_t* keys = reinterpret_cast<uint64_t*>(hsm);
+  uint32_t* alive = reinterpret_cast<uint32_t*>(hsm + 8 * FH_CAP);
+  uint32_t* keptm = alive + FH_CAP / 32;
+  uint4* cs = reinterpret_cast<uint4*>(hsm + 8 * FH_CAP + 2 * (FH_CAP / 8));
+  uint4* us = reinterpret_cast<uint4*>(hsm + 8 * FH_CAP + 2 * (FH_CAP / 8) + a.qbytes);
+  int* sh = reinterpret_cast<int*>(hsm + 8 * FH_CAP + 2 * (FH_CAP / 8) + 2 * a.qbytes);
+  // sh[0]: claimed row, sh[1]: cur (c*), sh[2]: kept, sh[3]: done, sh[4]: distinct count
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane / L::P, j = lane % L::P;
+  const int64_t total = (int64_t)*hcount;
+  unsigned long long ev = 0;
+  for (;;) {
+    if (tid == 0) sh[0] = (int)atomicAdd(claim, 1u);
+    __syncthreads();
+    const int64_t r = sh[0];
+    if (r >= total) break;
+    const int32_t u = hrows[r];
+    const int len0 = a.cnt[u];
+    const int64_t r0 = a.r_off[u];
+    const int len1 = (int)(a.r_off[u + 1] - r0);
+    const int N = len0 + len1;
+    int N2 = 32;
+    while (N2 < N) N2 <<= 1;
+    for (int i = tid; i < N2; i += FH_WARPS * 32) {
+      uint64_t k = PAD;
+      if (i < len0)
+        k = make_key(a.Ad[(int64_t)u * a.R + i], a.A[(int64_t)u * a.R + i]);
+      else if (i < N)
+        k = make_key(a.r_d[r0 + i - len0], a.r_ids[r0 + i - len0]);
+      keys[i] = k;
+    }
+    if (warp == 1) stage_row(us, a.V.X + (int64_t)u * a.V.ld_bytes, a.V.nchunks, lane);
+    __syncthreads();
+    // bitonic sort of the N2 keys
+    for (int kk = 2; kk <= N2; kk <<= 1) {
+      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+        for (int i = tid; i < N2; i += FH_WARPS * 32) {
+          const int l = i ^ jj;
+          if (l > i) {
+            const uint64_t x = keys[i], y = keys[l];
+            const bool up = (i & kk) == 0;
+            if ((x > y) == up) {
+              keys[i] = y;
+              keys[l] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // the distinct candidates are alive; the kept mask starts empty
+    const int nw = N2 / 32;
+    if (tid == 0) sh[4] = 0;
+    __syncthreads();
+    for (int w = tid; w < nw; w += FH_WARPS * 32) {
+      uint32_t bits = 0;
+      for (int t = 0; t < 32; ++t) {
+        const int i = 32 * w + t;
+        const uint64_t k = keys[i];
+        if (k != PAD && (i == 0 || keys[i - 1] != k)) bits |= 1u << t;
+      }
+      alive[w] = bits;
+      keptm[w] = 0u;
+      atomicAdd(&sh[4], __popc(bits));
+    }
+    __syncthreads();
+    const int m = sh[4];
+    ev += (unsigned long long)(tid == 0 ? m : 0);
+    // spine members outside C(u) cost one evaluation each (warp 0)
+    const int32_t p0 = a.parent0[u];
+    const int32_t* ch = a.c0_ids + a.c0_off[u];
+    const int sdeg = (p0 >= 0 ? 1 : 0) + (int)(a.c0_off[u + 1] - a.c0_off[u]);
+    if (warp == 0) {
+      for (int q = 0; q < sdeg; ++q) {
+        const int32_t v = (p0 >= 0) ? (q == 0 ? p0 : ch[q - 1]) : ch[q];
+        if (!keys_contain(keys, N2, v, lane) && lane == 0) ++ev;
+      }
+    }
+    if (m > a.R) {
+      if (tid == 0) {
+        sh[1] = -1;
+        sh[2] = 0;
+        sh[3] = 0;
+      }
+      __syncthreads();
+      for (;;) {
+        if (warp == 0) {
+          // the next alive candidate after c*
+          const int cur = sh[1];
+          int nxt = -1;
+          for (int w0 = (cur + 1) / 32; w0 < nw && nxt < 0; w0 += 32) {
+            const int w = w0 + lane;
+            uint32_t bits = w < nw ? alive[w] : 0u;
+            if (w == (cur + 1) / 32) bits &= ~((1u << ((cur + 1) % 32)) - 1u);
+            if (w < (cur + 1) / 32) bits = 0u;
+            const unsigned nz = __ballot_sync(FULL, bits != 0u);
+            if (nz) {
+              const int wl = __ffs(nz) - 1;
+              const uint32_t b = __shfl_sync(FULL, bits, wl);
+              nxt = (w0 + wl) * 32 + __ffs(b) - 1;
+            }
+          }
+          if (lane == 0) {
+            if (nxt < 0) {
+              sh[3] = 1;
+            } else {
+              alive[nxt / 32] &= ~(1u << (nxt % 32));
+              keptm[nxt / 32] |= 1u << (nxt % 32);
+              sh[1] = nxt;
+              sh[2] += 1;
+              if (sh[2] == a.R) sh[3] = 1;
+            }
+          }
+        }
+        __syncthreads();
+        if (sh[3]) break;
+        const int cur = sh[1];
+        for (int c = tid; c < a.V.nchunks; c += FH_WARPS * 32)
+          cs[c] = __ldg(reinterpret_cast<const uint4*>(a.V.X + (int64_t)key_id(keys[cur]) *
+                                                                   a.V.ld_bytes) + c);
+        __syncthreads();
+        // the removal pass: each warp its words of candidates after c*
+        for (int w = cur / 32 + warp; w < nw; w += FH_WARPS) {
+          uint32_t bits = alive[w];
+          if (w == cur / 32) bits &= ~((2u << (cur % 32)) - 1u);
+          if (lane == 0) ev += (unsigned long long)__popc(bits);
+          uint32_t kill = 0;
+          while (bits) {
+            const int nb = __popc(bits);
+            uint4 y[L::UW][L::VL][K];
+            int jx[L::UW];
+#pragma unroll
+            for (int uu = 0; uu < L::UW; ++uu) {
+              const int rr = uu * L::CPW + g;
+              jx[uu] = rr < nb ? nth_set_bit(bits, rr) : -1;
+              const int e = w * 32 + (jx[uu] >= 0 ? jx[uu] : 0);
+              load_slots<G, K>(a.V.X + (int64_t)key_id(keys[e]) * a.V.ld_bytes, a.V.nchunks, j,
+                               y[uu]);
+            }
+#pragma unroll
+            for (int uu = 0; uu < L::UW; ++uu) {
+              const float dd = slots_dist<METRIC, G, K>(cs, y[uu], a.V.nchunks, a.V.d, j);
+              if (jx[uu] >= 0 && j == 0) {
+                const float dp = key_dist(keys[w * 32 + jx[uu]]);
+                if (__fmul_rn(a.alpha2, dd) <= dp) kill |= 1u << jx[uu];
+              }
+            }
+            const int consumed = nb < L::CPW * L::UW ? nb : L::CPW * L::UW;
+            if (consumed >= nb)
+              bits = 0;
+            else
+              bits &= ~((1u << nth_set_bit(bits, consumed)) - 1u);
+          }
+          kill = __reduce_or_sync(FULL, kill);
+          if (lane == 0) alive[w] &= ~kill;
+        }
+        __syncthreads();
+      }
+    } else {
+      // every distinct candidate is kept
+      for (int w = tid; w < nw; w += FH_WARPS * 32) keptm[w] = alive[w];
+      __syncthreads();
+    }
+    // the kept keys to the front, in order, then the spine and the row (warp 0)
+    if (warp == 0) {
+      int outn = 0;
+      for (int base = 0; base < N2; base += 32) {
+        const int i = base + lane;
+        const bool keep = (keptm[i / 32] >> (i % 32)) & 1u;
+        const uint64_t k = keep ? keys[i] : PAD;
+        const unsigned msk = __ballot_sync(FULL, keep);
+        __syncwarp();
+        if (keep) keys[outn + __popc(msk & ((1u << lane) - 1u))] = k;
+        outn += __popc(msk);
+        __syncwarp();
+      }
+      final_spine_out<METRIC, G, K>(a, u, us, keys, outn, lane);
+    }
+    __syncthreads();
+  }
+  if (ev && a.ctr) atomicAdd(a.ctr, ev);
+}
+
+using FinalHeavyFn = void (*)(const FinalArgs, const int32_t*, const uint32_t*, uint32_t*);
+
+static FinalHeavyFn final_heavy_for(int metric, int G, int K) {
+#define HX(M, GG, KK) \
+  if (metric == M && G == GG && K == KK) return final_heavy_kernel<M, GG, KK>;
+#define HF(M) HX(M, 4, 1) HX(M, 8, 1) HX(M, 16, 1) HX(M, 32, 1) HX(M, 32, 2) HX(M, 32, 4) \
+  HX(M, 32, 8)
+  HF(0)
+  HF(1)
+  HX(2, 4, 1) HX(2, 8, 1) HX(2, 16, 1)
+#undef HF
+#undef HX
+  return nullptr;
+}
+
 static FinalKernelFn final_kernel_for(int metric, int G, int K) {
 #define FX(M, GG, KK) \
   if (metric == M && G == GG && K == KK) return final_rows_kernel<M, GG, KK>;
@@ -696,9 +933,12 @@ static int fin_smem(FinalKernelFn kern, int qbytes, int* sm_shared, int* sm_glob
 // The final graph's rows in the order the candidate kernel claims them: the
 // rows it prunes itself (more raw candidates than the CTA prune takes, or
 // than R when nothing is deferred) first, then the rest, so that the long
-// in-warp prunes start early instead of trailing the launch.
+// in-warp prunes start early instead of trailing the launch.  With hlist,
+// the rows the CTA-wide kernel takes (fh_takes) are also listed there (the
+// one-warp kernel skips them by the same test).
 __global__ void final_order_kernel(int64_t n, int heavy, const int32_t* cnt, const int64_t* r_off,
-                                   int32_t* order, uint32_t* ctr2) {
+                                   int32_t* order, uint32_t* ctr2, int R, const int32_t* parent0,
+                                   const int64_t* c0_off, int32_t* hlist, uint32_t* hcount) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t mraw = cnt[i] + (r_off[i + 1] - r_off[i]);
@@ -706,6 +946,10 @@ __global__ void final_order_kernel(int64_t n, int heavy, const int32_t* cnt, con
       order[atomicAdd(&ctr2[0], 1u)] = (int32_t)i;
     else
       order[n - 1 - atomicAdd(&ctr2[1], 1u)] = (int32_t)i;
+    if (hlist) {
+      const int sdeg = (parent0[i] >= 0 ? 1 : 0) + (int)(c0_off[i + 1] - c0_off[i]);
+      if (fh_takes((int)mraw, sdeg, R, heavy)) hlist[atomicAdd(hcount, 1u)] = (int32_t)i;
+    }
   }
 }
 
@@ -723,9 +967,12 @@ static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, int nu
   int32_t* long_rows = nullptr;
   uint32_t* small = nullptr;
   int32_t* order = nullptr;
+  int32_t* hlist = nullptr;
+  // small: [0] long rows, [1] their largest need, [2..3] order counters,
+  // [4] main claim, [5] CTA-wide rows, [6] their claim
   FG_CUDA(cudaMallocAsync(&long_rows, sizeof(int32_t) * std::max<int64_t>(nrows, 1), s));
-  FG_CUDA(cudaMallocAsync(&small, 5 * sizeof(uint32_t), s));
-  FG_CUDA(cudaMemsetAsync(small, 0, 5 * sizeof(uint32_t), s));
+  FG_CUDA(cudaMallocAsync(&small, 8 * sizeof(uint32_t), s));
+  FG_CUDA(cudaMemsetAsync(small, 0, 8 * sizeof(uint32_t), s));
   a.rowlist = nullptr;
   a.rowlist_len = nullptr;
   a.nrows = nrows;
@@ -737,20 +984,40 @@ static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, int nu
   int per_sm = 0;
   if (a.mode == 0 && num_sms > 0)
     FG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FIN_WARPS * 32, sm0));
+  // rows above the CTA prune's tile (or above R when nothing is deferred)
+  // go to the CTA-wide kernel when their keys are stored
+  const int heavy = a.def_keys ? a.def_cap : a.R;
+  FinalHeavyFn hkern = a.Ad ? final_heavy_for(L.metric, L.G, L.K) : nullptr;
+  int per_sm_h = 0;
+  const int hsm_bytes = fh_smem_bytes(a.qbytes);
+  if (per_sm > 0 && hkern) {
+    FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(hkern), hsm_bytes));
+    FG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_h, hkern, FH_WARPS * 32,
+                                                          hsm_bytes));
+  }
   if (per_sm > 0) {
     // final graph: heavy rows first, claimed one by one by a persistent grid
     FG_CUDA(cudaMallocAsync(&order, sizeof(int32_t) * std::max<int64_t>(nrows, 1), s));
+    if (per_sm_h > 0)
+      FG_CUDA(cudaMallocAsync(&hlist, sizeof(int32_t) * std::max<int64_t>(nrows, 1), s));
     final_order_kernel<<<grid1d(nrows, 256), 256, 0, s>>>(
-        nrows, a.def_keys ? a.def_cap : a.R, a.cnt, a.r_off, order, small + 2);
+        nrows, heavy, a.cnt, a.r_off, order, small + 2, a.R, a.parent0, a.c0_off, hlist,
+        small + 5);
     note_launch();
     FinalArgs m = a;
     m.rowlist = order;
     m.claim = small + 4;
+    m.heavy_thr = per_sm_h > 0 ? heavy : 0;
     kern<<<per_sm * num_sms, FIN_WARPS * 32, sm0, s>>>(m);
+    note_launch();
+    if (per_sm_h > 0) {
+      hkern<<<per_sm_h * num_sms, FH_WARPS * 32, hsm_bytes, s>>>(m, hlist, small + 5, small + 6);
+      note_launch();
+    }
   } else {
     kern<<<grid1d(nrows * 32, FIN_WARPS * 32), FIN_WARPS * 32, sm0, s>>>(a);
+    note_launch();
   }
-  note_launch();
   max_final_need_kernel<<<64, 256, 0, s>>>(nrows, long_rows, small, a.mode, a.R, a.cnt, a.r_off,
                                            a.parent0, a.c0_off, a.l_off, small + 1);
   note_launch();
@@ -825,6 +1092,7 @@ static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, int nu
   cudaFreeAsync(long_rows, s);
   cudaFreeAsync(small, s);
   cudaFreeAsync(order, s);
+  cudaFreeAsync(hlist, s);
   return rc;
 }
 
