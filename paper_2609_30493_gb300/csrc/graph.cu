@@ -445,8 +445,13 @@ struct FinalArgs {
   // A and of the reverse lists; the candidate keys are then read, not evaluated
   const float* Ad;
   const float* r_d;
-  // rows with more raw candidates than heavy_thr whose keys fit FH_CAP are
-  // left to final_heavy_kernel (0: none)
+  // the CTA-wide kernel's rows (hlist null: none): rows with more than
+  // fh_raw raw candidates whose keys fit FH_CAP are listed beforehand and
+  // skipped here; rows with more than heavy_thr distinct candidates are
+  // appended to hlist (count *hcount) here, once their keys are known
+  int32_t* hlist;
+  uint32_t* hcount;
+  int32_t fh_raw;
   int32_t heavy_thr;
 };
 
@@ -562,7 +567,7 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
       len1 = 0;
     }
     const int mraw = len0 + len1;
-    if (a.mode == 0 && fh_takes(mraw, sdeg, a.R, a.heavy_thr)) continue;  // the CTA-wide kernel's
+    if (a.mode == 0 && a.hlist && fh_takes(mraw, sdeg, a.R, a.fh_raw)) continue;  // listed already
     const int need = max(pow2_dev(mraw), pow2_dev(min(mraw, a.R) + sdeg));
     if (need > cap) {
       if (lane == 0) a.long_rows[atomicAdd(a.nlong, 1u)] = (int32_t)r;
@@ -601,6 +606,13 @@ __global__ void __launch_bounds__(FIN_WARPS * 32) final_rows_kernel(const FinalA
       __syncwarp();
       m = sort_unique(keys, mraw, lane);
       if (m > 0 && __shfl_sync(FULL, keys[m - 1] == PAD ? 1 : 0, 0)) --m;  // dropped owner
+    }
+    if (a.mode == 0 && a.hlist && m > a.heavy_thr) {
+      // more distinct candidates than the tensor-core prune takes: the
+      // CTA-wide kernel prunes the row (and counts it)
+      if (lane == 0) a.hlist[atomicAdd(a.hcount, 1u)] = u;
+      __syncwarp();
+      continue;
     }
     stage_row(us, a.V.X + (int64_t)u * a.V.ld_bytes, a.V.nchunks, lane);
     if (m > 0 && !(a.mode == 0 && a.Ad)) eval_keys_inplace<METRIC, G, K>(a.V, us, keys, m, lane);
@@ -934,11 +946,14 @@ static int fin_smem(FinalKernelFn kern, int qbytes, int* sm_shared, int* sm_glob
 // rows it prunes itself (more raw candidates than the CTA prune takes, or
 // than R when nothing is deferred) first, then the rest, so that the long
 // in-warp prunes start early instead of trailing the launch.  With hlist,
-// the rows the CTA-wide kernel takes (fh_takes) are also listed there (the
-// one-warp kernel skips them by the same test).
+// the rows whose keys the one-warp kernel cannot hold (more than fh_raw raw
+// candidates) and the CTA-wide kernel can (fh_takes) are listed there; the
+// one-warp kernel skips them by the same test and lists the others with
+// many distinct candidates itself.
 __global__ void final_order_kernel(int64_t n, int heavy, const int32_t* cnt, const int64_t* r_off,
                                    int32_t* order, uint32_t* ctr2, int R, const int32_t* parent0,
-                                   const int64_t* c0_off, int32_t* hlist, uint32_t* hcount) {
+                                   const int64_t* c0_off, int32_t* hlist, uint32_t* hcount,
+                                   int fh_raw) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t mraw = cnt[i] + (r_off[i + 1] - r_off[i]);
@@ -948,7 +963,7 @@ __global__ void final_order_kernel(int64_t n, int heavy, const int32_t* cnt, con
       order[n - 1 - atomicAdd(&ctr2[1], 1u)] = (int32_t)i;
     if (hlist) {
       const int sdeg = (parent0[i] >= 0 ? 1 : 0) + (int)(c0_off[i + 1] - c0_off[i]);
-      if (fh_takes((int)mraw, sdeg, R, heavy)) hlist[atomicAdd(hcount, 1u)] = (int32_t)i;
+      if (fh_takes((int)mraw, sdeg, R, fh_raw)) hlist[atomicAdd(hcount, 1u)] = (int32_t)i;
     }
   }
 }
@@ -1002,12 +1017,17 @@ static int run_final_rows(FinalArgs a, const VecLayout& L, int64_t nrows, int nu
       FG_CUDA(cudaMallocAsync(&hlist, sizeof(int32_t) * std::max<int64_t>(nrows, 1), s));
     final_order_kernel<<<grid1d(nrows, 256), 256, 0, s>>>(
         nrows, heavy, a.cnt, a.r_off, order, small + 2, a.R, a.parent0, a.c0_off, hlist,
-        small + 5);
+        small + 5, FIN_CAP);
     note_launch();
     FinalArgs m = a;
     m.rowlist = order;
     m.claim = small + 4;
-    m.heavy_thr = per_sm_h > 0 ? heavy : 0;
+    if (per_sm_h > 0) {
+      m.hlist = hlist;
+      m.hcount = small + 5;
+      m.fh_raw = FIN_CAP;
+      m.heavy_thr = heavy;
+    }
     kern<<<per_sm * num_sms, FIN_WARPS * 32, sm0, s>>>(m);
     note_launch();
     if (per_sm_h > 0) {
