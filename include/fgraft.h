@@ -413,7 +413,9 @@ fgraft_status fgraft_tune_scaffold_cap(int32_t cap);
  * wait gives up).  Every kernel that waits on the tensor cores (the TF32
  * prune of Section 3, the SAT's closest-child choice of Section 1, the dense
  * blocks of Section 5.3) polls its MMA-completion barrier at most `polls`
- * times before it gives up, sets an error flag, waits for its products in
+ * times (the prune bounds by the same count the waits with which its compute
+ * threads and its walker warp pass list slots to each other) before it gives
+ * up, sets an error flag, waits for its products in
  * flight with the full bound (2^22 polls), frees its tensor memory and
  * returns; the call that reads the flag returns FGRAFT_ETIMEOUT
  * (fgraft_build_scaffold, fgraft_harvest_block with counters, fgraft_prune,

@@ -229,7 +229,7 @@ int harvest_prune(const VecLayout& L, const uint64_t* Eg, const int32_t* Eg_cnt,
     t.long_cnt = lcnt;
     if (lcnt) FG_CUDA(cudaMemsetAsync(lcnt, 0, sizeof(uint32_t), s));
     FG_CUDA(raise_smem_limit(reinterpret_cast<const void*>(tk), t.smem));
-    tk<<<per_sm * num_sms, nc, t.smem, s>>>(t);
+    tk<<<per_sm * num_sms, nc + 32 * TCP_WALKERS, t.smem, s>>>(t);  // compute threads, walkers
     note_launch();
     FG_CUDA(cudaGetLastError());
     return 0;

@@ -49,5 +49,7 @@ using HPruneFn = void (*)(const HPruneArgs);
 // its shared memory per CTA.
 HPruneFn hprune_tc_kernel_for(int metric, int G, int K, int nc);
 int harvest_prune_tc_smem(int nchunks, int nc);
+// The tensor-core prune runs nc compute threads and this many walker warps.
+constexpr int TCP_WALKERS = 2;
 
 }  // namespace fg

@@ -101,6 +101,35 @@ __device__ __forceinline__ bool named_sync_or(int id, int nthreads, bool pred) {
       : "memory");
   return r != 0;
 }
+// Named barrier over `nthreads` threads (a multiple of 32).
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+// The same, returning the AND of `pred` over the threads.
+__device__ __forceinline__ bool named_sync_and(int id, int nthreads, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.b32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, %2, %3, p;\n\t"
+      "selp.b32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+// The same, returning how many of the threads have `pred` set.
+__device__ __forceinline__ int named_sync_count(int id, int nthreads, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %1, 0;\n\t"
+      "bar.red.popc.u32 %0, %2, %3, p;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
+      : "memory");
+  return (int)r;
+}
 // Polls barrier `bar` for the phase of parity `parity`, at most `polls`
 // times; gives up early when *abort becomes nonzero.  True when the phase
 // completed.
