@@ -269,27 +269,30 @@ __global__ void __launch_bounds__(NC + 32 * TCP_WALKERS, NC == 128 ? 3 : 1)
       // B = alpha2 * eps + 2^-21 (alpha2 |approx| + |delta(p, c_j)|) + tiny,
       // x <= -B means the canonical test certainly holds, x > B that it
       // certainly fails (the margins cover the rounding of the test and of x).
-      const int i = tid;
-      const float ni = i < m ? col[i].x : 0.0f;
-      float c1, c0;  // eps = c1 * n_j + c0 for this row
-      if constexpr (METRIC == ANGULAR_F32) {
-        c1 = 0.5f * a.tc_e1;
-        c0 = 0.5f * a.tc_e1 * ni + a.tc_e0;
-      } else {
-        c1 = a.tc_e1;
-        c0 = a.tc_e1 * ni + a.tc_e0;
-      }
       const float a2 = a.alpha2, a2m = a.alpha2 * 4.76837158e-7f;
-      for (int cb = 0; cb < W && 32 * cb < m; ++cb) {
-        if (32 * cb + 31 <= 32 * warp) {  // every column of the block is at or left of i
-          if (i < m) dom[i * W + cb] = 0u;
-          continue;
+      // A warp reads the TMEM lanes of its quarter, 32 (warp & 3) ..; the
+      // blocks (row block rb, column block cb >= rb) are spread over the
+      // warps so that none takes more than 3 (NC = 128) or 6 (NC = 256).
+      //
+      // Row job: thread i = 32 rb + lane reads row i of the Gram matrix and
+      // builds its word of block cb.
+      auto row_job = [&](int rb, int cb) {
+        if (32 * rb >= m || 32 * cb >= m) return;  // uniform over the warp
+        const int i = 32 * rb + lane;
+        const float ni = i < m ? col[i].x : 0.0f;
+        float c1, c0;  // eps = c1 * n_j + c0 for this row
+        if constexpr (METRIC == ANGULAR_F32) {
+          c1 = 0.5f * a.tc_e1;
+          c0 = 0.5f * a.tc_e1 * ni + a.tc_e0;
+        } else {
+          c1 = a.tc_e1;
+          c0 = a.tc_e1 * ni + a.tc_e0;
         }
         // rows 0..127: lane i, column j; rows 128..255: lane i - 128, column
         // 256 + j - 128 (only blocks right of the diagonal get here)
         uint32_t v[32];
-        const uint32_t tcol = warp < 4 ? (uint32_t)(32 * cb) : 256u + (uint32_t)(32 * cb - 128);
-        tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + tcol, v);
+        const uint32_t tcol = rb < 4 ? (uint32_t)(32 * cb) : 256u + (uint32_t)(32 * cb - 128);
+        tmem_ld32(tmem + ((uint32_t)(32 * (rb & 3)) << 16) + tcol, v);
         if (i < m) {
           uint32_t word = 0, unsure = 0;
 #pragma unroll
@@ -327,6 +330,88 @@ __global__ void __launch_bounds__(NC + 32 * TCP_WALKERS, NC == 128 ? 3 : 1)
           }
           dom[i * W + cb] = word;
         }
+      };
+      // Column job (rb < cb, rows 0..127 only): thread j = 32 cb + lane reads
+      // row j of the Gram matrix, whose columns 32 rb .. are the block's
+      // entries transposed, tests every row i of block rb against column j,
+      // and 32 ballots turn the columns' bits into the rows' words.  The
+      // Gram value's error bound holds in either orientation, and an
+      // undecided test is the canonical one (symmetric in its two rows), so
+      // the bits are those of the row job.
+      auto col_job = [&](int rb, int cb) {
+        if (32 * rb >= m || 32 * cb >= m) return;  // uniform over the warp
+        const int j = 32 * cb + lane;
+        const float4 cj = j < m ? col[j] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * (cb & 3)) << 16) + (uint32_t)(32 * rb), v);
+        uint32_t bits = 0;
+        if (j < m) {
+          uint32_t unsure = 0;
+#pragma unroll
+          for (int t = 0; t < 32; ++t) {
+            const int ii = 32 * rb + t;
+            if (ii >= m) continue;
+            const float ni = col[ii].x;
+            float c1, c0;  // eps = c1 * n_j + c0 for row ii
+            if constexpr (METRIC == ANGULAR_F32) {
+              c1 = 0.5f * a.tc_e1;
+              c0 = 0.5f * a.tc_e1 * ni + a.tc_e0;
+            } else {
+              c1 = a.tc_e1;
+              c0 = a.tc_e1 * ni + a.tc_e0;
+            }
+            const float g = __uint_as_float(v[t]);
+            float dt;
+            if constexpr (METRIC == ANGULAR_F32)
+              dt = 1.0f - g;
+            else
+              dt = (ni + cj.x) - 2.0f * g;
+            const float eps = fmaf(c1, cj.x, c0);
+            const float x = fmaf(a2, dt, -cj.y);
+            const float B = fmaf(a2, eps, fmaf(a2m, fabsf(dt), cj.z));
+            if (x <= -B)
+              bits |= 1u << t;
+            else if (!(x > B))
+              unsure |= 1u << t;
+          }
+          while (unsure) {
+            const int t = __ffs(unsure) - 1;
+            unsure &= unsure - 1u;
+            const int ii = 32 * rb + t;
+            const uint32_t slot = atomicAdd(qn, 1u);
+            if (slot < TCP_QCAP) {
+              uq[slot] = (uint32_t)(ii << 8 | j);
+            } else {
+              const float dd = canon_dist_thread<METRIC, G, K>(Cs, ii, Cs, j, NQ, nch, a.d);
+              if (__fmul_rn(a.alpha2, dd) <= key_dist(keys[j])) bits |= 1u << t;
+            }
+          }
+        }
+        uint32_t word = 0;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          const uint32_t b = __ballot_sync(FULL, (bits >> t) & 1u);
+          if (lane == t) word = b;
+        }
+        const int i = 32 * rb + lane;
+        if (i < m) dom[i * W + cb] = word;
+      };
+      if constexpr (NC == 256) {
+        // lane quarter q: row blocks q (8 - q column blocks) and q + 4
+        // (4 - q); warp q + 4 takes row block q's last two
+        const int q4 = warp & 3;
+        if (warp < 4) {
+          for (int cb = q4; cb < 6; ++cb) row_job(q4, cb);
+        } else {
+          for (int cb = q4 + 4; cb < 8; ++cb) row_job(q4 + 4, cb);
+          row_job(q4, 6);
+          row_job(q4, 7);
+        }
+      } else {
+        // warp 0 rows 0..31 x blocks 0 and 1; warps 2 and 3 take blocks
+        // (0, 2) and (0, 3) by columns
+        for (int cb = warp == 0 ? 0 : warp; cb < (warp == 0 ? 2 : W); ++cb) row_job(warp, cb);
+        if (warp >= 2) col_job(0, warp);
       }
       named_sync(1, NC);
       // the queued tests in canonical float32, spread over the CTA
