@@ -13,14 +13,16 @@
 namespace fg {
 
 // ---------------------------------------------------------------------------
-// Tensor-core variant for the float32 metrics and lists of at most 128.
+// Tensor-core variant for the float32 metrics and lists of at most 128 or
+// 256 candidates.
 //
 // The candidates are staged once, as float32, in the canonical K-major
 // operand layout of tcgen05 (core matrices of 8 rows x 16 bytes); their Gram
 // matrix C C^T is one chain of kind::tf32 MMAs (M = N = 128, 128 TMEM
 // columns), which reads the same float32 words with the low mantissa bits
-// ignored.  Thread i then reads row i of the Gram matrix from TMEM and
-// decides each bit j > i from the approximate distance when the decision is
+// ignored.  Thread i then reads row i of the Gram matrix from TMEM (or, for
+// a block taken by columns, thread j row j) and decides each bit "c_i
+// dominates c_j", j > i, from the approximate distance when the decision is
 // certain: with |approx - canonical| <= eps (input rounding to 10 mantissa
 // bits, float32 accumulation in any order, the canonical sum's own rounding,
 // times 2), the canonical test fl(alpha2 * delta) <= delta(p, c_j) has the
